@@ -20,8 +20,8 @@ Conventions (the paper is silent or garbled on these; each is a stated reading)
 * Rows of a cell: [W-face incoming (c_m>0) | E-face incoming (c_m<0) |
   S-face incoming (s_m>0) | N-face incoming (s_m<0)], directions ascending m.
   Each interior face's equations belong to the cell the direction enters.
-* Eigenvector normalisation: ||l||_inf = 1 with the sign chosen so that the
-  lowest index p with |l_p| >= (1 - 1e-8) max|l| is positive.
+* Eigenvector normalisation: l / l_p with p the lowest index such that
+  |l_p| >= (1 - 1e-8) max|l|, so ||l||_inf = 1 to 1e-8 and l_p = +1 exactly.
 """
 from __future__ import annotations
 
@@ -65,9 +65,12 @@ def hg_matrix(M: int, g: float):
 # Sec. 2.2: local eigenproblem [gamma K W - I] l = xi C l
 # --------------------------------------------------------------------------
 def _normalise(l: np.ndarray) -> np.ndarray:
+    """||l||_inf = 1 (Sec. 2.2): divide by the first entry within 1e-8 of the
+    largest magnitude, so near-ties (symmetric directions) pick the same entry
+    on any machine; that entry becomes exactly +1, ||l||_inf <= 1 + 1e-8."""
     amax = np.max(np.abs(l))
     p = int(np.nonzero(np.abs(l) >= (1.0 - 1e-8) * amax)[0][0])
-    return l * (np.sign(l[p]) / amax)
+    return l / l[p]
 
 
 def eigenbasis(one_minus_gamma: float, K: np.ndarray, d: np.ndarray):
