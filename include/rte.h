@@ -1,0 +1,218 @@
+/*
+ * rte.h -- C ABI of the GB300 radiative-transfer solver library (librte.so).
+ *
+ * The library solves the discrete-ordinates / tailored-finite-point (TFPS)
+ * system  A alpha = b  of the steady radiative transfer equation in x-y
+ * geometry (Song, Zhang, Liu, "A filtered MgNet solver for radiative transfer
+ * equations", Sec. 2.1-2.2, Eqs. RTE, hg, DORTE_2d, 2DTFPS_continuity_cond,
+ * 2DTFPS_boundary_cond, 2DTFPS_linear_sys) with flexible GMRES preconditioned
+ * by block Jacobi or by a learned MgNet V-cycle (Sec. 3, Sec. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid: unit square, I x I cells, h = 1/I; cell index c = iy*I + ix covers
+ *   [ix h, (ix+1) h] x [iy h, (iy+1) h].  N = I*I.
+ * Directions: M (a positive multiple of 4) uniform on the circle,
+ *   theta_m = 2 pi (m + 1/2) / M, weights 1/M.  (The paper's direction count
+ *   is 4M in its own notation; M here is the total.)
+ * Unknowns: n = 2 M N.  Every vector (x, b, r, z) is direction-major,
+ *   element [k * N + c] for slot k in 0..2M-1 and cell c.
+ *   Slots of a cell: [W-centred M/2 | E-centred M/2 | S-centred M/2 |
+ *   N-centred M/2] basis functions (x-type with xi<0, x-type xi>0, y-type
+ *   xi<0, y-type xi>0, each ascending in xi).
+ *   Rows of a cell: [W-face incoming (c_m>0) | E-face incoming (c_m<0) |
+ *   S-face incoming (s_m>0) | N-face incoming (s_m<0)], directions ascending.
+ * Angular flux output psi: [M][N] at cell centres.
+ *
+ * Ownership: host arrays are read during the call only.  Device arrays are
+ * owned by the caller, must hold the stated number of elements, and are used
+ * on the context's stream; the call returns before the work finishes unless
+ * stated otherwise.  The context owns every internal buffer.
+ * Errors: every call returns an rte_status and never aborts; rte_last_error()
+ * gives a message.  A context is not thread-safe; distinct contexts are
+ * independent.  Device pointers must be 16-byte aligned.
+ */
+#ifndef RTE_H_
+#define RTE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTE_API __attribute__((visibility("default")))
+
+typedef enum rte_status {
+    RTE_OK = 0,
+    RTE_EINVAL = 1,      /* invalid argument */
+    RTE_ENOMEM = 2,      /* device or host allocation failed */
+    RTE_ECUDA = 3,       /* CUDA runtime error */
+    RTE_ENOTCONV = 4,    /* iteration limit reached before the tolerance */
+    RTE_ESTALL = 5,      /* the solver stalled */
+    RTE_ETIMEOUT = 6,    /* a time limit or a bounded device wait ran out */
+    RTE_ESINGULAR = 7,   /* a per-cell block could not be inverted */
+    RTE_ECANCELLED = 8,  /* the request was cancelled */
+    RTE_ENOTSUP = 9      /* unsupported configuration */
+} rte_status;
+
+typedef enum rte_precision {
+    RTE_F64 = 0,   /* double in, double out, FP64 arithmetic */
+    RTE_F32 = 1    /* float in, float out, FP32 arithmetic */
+} rte_precision;
+
+typedef struct rte_ctx rte_ctx;
+typedef struct mgnet mgnet;
+
+typedef struct rte_grid { int I; } rte_grid;                 /* Sec. 2.2: I x I cells, h = 1/I */
+typedef struct rte_quadrature { int M; } rte_quadrature;     /* Sec. 2.1: M uniform directions */
+
+typedef struct rte_ctx_info {
+    int I, M, N;          /* cells per side, directions, cells */
+    int nmat;             /* distinct scattering ratios (one eigenbasis each) */
+    int64_t n;            /* unknowns, 2 M N */
+    size_t device_bytes;  /* bytes the context holds on the device */
+} rte_ctx_info;
+
+/* ---------------------------------------------------------------------------
+ * rte_setup -- build the TFPS system for one medium (Sec. 2.2).
+ *
+ * sigma_T, sigma_a, q : host [N] cell averages (Sec. 2.2); sigma_T > 0,
+ *   sigma_a > 0 (the paper assumes a non-zero absorption), q >= 0.
+ * eps : host pointer; one value if eps_is_scalar, else [N] per cell
+ *   (Eq. RTE diffusive scaling: sigma_T/eps, sigma_T/eps - eps sigma_a, eps q).
+ * g : Henyey-Greenstein anisotropy, |g| < 1 (Eq. hg).
+ * inflow : host [4][I][M] (side W,E,S,N; face along the side, iy for W/E and
+ *   ix for S/N; direction) or NULL for zero inflow; only incoming directions
+ *   are read (Eq. boundary_condition_2d).
+ * stream : cudaStream_t (NULL = legacy default stream) on which every later
+ *   call of this context runs.
+ * On success *out owns: the eigenbases (one per distinct 1 - gamma, computed
+ * on the host in FP64), the per-cell optical thickness, b, and the per-cell
+ * inverse diagonal blocks D_C = G_C^{-1} (FP32, inverted on the device).
+ * Synchronous.  Errors: EINVAL (bad sizes or values), ENOMEM, ECUDA,
+ * ESINGULAR (a block has a zero pivot).
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
+                             const double* sigma_T, const double* sigma_a, const double* q,
+                             const double* eps, int eps_is_scalar, double g,
+                             const double* inflow, void* stream, rte_ctx** out);
+
+RTE_API void rte_destroy(rte_ctx* ctx);
+
+/* Message of the last error of ctx (or of the calling thread if ctx is NULL). */
+RTE_API const char* rte_last_error(const rte_ctx* ctx);
+
+RTE_API rte_status rte_info(const rte_ctx* ctx, rte_ctx_info* info);
+
+/* b of Eq. 2DTFPS_linear_sys into b_dev [n] (double). */
+RTE_API rte_status rte_rhs(rte_ctx* ctx, double* b_dev);
+
+/* ---------------------------------------------------------------------------
+ * rte_apply -- y = A x, the TFPS operator (Eq. 2DTFPS_linear_sys): for every
+ * cell C, face f and direction m entering C through f, the trace of
+ * sum_k x_Ck chi_C^k at the midpoint of f minus the neighbour's trace there
+ * (Eq. 2DTFPS_continuity_cond), or the trace alone on the boundary
+ * (Eq. 2DTFPS_boundary_cond).
+ * precision RTE_F64: x_dev, y_dev double [n]; RTE_F32: float [n].
+ * x_dev and y_dev must not overlap.  Asynchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_apply(rte_ctx* ctx, int precision, const void* x_dev, void* y_dev);
+
+/* x = A^T y (the transpose of rte_apply), same layout and precision rules. */
+RTE_API rte_status rte_apply_adjoint(rte_ctx* ctx, int precision, const void* y_dev, void* x_dev);
+
+/* ---------------------------------------------------------------------------
+ * rte_block_apply -- z_C = D_C r_C (transpose = 0) or D_C^T r_C (1) for every
+ * cell, D_C = G_C^{-1} the inverse of the cell's diagonal block of A: the
+ * block-Jacobi preconditioner of Sec. 4 and the map D of Eq. loss.
+ * r_dev, z_dev: float [n], must not overlap.  Asynchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_block_apply(rte_ctx* ctx, int transpose, const float* r_dev, float* z_dev);
+
+/* psi at cell centres, psi_dev double [M][N] (Eq. 2DTFPS_sol). Asynchronous. */
+RTE_API rte_status rte_reconstruct(rte_ctx* ctx, const double* x_dev, double* psi_dev);
+
+/* ---------------------------------------------------------------------------
+ * rte_export_basis -- copy the host-side eigenbases (Eq.
+ * discretization_2D_eigenfunc_constraint) out: xi [nmat][2M] (slot order),
+ * L [nmat][M][2M] (row = direction, column = slot), mat_id [N].  Any pointer
+ * may be NULL.  Synchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_export_basis(const rte_ctx* ctx, double* xi, double* L, int* mat_id);
+
+/* Copy the inverse blocks out: D [N][2M][2M] row-major float (host). Synchronous. */
+RTE_API rte_status rte_export_blocks(rte_ctx* ctx, float* D_host);
+
+/* ---------------------------------------------------------------------------
+ * Krylov building block (Arnoldi step of flexible GMRES): orthogonalise w
+ * against the k orthonormal columns V[0..k-1] (V_dev: k x n doubles, vector j
+ * at V_dev + j*n) by classical Gram-Schmidt with one reorthogonalisation,
+ * w <- w - V (V^T w) twice; h_dev[0..k-1] receives the summed projections and
+ * h_dev[k] = ||w|| after orthogonalisation; w is then scaled to unit norm
+ * unless that norm is zero.  1 <= k <= 128.  Asynchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_dev, double* h_dev);
+
+/* ---------------------------------------------------------------------------
+ * rte_solve -- solve A x = b for this context's b by right-preconditioned
+ * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt plus
+ * reorthogonalisation, Givens/Hessenberg least squares in FP64 on the device,
+ * inner operator applies in opts->inner_precision, and the true residual
+ * ||b - A x|| / ||b|| recomputed in FP64 at the end of every cycle decides
+ * convergence.  pc: NULL = block Jacobi (Sec. 4); else the MgNet
+ * preconditioner z = D Net(r) (Sec. 3), replaced by block Jacobi for the
+ * remaining cycles when a cycle reduces the true residual by less than
+ * opts->stall_ratio or produces a non-finite value.
+ * x_dev: double [n]; the initial guess if opts->use_x0, else zeroed.
+ * Synchronous.  Returns RTE_OK when converged, RTE_ENOTCONV when max_iter is
+ * reached (x holds the last iterate), RTE_ETIMEOUT when timeout_ms elapses.
+ * ------------------------------------------------------------------------- */
+typedef struct rte_solve_opts {
+    double tol;            /* relative residual target (default 1e-8) */
+    int restart;           /* Krylov dimension per cycle (default 50, <= 128) */
+    int max_iter;          /* total Arnoldi steps (default 20000) */
+    int inner_precision;   /* RTE_F32 (default) or RTE_F64 for the inner applies */
+    int use_x0;            /* 1: x_dev holds the initial guess */
+    double stall_ratio;    /* MgNet fallback threshold per cycle (default 0.9) */
+    double timeout_ms;     /* wall-clock limit, <= 0 for none */
+} rte_solve_opts;
+
+typedef struct rte_solve_info {
+    int iterations;        /* Arnoldi steps taken */
+    int cycles;            /* restart cycles */
+    int converged;         /* 1 if the true residual <= tol */
+    int fell_back;         /* 1 if MgNet was replaced by block Jacobi */
+    double relres;         /* final true relative residual (FP64) */
+    double seconds;        /* wall time of the call */
+} rte_solve_info;
+
+RTE_API void rte_solve_opts_default(rte_solve_opts* opts);
+RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts,
+                             double* x_dev, rte_solve_info* info);
+
+/* ---------------------------------------------------------------------------
+ * Per-kernel accounting (no counterpart in the paper: instrumentation).
+ * Every kernel launch of a context is counted with its algorithmic bytes (the
+ * bytes its operation must move: inputs read once, outputs written once).
+ * rte_profile(ctx, 1) clears the counters and also brackets every launch with
+ * CUDA events on the context's stream; rte_profile(ctx, 0) clears and stops
+ * the timing.  rte_profile_read fills up to max entries (one per kernel
+ * class, in a fixed order) and returns how many it wrote, or the number of
+ * classes if out is NULL, or -1 on error.  Both synchronise the stream.
+ * ------------------------------------------------------------------------- */
+typedef struct rte_kernel_stat {
+    const char* name;      /* kernel class (static string) */
+    long long launches;    /* launches since the last rte_profile call */
+    double ms;             /* summed event time (0 unless timing is on) */
+    double bytes;          /* summed algorithmic bytes */
+} rte_kernel_stat;
+
+RTE_API rte_status rte_profile(rte_ctx* ctx, int enable);
+RTE_API int rte_profile_read(rte_ctx* ctx, rte_kernel_stat* out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_H_ */

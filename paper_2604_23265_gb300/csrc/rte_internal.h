@@ -1,0 +1,149 @@
+// Internal declarations shared by the translation units of librte.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rte.h"
+
+namespace rte {
+
+constexpr int kMaxKrylov = 64;      // largest restart (vectors orthogonalised against)
+constexpr int kRedThreads = 256;    // block size of the reduction kernels
+constexpr int kScal = 256;          // small device scalars per context
+
+struct Workspace;                   // Krylov buffers of rte_solve (solve.cu)
+
+// Kernel classes counted (always) and timed (when profiling is on).
+enum KernelId {
+    K_TRACES, K_COMBINE, K_ADJOINT, K_RECONSTRUCT, K_RHS, K_INVERT, K_BLOCK, K_BLOCK_T,
+    K_MDOT, K_UPDATE_DOT, K_UPDATE_NORM, K_NORM, K_SCALE, K_XUPDATE, K_GIVENS, K_BACKSUB,
+    K_CYCLE, K_F2D, K_MGNET, K_COUNT
+};
+extern const char* const kKernelNames[K_COUNT];
+
+struct Profiler {
+    bool on = false;
+    struct Pending {
+        int kid;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Pending> pending;
+    double ms[K_COUNT] = {};
+    double bytes[K_COUNT] = {};
+    long long launches[K_COUNT] = {};
+};
+
+}  // namespace rte
+
+struct rte_ctx {
+    int I = 0, M = 0, N = 0, nmat = 0;
+    int64_t n = 0;
+    double g = 0.0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 0;
+
+    // host copies of the set-up tables
+    std::vector<double> xi_h;        // [nmat][2M]
+    std::vector<double> L_h;         // [nmat][M][2M]
+    std::vector<int> mat_h;          // [N]
+
+    // device tables
+    int* mat = nullptr;              // [N] material of each cell
+    double* tau = nullptr;           // [N] sigma_T_eff * h
+    double* chis = nullptr;          // [N] particular solution q / sigma_a
+    double* xi = nullptr;            // [nmat][2M]
+    double* Lt64 = nullptr;          // [nmat][2M][M]  Lt[k][m] = L[m][k]
+    float* Lt32 = nullptr;
+    double* L64 = nullptr;           // [nmat][M][2M]
+    float* L32 = nullptr;
+    int* rowinfo = nullptr;          // [4][M]: j >= 0 incoming row j of face f, -(j+1) outgoing
+    int* rowdir = nullptr;           // [2M] direction of each row slot
+    double* inflow = nullptr;        // [4][I][M]
+    double* b = nullptr;             // [n]
+    float* Dt = nullptr;             // [N][2M][2M], Dt[c][j][i] = D_c[i][j]
+
+    // scratch
+    double* trace_out = nullptr;     // n elements (float or double) of outgoing traces
+    double* partials = nullptr;      // reduction partial sums
+    unsigned* counter = nullptr;     // last-block counter of the reductions
+    double* scal = nullptr;          // [kScal] small device scalars (projections, flags)
+    int max_red_blocks = 0;
+
+    size_t device_bytes = 0;
+    rte::Workspace* ws = nullptr;
+    rte::Profiler prof;
+    std::vector<void*> allocations;
+};
+
+namespace rte {
+
+// error helpers ------------------------------------------------------------
+void set_error(rte_ctx* ctx, const std::string& msg);
+rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where);
+void* dev_alloc(rte_ctx* ctx, size_t bytes);      // tracked, zeroed; throws on failure
+void free_workspace(rte_ctx* ctx);                 // releases the rte_solve buffers
+
+struct CudaError {
+    cudaError_t code;
+    const char* where;
+};
+struct StatusError {
+    rte_status code;
+    std::string msg;
+};
+inline void check(cudaError_t e, const char* where) {
+    if (e != cudaSuccess) throw CudaError{e, where};
+}
+
+// profiling (setup.cu): wrap every launch of the library.
+// Counts the launch and its algorithmic bytes; with profiling on, brackets the
+// launch with events on the context's stream (resolved at sync points).
+struct ProfScope {
+    rte_ctx* ctx;
+    int kid;
+    cudaEvent_t b = nullptr;
+    ProfScope(rte_ctx* c, int k, double bytes, int launches = 1);
+    ~ProfScope();
+};
+void prof_resolve(rte_ctx* ctx);      // after a stream synchronisation
+void prof_free(rte_ctx* ctx);
+
+// operator kernels (apply.cu) ---------------------------------------------
+// y = A x (precision of T); if b != nullptr the output is b - A x.
+void launch_apply(rte_ctx* ctx, bool f64, const void* x, void* y, bool y_is_double,
+                  const double* b);
+void launch_apply_adjoint(rte_ctx* ctx, bool f64, const void* y, void* x);
+void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi);
+void launch_rhs(rte_ctx* ctx);
+
+// block kernels (blocks.cu) ------------------------------------------------
+// builds G_C for every cell and inverts it into ctx->Dt; *singular_dev set
+// to 1 if a zero pivot appears.
+void launch_build_invert(rte_ctx* ctx, int* singular_dev);
+// z = D r (or D^T r); input float or double, output float
+void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double,
+                        float* z, const double* scale_dev);
+
+// krylov kernels (krylov.cu) -----------------------------------------------
+// h[0..k) = V^T w (deterministic, last-block reduction into h)
+void launch_mdot(rte_ctx* ctx, const double* V, int k, const double* w, double* h);
+// w <- w - V h1 ; h2 = V^T w
+void launch_update_dot(rte_ctx* ctx, const double* V, int k, double* w, const double* h1,
+                       double* h2);
+// w <- w - V h2 ; out[0..k) = h1 + h2 ; out[k] = ||w||
+void launch_update_norm(rte_ctx* ctx, const double* V, int k, double* w, const double* h1,
+                        const double* h2, double* out);
+// out[0] = ||x||
+void launch_norm(rte_ctx* ctx, const double* x, double* out);
+// y = x * (1 / s[0]) unless s[0] == 0 (then y = x)
+void launch_scale(rte_ctx* ctx, const double* x, const double* s, double* y);
+// x += sum_k Z[k] y[k]  (Z float, k vectors)
+void launch_combine_update(rte_ctx* ctx, double* x, const float* Z, int k, const double* y);
+
+}  // namespace rte

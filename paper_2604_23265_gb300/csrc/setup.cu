@@ -1,0 +1,570 @@
+// Host set-up of one TFPS system (Sec. 2.1-2.2) and the plain entry points.
+//
+// The host computes, in FP64, the direction set, the normalised HG matrix
+// (Eq. hg), and one eigenbasis per distinct scattering ratio (Eq.
+// discretization_2D_eigenfunc_constraint) by a cyclic Jacobi eigen-solver of
+// the symmetric-definite pencil diag(c) l = mu (I - gamma K W) l, xi = -1/mu.
+// Everything proportional to the grid (b, the per-cell blocks and their
+// inverses) is built on the device.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "rte_internal.h"
+
+namespace rte {
+
+static thread_local std::string g_thread_error;
+
+void set_error(rte_ctx* ctx, const std::string& msg) {
+    g_thread_error = msg;
+    if (ctx) ctx->err = msg;
+}
+
+rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where) {
+    set_error(ctx, std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? RTE_ENOMEM : RTE_ECUDA;
+}
+
+void* dev_alloc(rte_ctx* ctx, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc"};
+    ctx->allocations.push_back(p);
+    ctx->device_bytes += bytes;
+    check(cudaMemsetAsync(p, 0, bytes, ctx->stream), "cudaMemset");
+    return p;
+}
+
+const char* const kKernelNames[K_COUNT] = {
+    "traces", "combine", "adjoint", "reconstruct", "rhs", "build_invert", "block_apply",
+    "block_apply_t", "mdot", "update_dot", "update_norm", "norm", "scale", "x_update",
+    "givens", "backsub", "cycle_start", "f2d", "mgnet"};
+
+static cudaEvent_t prof_event(rte_ctx* ctx) {
+    if (!ctx->prof.pool.empty()) {
+        cudaEvent_t e = ctx->prof.pool.back();
+        ctx->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    check(cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+}
+
+ProfScope::ProfScope(rte_ctx* c, int k, double bytes, int launches) : ctx(c), kid(k) {
+    ctx->prof.launches[k] += launches;
+    ctx->prof.bytes[k] += bytes;
+    if (ctx->prof.on) {
+        b = prof_event(ctx);
+        check(cudaEventRecord(b, ctx->stream), "cudaEventRecord");
+    }
+}
+
+ProfScope::~ProfScope() {
+    if (!b) return;
+    cudaEvent_t e = nullptr;
+    try {
+        e = prof_event(ctx);
+    } catch (...) {
+        return;
+    }
+    cudaEventRecord(e, ctx->stream);
+    ctx->prof.pending.push_back({kid, b, e});
+}
+
+void prof_resolve(rte_ctx* ctx) {
+    for (auto& p : ctx->prof.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) ctx->prof.ms[p.kid] += ms;
+        ctx->prof.pool.push_back(p.a);
+        ctx->prof.pool.push_back(p.b);
+    }
+    ctx->prof.pending.clear();
+}
+
+void prof_free(rte_ctx* ctx) {
+    for (auto& p : ctx->prof.pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : ctx->prof.pool) cudaEventDestroy(e);
+    ctx->prof.pending.clear();
+    ctx->prof.pool.clear();
+}
+
+namespace {
+
+// ---------------------------------------------------------------- linear algebra
+// Cyclic Jacobi eigen-decomposition of the symmetric n x n matrix A (row-major,
+// overwritten).  On return w holds the eigenvalues and the columns of V the
+// orthonormal eigenvectors (V row-major).
+void jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += A[(size_t)p * n + p] * A[(size_t)p * n + p];
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        }
+        if (off <= 1e-34 * diag || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                double t;
+                if (std::fabs(theta) > 1e150)
+                    t = 0.5 / theta;
+                else
+                    t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - s * vkq;
+                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// Eigenpairs of (gamma K W - I) l = xi diag(d) l for one value of 1 - gamma.
+// Returns xi ascending and L (row-major M x M, column k = eigenvector k) with
+// ||l||_inf = 1 (to 1e-8): each vector is divided by its first entry within
+// 1e-8 of the largest magnitude.
+void eigenbasis(int M, double omg, const std::vector<double>& K, const std::vector<double>& d,
+                std::vector<double>& xi, std::vector<double>& L) {
+    const double gamma = 1.0 - omg;
+    // S = (1 - gamma) I + gamma (I - K W); the diagonal of I - KW is written as
+    // the sum of the off-diagonal K W entries of its row.
+    std::vector<double> S((size_t)M * M);
+    for (int i = 0; i < M; ++i) {
+        double offsum = 0.0;
+        for (int j = 0; j < M; ++j) {
+            if (j == i) continue;
+            const double kw = K[(size_t)i * M + j] / M;
+            offsum += kw;
+            S[(size_t)i * M + j] = -gamma * kw;
+        }
+        S[(size_t)i * M + i] = omg + gamma * offsum;
+    }
+    // Cholesky S = R^T R (R upper)
+    std::vector<double> R((size_t)M * M, 0.0);
+    for (int j = 0; j < M; ++j) {
+        double s = S[(size_t)j * M + j];
+        for (int k = 0; k < j; ++k) s -= R[(size_t)k * M + j] * R[(size_t)k * M + j];
+        if (!(s > 0.0)) throw StatusError{RTE_ESINGULAR, "scattering operator not positive definite"};
+        const double rjj = std::sqrt(s);
+        R[(size_t)j * M + j] = rjj;
+        for (int i = j + 1; i < M; ++i) {
+            double t = S[(size_t)j * M + i];
+            for (int k = 0; k < j; ++k) t -= R[(size_t)k * M + j] * R[(size_t)k * M + i];
+            R[(size_t)j * M + i] = t / rjj;
+        }
+    }
+    // Rinv (upper triangular)
+    std::vector<double> Ri((size_t)M * M, 0.0);
+    for (int col = 0; col < M; ++col) {
+        for (int i = col; i >= 0; --i) {
+            double t = (i == col) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= col; ++k) t -= R[(size_t)i * M + k] * Ri[(size_t)k * M + col];
+            Ri[(size_t)i * M + col] = t / R[(size_t)i * M + i];
+        }
+    }
+    // B = Ri^T diag(d) Ri
+    std::vector<double> B((size_t)M * M, 0.0);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double t = 0.0;
+            for (int k = 0; k <= std::min(i, j); ++k)
+                t += Ri[(size_t)k * M + i] * d[k] * Ri[(size_t)k * M + j];
+            B[(size_t)i * M + j] = t;
+        }
+    for (int i = 0; i < M; ++i)
+        for (int j = i + 1; j < M; ++j) {
+            const double a = 0.5 * (B[(size_t)i * M + j] + B[(size_t)j * M + i]);
+            B[(size_t)i * M + j] = B[(size_t)j * M + i] = a;
+        }
+    std::vector<double> mu, Y;
+    jacobi_eigh(M, B, mu, Y);
+    std::vector<int> order(M);
+    for (int i = 0; i < M; ++i) order[i] = i;
+    std::vector<double> xv(M);
+    for (int i = 0; i < M; ++i) xv[i] = -1.0 / mu[i];
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return xv[a] < xv[b]; });
+    xi.resize(M);
+    L.assign((size_t)M * M, 0.0);
+    std::vector<double> l(M);
+    for (int kk = 0; kk < M; ++kk) {
+        const int k = order[kk];
+        xi[kk] = xv[k];
+        double amax = 0.0;
+        for (int i = 0; i < M; ++i) {
+            double t = 0.0;
+            for (int j = i; j < M; ++j) t += Ri[(size_t)i * M + j] * Y[(size_t)j * M + k];
+            l[i] = t;
+            amax = std::max(amax, std::fabs(t));
+        }
+        // divide by the first entry within 1e-8 of the largest magnitude: that
+        // entry becomes +1 and near-ties resolve the same way on any machine
+        int p = 0;
+        while (std::fabs(l[p]) < (1.0 - 1e-8) * amax) ++p;
+        const double lp = l[p];
+        for (int i = 0; i < M; ++i) L[(size_t)i * M + kk] = (i == p) ? 1.0 : l[i] / lp;
+    }
+}
+
+template <typename T>
+T* upload(rte_ctx* ctx, const std::vector<T>& h) {
+    T* d = static_cast<T*>(dev_alloc(ctx, h.size() * sizeof(T)));
+    check(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream),
+          "upload");
+    return d;
+}
+
+void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const double* q,
+           const double* eps, int eps_is_scalar, const double* inflow) {
+    const int I = ctx->I, M = ctx->M, N = ctx->N, M2 = M / 2;
+    const double h = 1.0 / I;
+    int dev = 0;
+    check(cudaGetDevice(&dev), "cudaGetDevice");
+    check(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+    // directions and HG matrix
+    std::vector<double> cdir(M), sdir(M);
+    for (int m = 0; m < M; ++m) {
+        const double th = 2.0 * M_PI * (m + 0.5) / M;
+        cdir[m] = std::cos(th);
+        sdir[m] = std::sin(th);
+    }
+    std::vector<double> K((size_t)M * M);
+    double total = 0.0;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            const double th_i = 2.0 * M_PI * (i + 0.5) / M, th_j = 2.0 * M_PI * (j + 0.5) / M;
+            const double mu = std::cos(th_i - th_j);
+            const double g = ctx->g;
+            const double v = (1.0 - g * g) / std::pow(1.0 + g * g - 2.0 * g * mu, 1.5);
+            K[(size_t)i * M + j] = v;
+            total += v / M;
+        }
+    const double rowmean = total / M;
+    for (auto& v : K) v /= rowmean;
+    // cell data and materials (one per distinct 1 - gamma)
+    std::vector<double> tau(N), chis(N), omg(N);
+    for (int c = 0; c < N; ++c) {
+        const double e = eps_is_scalar ? eps[0] : eps[c];
+        if (!(sigma_T[c] > 0.0) || !(sigma_a[c] > 0.0) || !(e > 0.0) || !(q[c] >= 0.0) ||
+            !std::isfinite(sigma_T[c]) || !std::isfinite(sigma_a[c]) || !std::isfinite(q[c]) ||
+            !std::isfinite(e))
+            throw StatusError{RTE_EINVAL, "sigma_T, sigma_a, eps must be positive and finite, q >= 0"};
+        tau[c] = sigma_T[c] / e * h;
+        chis[c] = q[c] / sigma_a[c];
+        omg[c] = e * e * sigma_a[c] / sigma_T[c];
+        if (!(omg[c] < 1.0 + 1e-15))
+            throw StatusError{RTE_EINVAL, "eps^2 sigma_a must not exceed sigma_T (negative scattering)"};
+    }
+    std::map<double, int> mats;
+    for (int c = 0; c < N; ++c) mats.emplace(omg[c], 0);
+    int id = 0;
+    for (auto& kv : mats) kv.second = id++;
+    ctx->nmat = id;
+    ctx->mat_h.resize(N);
+    for (int c = 0; c < N; ++c) ctx->mat_h[c] = mats[omg[c]];
+    const int n2 = 2 * M;
+    ctx->xi_h.assign((size_t)ctx->nmat * n2, 0.0);
+    ctx->L_h.assign((size_t)ctx->nmat * M * n2, 0.0);
+    for (auto& kv : mats) {
+        std::vector<double> xx, Lx, xy, Ly;
+        eigenbasis(M, std::min(kv.first, 1.0), K, cdir, xx, Lx);
+        eigenbasis(M, std::min(kv.first, 1.0), K, sdir, xy, Ly);
+        for (int k = 0; k < M2; ++k) {
+            if (!(xx[k] < 0 && xx[M2 + k] > 0 && xy[k] < 0 && xy[M2 + k] > 0))
+                throw StatusError{RTE_ESINGULAR, "eigenvalue inertia is not M/2 negative, M/2 positive"};
+        }
+        const int j = kv.second;
+        for (int k = 0; k < M; ++k) {
+            ctx->xi_h[(size_t)j * n2 + k] = xx[k];
+            ctx->xi_h[(size_t)j * n2 + M + k] = xy[k];
+        }
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < M; ++k) {
+                ctx->L_h[((size_t)j * M + m) * n2 + k] = Lx[(size_t)m * M + k];
+                ctx->L_h[((size_t)j * M + m) * n2 + M + k] = Ly[(size_t)m * M + k];
+            }
+    }
+    // row tables
+    std::vector<int> dirs[4];
+    for (int m = 0; m < M; ++m) {
+        if (cdir[m] > 0) dirs[0].push_back(m); else dirs[1].push_back(m);
+        if (sdir[m] > 0) dirs[2].push_back(m); else dirs[3].push_back(m);
+    }
+    for (int f = 0; f < 4; ++f)
+        if ((int)dirs[f].size() != M2) throw StatusError{RTE_EINVAL, "direction set not symmetric"};
+    std::vector<int> rowinfo(4 * M), rowdir(n2);
+    for (int f = 0; f < 4; ++f) {
+        for (int j = 0; j < M2; ++j) {
+            rowinfo[f * M + dirs[f][j]] = j;
+            rowinfo[f * M + dirs[f ^ 1][j]] = -(j + 1);
+            rowdir[f * M2 + j] = dirs[f][j];
+        }
+    }
+    std::vector<double> Lt64((size_t)ctx->nmat * n2 * M);
+    std::vector<float> Lt32(Lt64.size()), L32(ctx->L_h.size());
+    for (int j = 0; j < ctx->nmat; ++j)
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < n2; ++k) {
+                const double v = ctx->L_h[((size_t)j * M + m) * n2 + k];
+                Lt64[((size_t)j * n2 + k) * M + m] = v;
+                Lt32[((size_t)j * n2 + k) * M + m] = (float)v;
+                L32[((size_t)j * M + m) * n2 + k] = (float)v;
+            }
+    std::vector<double> infl((size_t)4 * I * M, 0.0);
+    if (inflow) std::memcpy(infl.data(), inflow, infl.size() * sizeof(double));
+    ctx->mat = upload(ctx, ctx->mat_h);
+    ctx->tau = upload(ctx, tau);
+    ctx->chis = upload(ctx, chis);
+    ctx->xi = upload(ctx, ctx->xi_h);
+    ctx->L64 = upload(ctx, ctx->L_h);
+    ctx->L32 = upload(ctx, L32);
+    ctx->Lt64 = upload(ctx, Lt64);
+    ctx->Lt32 = upload(ctx, Lt32);
+    ctx->rowinfo = upload(ctx, rowinfo);
+    ctx->rowdir = upload(ctx, rowdir);
+    ctx->inflow = upload(ctx, infl);
+    // vectors and scratch
+    ctx->b = static_cast<double*>(dev_alloc(ctx, ctx->n * sizeof(double)));
+    ctx->trace_out = static_cast<double*>(dev_alloc(ctx, 2 * ctx->n * sizeof(double)));
+    ctx->max_red_blocks = ctx->num_sms * 4;
+    ctx->partials = static_cast<double*>(
+        dev_alloc(ctx, (size_t)ctx->max_red_blocks * kMaxKrylov * sizeof(double)));
+    ctx->counter = static_cast<unsigned*>(dev_alloc(ctx, 64));
+    ctx->scal = static_cast<double*>(dev_alloc(ctx, kScal * sizeof(double)));
+    ctx->Dt = static_cast<float*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(float)));
+    launch_rhs(ctx);
+    int* sing = reinterpret_cast<int*>(ctx->scal + kScal - 1);
+    launch_build_invert(ctx, sing);
+    int sing_h = 0;
+    check(cudaMemcpyAsync(&sing_h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "d2h");
+    check(cudaStreamSynchronize(ctx->stream), "setup sync");
+    if (sing_h) throw StatusError{RTE_ESINGULAR, "a per-cell block has a zero pivot"};
+}
+
+}  // namespace
+}  // namespace rte
+
+using namespace rte;
+
+#define RTE_GUARD_BEGIN try {
+#define RTE_GUARD_END(ctx)                                                      \
+    }                                                                           \
+    catch (const CudaError& e) { return cuda_status(ctx, e.code, e.where); }   \
+    catch (const StatusError& e) { set_error(ctx, e.msg); return e.code; }     \
+    catch (const std::bad_alloc&) { set_error(ctx, "host allocation failed"); return RTE_ENOMEM; } \
+    catch (...) { set_error(ctx, "unexpected exception"); return RTE_EINVAL; }
+
+extern "C" {
+
+RTE_API const char* rte_last_error(const rte_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_thread_error.c_str();
+}
+
+RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
+                             const double* sigma_T, const double* sigma_a, const double* q,
+                             const double* eps, int eps_is_scalar, double g,
+                             const double* inflow, void* stream, rte_ctx** out) {
+    if (!out) { set_error(nullptr, "out is NULL"); return RTE_EINVAL; }
+    *out = nullptr;
+    if (!grid || !quad || !sigma_T || !sigma_a || !q || !eps) {
+        set_error(nullptr, "NULL argument");
+        return RTE_EINVAL;
+    }
+    if (grid->I < 1 || grid->I > 8192 || quad->M < 4 || quad->M % 4 != 0 || quad->M > 112) {
+        set_error(nullptr, "need I in [1, 8192] and M a multiple of 4 in [4, 112]");
+        return RTE_EINVAL;
+    }
+    if (!(std::fabs(g) < 1.0)) { set_error(nullptr, "need |g| < 1"); return RTE_EINVAL; }
+    rte_ctx* ctx = new (std::nothrow) rte_ctx();
+    if (!ctx) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; }
+    ctx->I = grid->I;
+    ctx->M = quad->M;
+    ctx->N = grid->I * grid->I;
+    ctx->n = (int64_t)2 * ctx->M * ctx->N;
+    ctx->g = g;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    rte_status st = RTE_OK;
+    try {
+        build(ctx, sigma_T, sigma_a, q, eps, eps_is_scalar, inflow);
+    } catch (const CudaError& e) {
+        st = cuda_status(ctx, e.code, e.where);
+    } catch (const StatusError& e) {
+        set_error(ctx, e.msg);
+        st = e.code;
+    } catch (const std::bad_alloc&) {
+        set_error(ctx, "host allocation failed");
+        st = RTE_ENOMEM;
+    }
+    if (st != RTE_OK) {
+        rte_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_info(const rte_ctx* ctx, rte_ctx_info* info) {
+    if (!ctx || !info) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    info->I = ctx->I;
+    info->M = ctx->M;
+    info->N = ctx->N;
+    info->nmat = ctx->nmat;
+    info->n = ctx->n;
+    info->device_bytes = ctx->device_bytes;
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_rhs(rte_ctx* ctx, double* b_dev) {
+    if (!ctx || !b_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    check(cudaMemcpyAsync(b_dev, ctx->b, ctx->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                          ctx->stream), "rhs copy");
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_apply(rte_ctx* ctx, int precision, const void* x_dev, void* y_dev) {
+    if (!ctx || !x_dev || !y_dev || x_dev == y_dev) { set_error(ctx, "bad argument"); return RTE_EINVAL; }
+    if (precision != RTE_F64 && precision != RTE_F32) { set_error(ctx, "bad precision"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    launch_apply(ctx, precision == RTE_F64, x_dev, y_dev, precision == RTE_F64, nullptr);
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_apply_adjoint(rte_ctx* ctx, int precision, const void* y_dev, void* x_dev) {
+    if (!ctx || !x_dev || !y_dev || x_dev == y_dev) { set_error(ctx, "bad argument"); return RTE_EINVAL; }
+    if (precision != RTE_F64 && precision != RTE_F32) { set_error(ctx, "bad precision"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    launch_apply_adjoint(ctx, precision == RTE_F64, y_dev, x_dev);
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_block_apply(rte_ctx* ctx, int transpose, const float* r_dev, float* z_dev) {
+    if (!ctx || !r_dev || !z_dev || (const void*)r_dev == (const void*)z_dev) {
+        set_error(ctx, "bad argument");
+        return RTE_EINVAL;
+    }
+    RTE_GUARD_BEGIN
+    launch_block_apply(ctx, transpose != 0, r_dev, false, z_dev, nullptr);
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_reconstruct(rte_ctx* ctx, const double* x_dev, double* psi_dev) {
+    if (!ctx || !x_dev || !psi_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    launch_reconstruct(ctx, x_dev, psi_dev);
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_export_basis(const rte_ctx* ctx, double* xi, double* L, int* mat_id) {
+    if (!ctx) { set_error(nullptr, "NULL ctx"); return RTE_EINVAL; }
+    if (xi) std::memcpy(xi, ctx->xi_h.data(), ctx->xi_h.size() * sizeof(double));
+    if (L) std::memcpy(L, ctx->L_h.data(), ctx->L_h.size() * sizeof(double));
+    if (mat_id) std::memcpy(mat_id, ctx->mat_h.data(), ctx->mat_h.size() * sizeof(int));
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_export_blocks(rte_ctx* ctx, float* D_host) {
+    if (!ctx || !D_host) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    const size_t n2 = 2 * (size_t)ctx->M, per = n2 * n2;
+    std::vector<float> tmp(per * ctx->N);
+    check(cudaMemcpyAsync(tmp.data(), ctx->Dt, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                          ctx->stream), "export blocks");
+    check(cudaStreamSynchronize(ctx->stream), "export sync");
+    for (int c = 0; c < ctx->N; ++c)
+        for (size_t j = 0; j < n2; ++j)
+            for (size_t i = 0; i < n2; ++i) D_host[c * per + i * n2 + j] = tmp[c * per + j * n2 + i];
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_dev, double* h_dev) {
+    if (!ctx || !V_dev || !w_dev || !h_dev || k < 1 || k > kMaxKrylov) {
+        set_error(ctx, "bad argument (need 1 <= k <= 64)");
+        return RTE_EINVAL;
+    }
+    RTE_GUARD_BEGIN
+    double* h1 = ctx->scal;                 // [64] first projection
+    double* h2 = ctx->scal + kMaxKrylov;    // [64] second projection
+    launch_mdot(ctx, V_dev, k, w_dev, h1);
+    launch_update_dot(ctx, V_dev, k, w_dev, h1, h2);
+    launch_update_norm(ctx, V_dev, k, w_dev, h1, h2, h_dev);  // h1 + h2, then ||w||
+    launch_scale(ctx, w_dev, h_dev + k, w_dev);
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_profile(rte_ctx* ctx, int enable) {
+    if (!ctx) { set_error(nullptr, "NULL ctx"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    check(cudaStreamSynchronize(ctx->stream), "profile sync");
+    prof_resolve(ctx);
+    for (int k = 0; k < K_COUNT; ++k) {
+        ctx->prof.ms[k] = 0.0;
+        ctx->prof.bytes[k] = 0.0;
+        ctx->prof.launches[k] = 0;
+    }
+    ctx->prof.on = enable != 0;
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API int rte_profile_read(rte_ctx* ctx, rte_kernel_stat* out, int max) {
+    if (!ctx) return -1;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;
+    prof_resolve(ctx);
+    int n = 0;
+    for (int k = 0; k < K_COUNT && n < max; ++k) {
+        if (!out) break;
+        out[n].name = kKernelNames[k];
+        out[n].launches = ctx->prof.launches[k];
+        out[n].ms = ctx->prof.ms[k];
+        out[n].bytes = ctx->prof.bytes[k];
+        ++n;
+    }
+    return out ? n : K_COUNT;
+}
+
+RTE_API void rte_destroy(rte_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_workspace(ctx);
+    prof_free(ctx);
+    for (void* p : ctx->allocations) cudaFree(p);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+"""Python binding of librte.so (ctypes).  Argument marshalling only: every step of
+the solver runs in the library's CUDA kernels; there is no fallback.
+
+Device arrays are torch CUDA tensors (contiguous, on the context's device);
+they are passed to the C ABI as raw pointers.  Names follow ``include/rte.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librte.so")
+_lib = None
+
+RTE_OK, RTE_EINVAL, RTE_ENOMEM, RTE_ECUDA, RTE_ENOTCONV, RTE_ESTALL, RTE_ETIMEOUT, \
+    RTE_ESINGULAR, RTE_ECANCELLED, RTE_ENOTSUP = range(10)
+RTE_F64, RTE_F32 = 0, 1
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ESTALL", "ETIMEOUT",
+                "ESINGULAR", "ECANCELLED", "ENOTSUP"]
+
+
+class RteError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 10 else status}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int)]
+
+
+class Quadrature(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int)]
+
+
+class CtxInfo(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int), ("M", ctypes.c_int), ("N", ctypes.c_int),
+                ("nmat", ctypes.c_int), ("n", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("inner_precision", ctypes.c_int), ("use_x0", ctypes.c_int),
+                ("stall_ratio", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
+                ("fell_back", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name -> (restype, argtypes); the C declarations live in include/rte.h
+SIGNATURES = {
+    "rte_setup": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(Quadrature), _P, _P, _P, _P, _I, _D, _P,
+                       _P, ctypes.POINTER(_P)]),
+    "rte_destroy": (None, [_P]),
+    "rte_last_error": (ctypes.c_char_p, [_P]),
+    "rte_info": (_I, [_P, ctypes.POINTER(CtxInfo)]),
+    "rte_rhs": (_I, [_P, _P]),
+    "rte_apply": (_I, [_P, _I, _P, _P]),
+    "rte_apply_adjoint": (_I, [_P, _I, _P, _P]),
+    "rte_block_apply": (_I, [_P, _I, _P, _P]),
+    "rte_reconstruct": (_I, [_P, _P, _P]),
+    "rte_export_basis": (_I, [_P, _P, _P, _P]),
+    "rte_export_blocks": (_I, [_P, _P]),
+    "rte_cgs2": (_I, [_P, _P, _I, _P, _P]),
+    "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
+    "rte_profile": (_I, [_P, _I]),
+    "rte_profile_read": (_I, [_P, ctypes.POINTER(KernelStat), _I]),
+}
+
+
+def load(path: Optional[str] = None):
+    """Load librte.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, ctx_ptr=None):
+    if st != RTE_OK:
+        msg = load().rte_last_error(ctx_ptr)
+        raise RteError(st, msg.decode() if msg else "")
+
+
+def _host(a, dtype=np.float64):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev(t, dtype, numel):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+        raise ValueError(f"expected contiguous {dtype} with >= {numel} elements, got {t.dtype} "
+                         f"{tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One RTE system (rte_setup); see include/rte.h for the layouts."""
+
+    def __init__(self, I, M, sigma_T, sigma_a, q, eps, g, inflow=None, stream=None):
+        lib = load()
+        N = I * I
+        self._keep = []
+        sT, psT = _host(np.broadcast_to(sigma_T, (N,)))
+        sa, psa = _host(np.broadcast_to(sigma_a, (N,)))
+        qq, pq = _host(np.broadcast_to(q, (N,)))
+        e = np.asarray(eps, np.float64)
+        scalar = int(e.size == 1)
+        ee, pe = _host(e.reshape(-1) if not scalar else e.reshape(1))
+        if inflow is not None:
+            fl, pf = _host(np.asarray(inflow).reshape(4 * I * M))
+        else:
+            fl, pf = None, None
+        out = ctypes.c_void_p()
+        st = lib.rte_setup(ctypes.byref(Grid(I)), ctypes.byref(Quadrature(M)), psT, psa, pq, pe,
+                           scalar, float(g), pf, _stream_ptr(stream), ctypes.byref(out))
+        _check(st, None)
+        self.ptr = out
+        self.I, self.M, self.N = I, M, N
+        self.n = 2 * M * N
+
+    @classmethod
+    def from_medium(cls, md, stream=None):
+        return cls(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow, stream)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().rte_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        i = CtxInfo()
+        _check(load().rte_info(self.ptr, ctypes.byref(i)), self.ptr)
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def rhs(self, b):
+        import torch
+        _check(load().rte_rhs(self.ptr, _dev(b, torch.float64, self.n)), self.ptr)
+        return b
+
+    def apply(self, x, y, precision=RTE_F64):
+        import torch
+        dt = torch.float64 if precision == RTE_F64 else torch.float32
+        _check(load().rte_apply(self.ptr, precision, _dev(x, dt, self.n), _dev(y, dt, self.n)), self.ptr)
+        return y
+
+    def apply_adjoint(self, y, x, precision=RTE_F64):
+        import torch
+        dt = torch.float64 if precision == RTE_F64 else torch.float32
+        _check(load().rte_apply_adjoint(self.ptr, precision, _dev(y, dt, self.n), _dev(x, dt, self.n)),
+               self.ptr)
+        return x
+
+    def block_apply(self, r, z, transpose=False):
+        import torch
+        _check(load().rte_block_apply(self.ptr, int(transpose), _dev(r, torch.float32, self.n),
+                                      _dev(z, torch.float32, self.n)), self.ptr)
+        return z
+
+    def reconstruct(self, x, psi):
+        import torch
+        _check(load().rte_reconstruct(self.ptr, _dev(x, torch.float64, self.n),
+                                      _dev(psi, torch.float64, self.M * self.N)), self.ptr)
+        return psi
+
+    def export_basis(self):
+        info = self.info()
+        nmat, M, N = info["nmat"], self.M, self.N
+        xi = np.zeros((nmat, 2 * M))
+        L = np.zeros((nmat, M, 2 * M))
+        mat = np.zeros(N, np.int32)
+        _check(load().rte_export_basis(self.ptr, xi.ctypes.data_as(_P), L.ctypes.data_as(_P),
+                                       mat.ctypes.data_as(_P)), self.ptr)
+        return xi, L, mat
+
+    def export_blocks(self):
+        D = np.zeros((self.N, 2 * self.M, 2 * self.M), np.float32)
+        _check(load().rte_export_blocks(self.ptr, D.ctypes.data_as(_P)), self.ptr)
+        return D
+
+    def cgs2(self, V, k, w, h):
+        import torch
+        _check(load().rte_cgs2(self.ptr, _dev(V, torch.float64, k * self.n), int(k),
+                               _dev(w, torch.float64, self.n), _dev(h, torch.float64, k + 1)),
+               self.ptr)
+        return h
+
+    def profile(self, enable=True):
+        """Clear the per-kernel counters; enable=True also times every launch."""
+        _check(load().rte_profile(self.ptr, int(enable)), self.ptr)
+
+    def profile_read(self):
+        """{kernel class: (launches, ms, algorithmic bytes)}."""
+        n = load().rte_profile_read(self.ptr, None, 0)
+        arr = (KernelStat * n)()
+        got = load().rte_profile_read(self.ptr, arr, n)
+        if got < 0:
+            _check(RTE_ECUDA, self.ptr)
+        return {a.name.decode(): (a.launches, a.ms, a.bytes) for a in arr[:got]}
+
+    def solve(self, x, pc=None, tol=1e-8, restart=50, max_iter=20000, inner_precision=RTE_F32,
+              use_x0=False, stall_ratio=0.9, timeout_ms=0.0, raise_on_error=True):
+        import torch
+        o = SolveOpts()
+        load().rte_solve_opts_default(ctypes.byref(o))
+        o.tol, o.restart, o.max_iter = float(tol), int(restart), int(max_iter)
+        o.inner_precision, o.use_x0 = int(inner_precision), int(use_x0)
+        o.stall_ratio, o.timeout_ms = float(stall_ratio), float(timeout_ms)
+        inf = SolveInfo()
+        pcp = pc.ptr if pc is not None else None
+        st = load().rte_solve(self.ptr, pcp, ctypes.byref(o), _dev(x, torch.float64, self.n),
+                              ctypes.byref(inf))
+        d = inf.as_dict()
+        d["status"] = STATUS_NAMES[st] if 0 <= st < 10 else st
+        if raise_on_error and st not in (RTE_OK, RTE_ENOTCONV):
+            _check(st, self.ptr)
+        return d

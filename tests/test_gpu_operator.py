@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs.  Sizes span several 32-cell tiles with a ragged tail."""
+import numpy as np
+import pytest
+
+from oracle import krylov, tfps
+from paper_2604_23265_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def _oracle(md):
+    return tfps.Problem(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow)
+
+
+def _gpu(md):
+    from paper_2604_23265_gb300 import rte
+    return rte.Context.from_medium(md)
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a).ravel(), dtype=dtype, device="cuda")
+
+
+def _generic(I, M, seed, eps=0.3, g=0.5, inflow=True):
+    """A medium with two-material blocks, random source and inflow (non-degenerate bases)."""
+    rng = np.random.default_rng(seed)
+    N = I * I
+    sT = W.checkerboard_sigma_T(I, 3, (0.7, 4.0), seed)
+    sa = np.where(sT > 1, 0.3, 0.1)
+    q = rng.uniform(0, 1, N)
+    fl = W.random_inflow(I, M, seed + 1) if inflow else None
+    return W.Medium(I, M, sT, sa, q, np.full(N, eps), g, fl if fl is not None else W.zero_inflow(I, M))
+
+
+CASES = [(9, 4, 0), (13, 8, 1), (37, 16, 2), (20, 32, 3), (11, 64, 4), (1, 8, 5)]
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_basis_matches_oracle(lib, I, M, seed):
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    xi, L, mat = ctx.export_basis()
+    np.testing.assert_array_equal(mat, p.mat_id)
+    np.testing.assert_allclose(xi, p.xi, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(L, p.L, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_rhs_matches_oracle(lib, I, M, seed):
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    b = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.rhs(b)
+    np.testing.assert_allclose(b.cpu().numpy(), p.rhs().ravel(), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_apply_f64_matches_oracle(lib, I, M, seed):
+    """FP64 operator apply: relative L2 <= 1e-12."""
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    x = W.random_vector(ctx.n, seed + 10)
+    y = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.apply(_t(x), y)
+    ref = p.apply(x.reshape(2 * M, -1)).ravel()
+    assert _rel(y.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_apply_adjoint_f64_matches_oracle(lib, I, M, seed):
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    yv = W.random_vector(ctx.n, seed + 11)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.apply_adjoint(_t(yv), x)
+    ref = p.apply_adjoint(yv.reshape(2 * M, -1)).ravel()
+    assert _rel(x.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_apply_f32_matches_oracle(lib, I, M, seed):
+    """FP32 apply: sums of 2M products in FP32, relative L2 <= 2M * 2^-24 * 4."""
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    from paper_2604_23265_gb300 import rte
+    x = W.random_vector(ctx.n, seed + 12).astype(np.float32)
+    y = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
+    ctx.apply(_t(x, torch.float32), y, precision=rte.RTE_F32)
+    ref = p.apply(x.astype(np.float64).reshape(2 * M, -1)).ravel()
+    assert _rel(y.cpu().numpy(), ref) <= 8 * M * 2.0 ** -24
+    ya = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
+    ctx.apply_adjoint(_t(x, torch.float32), ya, precision=rte.RTE_F32)
+    refa = p.apply_adjoint(x.astype(np.float64).reshape(2 * M, -1)).ravel()
+    assert _rel(ya.cpu().numpy(), refa) <= 8 * M * 2.0 ** -24
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_reconstruct_matches_oracle(lib, I, M, seed):
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    x = W.random_vector(ctx.n, seed + 13)
+    psi = torch.zeros(M * I * I, dtype=torch.float64, device="cuda")
+    ctx.reconstruct(_t(x), psi)
+    ref = p.reconstruct(x.reshape(2 * M, -1)).ravel()
+    assert _rel(psi.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_block_inverse_and_apply(lib, I, M, seed):
+    """D_C (FP32 Gauss-Jordan) against the oracle's LU inverse, and z = D r,
+    D^T r against the same products in FP64; tolerances scale with cond(G_C)."""
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    G = p.blocks()
+    Dref = np.linalg.inv(G)
+    cond = np.linalg.cond(G).max()
+    tol = 64 * M * 2.0 ** -24 * cond
+    D = ctx.export_blocks().astype(np.float64)
+    assert np.linalg.norm(D - Dref) / np.linalg.norm(Dref) <= tol
+    r = W.random_vector(ctx.n, seed + 14).astype(np.float32)
+    z = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
+    ctx.block_apply(_t(r, torch.float32), z)
+    zref = tfps.block_apply(D, r.astype(np.float64).reshape(2 * M, -1)).ravel()
+    assert _rel(z.cpu().numpy(), zref) <= 8 * M * 2.0 ** -24 * 16
+    ctx.block_apply(_t(r, torch.float32), z, transpose=True)
+    zref = tfps.block_apply_T(D, r.astype(np.float64).reshape(2 * M, -1)).ravel()
+    assert _rel(z.cpu().numpy(), zref) <= 8 * M * 2.0 ** -24 * 16
+
+
+@pytest.mark.parametrize("k", [1, 5, 17, 40, 64])
+def test_cgs2_projection(lib, k):
+    """CGS2: h = V^T w and w_out = (I - V V^T) w / ||.|| for orthonormal V."""
+    md = _generic(13, 8, 3)
+    ctx = _gpu(md)
+    n = ctx.n
+    rng = np.random.default_rng(k)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    V = np.ascontiguousarray(Q.T)
+    w = rng.standard_normal(n) + V.T @ rng.standard_normal(k) * 10
+    wt, h = _t(w), torch.zeros(k + 1, dtype=torch.float64, device="cuda")
+    ctx.cgs2(_t(V), k, wt, h)
+    href = V @ w
+    r = w - V.T @ href
+    np.testing.assert_allclose(h.cpu().numpy()[:k], href, rtol=1e-12, atol=1e-12)
+    assert abs(h.cpu().numpy()[k] - np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(w)
+    np.testing.assert_allclose(wt.cpu().numpy(), r / np.linalg.norm(r), atol=1e-12)
+
+
+@pytest.mark.parametrize("I,M,seed", [(9, 4, 0), (13, 8, 1), (16, 8, 2), (1, 8, 5)])
+def test_solve_matches_dense_lu(lib, I, M, seed):
+    """FGMRES with block Jacobi to 1e-12 equals the oracle's dense LU solution."""
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, tol=1e-12, restart=30)
+    assert info["converged"] and info["relres"] <= 1e-12
+    xl = krylov.dense_solve(p.assemble(), p.rhs().ravel())
+    psi = torch.zeros(M * I * I, dtype=torch.float64, device="cuda")
+    ctx.reconstruct(x, psi)
+    ref = p.reconstruct(xl.reshape(2 * M, -1)).ravel()
+    assert _rel(psi.cpu().numpy(), ref) <= 1e-9
+    r = p.rhs().ravel() - p.apply(x.cpu().numpy().reshape(2 * M, -1)).ravel()
+    assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 2e-12
+
+
+def test_solve_checkerboard_32_to_1e10(lib):
+    """32x32, M=16 checkerboard (transport): the oracle-recomputed residual of the
+    GPU solution is <= 1e-10 and psi agrees with the oracle's own FGMRES solve."""
+    md = W.checkerboard_transport(0)
+    p, ctx = _oracle(md), _gpu(md)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, tol=1e-10, restart=50)
+    assert info["converged"]
+    b = p.rhs().ravel()
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(b - p.apply(xg.reshape(32, -1)).ravel()) / np.linalg.norm(b) <= 1e-10
+    D = p.block_inverse()
+    xo, io = krylov.fgmres(lambda v: p.apply(v.reshape(32, -1)).ravel(), b,
+                           lambda v, j: tfps.block_apply(D, v.reshape(32, -1)).ravel(),
+                           tol=1e-10, restart=50)
+    assert _rel(p.reconstruct(xg.reshape(32, -1)), p.reconstruct(xo.reshape(32, -1))) <= 1e-8
+    assert abs(info["iterations"] - io["iters"]) <= 0.2 * io["iters"] + 5
+
+
+def test_solve_zero_rhs_and_exact_guess(lib):
+    """Degenerate cases: b = 0 gives x = 0 at once; an exact x0 needs no iteration."""
+    I, M = 6, 8
+    N = I * I
+    sa = np.linspace(0.2, 1.0, N)
+    md = W.Medium(I, M, sa + 1.0, sa, 0.5 * sa, np.full(N, 0.1), 0.3, np.full((4, I, M), 0.5))
+    ctx = _gpu(md)
+    x = torch.full((ctx.n,), 3.0, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x)
+    assert info["converged"] and info["iterations"] == 0
+    assert torch.count_nonzero(x).item() == 0
+    md2 = _generic(7, 8, 9)
+    p, ctx2 = _oracle(md2), _gpu(md2)
+    xl = krylov.dense_solve(p.assemble(), p.rhs().ravel())
+    x2 = _t(xl)
+    info = ctx2.solve(x2, tol=1e-8, use_x0=True)
+    assert info["converged"] and info["iterations"] == 0
+
+
+def test_invalid_inputs_raise(lib):
+    from paper_2604_23265_gb300 import rte
+    md = _generic(4, 8, 0)
+    with pytest.raises(rte.RteError) as e:
+        rte.Context(4, 8, md.sigma_T, -md.sigma_a, md.q, md.eps, md.g)
+    assert e.value.status == rte.RTE_EINVAL
+    with pytest.raises(rte.RteError):
+        rte.Context(4, 10, md.sigma_T, md.sigma_a, md.q, md.eps, md.g)
+    ctx = _gpu(md)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(rte.RteError):
+        ctx.solve(x, restart=65)
+    with pytest.raises(ValueError):
+        ctx.apply(torch.zeros(3, dtype=torch.float64, device="cuda"), x)
+
+
+def test_full_size_diffusive_apply_matches_oracle(lib):
+    """256x256, M=64, eps=1e-3 GRF medium (the benchmark workload): the FP64 apply
+    against the oracle on the whole vector.  The slow eigenvalues carry a
+    conditioning of 1/(1-gamma) = 2e7 on either side, so the bar is 1e-12 plus
+    2^-52/(1-gamma)."""
+    md = W.grf_diffusive(0)
+    p, ctx = _oracle(md), _gpu(md)
+    x = W.random_vector(ctx.n, 99)
+    y = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.apply(_t(x), y)
+    ref = p.apply(x.reshape(2 * md.M, -1)).ravel()
+    tol = 1e-12 + 2.0 ** -52 / p.omg.min()
+    assert _rel(y.cpu().numpy(), ref) <= tol
+    b = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.rhs(b)
+    np.testing.assert_allclose(b.cpu().numpy(), p.rhs().ravel(), rtol=0, atol=1e-15)
