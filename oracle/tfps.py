@@ -73,15 +73,15 @@ def _normalise(l: np.ndarray) -> np.ndarray:
     return l / l[p]
 
 
-def eigenbasis(one_minus_gamma: float, K: np.ndarray, d: np.ndarray):
-    """Eigenpairs of (gamma K W - I) l = xi diag(d) l (Eq. discretization_2D_eigenfunc_constraint).
+def reflection(M: int, axis: int) -> np.ndarray:
+    """Direction permutation that fixes c (axis 0: theta -> -theta) or s
+    (axis 1: theta -> pi - theta); it pairs the M directions without fixed points."""
+    m = np.arange(M)
+    return (M - 1 - m) if axis == 0 else (M // 2 - 1 - m) % M
 
-    d = c (x-type, xi_y = 0) or s (y-type, xi_x = 0).  Solved as the symmetric
-    definite pencil diag(d) l = mu S l with S = I - gamma K W (SPD), mu = -1/xi,
-    via Cholesky S = R^T R and the symmetric eigenproblem of R^-T diag(d) R^-1
-    (library primitives).  Returns xi ascending (M,) and L (M, M) with columns
-    the normalised eigenvectors.  Pinned by P2, P3, P4.
-    """
+
+def _pencil(one_minus_gamma, K, d, P):
+    """Eigenpairs of diag(d) l = mu S l restricted to the orthonormal columns P."""
     M = K.shape[0]
     gamma = 1.0 - one_minus_gamma
     KW = K / M
@@ -90,16 +90,50 @@ def eigenbasis(one_minus_gamma: float, K: np.ndarray, d: np.ndarray):
     # its row (equal to 1 - KW_mm when rows of KW sum to one)
     off = KW.sum(axis=1) - np.diag(KW)
     ImKW[np.diag_indices(M)] = off
-    S = one_minus_gamma * np.eye(M) + gamma * ImKW
+    S = P.T @ (one_minus_gamma * np.eye(M) + gamma * ImKW) @ P
+    S = 0.5 * (S + S.T)
+    Dg = P.T @ np.diag(d) @ P
     R = sla.cholesky(S, lower=False)          # S = R^T R
-    Rinv = sla.solve_triangular(R, np.eye(M), lower=False)
-    B = Rinv.T @ np.diag(d) @ Rinv
+    Rinv = sla.solve_triangular(R, np.eye(S.shape[0]), lower=False)
+    B = Rinv.T @ Dg @ Rinv
     B = 0.5 * (B + B.T)
     mu, Y = np.linalg.eigh(B)
-    xi = -1.0 / mu
-    L = Rinv @ Y
+    return -1.0 / mu, P @ (Rinv @ Y)
+
+
+def eigenbasis(one_minus_gamma: float, K: np.ndarray, d: np.ndarray, axis: int = None):
+    """Eigenpairs of (gamma K W - I) l = xi diag(d) l (Eq. discretization_2D_eigenfunc_constraint).
+
+    d = c (x-type, xi_y = 0, axis 0) or s (y-type, xi_x = 0, axis 1).  Solved as
+    the symmetric definite pencil diag(d) l = mu S l with S = I - gamma K W (SPD),
+    mu = -1/xi.  The pencil commutes with the reflection of the directions that
+    leaves d unchanged, so it splits into mirror-symmetric and antisymmetric
+    halves (orthonormal bases (e_a +- e_R(a))/sqrt 2); each half is solved by
+    Cholesky S = R^T R and the symmetric eigenproblem of R^-T D R^-1 (library
+    primitives).  The split makes the basis unique where a symmetric and an
+    antisymmetric mode nearly share xi.  Returns xi ascending (ties: symmetric
+    first) and L (M, M) with columns the normalised eigenvectors.
+    Pinned by P2, P3, P4.
+    """
+    M = K.shape[0]
+    if axis is None:
+        axis = 0 if np.allclose(d, d[reflection(M, 0)]) else 1
+    Rm = reflection(M, axis)
+    if not np.allclose(d, d[Rm], rtol=0, atol=1e-14):
+        raise ValueError("d is not invariant under the reflection of its axis")
+    a = np.array([m for m in range(M) if m < Rm[m]])
+    Ps = np.zeros((M, M // 2))
+    Pa = np.zeros((M, M // 2))
+    Ps[a, np.arange(M // 2)] = Ps[Rm[a], np.arange(M // 2)] = np.sqrt(0.5)
+    Pa[a, np.arange(M // 2)] = np.sqrt(0.5)
+    Pa[Rm[a], np.arange(M // 2)] = -np.sqrt(0.5)
+    xs, Ls = _pencil(one_minus_gamma, K, d, Ps)
+    xa, La = _pencil(one_minus_gamma, K, d, Pa)
+    xi = np.concatenate([xs, xa])
+    L = np.concatenate([Ls, La], axis=1)
     L = np.stack([_normalise(L[:, k]) for k in range(M)], axis=1)
-    order = np.argsort(xi, kind="stable")
+    parity = np.concatenate([np.zeros(M // 2), np.ones(M // 2)])
+    order = np.lexsort((parity, xi))
     return xi[order], L[:, order]
 
 
@@ -144,8 +178,8 @@ class Problem:
         self.xi = np.zeros((self.nmat, 2 * self.M))
         self.L = np.zeros((self.nmat, self.M, 2 * self.M))
         for j, om in enumerate(vals):
-            xx, Lx = eigenbasis(om, self.K, self.c)
-            xy, Ly = eigenbasis(om, self.K, self.s)
+            xx, Lx = eigenbasis(om, self.K, self.c, 0)
+            xy, Ly = eigenbasis(om, self.K, self.s, 1)
             # slots: W (xi<0), E (xi>0), S (xi<0), N (xi>0)
             self.xi[j] = np.concatenate([xx, xy])
             self.L[j] = np.concatenate([Lx, Ly], axis=1)
