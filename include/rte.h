@@ -142,6 +142,18 @@ RTE_API rte_status rte_reconstruct(rte_ctx* ctx, const double* x_dev, double* ps
  * ------------------------------------------------------------------------- */
 RTE_API rte_status rte_export_basis(const rte_ctx* ctx, double* xi, double* L, int* mat_id);
 
+/* ---------------------------------------------------------------------------
+ * rte_eigenbasis -- host-only FP64 eigenpairs of the local TFPS problem
+ * (Eq. discretization_2D_eigenfunc_constraint) for M uniform directions, HG
+ * anisotropy g (Eq. hg) and 1 - gamma = eps^2 sigma_a / sigma_T in (0, 1]:
+ * axis 0 solves (gamma K W - I) l = xi C l (xi_y = 0), axis 1 the S version.
+ * xi [M] ascending, L [M][M] row-major (row = direction, column = mode),
+ * each column divided by its first entry within 1e-8 of its largest
+ * magnitude.  The same routine rte_setup uses.  Needs no GPU.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_eigenbasis(int M, double g, double one_minus_gamma, int axis, double* xi,
+                                  double* L);
+
 /* Copy the inverse blocks out: D [N][2M][2M] row-major float (host). Synchronous. */
 RTE_API rte_status rte_export_blocks(rte_ctx* ctx, float* D_host);
 

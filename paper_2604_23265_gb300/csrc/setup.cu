@@ -147,12 +147,12 @@ void jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& w, std::vec
     for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
 }
 
-// Eigenpairs of (gamma K W - I) l = xi diag(d) l for one value of 1 - gamma.
-// Returns xi ascending and L (row-major M x M, column k = eigenvector k) with
-// ||l||_inf = 1 (to 1e-8): each vector is divided by its first entry within
-// 1e-8 of the largest magnitude.
-void eigenbasis(int M, double omg, const std::vector<double>& K, const std::vector<double>& d,
-                std::vector<double>& xi, std::vector<double>& L) {
+// Eigenpairs of the pencil diag(d) l = mu S l, S = I - gamma K W, restricted to
+// the h orthonormal columns of P (M x h, row-major): xi = -1/mu and the
+// eigenvectors l = P R^-1 y (unnormalised), from Cholesky S_P = R^T R of
+// S_P = P^T S P and the symmetric eigenproblem of R^-T (P^T diag(d) P) R^-1.
+void pencil(int M, int h, double omg, const std::vector<double>& K, const std::vector<double>& d,
+            const std::vector<double>& P, std::vector<double>& xi, std::vector<double>& Lcols) {
     const double gamma = 1.0 - omg;
     // S = (1 - gamma) I + gamma (I - K W); the diagonal of I - KW is written as
     // the sum of the off-diagonal K W entries of its row.
@@ -167,63 +167,136 @@ void eigenbasis(int M, double omg, const std::vector<double>& K, const std::vect
         }
         S[(size_t)i * M + i] = omg + gamma * offsum;
     }
-    // Cholesky S = R^T R (R upper)
-    std::vector<double> R((size_t)M * M, 0.0);
-    for (int j = 0; j < M; ++j) {
-        double s = S[(size_t)j * M + j];
-        for (int k = 0; k < j; ++k) s -= R[(size_t)k * M + j] * R[(size_t)k * M + j];
-        if (!(s > 0.0)) throw StatusError{RTE_ESINGULAR, "scattering operator not positive definite"};
-        const double rjj = std::sqrt(s);
-        R[(size_t)j * M + j] = rjj;
-        for (int i = j + 1; i < M; ++i) {
-            double t = S[(size_t)j * M + i];
-            for (int k = 0; k < j; ++k) t -= R[(size_t)k * M + j] * R[(size_t)k * M + i];
-            R[(size_t)j * M + i] = t / rjj;
+    // S_P = P^T S P, D_P = P^T diag(d) P
+    std::vector<double> SP((size_t)M * h, 0.0), Sh((size_t)h * h, 0.0), Dh((size_t)h * h, 0.0);
+    for (int i = 0; i < M; ++i)
+        for (int b = 0; b < h; ++b) {
+            double t = 0.0;
+            for (int j = 0; j < M; ++j) t += S[(size_t)i * M + j] * P[(size_t)j * h + b];
+            SP[(size_t)i * h + b] = t;
+        }
+    for (int a = 0; a < h; ++a)
+        for (int b = 0; b < h; ++b) {
+            double t = 0.0, u = 0.0;
+            for (int i = 0; i < M; ++i) {
+                t += P[(size_t)i * h + a] * SP[(size_t)i * h + b];
+                u += P[(size_t)i * h + a] * d[i] * P[(size_t)i * h + b];
+            }
+            Sh[(size_t)a * h + b] = t;
+            Dh[(size_t)a * h + b] = u;
+        }
+    for (int a = 0; a < h; ++a)
+        for (int b = a + 1; b < h; ++b) {
+            const double t = 0.5 * (Sh[(size_t)a * h + b] + Sh[(size_t)b * h + a]);
+            Sh[(size_t)a * h + b] = Sh[(size_t)b * h + a] = t;
+        }
+    // Cholesky S_P = R^T R (R upper)
+    std::vector<double> R((size_t)h * h, 0.0);
+    for (int j = 0; j < h; ++j) {
+        double sjj = Sh[(size_t)j * h + j];
+        for (int k = 0; k < j; ++k) sjj -= R[(size_t)k * h + j] * R[(size_t)k * h + j];
+        if (!(sjj > 0.0)) throw StatusError{RTE_ESINGULAR, "scattering operator not positive definite"};
+        const double rjj = std::sqrt(sjj);
+        R[(size_t)j * h + j] = rjj;
+        for (int i = j + 1; i < h; ++i) {
+            double t = Sh[(size_t)j * h + i];
+            for (int k = 0; k < j; ++k) t -= R[(size_t)k * h + j] * R[(size_t)k * h + i];
+            R[(size_t)j * h + i] = t / rjj;
         }
     }
-    // Rinv (upper triangular)
-    std::vector<double> Ri((size_t)M * M, 0.0);
-    for (int col = 0; col < M; ++col) {
+    // Ri = R^-1 (upper triangular)
+    std::vector<double> Ri((size_t)h * h, 0.0);
+    for (int col = 0; col < h; ++col)
         for (int i = col; i >= 0; --i) {
             double t = (i == col) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= col; ++k) t -= R[(size_t)i * M + k] * Ri[(size_t)k * M + col];
-            Ri[(size_t)i * M + col] = t / R[(size_t)i * M + i];
+            for (int k = i + 1; k <= col; ++k) t -= R[(size_t)i * h + k] * Ri[(size_t)k * h + col];
+            Ri[(size_t)i * h + col] = t / R[(size_t)i * h + i];
         }
-    }
-    // B = Ri^T diag(d) Ri
-    std::vector<double> B((size_t)M * M, 0.0);
-    for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j) {
+    // B = Ri^T D_P Ri
+    std::vector<double> T((size_t)h * h, 0.0), B((size_t)h * h, 0.0);
+    for (int a = 0; a < h; ++a)
+        for (int j = 0; j < h; ++j) {
             double t = 0.0;
-            for (int k = 0; k <= std::min(i, j); ++k)
-                t += Ri[(size_t)k * M + i] * d[k] * Ri[(size_t)k * M + j];
-            B[(size_t)i * M + j] = t;
+            for (int k = 0; k <= j; ++k) t += Dh[(size_t)a * h + k] * Ri[(size_t)k * h + j];
+            T[(size_t)a * h + j] = t;
         }
-    for (int i = 0; i < M; ++i)
-        for (int j = i + 1; j < M; ++j) {
-            const double a = 0.5 * (B[(size_t)i * M + j] + B[(size_t)j * M + i]);
-            B[(size_t)i * M + j] = B[(size_t)j * M + i] = a;
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < h; ++j) {
+            double t = 0.0;
+            for (int k = 0; k <= i; ++k) t += Ri[(size_t)k * h + i] * T[(size_t)k * h + j];
+            B[(size_t)i * h + j] = t;
+        }
+    for (int i = 0; i < h; ++i)
+        for (int j = i + 1; j < h; ++j) {
+            const double t = 0.5 * (B[(size_t)i * h + j] + B[(size_t)j * h + i]);
+            B[(size_t)i * h + j] = B[(size_t)j * h + i] = t;
         }
     std::vector<double> mu, Y;
-    jacobi_eigh(M, B, mu, Y);
-    std::vector<int> order(M);
-    for (int i = 0; i < M; ++i) order[i] = i;
+    jacobi_eigh(h, B, mu, Y);
+    xi.resize(h);
+    Lcols.assign((size_t)h * M, 0.0);          // column-major: mode k at Lcols[k*M ..]
+    std::vector<double> v(h);
+    for (int k = 0; k < h; ++k) {
+        xi[k] = -1.0 / mu[k];
+        for (int i = 0; i < h; ++i) {
+            double t = 0.0;
+            for (int j = i; j < h; ++j) t += Ri[(size_t)i * h + j] * Y[(size_t)j * h + k];
+            v[i] = t;
+        }
+        for (int m = 0; m < M; ++m) {
+            double t = 0.0;
+            for (int b = 0; b < h; ++b) t += P[(size_t)m * h + b] * v[b];
+            Lcols[(size_t)k * M + m] = t;
+        }
+    }
+}
+
+// Eigenpairs of (gamma K W - I) l = xi diag(d) l for one value of 1 - gamma,
+// d = c (axis 0) or s (axis 1).  The pencil commutes with the reflection of
+// the directions that leaves d unchanged, so it is solved separately on the
+// mirror-symmetric and antisymmetric halves; this fixes the basis uniquely
+// where a symmetric and an antisymmetric mode nearly share xi.
+// Returns xi ascending (ties: symmetric first) and L (row-major M x M, column
+// k = eigenvector k) with ||l||_inf = 1 (to 1e-8): each vector is divided by
+// its first entry within 1e-8 of the largest magnitude.
+void eigenbasis(int M, double omg, const std::vector<double>& K, const std::vector<double>& d,
+                int axis, std::vector<double>& xi, std::vector<double>& L) {
+    const int h = M / 2;
+    std::vector<int> refl(M);
+    for (int m = 0; m < M; ++m) refl[m] = axis == 0 ? M - 1 - m : (((M / 2 - 1 - m) % M) + M) % M;
+    std::vector<double> Ps((size_t)M * h, 0.0), Pa((size_t)M * h, 0.0);
+    const double r2 = std::sqrt(0.5);
+    int col = 0;
+    for (int m = 0; m < M; ++m) {
+        if (m < refl[m]) {
+            Ps[(size_t)m * h + col] = r2;
+            Ps[(size_t)refl[m] * h + col] = r2;
+            Pa[(size_t)m * h + col] = r2;
+            Pa[(size_t)refl[m] * h + col] = -r2;
+            ++col;
+        }
+    }
+    std::vector<double> xs, Ls, xa, La;
+    pencil(M, h, omg, K, d, Ps, xs, Ls);
+    pencil(M, h, omg, K, d, Pa, xa, La);
     std::vector<double> xv(M);
-    for (int i = 0; i < M; ++i) xv[i] = -1.0 / mu[i];
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return xv[a] < xv[b]; });
+    std::vector<int> order(M);
+    for (int k = 0; k < M; ++k) {
+        xv[k] = k < h ? xs[k] : xa[k - h];
+        order[k] = k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (xv[a] != xv[b]) return xv[a] < xv[b];
+        return (a < h) && !(b < h);
+    });
     xi.resize(M);
     L.assign((size_t)M * M, 0.0);
-    std::vector<double> l(M);
     for (int kk = 0; kk < M; ++kk) {
         const int k = order[kk];
         xi[kk] = xv[k];
+        const double* l = (k < h) ? &Ls[(size_t)k * M] : &La[(size_t)(k - h) * M];
         double amax = 0.0;
-        for (int i = 0; i < M; ++i) {
-            double t = 0.0;
-            for (int j = i; j < M; ++j) t += Ri[(size_t)i * M + j] * Y[(size_t)j * M + k];
-            l[i] = t;
-            amax = std::max(amax, std::fabs(t));
-        }
+        for (int i = 0; i < M; ++i) amax = std::max(amax, std::fabs(l[i]));
         // divide by the first entry within 1e-8 of the largest magnitude: that
         // entry becomes +1 and near-ties resolve the same way on any machine
         int p = 0;
@@ -231,6 +304,24 @@ void eigenbasis(int M, double omg, const std::vector<double>& K, const std::vect
         const double lp = l[p];
         for (int i = 0; i < M; ++i) L[(size_t)i * M + kk] = (i == p) ? 1.0 : l[i] / lp;
     }
+}
+
+// Normalised HG scattering matrix (Eq. hg): one scalar so that rows sum to M
+// (sum_n kappa_mn w_n = 1 with w = 1/M).
+std::vector<double> hg_matrix(int M, double g) {
+    std::vector<double> K((size_t)M * M);
+    double total = 0.0;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            const double th_i = 2.0 * M_PI * (i + 0.5) / M, th_j = 2.0 * M_PI * (j + 0.5) / M;
+            const double mu = std::cos(th_i - th_j);
+            const double v = (1.0 - g * g) / std::pow(1.0 + g * g - 2.0 * g * mu, 1.5);
+            K[(size_t)i * M + j] = v;
+            total += v / M;
+        }
+    const double rowmean = total / M;
+    for (auto& v : K) v /= rowmean;
+    return K;
 }
 
 template <typename T>
@@ -255,19 +346,7 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         cdir[m] = std::cos(th);
         sdir[m] = std::sin(th);
     }
-    std::vector<double> K((size_t)M * M);
-    double total = 0.0;
-    for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j) {
-            const double th_i = 2.0 * M_PI * (i + 0.5) / M, th_j = 2.0 * M_PI * (j + 0.5) / M;
-            const double mu = std::cos(th_i - th_j);
-            const double g = ctx->g;
-            const double v = (1.0 - g * g) / std::pow(1.0 + g * g - 2.0 * g * mu, 1.5);
-            K[(size_t)i * M + j] = v;
-            total += v / M;
-        }
-    const double rowmean = total / M;
-    for (auto& v : K) v /= rowmean;
+    const std::vector<double> K = hg_matrix(M, ctx->g);
     // cell data and materials (one per distinct 1 - gamma)
     std::vector<double> tau(N), chis(N), omg(N);
     for (int c = 0; c < N; ++c) {
@@ -294,8 +373,8 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     ctx->L_h.assign((size_t)ctx->nmat * M * n2, 0.0);
     for (auto& kv : mats) {
         std::vector<double> xx, Lx, xy, Ly;
-        eigenbasis(M, std::min(kv.first, 1.0), K, cdir, xx, Lx);
-        eigenbasis(M, std::min(kv.first, 1.0), K, sdir, xy, Ly);
+        eigenbasis(M, std::min(kv.first, 1.0), K, cdir, 0, xx, Lx);
+        eigenbasis(M, std::min(kv.first, 1.0), K, sdir, 1, xy, Ly);
         for (int k = 0; k < M2; ++k) {
             if (!(xx[k] < 0 && xx[M2 + k] > 0 && xy[k] < 0 && xy[M2 + k] > 0))
                 throw StatusError{RTE_ESINGULAR, "eigenvalue inertia is not M/2 negative, M/2 positive"};
@@ -525,6 +604,26 @@ RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_
     launch_scale(ctx, w_dev, h_dev + k, w_dev);
     return RTE_OK;
     RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_eigenbasis(int M, double g, double one_minus_gamma, int axis, double* xi,
+                                  double* L) {
+    if (M < 4 || M % 4 != 0 || M > 112 || !(std::fabs(g) < 1.0) || !(one_minus_gamma > 0.0) ||
+        !(one_minus_gamma <= 1.0) || (axis != 0 && axis != 1) || !xi || !L) {
+        set_error(nullptr, "bad argument");
+        return RTE_EINVAL;
+    }
+    RTE_GUARD_BEGIN
+    std::vector<double> d(M), x, Lv;
+    for (int m = 0; m < M; ++m) {
+        const double th = 2.0 * M_PI * (m + 0.5) / M;
+        d[m] = axis == 0 ? std::cos(th) : std::sin(th);
+    }
+    eigenbasis(M, one_minus_gamma, hg_matrix(M, g), d, axis, x, Lv);
+    std::memcpy(xi, x.data(), M * sizeof(double));
+    std::memcpy(L, Lv.data(), (size_t)M * M * sizeof(double));
+    return RTE_OK;
+    RTE_GUARD_END(nullptr)
 }
 
 RTE_API rte_status rte_profile(rte_ctx* ctx, int enable) {

@@ -82,6 +82,7 @@ SIGNATURES = {
     "rte_cgs2": (_I, [_P, _P, _I, _P, _P]),
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
+    "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
     "rte_profile": (_I, [_P, _I]),
     "rte_profile_read": (_I, [_P, ctypes.POINTER(KernelStat), _I]),
 }
@@ -130,6 +131,15 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def eigenbasis(M, g, one_minus_gamma, axis):
+    """Host FP64 eigenpairs of the local TFPS problem (rte_eigenbasis); no GPU needed."""
+    xi = np.zeros(M)
+    L = np.zeros((M, M))
+    _check(load().rte_eigenbasis(int(M), float(g), float(one_minus_gamma), int(axis),
+                                 xi.ctypes.data_as(_P), L.ctypes.data_as(_P)))
+    return xi, L
 
 
 class Context:

@@ -48,8 +48,9 @@ def test_basis_matches_oracle(lib, I, M, seed):
     p, ctx = _oracle(md), _gpu(md)
     xi, L, mat = ctx.export_basis()
     np.testing.assert_array_equal(mat, p.mat_id)
-    np.testing.assert_allclose(xi, p.xi, rtol=1e-12, atol=0)
-    np.testing.assert_allclose(L, p.L, rtol=0, atol=1e-12)
+    cond = 2.0 ** -52 / p.omg.min()      # conditioning of the slow modes
+    np.testing.assert_allclose(xi, p.xi, rtol=1e-12 + 8 * cond, atol=0)
+    np.testing.assert_allclose(L, p.L, rtol=0, atol=1e-12 + 8 * cond)
 
 
 @pytest.mark.parametrize("I,M,seed", CASES)
