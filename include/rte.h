@@ -89,8 +89,9 @@ typedef struct rte_ctx_info {
  * stream : cudaStream_t (NULL = legacy default stream) on which every later
  *   call of this context runs.
  * On success *out owns: the eigenbases (one per distinct 1 - gamma, computed
- * on the host in FP64), the per-cell optical thickness, b, and the per-cell
- * inverse diagonal blocks D_C = G_C^{-1} (FP32, inverted on the device).
+ * on the host in FP64), the per-cell optical thickness, b, the per-cell
+ * inverse diagonal blocks D_C = G_C^{-1} (FP64, Gauss-Jordan on the device)
+ * and the response matrices R_C (FP32).  M <= 80.
  * Synchronous.  Errors: EINVAL (bad sizes or values), ENOMEM, ECUDA,
  * ESINGULAR (a block has a zero pivot).
  * ------------------------------------------------------------------------- */
@@ -126,8 +127,9 @@ RTE_API rte_status rte_apply_adjoint(rte_ctx* ctx, int precision, const void* y_
 /* ---------------------------------------------------------------------------
  * rte_block_apply -- z_C = D_C r_C (transpose = 0) or D_C^T r_C (1) for every
  * cell, D_C = G_C^{-1} the inverse of the cell's diagonal block of A: the
- * block-Jacobi preconditioner of Sec. 4 and the map D of Eq. loss.
- * r_dev, z_dev: float [n], must not overlap.  Asynchronous.
+ * block-Jacobi preconditioner of Sec. 4 and the map D of Eq. loss (D in FP64,
+ * FP64 accumulation).  r_dev, z_dev: float [n], must not overlap.
+ * Asynchronous.
  * ------------------------------------------------------------------------- */
 RTE_API rte_status rte_block_apply(rte_ctx* ctx, int transpose, const float* r_dev, float* z_dev);
 
@@ -154,8 +156,22 @@ RTE_API rte_status rte_export_basis(const rte_ctx* ctx, double* xi, double* L, i
 RTE_API rte_status rte_eigenbasis(int M, double g, double one_minus_gamma, int axis, double* xi,
                                   double* L);
 
-/* Copy the inverse blocks out: D [N][2M][2M] row-major float (host). Synchronous. */
-RTE_API rte_status rte_export_blocks(rte_ctx* ctx, float* D_host);
+/* Copy the per-cell matrices out (host, row-major, either pointer may be NULL):
+ * D [N][2M][2M] double, D_C = G_C^{-1} (rows = slots, columns = rows of A);
+ * R [N][2M][2M] float, the response R_C = T_out,C D_C whose row (f, j) is
+ * the value leaving C through face f in direction dirs[opp f][j] for unit
+ * incoming data.  Synchronous. */
+RTE_API rte_status rte_export_blocks(rte_ctx* ctx, double* D_host, float* R_host);
+
+/* ---------------------------------------------------------------------------
+ * rte_response_apply -- w = A D v for v in the row space (face-flux space):
+ * every cell's own rows give v back (G_C D_C = I) and each row loses the
+ * neighbour's outgoing value, w = v - P R v, with R the FP32 response
+ * matrices (products in FP32, v and w double [n]).  This is the operator the
+ * Krylov iteration of rte_solve works on (block-Jacobi right
+ * preconditioning, Sec. 4).  v and w must not overlap.  Asynchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_response_apply(rte_ctx* ctx, const double* v_dev, double* w_dev);
 
 /* ---------------------------------------------------------------------------
  * Krylov building block (Arnoldi step of flexible GMRES): orthogonalise w

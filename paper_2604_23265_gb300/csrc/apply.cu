@@ -117,6 +117,91 @@ __global__ void __launch_bounds__(256) k_traces(OpArgs a, const T* __restrict__ 
     }
 }
 
+// Kernel 1, single-material variant: the basis (Lt, 2M x M) is staged in
+// shared memory once per block and read with 16-byte broadcast loads; each
+// thread keeps a 6 x MB register tile (MB = 16 directions).
+template <typename T, int MB>
+__global__ void __launch_bounds__(256) k_traces_shl(OpArgs a, const T* __restrict__ Lt,
+                                                    const T* __restrict__ x, T* __restrict__ y,
+                                                    T* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = a.M, N = a.N, M2 = M / 2;
+    T* Ls = reinterpret_cast<T*>(smem_raw);        // [2M][M]
+    T* s = Ls + 2 * M * M;                          // [6][M][32]
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int c = blockIdx.x * kCellsPerBlock + lane;
+    const bool valid = c < N;
+    const T tau = valid ? (T)a.tau[c] : (T)0;
+    const double* xim = a.xi;                       // material 0
+    for (int e = threadIdx.x; e < 2 * M * M; e += blockDim.x) Ls[e] = Lt[e];
+    for (int k = warp; k < 2 * M; k += nwarps) {
+        T v = valid ? x[(size_t)k * N + c] : (T)0;
+        T half = dexp<T>((T)(-0.5) * tau * (T)fabs(xim[k]));
+        T full = half * half;
+        int grp = k / M2;
+        int kk = k % M;
+        T* base = s + (grp < 2 ? 0 : 3 * M * 32);
+        T dfirst = (grp == 0 || grp == 2) ? (T)1 : full;
+        T dsecond = (grp == 0 || grp == 2) ? full : (T)1;
+        base[(0 * M + kk) * 32 + lane] = v * dfirst;
+        base[(1 * M + kk) * 32 + lane] = v * dsecond;
+        base[(2 * M + kk) * 32 + lane] = v * half;
+    }
+    __syncthreads();
+    constexpr int VW = 16 / sizeof(T);              // elements per 16-byte load
+    using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    for (int m0 = warp * MB; m0 < M; m0 += nwarps * MB) {
+        T xw[MB], xe[MB], xp[MB], ys[MB], yn[MB], yp[MB];
+#pragma unroll
+        for (int i = 0; i < MB; ++i) xw[i] = xe[i] = xp[i] = ys[i] = yn[i] = yp[i] = (T)0;
+#pragma unroll 2
+        for (int k = 0; k < M; ++k) {
+            const T sw = s[(0 * M + k) * 32 + lane];
+            const T se = s[(1 * M + k) * 32 + lane];
+            const T sp = s[(2 * M + k) * 32 + lane];
+            const T ss = s[(3 * M + k) * 32 + lane];
+            const T sn = s[(4 * M + k) * 32 + lane];
+            const T sq = s[(5 * M + k) * 32 + lane];
+            const V16* lx4 = reinterpret_cast<const V16*>(Ls + (size_t)k * M + m0);
+            const V16* ly4 = reinterpret_cast<const V16*>(Ls + (size_t)(M + k) * M + m0);
+#pragma unroll
+            for (int q = 0; q < MB / VW; ++q) {
+                const V16 lxv = lx4[q];
+                const V16 lyv = ly4[q];
+                const T* lx = reinterpret_cast<const T*>(&lxv);
+                const T* ly = reinterpret_cast<const T*>(&lyv);
+#pragma unroll
+                for (int t = 0; t < VW; ++t) {
+                    const int i = q * VW + t;
+                    xw[i] = fma(lx[t], sw, xw[i]);
+                    xe[i] = fma(lx[t], se, xe[i]);
+                    xp[i] = fma(lx[t], sp, xp[i]);
+                    ys[i] = fma(ly[t], ss, ys[i]);
+                    yn[i] = fma(ly[t], sn, yn[i]);
+                    yp[i] = fma(ly[t], sq, yp[i]);
+                }
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < MB; ++i) {
+                const int m = m0 + i;
+                const T tr[4] = {xw[i] + yp[i], xe[i] + yp[i], xp[i] + ys[i], xp[i] + yn[i]};
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const int info = a.rowinfo[f * M + m];
+                    if (info >= 0)
+                        y[(size_t)(f * M2 + info) * N + c] = tr[f];
+                    else
+                        out[(size_t)(f * M2 + (-info - 1)) * N + c] = tr[f];
+                }
+            }
+        }
+    }
+}
+
 // Kernel 2: subtract the neighbour's outgoing trace; optionally r = b - A x.
 template <typename T, typename TO>
 __global__ void k_combine(int I, int M, const T* __restrict__ yown, const T* __restrict__ out,
@@ -301,19 +386,29 @@ int grid_stride_blocks(rte_ctx* ctx, int64_t n) {
 template <typename T>
 void apply_impl(rte_ctx* ctx, const T* x, void* y, bool y_is_double, const double* b) {
     const int M = ctx->M;
-    const int MB = (M % 8 == 0) ? 8 : 4;
-    const int warps = M / MB < 8 ? M / MB : 8;
     const int blocks = (ctx->N + kCellsPerBlock - 1) / kCellsPerBlock;
-    const size_t smem = sizeof(T) * 6 * M * 32;
     T* own = reinterpret_cast<T*>(ctx->trace_out);                    // first half of scratch
     T* out = own + ctx->n;                                            // second half
     const T* Lt = std::is_same<T, double>::value ? (const T*)ctx->Lt64 : (const T*)ctx->Lt32;
-    auto kern = (MB == 8) ? k_traces<T, 8> : k_traces<T, 4>;
-    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-          "traces smem");
     {
         ProfScope ps(ctx, K_TRACES, (double)ctx->n * sizeof(T));
-        kern<<<blocks, warps * 32, smem, ctx->stream>>>(op_args(ctx), Lt, x, own, out);
+        constexpr int MBS = sizeof(T) == 4 ? 16 : 8;
+        const size_t smem_shl = sizeof(T) * (2 * (size_t)M * M + 6 * (size_t)M * 32);
+        if (ctx->nmat == 1 && M % MBS == 0 && smem_shl <= 200 * 1024) {
+            const int warps = M / MBS < 8 ? M / MBS : 8;
+            auto kern = k_traces_shl<T, MBS>;
+            check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_shl), "traces smem");
+            kern<<<blocks, warps * 32, smem_shl, ctx->stream>>>(op_args(ctx), Lt, x, own, out);
+        } else {
+            const int MB = (M % 8 == 0) ? 8 : 4;
+            const int warps = M / MB < 8 ? M / MB : 8;
+            const size_t smem = sizeof(T) * 6 * M * 32;
+            auto kern = (MB == 8) ? k_traces<T, 8> : k_traces<T, 4>;
+            check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "traces smem");
+            kern<<<blocks, warps * 32, smem, ctx->stream>>>(op_args(ctx), Lt, x, own, out);
+        }
         check(cudaGetLastError(), "k_traces");
     }
     const int g = grid_stride_blocks(ctx, ctx->n);

@@ -7,9 +7,10 @@
 //
 // Inversion: one CTA per cell, the 2M x 2M block in shared memory (row stride
 // 2M+1 so column walks are conflict-free), in-place Gauss-Jordan with partial
-// pivoting in FP32; row swaps are undone as column swaps at the end.  FP32 is
-// enough here: the block only preconditions, and the flexible Krylov method
-// absorbs its rounding.
+// pivoting in FP64; row swaps are undone as column swaps at the end.  FP64 is
+// needed: in the diffusive limit the four slow basis functions of a cell are
+// nearly parallel, cond(G_C) reaches 1e8, and D_C maps the Krylov correction
+// back to the coefficients once per restart cycle.
 //
 // Storage: Dt[c][j][i] = D_C[i][j] (column-major per cell) so that the apply
 // z_i = sum_j D_ij r_j streams each block once with 16-byte loads.
@@ -23,41 +24,41 @@ __global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restri
                                                       const double* __restrict__ xi,
                                                       const double* __restrict__ L,
                                                       const int* __restrict__ rowdir,
-                                                      float* __restrict__ Dt,
+                                                      double* __restrict__ Dt,
                                                       int* __restrict__ singular) {
-    extern __shared__ float sm[];
+    extern __shared__ double smd[];
     const int n2 = 2 * M, M2 = M / 2, ld = n2 + 1;
-    float* A = sm;                       // [n2][ld]
-    float* fac = A + n2 * ld;            // [n2]
-    float* half = fac + n2;              // [n2]
+    double* A = smd;                     // [n2][ld]
+    double* fac = A + n2 * ld;           // [n2]
+    double* half = fac + n2;             // [n2]
     int* perm = reinterpret_cast<int*>(half + n2);   // [n2]
     __shared__ int s_piv;
-    __shared__ float s_pivval;
+    __shared__ double s_pivval;
     const int c = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int mc = mat[c];
     const double t = tau[c];
-    for (int k = tid; k < n2; k += nt) half[k] = (float)exp(-0.5 * t * fabs(xi[(size_t)mc * n2 + k]));
+    for (int k = tid; k < n2; k += nt) half[k] = exp(-0.5 * t * fabs(xi[(size_t)mc * n2 + k]));
     __syncthreads();
     const double* Lm = L + (size_t)mc * M * n2;
     for (int e = tid; e < n2 * n2; e += nt) {
         const int r = e / n2, k = e - r * n2;
         const int f = r / M2, fk = k / M2;
-        const float d = (f == fk) ? 1.0f : ((f == (fk ^ 1)) ? half[k] * half[k] : half[k]);
-        A[r * ld + k] = (float)Lm[(size_t)rowdir[r] * n2 + k] * d;
+        const double d = (f == fk) ? 1.0 : ((f == (fk ^ 1)) ? half[k] * half[k] : half[k]);
+        A[r * ld + k] = Lm[(size_t)rowdir[r] * n2 + k] * d;
     }
     __syncthreads();
     bool bad = false;
     for (int k = 0; k < n2; ++k) {
         if (tid < 32) {
-            float best = -1.0f;
+            double best = -1.0;
             int bi = k;
             for (int r = k + tid; r < n2; r += 32) {
-                const float v = fabsf(A[r * ld + k]);
+                const double v = fabs(A[r * ld + k]);
                 if (v > best) { best = v; bi = r; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_down_sync(0xffffffffu, best, o);
+                const double ob = __shfl_down_sync(0xffffffffu, best, o);
                 const int oi = __shfl_down_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
@@ -65,29 +66,29 @@ __global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restri
         }
         __syncthreads();
         const int p = s_piv;
-        const float pv = s_pivval;
-        if (!(fabsf(pv) > 0.0f) || !isfinite(pv)) bad = true;
+        const double pv = s_pivval;
+        if (!(fabs(pv) > 0.0) || !isfinite(pv)) bad = true;
         if (p != k) {
             for (int j = tid; j < n2; j += nt) {
-                const float tmp = A[k * ld + j];
+                const double tmp = A[k * ld + j];
                 A[k * ld + j] = A[p * ld + j];
                 A[p * ld + j] = tmp;
             }
         }
         if (tid == 0) perm[k] = p;
         __syncthreads();
-        const float inv = 1.0f / pv;
+        const double inv = 1.0 / pv;
         for (int j = tid; j < n2; j += nt) {
-            const float v = (j == k) ? 1.0f : A[k * ld + j];
+            const double v = (j == k) ? 1.0 : A[k * ld + j];
             A[k * ld + j] = v * inv;
         }
-        for (int i = tid; i < n2; i += nt) fac[i] = (i == k) ? 0.0f : A[i * ld + k];
+        for (int i = tid; i < n2; i += nt) fac[i] = (i == k) ? 0.0 : A[i * ld + k];
         __syncthreads();
         for (int e = tid; e < n2 * n2; e += nt) {
             const int i = e / n2, j = e - i * n2;
             if (i == k) continue;
-            const float base = (j == k) ? 0.0f : A[i * ld + j];
-            A[i * ld + j] = fmaf(-fac[i], A[k * ld + j], base);
+            const double base = (j == k) ? 0.0 : A[i * ld + j];
+            A[i * ld + j] = fma(-fac[i], A[k * ld + j], base);
         }
         __syncthreads();
     }
@@ -95,14 +96,14 @@ __global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restri
         const int p = perm[k];
         if (p != k) {
             for (int i = tid; i < n2; i += nt) {
-                const float tmp = A[i * ld + k];
+                const double tmp = A[i * ld + k];
                 A[i * ld + k] = A[i * ld + p];
                 A[i * ld + p] = tmp;
             }
         }
         __syncthreads();
     }
-    float* out = Dt + (size_t)c * n2 * n2;
+    double* out = Dt + (size_t)c * n2 * n2;
     for (int e = tid; e < n2 * n2; e += nt) {
         const int j = e / n2, i = e - j * n2;
         out[e] = A[i * ld + j];
@@ -110,90 +111,159 @@ __global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restri
     if (bad && tid == 0) atomicExch(singular, 1);
 }
 
-template <typename TIN>
-__device__ __forceinline__ float load_in(const TIN* p, size_t i, float s) {
-    return (float)((double)p[i] * (double)s);
+// Response matrix of every cell, R_C = T_out,C D_C: row (f, j) of T_out is the
+// trace at face f, direction dirs[opp f][j] (leaving C), of every basis
+// function -- so R_C maps the cell's incoming face data to its outgoing face
+// data.  Computed in FP64 from the FP64 inverse, stored in FP32 as
+// Rt[c][i][row] = R_C[row][i].  Its entries are bounded transfer
+// coefficients (row sums of |R| near one), so FP32 keeps them accurate where
+// D_C itself (entries up to ~1e5 in the diffusive limit) would not.
+__global__ void __launch_bounds__(256) k_response(int M, const int* __restrict__ mat,
+                                                  const double* __restrict__ tau,
+                                                  const double* __restrict__ xi,
+                                                  const double* __restrict__ L,
+                                                  const int* __restrict__ rowdir,
+                                                  const double* __restrict__ Dt,
+                                                  float* __restrict__ Rt) {
+    extern __shared__ double smd[];
+    const int n2 = 2 * M, M2 = M / 2, ld = n2 + 1;
+    double* T = smd;                     // [n2][ld] outgoing traces
+    double* half = T + n2 * ld;          // [n2]
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int mc = mat[c];
+    const double t = tau[c];
+    for (int k = tid; k < n2; k += nt) half[k] = exp(-0.5 * t * fabs(xi[(size_t)mc * n2 + k]));
+    __syncthreads();
+    const double* Lm = L + (size_t)mc * M * n2;
+    for (int e = tid; e < n2 * n2; e += nt) {
+        const int r = e / n2, k = e - r * n2;
+        const int f = r / M2, fk = k / M2, j = r - f * M2;
+        const int m = rowdir[(f ^ 1) * M2 + j];           // a direction leaving through f
+        const double d = (f == fk) ? 1.0 : ((f == (fk ^ 1)) ? half[k] * half[k] : half[k]);
+        T[r * ld + k] = Lm[(size_t)m * n2 + k] * d;
+    }
+    __syncthreads();
+    const double* D = Dt + (size_t)c * n2 * n2;      // D[k][i] = Dt[i][k]
+    float* out = Rt + (size_t)c * n2 * n2;
+    for (int e = tid; e < n2 * n2; e += nt) {
+        const int i = e / n2, r = e - i * n2;
+        const double* di = D + (size_t)i * n2;
+        double acc = 0.0;
+        for (int k = 0; k < n2; ++k) acc = fma(T[r * ld + k], __ldg(di + k), acc);
+        out[e] = (float)acc;
+    }
 }
 
-// z_C = D_C r_C.  threads per cell G = 2M/4 (four rows each); block = 256
-// threads = 256/G cells; r staged in shared memory.
-template <typename TIN>
-__global__ void __launch_bounds__(256) k_block_apply(int M, int N, const float* __restrict__ Dt,
+// z_C = X_C r_C for per-cell column-major matrices Xt[c][j][i] = X_C[i][j]
+// (D or the response R).  Threads per cell G = 2M/4 (four rows each); block =
+// 256 threads = 256/G cells; r staged in shared memory; accumulation in the
+// matrix's precision.
+template <typename TD, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256) k_block_apply(int M, int N, const TD* __restrict__ Xt,
                                                      const TIN* __restrict__ r,
-                                                     const double* __restrict__ scale,
-                                                     float* __restrict__ z) {
-    extern __shared__ float sm[];
+                                                     TOUT* __restrict__ z) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    TD* rs = reinterpret_cast<TD*>(smb);
     const int n2 = 2 * M, G = n2 / 4;
     const int cells = blockDim.x / G;
-    float* rs = sm;                    // [n2][cells]
-    float* zs = sm + n2 * cells;       // [n2][cells]
+    TD* zs = rs + n2 * cells;
     const int c0 = blockIdx.x * cells;
-    const float s = scale ? (float)(1.0 / scale[0]) : 1.0f;
     for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
         const int j = e / cells, cc = e - j * cells;
         const int c = c0 + cc;
-        rs[e] = (c < N) ? load_in(r, (size_t)j * N + c, s) : 0.0f;
+        rs[e] = (c < N) ? (TD)r[(size_t)j * N + c] : (TD)0;
     }
     __syncthreads();
     const int cc = threadIdx.x / G, g = threadIdx.x - cc * G;
     const int c = c0 + cc;
     if (cc < cells && c < N) {
-        const float4* D4 = reinterpret_cast<const float4*>(Dt + (size_t)c * n2 * n2) + g;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        const TD* X = Xt + (size_t)c * n2 * n2 + 4 * g;
+        TD a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll 8
         for (int j = 0; j < n2; ++j) {
-            const float4 d = __ldg(D4 + (size_t)j * G);
-            const float rv = rs[j * cells + cc];
-            acc.x = fmaf(d.x, rv, acc.x);
-            acc.y = fmaf(d.y, rv, acc.y);
-            acc.z = fmaf(d.z, rv, acc.z);
-            acc.w = fmaf(d.w, rv, acc.w);
+            const TD* p = X + (size_t)j * n2;
+            TD d0, d1, d2, d3;
+            if (sizeof(TD) == 4) {
+                const float4 d = __ldg(reinterpret_cast<const float4*>(p));
+                d0 = d.x; d1 = d.y; d2 = d.z; d3 = d.w;
+            } else {
+                const double2 u = __ldg(reinterpret_cast<const double2*>(p));
+                const double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
+                d0 = u.x; d1 = u.y; d2 = v.x; d3 = v.y;
+            }
+            const TD rv = rs[j * cells + cc];
+            a0 = fma(d0, rv, a0);
+            a1 = fma(d1, rv, a1);
+            a2 = fma(d2, rv, a2);
+            a3 = fma(d3, rv, a3);
         }
-        zs[(4 * g + 0) * cells + cc] = acc.x;
-        zs[(4 * g + 1) * cells + cc] = acc.y;
-        zs[(4 * g + 2) * cells + cc] = acc.z;
-        zs[(4 * g + 3) * cells + cc] = acc.w;
+        zs[(4 * g + 0) * cells + cc] = a0;
+        zs[(4 * g + 1) * cells + cc] = a1;
+        zs[(4 * g + 2) * cells + cc] = a2;
+        zs[(4 * g + 3) * cells + cc] = a3;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
         const int i = e / cells, c2 = e - i * cells;
-        if (c0 + c2 < N) z[(size_t)i * N + c0 + c2] = zs[e];
+        if (c0 + c2 < N) z[(size_t)i * N + c0 + c2] = (TOUT)zs[e];
     }
 }
 
-// z_C = D_C^T r_C: output j = row j of Dt dotted with r.
-template <typename TIN>
-__global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const float* __restrict__ Dt,
+// w = v - P o: subtract the outgoing data o of the neighbour across each face
+// (o laid out like the rows: row (f, j) of cell C holds the value leaving C
+// through f in direction dirs[opp f][j]).  With o = R v this is w = A D v.
+template <typename TV, typename TO, typename TW>
+__global__ void k_gather(int I, int M, const TV* __restrict__ v, const TO* __restrict__ o,
+                         TW* __restrict__ w) {
+    const int N = I * I, M2 = M / 2;
+    const int64_t n = (int64_t)2 * M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(e / N);
+        const int c = (int)(e - (int64_t)row * N);
+        const int f = row / M2, j = row - f * M2;
+        const int iy = c / I, ix = c - iy * I;
+        int nb = -1;
+        if (f == 0 && ix > 0) nb = c - 1;
+        if (f == 1 && ix < I - 1) nb = c + 1;
+        if (f == 2 && iy > 0) nb = c - I;
+        if (f == 3 && iy < I - 1) nb = c + I;
+        double val = (double)v[e];
+        if (nb >= 0) val -= (double)o[(int64_t)((f ^ 1) * M2 + j) * N + nb];
+        w[e] = (TW)val;
+    }
+}
+
+// z_C = D_C^T r_C: output j = row j of Dt dotted with r (FP64 accumulation).
+template <typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const double* __restrict__ Dt,
                                                        const TIN* __restrict__ r,
-                                                       const double* __restrict__ scale,
-                                                       float* __restrict__ z) {
-    extern __shared__ float sm[];
+                                                       TOUT* __restrict__ z) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    double* rs = reinterpret_cast<double*>(smb);
     const int n2 = 2 * M, G = n2 / 4;
     const int cells = blockDim.x / G;
-    float* rs = sm;
-    float* zs = sm + n2 * cells;
+    double* zs = rs + n2 * cells;
     const int c0 = blockIdx.x * cells;
-    const float s = scale ? (float)(1.0 / scale[0]) : 1.0f;
     for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
         const int j = e / cells, cc = e - j * cells;
         const int c = c0 + cc;
-        rs[e] = (c < N) ? load_in(r, (size_t)j * N + c, s) : 0.0f;
+        rs[e] = (c < N) ? (double)r[(size_t)j * N + c] : 0.0;
     }
     __syncthreads();
     const int cc = threadIdx.x / G, g = threadIdx.x - cc * G;
     const int c = c0 + cc;
     if (cc < cells && c < N) {
-        const float* D = Dt + (size_t)c * n2 * n2;
+        const double* D = Dt + (size_t)c * n2 * n2;
         for (int t = 0; t < 4; ++t) {
             const int j = 4 * g + t;
-            const float4* row = reinterpret_cast<const float4*>(D + (size_t)j * n2);
-            float acc = 0.f;
-            for (int i4 = 0; i4 < G; ++i4) {
-                const float4 d = __ldg(row + i4);
-                acc = fmaf(d.x, rs[(4 * i4 + 0) * cells + cc], acc);
-                acc = fmaf(d.y, rs[(4 * i4 + 1) * cells + cc], acc);
-                acc = fmaf(d.z, rs[(4 * i4 + 2) * cells + cc], acc);
-                acc = fmaf(d.w, rs[(4 * i4 + 3) * cells + cc], acc);
+            const double2* row = reinterpret_cast<const double2*>(D + (size_t)j * n2);
+            double acc = 0.0;
+            for (int i2 = 0; i2 < n2 / 2; ++i2) {
+                const double2 d = __ldg(row + i2);
+                acc = fma(d.x, rs[(2 * i2 + 0) * cells + cc], acc);
+                acc = fma(d.y, rs[(2 * i2 + 1) * cells + cc], acc);
             }
             zs[j * cells + cc] = acc;
         }
@@ -201,7 +271,7 @@ __global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const float
     __syncthreads();
     for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
         const int i = e / cells, c2 = e - i * cells;
-        if (c0 + c2 < N) z[(size_t)i * N + c0 + c2] = zs[e];
+        if (c0 + c2 < N) z[(size_t)i * N + c0 + c2] = (TOUT)zs[e];
     }
 }
 
@@ -209,52 +279,104 @@ __global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const float
 
 void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
     const int M = ctx->M, n2 = 2 * M;
-    const size_t smem = sizeof(float) * ((size_t)n2 * (n2 + 1) + 3 * n2);
+    const size_t smem = sizeof(double) * ((size_t)n2 * (n2 + 1) + 3 * n2);
     check(cudaFuncSetAttribute(k_build_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem), "build_invert smem");
     const int threads = n2 >= 64 ? 256 : 128;
-    ProfScope ps(ctx, K_INVERT, (double)ctx->N * n2 * n2 * 4);
-    k_build_invert<<<ctx->N, threads, smem, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi,
-                                                           ctx->L64, ctx->rowdir, ctx->Dt,
-                                                           singular_dev);
-    check(cudaGetLastError(), "k_build_invert");
+    {
+        ProfScope ps(ctx, K_INVERT, (double)ctx->N * n2 * n2 * 8);
+        k_build_invert<<<ctx->N, threads, smem, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi,
+                                                               ctx->L64, ctx->rowdir, ctx->Dt,
+                                                               singular_dev);
+        check(cudaGetLastError(), "k_build_invert");
+    }
+    const size_t smem2 = sizeof(double) * ((size_t)n2 * (n2 + 1) + n2);
+    check(cudaFuncSetAttribute(k_response, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
+          "response smem");
+    ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * n2 * n2 * 12);
+    k_response<<<ctx->N, threads, smem2, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi, ctx->L64,
+                                                        ctx->rowdir, ctx->Dt, ctx->Rt);
+    check(cudaGetLastError(), "k_response");
 }
 
-void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double, float* z,
-                        const double* scale_dev) {
+namespace {
+template <typename TD, typename TIN, typename TOUT>
+void block_apply_t(rte_ctx* ctx, const TD* X, const void* r, void* z, int kid, double bytes) {
     const int M = ctx->M, n2 = 2 * M, G = n2 / 4;
     const int threads = G >= 256 ? G : (256 / G) * G;
     const int cells = threads / G;
     const int blocks = (ctx->N + cells - 1) / cells;
-    const size_t smem = sizeof(float) * 2 * n2 * cells;
-    ProfScope ps(ctx, transpose ? K_BLOCK_T : K_BLOCK,
-                 (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * ((r_is_double ? 8 : 4) + 4));
-    if (!transpose) {
-        if (r_is_double) {
-            check(cudaFuncSetAttribute(k_block_apply<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "ba");
-            k_block_apply<double><<<blocks, threads, smem, ctx->stream>>>(
-                M, ctx->N, ctx->Dt, (const double*)r, scale_dev, z);
-        } else {
-            check(cudaFuncSetAttribute(k_block_apply<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "ba");
-            k_block_apply<float><<<blocks, threads, smem, ctx->stream>>>(
-                M, ctx->N, ctx->Dt, (const float*)r, scale_dev, z);
-        }
-    } else {
-        if (r_is_double) {
-            check(cudaFuncSetAttribute(k_block_apply_t<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "bat");
-            k_block_apply_t<double><<<blocks, threads, smem, ctx->stream>>>(
-                M, ctx->N, ctx->Dt, (const double*)r, scale_dev, z);
-        } else {
-            check(cudaFuncSetAttribute(k_block_apply_t<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "bat");
-            k_block_apply_t<float><<<blocks, threads, smem, ctx->stream>>>(
-                M, ctx->N, ctx->Dt, (const float*)r, scale_dev, z);
-        }
-    }
+    const size_t smem = sizeof(TD) * 2 * n2 * cells;
+    auto kern = k_block_apply<TD, TIN, TOUT>;
+    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "ba");
+    ProfScope ps(ctx, kid, bytes);
+    kern<<<blocks, threads, smem, ctx->stream>>>(M, ctx->N, X, (const TIN*)r, (TOUT*)z);
     check(cudaGetLastError(), "k_block_apply");
+}
+}  // namespace
+
+void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double, void* z,
+                        bool z_is_double) {
+    const int M = ctx->M, n2 = 2 * M, G = n2 / 4;
+    const double bytes = (double)ctx->N * n2 * n2 * 8 +
+                         (double)ctx->n * ((r_is_double ? 8 : 4) + (z_is_double ? 8 : 4));
+    if (!transpose) {
+        if (r_is_double && z_is_double)
+            block_apply_t<double, double, double>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
+        else if (r_is_double)
+            block_apply_t<double, double, float>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
+        else if (z_is_double)
+            block_apply_t<double, float, double>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
+        else
+            block_apply_t<double, float, float>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
+        return;
+    }
+    const int threads = G >= 256 ? G : (256 / G) * G;
+    const int cells = threads / G;
+    const int blocks = (ctx->N + cells - 1) / cells;
+    const size_t smem = sizeof(double) * 2 * n2 * cells;
+    ProfScope ps(ctx, K_BLOCK_T, bytes);
+    if (r_is_double && z_is_double) {
+        check(cudaFuncSetAttribute(k_block_apply_t<double, double>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "bat");
+        k_block_apply_t<double, double><<<blocks, threads, smem, ctx->stream>>>(
+            M, ctx->N, ctx->Dt, (const double*)r, (double*)z);
+    } else if (!r_is_double && !z_is_double) {
+        check(cudaFuncSetAttribute(k_block_apply_t<float, float>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "bat");
+        k_block_apply_t<float, float><<<blocks, threads, smem, ctx->stream>>>(
+            M, ctx->N, ctx->Dt, (const float*)r, (float*)z);
+    } else {
+        throw StatusError{RTE_EINVAL, "transposed block apply needs matching precisions"};
+    }
+    check(cudaGetLastError(), "k_block_apply_t");
+}
+
+void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* w,
+                           bool w_is_double) {
+    const int M = ctx->M, n2 = 2 * M;
+    float* o = reinterpret_cast<float*>(ctx->trace_out);
+    const double bytes = (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * ((v_is_double ? 8 : 4) + 4);
+    if (v_is_double)
+        block_apply_t<float, double, float>(ctx, ctx->Rt, v, o, K_RESPONSE_APPLY, bytes);
+    else
+        block_apply_t<float, float, float>(ctx, ctx->Rt, v, o, K_RESPONSE_APPLY, bytes);
+    int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
+    const int g = (int)(want < cap ? want : cap);
+    ProfScope ps(ctx, K_GATHER, (double)ctx->n * ((v_is_double ? 8 : 4) + (w_is_double ? 8 : 4)));
+    if (v_is_double && w_is_double)
+        k_gather<double, float, double><<<g, 256, 0, ctx->stream>>>(ctx->I, M, (const double*)v, o,
+                                                                    (double*)w);
+    else if (!v_is_double && !w_is_double)
+        k_gather<float, float, float><<<g, 256, 0, ctx->stream>>>(ctx->I, M, (const float*)v, o,
+                                                                  (float*)w);
+    else if (!v_is_double && w_is_double)
+        k_gather<float, float, double><<<g, 256, 0, ctx->stream>>>(ctx->I, M, (const float*)v, o,
+                                                                   (double*)w);
+    else
+        k_gather<double, float, float><<<g, 256, 0, ctx->stream>>>(ctx->I, M, (const double*)v, o,
+                                                                   (float*)w);
+    check(cudaGetLastError(), "k_gather");
 }
 
 }  // namespace rte

@@ -5,8 +5,11 @@
 // Classical Gram-Schmidt with one reorthogonalisation is done in three passes
 // over the basis V (k vectors of n doubles, vector j at V + j*n):
 //   pass 1  h1 = V^T w
-//   pass 2  w <- w - V h1,  h2 = V^T w        (fused: V read once)
+//   pass 2  w <- w - V h1,  h2 = V^T w        (fused: V streamed from HBM once,
+//                                              its re-read served by L1/L2)
 //   pass 3  w <- w - V h2,  ||w||^2            (fused)
+// Each block walks 1024-element chunks with the chunk of w in registers and
+// reduces one dot per basis vector across the warp.
 // Reductions are deterministic: every block writes its partial sums, the last
 // block to finish (atomic ticket) adds them in block order with a fixed tree,
 // so a result does not depend on scheduling -- an instance gives the same
@@ -62,77 +65,190 @@ __device__ void block_reduce_finish(double (&acc)[KMAX], int K, double* __restri
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-template <int KMAX>
+// Chunked streaming layout: a block owns chunks of kChunk = 4 * kT consecutive
+// elements; lane l of warp w holds elements base + 2l + {0,1} and
+// base + 64 + 2l + {0,1} of its 128-element slice (two 16-byte loads per
+// vector), so every load instruction of a warp covers 512 contiguous bytes.
+constexpr int kChunk = 4 * kT;
+
+struct Slice {
+    double v[4];
+};
+
+__device__ __forceinline__ int64_t slice_base(int64_t chunk) {
+    return chunk * kChunk + (int64_t)(threadIdx.x >> 5) * 128 + 2 * (threadIdx.x & 31);
+}
+
+__device__ __forceinline__ Slice load_slice(const double* __restrict__ p, int64_t base, int64_t n) {
+    Slice s;
+    if (base + 65 < n) {
+        const double2 a = *reinterpret_cast<const double2*>(p + base);
+        const double2 b = *reinterpret_cast<const double2*>(p + base + 64);
+        s.v[0] = a.x; s.v[1] = a.y; s.v[2] = b.x; s.v[3] = b.y;
+    } else {
+        s.v[0] = base < n ? p[base] : 0.0;
+        s.v[1] = base + 1 < n ? p[base + 1] : 0.0;
+        s.v[2] = base + 64 < n ? p[base + 64] : 0.0;
+        s.v[3] = base + 65 < n ? p[base + 65] : 0.0;
+    }
+    return s;
+}
+
+__device__ __forceinline__ void store_slice(double* __restrict__ p, int64_t base, int64_t n,
+                                            const Slice& s) {
+    if (base + 65 < n) {
+        *reinterpret_cast<double2*>(p + base) = make_double2(s.v[0], s.v[1]);
+        *reinterpret_cast<double2*>(p + base + 64) = make_double2(s.v[2], s.v[3]);
+    } else {
+        if (base < n) p[base] = s.v[0];
+        if (base + 1 < n) p[base + 1] = s.v[1];
+        if (base + 64 < n) p[base + 64] = s.v[2];
+        if (base + 65 < n) p[base + 65] = s.v[3];
+    }
+}
+
+__device__ __forceinline__ double slice_dot(const Slice& a, const Slice& b) {
+    return fma(a.v[0], b.v[0], fma(a.v[1], b.v[1], fma(a.v[2], b.v[2], a.v[3] * b.v[3])));
+}
+
+// Every thread accumulates its own partial dot products in shared memory,
+// s_part[k * kT + tid]; at the end the block reduces them (fixed order) and
+// hands the block sums to the last block.
+__device__ void finish_dots(const double* s_part, int K, double* partials, unsigned* counter,
+                            double* res) {
+    __shared__ bool s_last;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < K; k += kT / 32) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kT / 32; ++q) t += s_part[k * kT + q * 32 + lane];
+        t = warp_sum(t);
+        if (lane == 0) partials[(size_t)blockIdx.x * kMaxKrylov + k] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int k = warp; k < K; k += kT / 32) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * kMaxKrylov + k);
+        t = warp_sum(t);
+        if (lane == 0) res[k] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// h[k] = V[k] . w for k < K
 __global__ void __launch_bounds__(kT) k_mdot(const double* __restrict__ V, int K, int64_t n,
                                              const double* __restrict__ w, double* partials,
                                              unsigned* counter, double* h) {
-    double acc[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < K) acc[k] = fma(V[(size_t)k * n + i], wi, acc[k]);
+    extern __shared__ double s_part[];          // [K][kT]
+    const int tid = threadIdx.x;
+    for (int k = 0; k < K; ++k) s_part[k * kT + tid] = 0.0;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = slice_base(ch);
+        const Slice ws = load_slice(w, base, n);
+        int k = 0;
+        for (; k + 4 <= K; k += 4) {
+            const Slice v0 = load_slice(V + (size_t)(k + 0) * n, base, n);
+            const Slice v1 = load_slice(V + (size_t)(k + 1) * n, base, n);
+            const Slice v2 = load_slice(V + (size_t)(k + 2) * n, base, n);
+            const Slice v3 = load_slice(V + (size_t)(k + 3) * n, base, n);
+            s_part[(k + 0) * kT + tid] += slice_dot(v0, ws);
+            s_part[(k + 1) * kT + tid] += slice_dot(v1, ws);
+            s_part[(k + 2) * kT + tid] += slice_dot(v2, ws);
+            s_part[(k + 3) * kT + tid] += slice_dot(v3, ws);
+        }
+        for (; k < K; ++k) s_part[k * kT + tid] += slice_dot(load_slice(V + (size_t)k * n, base, n), ws);
     }
-    block_reduce_finish<KMAX>(acc, K, partials, counter, h, false);
+    finish_dots(s_part, K, partials, counter, h);
 }
 
-template <int KMAX>
+// w <- w - sum_k V[k] h1[k]; then h2[k] = V[k] . w   (V re-read from cache)
 __global__ void __launch_bounds__(kT) k_update_dot(const double* __restrict__ V, int K, int64_t n,
                                                    double* __restrict__ w,
                                                    const double* __restrict__ h1,
                                                    double* partials, unsigned* counter,
                                                    double* h2) {
-    __shared__ double sh[KMAX];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) sh[k] = h1[k];
+    extern __shared__ double s_part[];          // [K][kT]
+    __shared__ double sh[kMaxKrylov];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < K; k += blockDim.x) sh[k] = h1[k];
+    for (int k = 0; k < K; ++k) s_part[k * kT + tid] = 0.0;
     __syncthreads();
-    double acc[KMAX];
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = slice_base(ch);
+        Slice ws = load_slice(w, base, n);
+        int k = 0;
+        for (; k + 4 <= K; k += 4) {
+            const Slice v0 = load_slice(V + (size_t)(k + 0) * n, base, n);
+            const Slice v1 = load_slice(V + (size_t)(k + 1) * n, base, n);
+            const Slice v2 = load_slice(V + (size_t)(k + 2) * n, base, n);
+            const Slice v3 = load_slice(V + (size_t)(k + 3) * n, base, n);
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
+            for (int e = 0; e < 4; ++e) {
+                double t = ws.v[e];
+                t = fma(-sh[k], v0.v[e], t);
+                t = fma(-sh[k + 1], v1.v[e], t);
+                t = fma(-sh[k + 2], v2.v[e], t);
+                ws.v[e] = fma(-sh[k + 3], v3.v[e], t);
+            }
+        }
+        for (; k < K; ++k) {
+            const Slice v = load_slice(V + (size_t)k * n, base, n);
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < K) s = fma(V[(size_t)k * n + i], sh[k], s);
-        const double wi = w[i] - s;
-        w[i] = wi;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < K) acc[k] = fma(V[(size_t)k * n + i], wi, acc[k]);
+            for (int e = 0; e < 4; ++e) ws.v[e] = fma(-sh[k], v.v[e], ws.v[e]);
+        }
+        store_slice(w, base, n, ws);
+        k = 0;
+        for (; k + 4 <= K; k += 4) {
+            const Slice v0 = load_slice(V + (size_t)(k + 0) * n, base, n);
+            const Slice v1 = load_slice(V + (size_t)(k + 1) * n, base, n);
+            const Slice v2 = load_slice(V + (size_t)(k + 2) * n, base, n);
+            const Slice v3 = load_slice(V + (size_t)(k + 3) * n, base, n);
+            s_part[(k + 0) * kT + tid] += slice_dot(v0, ws);
+            s_part[(k + 1) * kT + tid] += slice_dot(v1, ws);
+            s_part[(k + 2) * kT + tid] += slice_dot(v2, ws);
+            s_part[(k + 3) * kT + tid] += slice_dot(v3, ws);
+        }
+        for (; k < K; ++k) s_part[k * kT + tid] += slice_dot(load_slice(V + (size_t)k * n, base, n), ws);
     }
-    block_reduce_finish<KMAX>(acc, K, partials, counter, h2, false);
+    finish_dots(s_part, K, partials, counter, h2);
 }
 
-template <int KMAX>
+// w <- w - sum_k V[k] h2[k]; out[K] = ||w||; out[k] = h1[k] + h2[k]
 __global__ void __launch_bounds__(kT) k_update_norm(const double* __restrict__ V, int K, int64_t n,
                                                     double* __restrict__ w,
                                                     const double* __restrict__ h1,
                                                     const double* __restrict__ h2,
                                                     double* partials, unsigned* counter,
                                                     double* out) {
-    __shared__ double sh[KMAX];
+    __shared__ double sh[kMaxKrylov];
     for (int k = threadIdx.x; k < K; k += blockDim.x) sh[k] = h2[k];
     __syncthreads();
     double acc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = slice_base(ch);
+        Slice ws = load_slice(w, base, n);
+        for (int k = 0; k < K; ++k) {
+            const Slice v = load_slice(V + (size_t)k * n, base, n);
+            const double hk = sh[k];
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < K) s = fma(V[(size_t)k * n + i], sh[k], s);
-        const double wi = w[i] - s;
-        w[i] = wi;
-        acc[0] = fma(wi, wi, acc[0]);
+            for (int e = 0; e < 4; ++e) ws.v[e] = fma(-hk, v.v[e], ws.v[e]);
+        }
+        store_slice(w, base, n, ws);
+        acc[0] += slice_dot(ws, ws);
     }
-    // out[K] = ||w||; the last block also writes out[k] = h1[k] + h2[k]
+    // out[K] = ||w||; block 0 also writes out[k] = h1[k] + h2[k]
     block_reduce_finish<1>(acc, 1, partials, counter, out + K, true);
-    if (blockIdx.x == 0) {
-        // every block could do this; block 0 does it once (h1, h2 are final)
+    if (blockIdx.x == 0)
         for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = h1[k] + h2[k];
-    }
 }
 
 __global__ void __launch_bounds__(kT) k_norm(const double* __restrict__ x, int64_t n,
@@ -166,6 +282,20 @@ __global__ void k_combine_update(double* __restrict__ x, const float* __restrict
     }
 }
 
+// Grid for the kernels with K x kT doubles of dynamic shared memory: as many
+// resident blocks per SM as the shared memory allows (at most 4).
+int dot_blocks(rte_ctx* ctx, int64_t n, int K, const void* kern) {
+    const size_t smem = (size_t)K * kT * sizeof(double);
+    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kMaxKrylov * kT * sizeof(double))), "dot smem");
+    int per_sm = 0;
+    check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem), "occupancy");
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int64_t want = (n + kT - 1) / kT;
+    int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
 int red_blocks(rte_ctx* ctx, int64_t n) {
     int64_t want = (n + kT - 1) / kT;
     int64_t cap = ctx->max_red_blocks;
@@ -175,26 +305,20 @@ int red_blocks(rte_ctx* ctx, int64_t n) {
 }  // namespace
 
 void launch_mdot(rte_ctx* ctx, const double* V, int k, const double* w, double* h) {
-    const int g = red_blocks(ctx, ctx->n);
+    const int g = dot_blocks(ctx, ctx->n, k, (const void*)k_mdot);
     ProfScope ps(ctx, K_MDOT, (double)(k + 1) * ctx->n * 8);
-#define RTE_MDOT(KM) \
-    k_mdot<KM><<<g, kT, 0, ctx->stream>>>(V, k, ctx->n, w, ctx->partials, ctx->counter, h)
-    if (k <= 8) RTE_MDOT(8); else if (k <= 16) RTE_MDOT(16); else if (k <= 32) RTE_MDOT(32);
-    else RTE_MDOT(64);
-#undef RTE_MDOT
+    k_mdot<<<g, kT, (size_t)k * kT * sizeof(double), ctx->stream>>>(V, k, ctx->n, w, ctx->partials,
+                                                                 ctx->counter, h);
     check(cudaGetLastError(), "k_mdot");
 }
 
 void launch_update_dot(rte_ctx* ctx, const double* V, int k, double* w, const double* h1,
                        double* h2) {
-    const int g = red_blocks(ctx, ctx->n);
+    const int g = dot_blocks(ctx, ctx->n, k, (const void*)k_update_dot);
     ProfScope ps(ctx, K_UPDATE_DOT, (double)(k + 2) * ctx->n * 8);
-#define RTE_UD(KM)                                                                     \
-    k_update_dot<KM><<<g, kT, 0, ctx->stream>>>(V, k, ctx->n, w, h1, ctx->partials, \
-                                                ctx->counter, h2)
-    if (k <= 8) RTE_UD(8); else if (k <= 16) RTE_UD(16); else if (k <= 32) RTE_UD(32);
-    else RTE_UD(64);
-#undef RTE_UD
+    k_update_dot<<<g, kT, (size_t)k * kT * sizeof(double), ctx->stream>>>(V, k, ctx->n, w, h1,
+                                                                       ctx->partials, ctx->counter,
+                                                                       h2);
     check(cudaGetLastError(), "k_update_dot");
 }
 
@@ -202,12 +326,8 @@ void launch_update_norm(rte_ctx* ctx, const double* V, int k, double* w, const d
                         const double* h2, double* out) {
     const int g = red_blocks(ctx, ctx->n);
     ProfScope ps(ctx, K_UPDATE_NORM, (double)(k + 2) * ctx->n * 8);
-#define RTE_UN(KM)                                                                         \
-    k_update_norm<KM><<<g, kT, 0, ctx->stream>>>(V, k, ctx->n, w, h1, h2, ctx->partials, \
-                                                 ctx->counter, out)
-    if (k <= 8) RTE_UN(8); else if (k <= 16) RTE_UN(16); else if (k <= 32) RTE_UN(32);
-    else RTE_UN(64);
-#undef RTE_UN
+    k_update_norm<<<g, kT, 0, ctx->stream>>>(V, k, ctx->n, w, h1, h2, ctx->partials, ctx->counter,
+                                             out);
     check(cudaGetLastError(), "k_update_norm");
 }
 

@@ -21,7 +21,7 @@ struct Workspace;                   // Krylov buffers of rte_solve (solve.cu)
 enum KernelId {
     K_TRACES, K_COMBINE, K_ADJOINT, K_RECONSTRUCT, K_RHS, K_INVERT, K_BLOCK, K_BLOCK_T,
     K_MDOT, K_UPDATE_DOT, K_UPDATE_NORM, K_NORM, K_SCALE, K_XUPDATE, K_GIVENS, K_BACKSUB,
-    K_CYCLE, K_F2D, K_MGNET, K_COUNT
+    K_CYCLE, K_F2D, K_MGNET, K_RESPONSE, K_RESPONSE_APPLY, K_GATHER, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -66,7 +66,8 @@ struct rte_ctx {
     int* rowdir = nullptr;           // [2M] direction of each row slot
     double* inflow = nullptr;        // [4][I][M]
     double* b = nullptr;             // [n]
-    float* Dt = nullptr;             // [N][2M][2M], Dt[c][j][i] = D_c[i][j]
+    double* Dt = nullptr;            // [N][2M][2M], Dt[c][j][i] = D_c[i][j]  (FP64)
+    float* Rt = nullptr;             // [N][2M][2M], Rt[c][i][row] = R_c[row][i] (FP32)
 
     // scratch
     double* trace_out = nullptr;     // n elements (float or double) of outgoing traces
@@ -123,12 +124,16 @@ void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi);
 void launch_rhs(rte_ctx* ctx);
 
 // block kernels (blocks.cu) ------------------------------------------------
-// builds G_C for every cell and inverts it into ctx->Dt; *singular_dev set
-// to 1 if a zero pivot appears.
+// builds G_C for every cell, inverts it into ctx->Dt (FP64) and forms the
+// response matrices ctx->Rt (FP32); *singular_dev set to 1 on a zero pivot.
 void launch_build_invert(rte_ctx* ctx, int* singular_dev);
-// z = D r (or D^T r); input float or double, output float
-void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double,
-                        float* z, const double* scale_dev);
+// z = D r (or D^T r), FP64 accumulation; float or double in and out
+void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double, void* z,
+                        bool z_is_double);
+// w = A D v = v - P R v (the block-Jacobi preconditioned operator in face-flux
+// space, R in FP32); v, w float or double; uses trace_out as scratch
+void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* w,
+                           bool w_is_double);
 
 // krylov kernels (krylov.cu) -----------------------------------------------
 // h[0..k) = V^T w (deterministic, last-block reduction into h)

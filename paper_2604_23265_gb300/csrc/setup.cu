@@ -43,7 +43,8 @@ void* dev_alloc(rte_ctx* ctx, size_t bytes) {
 const char* const kKernelNames[K_COUNT] = {
     "traces", "combine", "adjoint", "reconstruct", "rhs", "build_invert", "block_apply",
     "block_apply_t", "mdot", "update_dot", "update_norm", "norm", "scale", "x_update",
-    "givens", "backsub", "cycle_start", "f2d", "mgnet"};
+    "givens", "backsub", "cycle_start", "f2d", "mgnet", "response_build", "response_apply",
+    "gather"};
 
 static cudaEvent_t prof_event(rte_ctx* ctx) {
     if (!ctx->prof.pool.empty()) {
@@ -437,7 +438,8 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         dev_alloc(ctx, (size_t)ctx->max_red_blocks * kMaxKrylov * sizeof(double)));
     ctx->counter = static_cast<unsigned*>(dev_alloc(ctx, 64));
     ctx->scal = static_cast<double*>(dev_alloc(ctx, kScal * sizeof(double)));
-    ctx->Dt = static_cast<float*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(float)));
+    ctx->Dt = static_cast<double*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(double)));
+    ctx->Rt = static_cast<float*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(float)));
     launch_rhs(ctx);
     int* sing = reinterpret_cast<int*>(ctx->scal + kScal - 1);
     launch_build_invert(ctx, sing);
@@ -477,8 +479,8 @@ RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
         set_error(nullptr, "NULL argument");
         return RTE_EINVAL;
     }
-    if (grid->I < 1 || grid->I > 8192 || quad->M < 4 || quad->M % 4 != 0 || quad->M > 112) {
-        set_error(nullptr, "need I in [1, 8192] and M a multiple of 4 in [4, 112]");
+    if (grid->I < 1 || grid->I > 8192 || quad->M < 4 || quad->M % 4 != 0 || quad->M > 80) {
+        set_error(nullptr, "need I in [1, 8192] and M a multiple of 4 in [4, 80]");
         return RTE_EINVAL;
     }
     if (!(std::fabs(g) < 1.0)) { set_error(nullptr, "need |g| < 1"); return RTE_EINVAL; }
@@ -554,7 +556,7 @@ RTE_API rte_status rte_block_apply(rte_ctx* ctx, int transpose, const float* r_d
         return RTE_EINVAL;
     }
     RTE_GUARD_BEGIN
-    launch_block_apply(ctx, transpose != 0, r_dev, false, z_dev, nullptr);
+    launch_block_apply(ctx, transpose != 0, r_dev, false, z_dev, false);
     return RTE_OK;
     RTE_GUARD_END(ctx)
 }
@@ -575,17 +577,36 @@ RTE_API rte_status rte_export_basis(const rte_ctx* ctx, double* xi, double* L, i
     return RTE_OK;
 }
 
-RTE_API rte_status rte_export_blocks(rte_ctx* ctx, float* D_host) {
-    if (!ctx || !D_host) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
+RTE_API rte_status rte_export_blocks(rte_ctx* ctx, double* D_host, float* R_host) {
+    if (!ctx || (!D_host && !R_host)) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
     RTE_GUARD_BEGIN
     const size_t n2 = 2 * (size_t)ctx->M, per = n2 * n2;
-    std::vector<float> tmp(per * ctx->N);
-    check(cudaMemcpyAsync(tmp.data(), ctx->Dt, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost,
-                          ctx->stream), "export blocks");
-    check(cudaStreamSynchronize(ctx->stream), "export sync");
-    for (int c = 0; c < ctx->N; ++c)
-        for (size_t j = 0; j < n2; ++j)
-            for (size_t i = 0; i < n2; ++i) D_host[c * per + i * n2 + j] = tmp[c * per + j * n2 + i];
+    if (D_host) {
+        std::vector<double> tmp(per * ctx->N);
+        check(cudaMemcpyAsync(tmp.data(), ctx->Dt, tmp.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, ctx->stream), "export blocks");
+        check(cudaStreamSynchronize(ctx->stream), "export sync");
+        for (int c = 0; c < ctx->N; ++c)
+            for (size_t j = 0; j < n2; ++j)
+                for (size_t i = 0; i < n2; ++i) D_host[c * per + i * n2 + j] = tmp[c * per + j * n2 + i];
+    }
+    if (R_host) {
+        std::vector<float> tmp(per * ctx->N);
+        check(cudaMemcpyAsync(tmp.data(), ctx->Rt, tmp.size() * sizeof(float),
+                              cudaMemcpyDeviceToHost, ctx->stream), "export response");
+        check(cudaStreamSynchronize(ctx->stream), "export sync");
+        for (int c = 0; c < ctx->N; ++c)
+            for (size_t i = 0; i < n2; ++i)
+                for (size_t r = 0; r < n2; ++r) R_host[c * per + r * n2 + i] = tmp[c * per + i * n2 + r];
+    }
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
+RTE_API rte_status rte_response_apply(rte_ctx* ctx, const double* v_dev, double* w_dev) {
+    if (!ctx || !v_dev || !w_dev || v_dev == w_dev) { set_error(ctx, "bad argument"); return RTE_EINVAL; }
+    RTE_GUARD_BEGIN
+    launch_response_apply(ctx, v_dev, true, w_dev, true);
     return RTE_OK;
     RTE_GUARD_END(ctx)
 }

@@ -1,14 +1,21 @@
-// rte_solve: right-preconditioned flexible GMRES(restart) for A alpha = b.
+// rte_solve: flexible GMRES(restart) for A alpha = b, right-preconditioned by
+// block Jacobi, and optionally by the MgNet V-cycle on top.
 //
-// Per Arnoldi step j (all on the context's stream):
-//   z_j = P(v_j)                 block Jacobi (Sec. 4) or the MgNet V-cycle
-//   w   = A z_j                  inner precision (FP32 by default), FP64 out
-//   CGS2: h = V^T w twice, w /= ||w|| -> v_{j+1}          (FP64)
-//   Givens update of the Hessenberg column, |g_{j+1}|      (FP64, one thread)
+// The Krylov iteration works in face-flux space on B = A D (D = blockdiag
+// G_C^{-1}, block Jacobi, Sec. 4): B v = v - P R v with the per-cell response
+// matrices R_C = T_out D_C in FP32.  R is a bounded transfer map, so FP32
+// keeps B accurate, whereas alpha = D y itself cancels heavily in the
+// diffusive limit and needs FP64.  Per Arnoldi step j:
+//   z_j = Net(v_j)  (MgNet, in face-flux space)  or  z_j = v_j
+//   w   = B z_j                                   FP32 products, FP64 vectors
+//   CGS2: h = V^T w twice, w /= ||w|| -> v_{j+1}  (FP64)
+//   Givens update of the Hessenberg column         (FP64, one thread)
 // The host reads only the residual estimate after each step.  At the end of a
-// cycle y = H^{-1} g on the device, x += Z y, and the true residual
-// r = b - A x is recomputed in FP64: it alone decides convergence, so the
-// FP32 inner operator is corrected by the restarts (iterative refinement).
+// cycle y = H^{-1} g, dy = Z y, alpha += D dy (FP64), and the true residual
+// r = b - A alpha is recomputed in FP64: it alone decides convergence
+// (iterative refinement around the FP32 inner operator).  With
+// inner_precision = RTE_F64 the inner operator is instead A (D z) with the
+// FP64 trace kernel.
 #include <chrono>
 #include <cmath>
 
@@ -69,7 +76,7 @@ Workspace* get_workspace(rte_ctx* ctx, int m) {
     ws->m = m;
     const size_t n = (size_t)ctx->n;
     ws->V = ws_alloc<double>(ctx, ws, (size_t)(m + 1) * n);
-    ws->Z = ws_alloc<float>(ctx, ws, (size_t)m * n);
+    ws->Z = ws_alloc<float>(ctx, ws, (size_t)m * n);    // MgNet outputs (flexible GMRES)
     ws->w = ws_alloc<double>(ctx, ws, n);
     ws->tmp = ws_alloc<double>(ctx, ws, n);
     ws->H = ws_alloc<double>(ctx, ws, (size_t)(m + 1) * m);
@@ -134,6 +141,27 @@ __global__ void k_f2d(const float* __restrict__ x, int64_t n, double* __restrict
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (double)x[i];
+}
+
+// out = sum_k Z[k] y[k]   (Z float or double)
+template <typename TZ>
+__global__ void k_lincomb(const TZ* __restrict__ Z, int K, int64_t n, const double* __restrict__ y,
+                          double* __restrict__ out) {
+    __shared__ double sy[kMaxKrylov];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) sy[k] = y[k];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s = fma((double)Z[(size_t)k * n + i], sy[k], s);
+        out[i] = s;
+    }
+}
+
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += d[i];
 }
 
 __global__ void k_isfinite_f(const float* __restrict__ x, int64_t n, int* flag) {
@@ -233,23 +261,22 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                 k_cycle_start<<<1, 256, 0, ctx->stream>>>(m, ws->est + 3, ws->H, ws->g);
                 check(cudaGetLastError(), "k_cycle_start");
             }
+            const bool cycle_net = use_net;
             int k = 0;
             for (int j = 0; j < m; ++j) {
                 const double* vj = ws->V + (size_t)j * n;
-                float* zj = ws->Z + (size_t)j * n;
-                if (use_net) {
-                    mgnet_precondition(pc, ctx, vj, zj);
-                } else {
-                    launch_block_apply(ctx, false, vj, true, zj, nullptr);
+                const void* zj = vj;
+                bool z_double = true;
+                if (cycle_net) {
+                    float* zf = ws->Z + (size_t)j * n;
+                    mgnet_precondition(pc, ctx, vj, zf);
+                    zj = zf;
+                    z_double = false;
                 }
                 if (opts.inner_precision == RTE_F32) {
-                    launch_apply(ctx, false, zj, ws->w, true, nullptr);
+                    launch_response_apply(ctx, zj, z_double, ws->w, true);
                 } else {
-                    {
-                        ProfScope ps(ctx, K_F2D, (double)n * 12);
-                        k_f2d<<<gblk, 256, 0, ctx->stream>>>(zj, n, ws->tmp);
-                        check(cudaGetLastError(), "k_f2d");
-                    }
+                    launch_block_apply(ctx, false, zj, z_double, ws->tmp, true);
                     launch_apply(ctx, true, ws->tmp, ws->w, true, nullptr);
                 }
                 const int K = j + 1;
@@ -284,7 +311,20 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                     k_backsub<<<1, 32, 0, ctx->stream>>>(k, m, ws->H, ws->g, ws->y);
                     check(cudaGetLastError(), "k_backsub");
                 }
-                launch_combine_update(ctx, x_dev, ws->Z, k, ws->y);
+                {
+                    ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + (cycle_net ? 4 : 8) * k));
+                    if (cycle_net)
+                        k_lincomb<float><<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
+                    else
+                        k_lincomb<double><<<gblk, 256, 0, ctx->stream>>>(ws->V, k, n, ws->y, ws->tmp);
+                    check(cudaGetLastError(), "k_lincomb");
+                }
+                launch_block_apply(ctx, false, ws->tmp, true, ws->w, true);   // D dy
+                {
+                    ProfScope ps(ctx, K_XUPDATE, (double)n * 24);
+                    k_axpy<<<gblk, 256, 0, ctx->stream>>>(x_dev, ws->w, n);
+                    check(cudaGetLastError(), "k_axpy");
+                }
             }
             ++inf.cycles;
         }

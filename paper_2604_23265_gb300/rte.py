@@ -78,7 +78,8 @@ SIGNATURES = {
     "rte_block_apply": (_I, [_P, _I, _P, _P]),
     "rte_reconstruct": (_I, [_P, _P, _P]),
     "rte_export_basis": (_I, [_P, _P, _P, _P]),
-    "rte_export_blocks": (_I, [_P, _P]),
+    "rte_export_blocks": (_I, [_P, _P, _P]),
+    "rte_response_apply": (_I, [_P, _P, _P]),
     "rte_cgs2": (_I, [_P, _P, _I, _P, _P]),
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
@@ -228,9 +229,19 @@ class Context:
         return xi, L, mat
 
     def export_blocks(self):
-        D = np.zeros((self.N, 2 * self.M, 2 * self.M), np.float32)
-        _check(load().rte_export_blocks(self.ptr, D.ctypes.data_as(_P)), self.ptr)
-        return D
+        """(D [N][2M][2M] float64, R [N][2M][2M] float32), row-major per cell."""
+        D = np.zeros((self.N, 2 * self.M, 2 * self.M), np.float64)
+        R = np.zeros((self.N, 2 * self.M, 2 * self.M), np.float32)
+        _check(load().rte_export_blocks(self.ptr, D.ctypes.data_as(_P), R.ctypes.data_as(_P)),
+               self.ptr)
+        return D, R
+
+    def response_apply(self, v, w):
+        """w = A D v = v - P R v (face-flux space), double [n]."""
+        import torch
+        _check(load().rte_response_apply(self.ptr, _dev(v, torch.float64, self.n),
+                                         _dev(w, torch.float64, self.n)), self.ptr)
+        return w
 
     def cgs2(self, V, k, w, h):
         import torch

@@ -115,24 +115,39 @@ def test_reconstruct_matches_oracle(lib, I, M, seed):
 
 @pytest.mark.parametrize("I,M,seed", CASES)
 def test_block_inverse_and_apply(lib, I, M, seed):
-    """D_C (FP32 Gauss-Jordan) against the oracle's LU inverse, and z = D r,
-    D^T r against the same products in FP64; tolerances scale with cond(G_C)."""
+    """D_C (FP64 Gauss-Jordan) against the oracle's LU inverse (to cond(G_C) u64),
+    and z = D r, D^T r (FP32 in/out, FP64 accumulation) against FP64 products."""
     md = _generic(I, M, seed)
     p, ctx = _oracle(md), _gpu(md)
     G = p.blocks()
     Dref = np.linalg.inv(G)
     cond = np.linalg.cond(G).max()
-    tol = 64 * M * 2.0 ** -24 * cond
-    D = ctx.export_blocks().astype(np.float64)
-    assert np.linalg.norm(D - Dref) / np.linalg.norm(Dref) <= tol
+    D, R = ctx.export_blocks()
+    assert np.linalg.norm(D - Dref) / np.linalg.norm(Dref) <= 64 * M * 2.0 ** -52 * cond
     r = W.random_vector(ctx.n, seed + 14).astype(np.float32)
     z = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
     ctx.block_apply(_t(r, torch.float32), z)
-    zref = tfps.block_apply(D, r.astype(np.float64).reshape(2 * M, -1)).ravel()
-    assert _rel(z.cpu().numpy(), zref) <= 8 * M * 2.0 ** -24 * 16
+    zref = tfps.block_apply(Dref, r.astype(np.float64).reshape(2 * M, -1)).ravel()
+    assert _rel(z.cpu().numpy(), zref) <= 4 * 2.0 ** -24 + 64 * M * 2.0 ** -52 * cond
     ctx.block_apply(_t(r, torch.float32), z, transpose=True)
-    zref = tfps.block_apply_T(D, r.astype(np.float64).reshape(2 * M, -1)).ravel()
-    assert _rel(z.cpu().numpy(), zref) <= 8 * M * 2.0 ** -24 * 16
+    zref = tfps.block_apply_T(Dref, r.astype(np.float64).reshape(2 * M, -1)).ravel()
+    assert _rel(z.cpu().numpy(), zref) <= 4 * 2.0 ** -24 + 64 * M * 2.0 ** -52 * cond
+
+
+@pytest.mark.parametrize("I,M,seed", CASES)
+def test_response_apply_is_A_times_D(lib, I, M, seed):
+    """w = A D v through the FP32 response matrices, against the oracle's FP64
+    A(D v); R's rows hold bounded transfer coefficients, so the error is that
+    of 2M-term FP32 sums of O(1) terms."""
+    md = _generic(I, M, seed)
+    p, ctx = _oracle(md), _gpu(md)
+    v = W.random_vector(ctx.n, seed + 15)
+    w = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.response_apply(_t(v), w)
+    ref = p.apply(tfps.block_apply(p.block_inverse(), v.reshape(2 * M, -1))).ravel()
+    assert _rel(w.cpu().numpy(), ref) <= 8 * M * 2.0 ** -24
+    _, R = ctx.export_blocks()
+    assert np.abs(R).max() < 10.0
 
 
 @pytest.mark.parametrize("k", [1, 5, 17, 40, 64])
