@@ -184,6 +184,34 @@ RTE_API rte_status rte_response_apply(rte_ctx* ctx, const double* v_dev, double*
 RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_dev, double* h_dev);
 
 /* ---------------------------------------------------------------------------
+ * rte_cgs2_noalloc -- the Gram-Schmidt step of rte_cgs2 without a context and
+ * without any device allocation.  No counterpart in the paper: it exists for
+ * callers that cannot let a library allocate device memory -- an application
+ * that owns the whole device-memory budget through its own pool, or a
+ * latency-critical loop where cudaMalloc (which may synchronise the device,
+ * and may fail) is not allowed.
+ *
+ * Same arithmetic as rte_cgs2: V_dev holds k orthonormal vectors of n doubles
+ * (vector j at V_dev + j*n), w_dev is orthogonalised in place (two classical
+ * Gram-Schmidt passes) and scaled to unit norm unless that norm is zero;
+ * h_dev[0..k-1] receives the summed projections, h_dev[k] the norm.  All
+ * three are caller-owned device buffers; stream is a cudaStream_t (NULL =
+ * legacy default stream).  Asynchronous.
+ *
+ * Scratch: one file-scope device array of 328,960 bytes (partial sums of up to
+ * 640 blocks x 64 projections, the two projection vectors, a ticket counter),
+ * present on every GPU that loads the library until the process exits.
+ * Limits: 1 <= k <= 64 (EINVAL otherwise), n >= 1, device ordinal < 64.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call on a device shares the array and the ticket is cleared
+ * at the start of each call, so calls that overlap on the GPU (other streams
+ * or threads) race: serialise them.  Calls nothing that allocates.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_cgs2_noalloc(const double* V_dev, int k, int64_t n, double* w_dev,
+                                    double* h_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
  * rte_solve -- solve A x = b for this context's b by right-preconditioned
  * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt plus
  * reorthogonalisation, Givens/Hessenberg least squares in FP64 on the device,

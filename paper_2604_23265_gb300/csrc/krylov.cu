@@ -14,6 +14,8 @@
 // block to finish (atomic ticket) adds them in block order with a fixed tree,
 // so a result does not depend on scheduling -- an instance gives the same
 // bits alone or beside others.
+#include <mutex>
+
 #include "rte_internal.h"
 
 namespace rte {
@@ -353,3 +355,105 @@ void launch_combine_update(rte_ctx* ctx, double* x, const float* Z, int k, const
 }
 
 }  // namespace rte
+
+// ---------------------------------------------------------------------------
+// Allocation-free Gram-Schmidt step (rte_cgs2_noalloc).
+//
+// Same kernels as rte_cgs2, but the scratch they need (per-block partial
+// sums, the two projection vectors and the last-block ticket) lives in one
+// file-scope device array instead of context buffers, so the call allocates
+// nothing.  Layout, in doubles:
+//   [0, kNoAllocBlocks * kMaxKrylov)   per-block partial sums
+//   next kMaxKrylov                    h1 (first projection)
+//   next kMaxKrylov                    h2 (second projection)
+//   next 32                            ticket counter (first 4 bytes)
+// 640 blocks x 64 + 160 doubles = 328,960 bytes per device, held by every GPU
+// that loads the library until the process exits.
+// ---------------------------------------------------------------------------
+namespace rte {
+namespace {
+
+constexpr int kNoAllocBlocks = 640;
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocBlocks * kMaxKrylov + 2 * kMaxKrylov + 32;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Host side: the array's name is only a host stand-in; its device address is
+// looked up once per device with that device current and cached here.
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+    std::once_flag once;
+    double* ptr = nullptr;
+    int num_sms = 0;
+    cudaError_t err = cudaSuccess;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+int noalloc_grid(int64_t n, int num_sms, int per_sm) {
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int64_t want = (n + kT - 1) / kT;
+    int64_t cap = (int64_t)num_sms * per_sm;
+    if (cap > kNoAllocBlocks) cap = kNoAllocBlocks;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+}  // namespace rte
+
+extern "C" RTE_API rte_status rte_cgs2_noalloc(const double* V_dev, int k, int64_t n,
+                                               double* w_dev, double* h_dev, void* stream) {
+    using namespace rte;
+    if (!V_dev || !w_dev || !h_dev || n < 1) {
+        set_error(nullptr, "rte_cgs2_noalloc: NULL pointer or n < 1");
+        return RTE_EINVAL;
+    }
+    if (k < 1 || k > kMaxKrylov) {
+        set_error(nullptr, "rte_cgs2_noalloc: k must be in [1, 64] (the static scratch holds 64 "
+                           "projections per block)");
+        return RTE_EINVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(nullptr, e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error(nullptr, "rte_cgs2_noalloc: device ordinal above 63");
+        return RTE_EINVAL;
+    }
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    std::call_once(d.once, [&d, dev]() {
+        d.err = cudaGetSymbolAddress((void**)&d.ptr, g_noalloc_scratch);
+        if (d.err == cudaSuccess)
+            d.err = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (d.err == cudaSuccess)
+            d.err = cudaFuncSetAttribute(k_mdot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxKrylov * kT * sizeof(double)));
+        if (d.err == cudaSuccess)
+            d.err = cudaFuncSetAttribute(k_update_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxKrylov * kT * sizeof(double)));
+    });
+    if (d.err != cudaSuccess) return cuda_status(nullptr, d.err, "rte_cgs2_noalloc set-up");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* partials = d.ptr;
+    double* h1 = partials + (size_t)kNoAllocBlocks * kMaxKrylov;
+    double* h2 = h1 + kMaxKrylov;
+    unsigned* counter = reinterpret_cast<unsigned*>(h2 + kMaxKrylov);
+    const size_t smem = (size_t)k * kT * sizeof(double);
+    int per_mdot = 0, per_ud = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_mdot, k_mdot, kT, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_ud, k_update_dot, kT, smem);
+    if (e != cudaSuccess) return cuda_status(nullptr, e, "occupancy");
+    // the ticket must start at zero; the array keeps the previous call's bytes
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_status(nullptr, e, "cudaMemsetAsync");
+    const int g1 = noalloc_grid(n, d.num_sms, per_mdot);
+    const int g2 = noalloc_grid(n, d.num_sms, per_ud);
+    const int g3 = noalloc_grid(n, d.num_sms, 4);
+    k_mdot<<<g1, kT, smem, st>>>(V_dev, k, n, w_dev, partials, counter, h1);
+    k_update_dot<<<g2, kT, smem, st>>>(V_dev, k, n, w_dev, h1, partials, counter, h2);
+    k_update_norm<<<g3, kT, 0, st>>>(V_dev, k, n, w_dev, h1, h2, partials, counter, h_dev);
+    k_scale<<<g3, kT, 0, st>>>(w_dev, h_dev + k, n, w_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(nullptr, e, "rte_cgs2_noalloc launch");
+    return RTE_OK;
+}
+

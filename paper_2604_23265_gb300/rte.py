@@ -81,6 +81,7 @@ SIGNATURES = {
     "rte_export_blocks": (_I, [_P, _P, _P]),
     "rte_response_apply": (_I, [_P, _P, _P]),
     "rte_cgs2": (_I, [_P, _P, _I, _P, _P]),
+    "rte_cgs2_noalloc": (_I, [_P, _I, ctypes.c_int64, _P, _P, _P]),
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
     "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
