@@ -177,3 +177,73 @@ def polynomial_diffusion(seed: int, I: int = 32, M: int = 4) -> Medium:
 
 def random_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(n)
+
+
+# ---------------------------------------------------------------------------
+# MgNet / CoeffNet weights (seeded initial values, shared by both sides)
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class NetShape:
+    """Widths of CoeffNet and MgNet.  M: directions (2M input/output channels);
+    levels: V-cycle depth; c0/cmax: MgNet width at level 0 and its cap;
+    cc/ccmax: CoeffNet width at level 0 and its cap; cin: CoeffNet inputs."""
+    M: int
+    levels: int = 4
+    c0: int = 16
+    cmax: int = 128
+    cc: int = 8
+    ccmax: int = 32
+    cin: int = 4
+
+    def width(self, l):
+        return min(self.c0 * 2 ** l, self.cmax)
+
+    def cwidth(self, l):
+        return min(self.cc * 2 ** l, self.ccmax)
+
+
+def param_shapes(s: NetShape):
+    """Ordered (name, shape) of every parameter; conv weights [out][in][k][k],
+    transposed-conv weights [in][out][k][k]."""
+    out = []
+    for l in range(s.levels):
+        cin = s.cin if l == 0 else s.cwidth(l - 1)
+        out.append((f"coef{l}.w", (s.cwidth(l), cin, 3, 3)))
+        out.append((f"coef{l}.gamma", (s.cwidth(l),)))
+        out.append((f"coef{l}.beta", (s.cwidth(l),)))
+        out.append((f"a{l}.w", (s.width(l), s.cwidth(l))))
+        out.append((f"a{l}.b", (s.width(l),)))
+        out.append((f"ainv{l}.w", (s.width(l), s.cwidth(l))))
+        out.append((f"ainv{l}.b", (s.width(l),)))
+    out.append(("lift.w", (s.width(0), 2 * s.M)))
+    for l in range(s.levels):
+        out.append((f"A{l}.w", (s.width(l), s.width(l), 3, 3)))
+        out.append((f"B{l}.w", (s.width(l), s.width(l), 3, 3)))
+    for l in range(s.levels - 1):
+        out.append((f"R{l}.w", (s.width(l + 1), s.width(l), 3, 3)))
+        out.append((f"P{l}.w", (s.width(l + 1), s.width(l), 4, 4)))
+    out.append(("proj.w", (2 * s.M, s.width(0))))
+    return out
+
+
+def init_params(s: NetShape, seed: int = 0, proj_scale: float = 0.0):
+    """He-style normal weights, BN gamma = 1, beta = 0, head biases 0; the
+    projection starts at proj_scale (0: the network returns its input)."""
+    rng = np.random.default_rng(seed)
+    params = {}
+    for name, shape in param_shapes(s):
+        if name.endswith(".gamma"):
+            v = np.ones(shape)
+        elif name.endswith(".beta") or name.endswith(".b"):
+            v = np.zeros(shape)
+        else:
+            fan_in = int(np.prod(shape[1:])) if len(shape) > 1 else 1
+            if name.startswith("P"):
+                fan_in = shape[0] * 4          # transposed conv: inputs per output
+            v = rng.standard_normal(shape) * np.sqrt(2.0 / fan_in)
+            if name.startswith(("a", "ainv")):
+                v = v * 0.1
+            if name == "proj.w":
+                v = v * proj_scale
+        params[name] = v.astype(np.float64)
+    return params
