@@ -249,6 +249,64 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                              double* x_dev, rte_solve_info* info);
 
 /* ---------------------------------------------------------------------------
+ * MgNet preconditioner (Sec. 3): CoeffNet + MgNet V-cycle in face-flux space.
+ *
+ * Network: CoeffNet levels l = 0..levels-1 (conv 3x3, stride 2 after level 0,
+ * batch normalisation, ReLU; widths min(cc 2^l, ccmax)) on the per-cell
+ * inputs log sigma_T, log sigma_a, log eps, log tau, with 1x1 heads
+ * a_l = 1 + head, ainv_l = 1 + head of MgNet width min(c0 2^l, cmax);
+ * MgNet: lift 1x1 (2M -> c0), smoothing u <- u + (B_l * ReLU(f - (A_l * u) o a_l)) o ainv_l,
+ * restriction conv 3x3 stride 2, prolongation transposed conv 4x4 stride 2,
+ * one pre- and one post-smoothing step per level (two on the coarsest),
+ * projection 1x1 (c0 -> 2M) added to the input: psi_d = x + proj(u_0).
+ * Requirements: cc <= c0, ccmax <= cmax, I divisible by 2^(levels-1).
+ * Parameters are one float32 vector in this order, per level l:
+ * coef{l}.w [Cc_l][Cin][3][3], coef{l}.gamma, coef{l}.beta, a{l}.w [C_l][Cc_l],
+ * a{l}.b, ainv{l}.w, ainv{l}.b; then lift.w [C_0][2M]; A{l}.w, B{l}.w
+ * [C_l][C_l][3][3] for every l; R{l}.w [C_{l+1}][C_l][3][3] and P{l}.w
+ * [C_{l+1}][C_l][4][4] for l < levels-1; proj.w [2M][C_0].
+ * FP32 weights and activations.  A network and a context must share M.
+ * ------------------------------------------------------------------------- */
+typedef struct mgnet_config {
+    int M, levels, c0, cmax, cc, ccmax;
+} mgnet_config;
+
+RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** out);
+RTE_API void mgnet_destroy(mgnet* net);
+RTE_API int64_t mgnet_param_count(const mgnet* net);
+/* Host float32 [count] in the order above; set also resets the Adam state. */
+RTE_API rte_status mgnet_set_params(mgnet* net, const float* host, int64_t count);
+RTE_API rte_status mgnet_get_params(mgnet* net, float* host, int64_t count);
+
+/* z = rms(r) Net(r / rms(r)) in face-flux space (the preconditioner rte_solve
+ * applies before B = A D); r double [n], z float [n], device.  Asynchronous. */
+RTE_API rte_status mgnet_precond(mgnet* net, rte_ctx* ctx, const double* r_dev, float* z_dev);
+
+/* z = D rms(r) Net(r / rms(r)): the learned preconditioner mapped to the TFPS
+ * coefficients (D of Eq. loss); r, z double [n], device.  Asynchronous. */
+RTE_API rte_status mgnet_apply(mgnet* net, rte_ctx* ctx, const double* r_dev, double* z_dev);
+
+/* ---------------------------------------------------------------------------
+ * mgnet_train_step -- one Adam step (lr, beta 0.9/0.999, eps 1e-8) on the
+ * unfiltered physics-informed loss of Eq. loss for a batch of right-hand
+ * sides of one medium: mean_b ||x_b - A D psi_d,b|| / ||x_b||, x_b = r_b / rms(r_b).
+ * r_dev: host array of batch (1..16) device pointers, double [n] each.
+ * loss_out: the batch loss before the step.  Synchronous.
+ * mgnet_loss_grad: same loss and the gradient (host float32 [count], may be
+ * NULL) without updating the weights.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status mgnet_train_step(mgnet* net, rte_ctx* ctx, const double* const* r_dev, int batch,
+                                    double lr, double* loss_out);
+RTE_API rte_status mgnet_loss_grad(mgnet* net, rte_ctx* ctx, const double* const* r_dev, int batch,
+                                   double* loss_out, float* grad_host);
+
+/* Weights to / from a file: "MGNET001", six int32 (M, levels, c0, cmax, cc,
+ * ccmax), int64 count, count float32, uint32 word checksum.  Load checks the
+ * configuration and checksum (EINVAL on mismatch). */
+RTE_API rte_status mgnet_save(mgnet* net, const char* path);
+RTE_API rte_status mgnet_load(mgnet* net, const char* path);
+
+/* ---------------------------------------------------------------------------
  * Per-kernel accounting (no counterpart in the paper: instrumentation).
  * Every kernel launch of a context is counted with its algorithmic bytes (the
  * bytes its operation must move: inputs read once, outputs written once).

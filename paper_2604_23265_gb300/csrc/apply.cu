@@ -373,6 +373,18 @@ __global__ void k_rhs(int I, int M, const int* __restrict__ rowdir, const double
     }
 }
 
+// CoeffNet input channels per cell: log sigma_T, log sigma_a, log eps, log tau
+__global__ void k_coef_inputs(int N, double h, const double* __restrict__ sT,
+                              const double* __restrict__ sa, const double* __restrict__ eps,
+                              float* __restrict__ out) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        out[c] = (float)log(sT[c]);
+        out[N + c] = (float)log(sa[c]);
+        out[2 * N + c] = (float)log(eps[c]);
+        out[3 * N + c] = (float)log(sT[c] * h / eps[c]);
+    }
+}
+
 OpArgs op_args(rte_ctx* ctx) {
     return OpArgs{ctx->I, ctx->M, ctx->N, ctx->mat, ctx->tau, ctx->xi, ctx->rowinfo};
 }
@@ -466,6 +478,12 @@ void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi) {
     ProfScope ps(ctx, K_RECONSTRUCT, (double)ctx->n * 8 + (double)ctx->M * ctx->N * 8);
     kern<<<blocks, warps * 32, smem, ctx->stream>>>(op_args(ctx), ctx->Lt64, ctx->chis, x, psi);
     check(cudaGetLastError(), "k_reconstruct");
+}
+
+void launch_coef_inputs(rte_ctx* ctx, const double* sT, const double* sa, const double* eps) {
+    k_coef_inputs<<<(ctx->N + 255) / 256, 256, 0, ctx->stream>>>(ctx->N, 1.0 / ctx->I, sT, sa, eps,
+                                                                  ctx->coef_in);
+    check(cudaGetLastError(), "k_coef_inputs");
 }
 
 void launch_rhs(rte_ctx* ctx) {

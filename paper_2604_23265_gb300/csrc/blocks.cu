@@ -235,6 +235,72 @@ __global__ void k_gather(int I, int M, const TV* __restrict__ v, const TO* __res
     }
 }
 
+// q = P u: every row (f, j) of cell C takes the neighbour's row (opp f, j)
+// across f (zero on the boundary).  P is its own transpose.
+__global__ void k_permute(int I, int M, const float* __restrict__ u, float* __restrict__ q) {
+    const int N = I * I, M2 = M / 2;
+    const int64_t n = (int64_t)2 * M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(e / N);
+        const int c = (int)(e - (int64_t)row * N);
+        const int f = row / M2, j = row - f * M2;
+        const int iy = c / I, ix = c - iy * I;
+        int nb = -1;
+        if (f == 0 && ix > 0) nb = c - 1;
+        if (f == 1 && ix < I - 1) nb = c + 1;
+        if (f == 2 && iy > 0) nb = c - I;
+        if (f == 3 && iy < I - 1) nb = c + I;
+        q[e] = nb >= 0 ? u[(int64_t)((f ^ 1) * M2 + j) * N + nb] : 0.f;
+    }
+}
+
+// w = u - X_C^T q per cell with Xt[c][i][row] = X_C[row][i] (the transposed
+// response, used by the gradient of the loss): w_i = u_i - sum_row Xt[i][row] q_row.
+__global__ void __launch_bounds__(256) k_response_t(int M, int N, const float* __restrict__ Xt,
+                                                    const float* __restrict__ u,
+                                                    const float* __restrict__ q,
+                                                    float* __restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    float* qs = reinterpret_cast<float*>(smb);
+    const int n2 = 2 * M, G = n2 / 4;
+    const int cells = blockDim.x / G;
+    float* zs = qs + n2 * cells;
+    const int c0 = blockIdx.x * cells;
+    for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
+        const int j = e / cells, cc = e - j * cells;
+        const int c = c0 + cc;
+        qs[e] = (c < N) ? q[(size_t)j * N + c] : 0.f;
+    }
+    __syncthreads();
+    const int cc = threadIdx.x / G, g = threadIdx.x - cc * G;
+    const int c = c0 + cc;
+    if (cc < cells && c < N) {
+        const float* X = Xt + (size_t)c * n2 * n2;
+        for (int t = 0; t < 4; ++t) {
+            const int i = 4 * g + t;
+            const float4* row = reinterpret_cast<const float4*>(X + (size_t)i * n2);
+            float acc = 0.f;
+            for (int r4 = 0; r4 < G; ++r4) {
+                const float4 d = __ldg(row + r4);
+                acc = fmaf(d.x, qs[(4 * r4 + 0) * cells + cc], acc);
+                acc = fmaf(d.y, qs[(4 * r4 + 1) * cells + cc], acc);
+                acc = fmaf(d.z, qs[(4 * r4 + 2) * cells + cc], acc);
+                acc = fmaf(d.w, qs[(4 * r4 + 3) * cells + cc], acc);
+            }
+            zs[i * cells + cc] = acc;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
+        const int i = e / cells, c2 = e - i * cells;
+        if (c0 + c2 < N) {
+            const size_t idx = (size_t)i * N + c0 + c2;
+            w[idx] = u[idx] - zs[e];
+        }
+    }
+}
+
 // z_C = D_C^T r_C: output j = row j of Dt dotted with r (FP64 accumulation).
 template <typename TIN, typename TOUT>
 __global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const double* __restrict__ Dt,
@@ -350,6 +416,26 @@ void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_d
         throw StatusError{RTE_EINVAL, "transposed block apply needs matching precisions"};
     }
     check(cudaGetLastError(), "k_block_apply_t");
+}
+
+void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scratch) {
+    const int M = ctx->M, n2 = 2 * M, G = n2 / 4;
+    int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
+    const int g = (int)(want < cap ? want : cap);
+    {
+        ProfScope ps(ctx, K_GATHER, (double)ctx->n * 8);
+        k_permute<<<g, 256, 0, ctx->stream>>>(ctx->I, M, u, scratch);
+        check(cudaGetLastError(), "k_permute");
+    }
+    const int threads = G >= 256 ? G : (256 / G) * G;
+    const int cells = threads / G;
+    const int blocks = (ctx->N + cells - 1) / cells;
+    const size_t smem = sizeof(float) * 2 * n2 * cells;
+    check(cudaFuncSetAttribute(k_response_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+          "response_t smem");
+    ProfScope ps(ctx, K_RESPONSE_APPLY, (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * 12);
+    k_response_t<<<blocks, threads, smem, ctx->stream>>>(M, ctx->N, ctx->Rt, u, scratch, w);
+    check(cudaGetLastError(), "k_response_t");
 }
 
 void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* w,

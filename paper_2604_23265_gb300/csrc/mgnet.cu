@@ -1,14 +1,793 @@
-// MgNet preconditioner (Sec. 3).
+// MgNet preconditioner (Sec. 3): CoeffNet + MgNet V-cycle, the physics-informed
+// loss (Eq. loss), its gradient and Adam, all on the device.
+//
+// Network (readings of Sec. 3.2-3.3):
+//   CoeffNet, level l: z = conv3x3(g_{l-1}, stride 1 at l = 0 else 2),
+//     g_l = ReLU(BN(z)); a_l = 1 + head_a(g_l), ainv_l = 1 + head_ainv(g_l).
+//   MgNet: f_0 = lift(x); smoothing u <- u + (B_l * ReLU(f - (A_l * u) o a_l)) o ainv_l;
+//     restriction f_{l+1} = R_l *_{s2} (f_l - (A_l * u_l) o a_l);
+//     prolongation u_l <- u_l + P_l *^T u_{l+1}; one pre- and one
+//     post-smoothing step per level, two on the coarsest;
+//     psi_d = x + proj(u_0), x = r / rms(r), output rms(r) psi_d.
+// The network works in face-flux space; the Krylov operator there is
+// B = A D = I - P R (block-Jacobi preconditioned), so the loss of Eq. loss is
+// ||x - B psi_d|| / ||x||, and its gradient uses B^T = I - R^T P.
+// A batch is several right-hand sides of one medium: CoeffNet runs once and
+// its batch statistics are the medium's own, exactly as at inference.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <stdexcept>
+#include <string>
+
 #include "mgnet_internal.h"
+#include "nn_internal.h"
 
 namespace rte {
+namespace {
+using nn::ConvArgs;
+using nn::Taps;
+using nn::WgradArgs;
 
-void mgnet_prepare(mgnet*, rte_ctx*) {
-    throw StatusError{RTE_ENOTSUP, "MgNet preconditioner not built"};
+struct Param {
+    std::string name;
+    size_t off = 0, count = 0;
+};
+
+struct Features {            // CoeffNet outputs of one medium for one weight version
+    uint64_t version = ~0ull;
+    int I = 0;
+    void* block = nullptr;
+    std::vector<float*> zc, gc, mean, inv, a, ai;
+};
+
+}  // namespace
+}  // namespace rte
+
+struct mgnet {
+    int M = 0, L = 0, c0 = 0, cmax = 0, cc = 0, ccmax = 0, cin = 4;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<rte::Param> params;
+    std::map<std::string, size_t> off;
+    size_t np = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    int step = 0;
+    uint64_t version = 1;
+    // activations
+    int wsB = 0, wsI = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    std::map<uint64_t, rte::Features> feats;
+    // helpers for the per-sample scalars
+    double* d_scal = nullptr;
+    double* h_scal = nullptr;
+
+    int C(int l) const { int c = c0 << l; return c < cmax ? c : cmax; }
+    int Cc(int l) const { int c = cc << l; return c < ccmax ? c : ccmax; }
+};
+
+namespace rte {
+namespace {
+
+// ------------------------------------------------------------------ params
+void add_param(mgnet* n, const std::string& name, size_t count) {
+    n->params.push_back({name, n->np, count});
+    n->off[name] = n->np;
+    n->np += count;
 }
 
-void mgnet_precondition(mgnet*, rte_ctx*, const double*, float*) {
-    throw StatusError{RTE_ENOTSUP, "MgNet preconditioner not built"};
+void build_params(mgnet* n) {
+    const int L = n->L;
+    for (int l = 0; l < L; ++l) {
+        const int cin = l == 0 ? n->cin : n->Cc(l - 1);
+        add_param(n, "coef" + std::to_string(l) + ".w", (size_t)n->Cc(l) * cin * 9);
+        add_param(n, "coef" + std::to_string(l) + ".gamma", n->Cc(l));
+        add_param(n, "coef" + std::to_string(l) + ".beta", n->Cc(l));
+        add_param(n, "a" + std::to_string(l) + ".w", (size_t)n->C(l) * n->Cc(l));
+        add_param(n, "a" + std::to_string(l) + ".b", n->C(l));
+        add_param(n, "ainv" + std::to_string(l) + ".w", (size_t)n->C(l) * n->Cc(l));
+        add_param(n, "ainv" + std::to_string(l) + ".b", n->C(l));
+    }
+    add_param(n, "lift.w", (size_t)n->C(0) * 2 * n->M);
+    for (int l = 0; l < L; ++l) {
+        add_param(n, "A" + std::to_string(l) + ".w", (size_t)n->C(l) * n->C(l) * 9);
+        add_param(n, "B" + std::to_string(l) + ".w", (size_t)n->C(l) * n->C(l) * 9);
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        add_param(n, "R" + std::to_string(l) + ".w", (size_t)n->C(l + 1) * n->C(l) * 9);
+        add_param(n, "P" + std::to_string(l) + ".w", (size_t)n->C(l + 1) * n->C(l) * 16);
+    }
+    add_param(n, "proj.w", (size_t)2 * n->M * n->C(0));
+}
+
+float* P(mgnet* n, const std::string& name) { return n->p + n->off.at(name); }
+float* G(mgnet* n, const std::string& name) { return n->g + n->off.at(name); }
+std::string sl(const char* s, int l) { return std::string(s) + std::to_string(l) + ".w"; }
+
+// ------------------------------------------------------------------ arena
+struct Arena {
+    char* base;
+    size_t used = 0, cap;
+    float* f(size_t count) {
+        size_t bytes = (count * sizeof(float) + 255) & ~(size_t)255;
+        if (used + bytes > cap) throw StatusError{RTE_ENOMEM, "network workspace overflow"};
+        float* r = reinterpret_cast<float*>(base + used);
+        used += bytes;
+        return r;
+    }
+};
+
+// activation buffers of one forward/backward with batch B on an I x I grid
+struct Acts {
+    float *x, *psi;
+    std::vector<float*> f, upre, qpre, cdown, res, umid, cpost, tpost, qpost, uout;
+    float *q1, *u1, *c2, *t2, *q2, *u2;
+    // gradients
+    std::vector<float*> gf, gu, t1, t2b, t3;
+    float *gpsi, *gtmp;
+    float *wloss, *rloss, *scr;
+};
+
+size_t level_elems(mgnet* n, int B, int I, int l) { return (size_t)B * n->C(l) * (I >> l) * (I >> l); }
+
+Acts carve(mgnet* n, Arena& ar, int B, int I) {
+    Acts a{};
+    const size_t nin = (size_t)B * 2 * n->M * I * I;
+    a.x = ar.f(nin);
+    a.psi = ar.f(nin);
+    a.gpsi = ar.f(nin);
+    a.gtmp = ar.f(nin);
+    a.wloss = ar.f(nin);
+    a.rloss = ar.f(nin);
+    a.scr = ar.f(nin);
+    const int L = n->L;
+    for (int l = 0; l < L; ++l) {
+        const size_t e = level_elems(n, B, I, l);
+        a.f.push_back(ar.f(e));
+        a.upre.push_back(ar.f(e));
+        a.qpre.push_back(ar.f(e));
+        a.cdown.push_back(ar.f(e));
+        a.res.push_back(ar.f(e));
+        a.umid.push_back(ar.f(e));
+        a.cpost.push_back(ar.f(e));
+        a.tpost.push_back(ar.f(e));
+        a.qpost.push_back(ar.f(e));
+        a.uout.push_back(ar.f(e));
+        a.gf.push_back(ar.f(e));
+        a.gu.push_back(ar.f(e));
+        a.t1.push_back(ar.f(e));
+        a.t2b.push_back(ar.f(e));
+        a.t3.push_back(ar.f(e));
+    }
+    const size_t e = level_elems(n, B, I, L - 1);
+    a.q1 = ar.f(e);
+    a.u1 = ar.f(e);
+    a.c2 = ar.f(e);
+    a.t2 = ar.f(e);
+    a.q2 = ar.f(e);
+    a.u2 = ar.f(e);
+    return a;
+}
+
+size_t arena_bytes(mgnet* n, int B, int I) {
+    size_t total = 7 * ((size_t)B * 2 * n->M * I * I * 4 + 256);
+    for (int l = 0; l < n->L; ++l) total += 15 * (level_elems(n, B, I, l) * 4 + 256);
+    total += 6 * (level_elems(n, B, I, n->L - 1) * 4 + 256);
+    return total + 4096;
+}
+
+Acts workspace(mgnet* n, int B, int I) {
+    const size_t need = arena_bytes(n, B, I);
+    if (!n->ws || n->ws_bytes < need) {
+        if (n->ws) cudaFree(n->ws);
+        n->ws = nullptr;
+        check(cudaMalloc(&n->ws, need), "cudaMalloc (network workspace)");
+        n->ws_bytes = need;
+    }
+    Arena ar{static_cast<char*>(n->ws), 0, n->ws_bytes};
+    return carve(n, ar, B, I);
+}
+
+// ------------------------------------------------------------------ conv helpers
+ConvArgs cv(const float* x, int B, int Ci, int Hi, const float* w, int so, int si, int KK, int Co,
+            int Hg, int S, float* y, int Ho, const Taps& tp) {
+    ConvArgs a;
+    a.x = x; a.B = B; a.Ci = Ci; a.Hi = Hi; a.Wi = Hi;
+    a.w = w; a.so = so; a.si = si; a.KK = KK; a.Co = Co;
+    a.Hg = Hg; a.Wg = Hg; a.S = S;
+    a.y = y; a.Ho = Ho; a.Wo = Ho;
+    a.tp = tp;
+    return a;
+}
+
+WgradArgs wg(const float* g, int B, int Co, int Hg, const float* x, int Ci, int Hi, int S, float* dw,
+             int so, int si, int KK, const Taps& tp) {
+    WgradArgs a;
+    a.g = g; a.B = B; a.Co = Co; a.Hgo = Hg; a.Wgo = Hg; a.Hg = Hg; a.Wg = Hg;
+    a.x = x; a.Ci = Ci; a.Hi = Hi; a.Wi = Hi; a.S = S;
+    a.dw = dw; a.so = so; a.si = si; a.KK = KK;
+    a.tp = tp;
+    return a;
+}
+
+// backward data of a stride-1 kxk / 1x1 convolution with weight [Co][Ci]:
+// gin (Ci channels) (+)= conv(gout, flipped taps, swapped weight roles)
+void bwd_data_s1(mgnet* n, const float* gout, int B, int Co, int H, const float* w, int Ci, int k,
+                 float* gin, bool accumulate, const float* mask) {
+    ConvArgs a = cv(gout, B, Co, H, w, 1, Ci, k * k, Ci, H, 1, gin, H, nn::taps_conv_flipped(k, k / 2));
+    a.accumulate = accumulate;
+    a.mask = mask;
+    nn::conv(a, n->stream);
+}
+
+// ------------------------------------------------------------------ CoeffNet
+Features& features(mgnet* n, rte_ctx* ctx, bool force) {
+    Features& F = n->feats[ctx->uid];
+    const int I = ctx->I, L = n->L;
+    if (!force && F.version == n->version && F.I == I) return F;
+    if (!F.block || F.I != I) {
+        if (F.block) cudaFree(F.block);
+        F.block = nullptr;
+        size_t bytes = 0;
+        for (int l = 0; l < L; ++l) {
+            const size_t hw = (size_t)(I >> l) * (I >> l);
+            bytes += 2 * ((size_t)n->Cc(l) * hw * 4 + 256) + 2 * (n->Cc(l) * 4 + 256) +
+                     2 * ((size_t)n->C(l) * hw * 4 + 256);
+        }
+        check(cudaMalloc(&F.block, bytes), "cudaMalloc (CoeffNet features)");
+        Arena ar{static_cast<char*>(F.block), 0, bytes};
+        F.zc.clear(); F.gc.clear(); F.mean.clear(); F.inv.clear(); F.a.clear(); F.ai.clear();
+        for (int l = 0; l < L; ++l) {
+            const size_t hw = (size_t)(I >> l) * (I >> l);
+            F.zc.push_back(ar.f(n->Cc(l) * hw));
+            F.gc.push_back(ar.f(n->Cc(l) * hw));
+            F.mean.push_back(ar.f(n->Cc(l)));
+            F.inv.push_back(ar.f(n->Cc(l)));
+            F.a.push_back(ar.f(n->C(l) * hw));
+            F.ai.push_back(ar.f(n->C(l) * hw));
+        }
+        F.I = I;
+    }
+    const float* in = ctx->coef_in;
+    int cin = n->cin, Hin = I;
+    for (int l = 0; l < L; ++l) {
+        const int H = I >> l, S = l == 0 ? 1 : 2;
+        nn::conv(cv(in, 1, cin, Hin, P(n, "coef" + std::to_string(l) + ".w"), cin, 1, 9, n->Cc(l), H,
+                    S, F.zc[l], H, nn::taps_conv(3, 1)), n->stream);
+        nn::bn_stats(F.zc[l], 1, n->Cc(l), H * H, F.mean[l], F.inv[l], n->stream);
+        nn::bn_relu(F.zc[l], 1, n->Cc(l), H * H, F.mean[l], F.inv[l],
+                    P(n, "coef" + std::to_string(l) + ".gamma"), P(n, "coef" + std::to_string(l) + ".beta"),
+                    F.gc[l], n->stream);
+        for (int h = 0; h < 2; ++h) {
+            const std::string nm = (h == 0 ? "a" : "ainv") + std::to_string(l);
+            ConvArgs a = cv(F.gc[l], 1, n->Cc(l), H, P(n, nm + ".w"), n->Cc(l), 1, 1, n->C(l), H, 1,
+                            h == 0 ? F.a[l] : F.ai[l], H, nn::taps_conv(1, 0));
+            a.bias = P(n, nm + ".b");
+            a.cst = 1.f;
+            nn::conv(a, n->stream);
+        }
+        in = F.gc[l];
+        cin = n->Cc(l);
+        Hin = H;
+    }
+    F.version = n->version;
+    return F;
+}
+
+// ------------------------------------------------------------------ forward
+// x must already hold the normalised inputs [B][2M][I][I]; writes a.psi.
+void forward(mgnet* n, const Features& F, Acts& a, int B, int I) {
+    const int L = n->L, M2 = 2 * n->M;
+    const Taps t3 = nn::taps_conv(3, 1), t1 = nn::taps_conv(1, 0);
+    nn::conv(cv(a.x, B, M2, I, P(n, "lift.w"), M2, 1, 1, n->C(0), I, 1, a.f[0], I, t1), n->stream);
+    auto smooth_first = [&](int l, float* q, float* u) {     // u = (B * ReLU(f)) o ainv
+        const int H = I >> l, C = n->C(l);
+        ConvArgs c = cv(a.f[l], B, C, H, P(n, sl("B", l)), C, 1, 9, C, H, 1, u, H, t3);
+        c.relu_in = 1; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1;
+        nn::conv(c, n->stream);
+    };
+    auto residual = [&](int l, const float* u, float* craw, float* out) {   // f - (A * u) o a
+        const int H = I >> l, C = n->C(l);
+        ConvArgs c = cv(u, B, C, H, P(n, sl("A", l)), C, 1, 9, C, H, 1, out, H, t3);
+        c.raw = craw; c.gate = F.a[l]; c.gate_bcast = 1; c.sign = -1.f; c.base = a.f[l];
+        nn::conv(c, n->stream);
+    };
+    auto smooth_update = [&](int l, const float* t, float* q, const float* u, float* out) {
+        const int H = I >> l, C = n->C(l);
+        ConvArgs c = cv(t, B, C, H, P(n, sl("B", l)), C, 1, 9, C, H, 1, out, H, t3);
+        c.relu_in = 1; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1; c.base = u;
+        nn::conv(c, n->stream);
+    };
+    for (int l = 0; l + 1 < L; ++l) {
+        const int H = I >> l;
+        smooth_first(l, a.qpre[l], a.upre[l]);
+        residual(l, a.upre[l], a.cdown[l], a.res[l]);
+        nn::conv(cv(a.res[l], B, n->C(l), H, P(n, sl("R", l)), n->C(l), 1, 9, n->C(l + 1), H / 2, 2,
+                    a.f[l + 1], H / 2, t3), n->stream);
+    }
+    smooth_first(L - 1, a.q1, a.u1);
+    residual(L - 1, a.u1, a.c2, a.t2);
+    smooth_update(L - 1, a.t2, a.q2, a.u1, a.u2);
+    float* uup = a.u2;
+    for (int l = L - 2; l >= 0; --l) {
+        const int H = I >> l;
+        const size_t e = level_elems(n, B, I, l);
+        check(cudaMemcpyAsync(a.umid[l], a.upre[l], e * 4, cudaMemcpyDeviceToDevice, n->stream), "copy");
+        for (int py = 0; py < 2; ++py)
+            for (int px = 0; px < 2; ++px) {
+                ConvArgs c = cv(uup, B, n->C(l + 1), H / 2, P(n, sl("P", l)), 1, n->C(l), 16, n->C(l),
+                                H / 2, 1, a.umid[l], H, nn::taps_parity(4, py, px));
+                c.OS = 2; c.OY0 = py; c.OX0 = px; c.accumulate = 1;
+                nn::conv(c, n->stream);
+            }
+        residual(l, a.umid[l], a.cpost[l], a.tpost[l]);
+        smooth_update(l, a.tpost[l], a.qpost[l], a.umid[l], a.uout[l]);
+        uup = a.uout[l];
+    }
+    ConvArgs c = cv(uup, B, n->C(0), I, P(n, "proj.w"), n->C(0), 1, 1, M2, I, 1, a.psi, I, t1);
+    c.base = a.x;
+    nn::conv(c, n->stream);
+}
+
+// ------------------------------------------------------------------ backward
+// Given a.gpsi (dLoss/dpsi), accumulate every parameter gradient into n->g.
+void backward(mgnet* n, Features& F, Acts& a, rte_ctx* ctx, int B, int I) {
+    const int L = n->L, M2 = 2 * n->M;
+    const Taps t3 = nn::taps_conv(3, 1), t1 = nn::taps_conv(1, 0), t4 = nn::taps_conv(4, 1);
+    cudaStream_t st = n->stream;
+    std::vector<float*> ga(L), gai(L);
+    // gate gradients per level live in the t3 scratch of the level (size >= C H^2)
+    for (int l = 0; l < L; ++l) {
+        const size_t e = level_elems(n, B, I, l);
+        check(cudaMemsetAsync(a.gf[l], 0, e * 4, st), "memset");
+        ga[l] = a.t3[l];
+        gai[l] = a.t3[l] + (size_t)n->C(l) * (I >> l) * (I >> l);
+        check(cudaMemsetAsync(ga[l], 0, (size_t)2 * n->C(l) * (I >> l) * (I >> l) * 4, st), "memset");
+    }
+    (void)ctx;
+    // psi = x + proj * u_out0
+    const float* u0 = L > 1 ? a.uout[0] : a.u2;
+    nn::wgrad(wg(a.gpsi, B, M2, I, u0, n->C(0), I, 1, G(n, "proj.w"), n->C(0), 1, 1, t1), st);
+    float* gu_up = a.gu[0];      // gradient of the current level's output u
+    {
+        ConvArgs c = cv(a.gpsi, B, M2, I, P(n, "proj.w"), 1, n->C(0), 1, n->C(0), I, 1, gu_up, I, t1);
+        nn::conv(c, st);
+    }
+    // smoothing-step backward: u_out = u_in + (B * ReLU(t)) o ai ; t = f - (A * u_in) o a
+    // gu: gradient of u_out on entry, of u_in on exit (in place); t stored, q raw stored
+    auto smooth_bwd = [&](int l, float* gu, const float* t, const float* q, const float* c,
+                          const float* u_in, bool has_A) {
+        const int H = I >> l, C = n->C(l);
+        const size_t chw = (size_t)C * H * H;
+        float* gq = a.t1[l];
+        float* gt = a.t2b[l];
+        nn::gate_bwd(gu, F.ai[l], q, 1.f, B, chw, gq, gai[l], st);
+        // gt = bwd_data(B_l, gq) masked by t > 0 ; dB += wgrad(gq, ReLU(t))
+        bwd_data_s1(n, gq, B, C, H, P(n, sl("B", l)), C, 3, gt, false, t);
+        {
+            WgradArgs w = wg(gq, B, C, H, t, C, H, 1, G(n, sl("B", l)), C, 1, 9, t3);
+            w.relu_in = 1;
+            nn::wgrad(w, st);
+        }
+        nn::axpy(a.gf[l], gt, 1.f, (size_t)B * chw, st);
+        if (!has_A) return;
+        // t = f - c o a: gc = -gt o a ; ga += -gt o c
+        float* gc = a.t1[l];
+        nn::gate_bwd(gt, F.a[l], c, -1.f, B, chw, gc, ga[l], st);
+        bwd_data_s1(n, gc, B, C, H, P(n, sl("A", l)), C, 3, gu, true, nullptr);
+        nn::wgrad(wg(gc, B, C, H, u_in, C, H, 1, G(n, sl("A", l)), C, 1, 9, t3), st);
+    };
+    // up path, reversed: levels 0 .. L-2
+    for (int l = 0; l + 1 < L; ++l) {
+        const int H = I >> l, C = n->C(l), Cn = n->C(l + 1);
+        // post-smoothing at level l (input umid, t = tpost, q = qpost, c = cpost)
+        smooth_bwd(l, gu_up, a.tpost[l], a.qpost[l], a.cpost[l], a.umid[l], true);
+        // umid = upre + P^T-conv(u_{l+1}): g_upre = g_umid (kept in gu[l]);
+        // g_u_{l+1} = conv4x4 s2 of g_umid with P ; dP += wgrad
+        float* gnext = a.gu[l + 1];
+        const float* ucoarse = (l + 1 == L - 1) ? a.u2 : a.uout[l + 1];
+        nn::conv(cv(gu_up, B, C, H, P(n, sl("P", l)), C, 1, 16, Cn, H / 2, 2, gnext, H / 2, t4), st);
+        nn::wgrad(wg(ucoarse, B, Cn, H / 2, gu_up, C, H, 2, G(n, sl("P", l)), C, 1, 16, t4), st);
+        gu_up = gnext;
+    }
+    // coarsest: u2 = u1 + (B * ReLU(t2)) o ai ; t2 = f - (A * u1) o a ; u1 = (B * ReLU(f)) o ai
+    {
+        const int l = L - 1;
+        smooth_bwd(l, gu_up, a.t2, a.q2, a.c2, a.u1, true);
+        smooth_bwd(l, gu_up, a.f[l], a.q1, nullptr, nullptr, false);
+    }
+    // down path, reversed: levels L-2 .. 0; a.gu[l] holds g_umid == g_upre
+    for (int l = L - 2; l >= 0; --l) {
+        const int H = I >> l, C = n->C(l), Cn = n->C(l + 1);
+        // restriction f_{l+1} = R *s2 res: g_res = bwd data (parity classes) ; dR += wgrad
+        float* gres = a.t2b[l];
+        for (int py = 0; py < 2; ++py)
+            for (int px = 0; px < 2; ++px) {
+                ConvArgs c = cv(a.gf[l + 1], B, Cn, H / 2, P(n, sl("R", l)), 1, C, 9, C, H / 2, 1, gres, H,
+                                nn::taps_parity(3, py, px));
+                c.OS = 2; c.OY0 = py; c.OX0 = px;
+                nn::conv(c, st);
+            }
+        nn::wgrad(wg(a.gf[l + 1], B, Cn, H / 2, a.res[l], C, H, 2, G(n, sl("R", l)), C, 1, 9, t3), st);
+        // res = f - (A * upre) o a
+        const size_t chw = (size_t)C * H * H;
+        nn::axpy(a.gf[l], gres, 1.f, (size_t)B * chw, st);
+        float* gc = a.t1[l];
+        nn::gate_bwd(gres, F.a[l], a.cdown[l], -1.f, B, chw, gc, ga[l], st);
+        bwd_data_s1(n, gc, B, C, H, P(n, sl("A", l)), C, 3, a.gu[l], true, nullptr);
+        nn::wgrad(wg(gc, B, C, H, a.upre[l], C, H, 1, G(n, sl("A", l)), C, 1, 9, t3), st);
+        // upre = (B * ReLU(f)) o ai
+        smooth_bwd(l, a.gu[l], a.f[l], a.qpre[l], nullptr, nullptr, false);
+    }
+    // lift: f0 = lift * x
+    nn::wgrad(wg(a.gf[0], B, n->C(0), I, a.x, M2, I, 1, G(n, "lift.w"), M2, 1, 1, t1), st);
+    // CoeffNet: heads, then BN-ReLU and convolutions from the top level down
+    std::vector<float*> ggc(L);
+    for (int l = 0; l < L; ++l) {
+        const int H = I >> l;
+        ggc[l] = a.t2b[l];          // scratch of size >= Cc H^2 (batch 1)
+        check(cudaMemsetAsync(ggc[l], 0, (size_t)n->Cc(l) * H * H * 4, st), "memset");
+        for (int h = 0; h < 2; ++h) {
+            const std::string nm = (h == 0 ? "a" : "ainv") + std::to_string(l);
+            const float* gg = h == 0 ? ga[l] : gai[l];
+            ConvArgs c = cv(gg, 1, n->C(l), H, P(n, nm + ".w"), 1, n->Cc(l), 1, n->Cc(l), H, 1, ggc[l], H, t1);
+            c.accumulate = 1;
+            nn::conv(c, st);
+            nn::wgrad(wg(gg, 1, n->C(l), H, F.gc[l], n->Cc(l), H, 1, G(n, nm + ".w"), n->Cc(l), 1, 1, t1), st);
+            nn::channel_sum(gg, 1, n->C(l), H * H, G(n, nm + ".b"), st);
+        }
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const int H = I >> l;
+        float* gz = a.t1[l];
+        nn::bn_relu_bwd(F.zc[l], F.gc[l], ggc[l], 1, n->Cc(l), H * H, F.mean[l], F.inv[l],
+                        P(n, "coef" + std::to_string(l) + ".gamma"),
+                        G(n, "coef" + std::to_string(l) + ".gamma"),
+                        G(n, "coef" + std::to_string(l) + ".beta"), gz, st);
+        const float* xin = l == 0 ? ctx->coef_in : F.gc[l - 1];
+        const int cin = l == 0 ? n->cin : n->Cc(l - 1);
+        const int Hin = l == 0 ? I : (I >> (l - 1));
+        const int S = l == 0 ? 1 : 2;
+        nn::wgrad(wg(gz, 1, n->Cc(l), H, xin, cin, Hin, S, G(n, "coef" + std::to_string(l) + ".w"), cin, 1, 9, t3), st);
+        if (l > 0) {
+            for (int py = 0; py < 2; ++py)
+                for (int px = 0; px < 2; ++px) {
+                    ConvArgs c = cv(gz, 1, n->Cc(l), H, P(n, "coef" + std::to_string(l) + ".w"), 1, cin, 9, cin,
+                                    H, 1, ggc[l - 1], Hin, nn::taps_parity(3, py, px));
+                    c.OS = 2; c.OY0 = py; c.OX0 = px; c.accumulate = 1;
+                    nn::conv(c, st);
+                }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ glue kernels
+// x[b] = r_b * sqrt(n) / ||r_b|| as float (norms in scal[b])
+__global__ void k_normalise_in(const double* __restrict__ r, int64_t n, const double* __restrict__ nrm,
+                               float* __restrict__ x) {
+    const double s = nrm[0] > 0.0 ? sqrt((double)n) / nrm[0] : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (float)(r[i] * s);
+}
+
+__global__ void k_scale_out(const float* __restrict__ psi, int64_t n, const double* __restrict__ nrm,
+                            float* __restrict__ z) {
+    const float s = (float)(nrm[0] / sqrt((double)n));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = psi[i] * s;
+}
+
+// out[0] += sum a^2, out[1] += sum b^2 (float inputs, double sums)
+__global__ void k_norms2(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                         double* __restrict__ out) {
+    __shared__ double ra[32], rb[32];
+    double sa = 0.0, sb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        sa += (double)a[i] * a[i];
+        sb += (double)b[i] * b[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = sa; rb[threadIdx.x >> 5] = sb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += ra[w]; tb += rb[w]; }
+        atomicAdd(out, ta);
+        atomicAdd(out + 1, tb);
+    }
+}
+
+__global__ void k_sub_f(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                        float* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+__global__ void k_double_norm(const double* __restrict__ r, int64_t n, double* __restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += r[i] * r[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(out, t);
+    }
+}
+
+__global__ void k_sqrt_inplace(double* v, int count) {
+    if (threadIdx.x < count) v[threadIdx.x] = sqrt(v[threadIdx.x]);
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (int)(b < 2048 ? (b > 0 ? b : 1) : 2048);
+}
+
+void check_ctx(mgnet* n, rte_ctx* ctx) {
+    if (ctx->M != n->M) throw StatusError{RTE_EINVAL, "network and context have different M"};
+    if (ctx->I % (1 << (n->L - 1)) != 0 || (ctx->I >> (n->L - 1)) < 1)
+        throw StatusError{RTE_EINVAL, "I must be divisible by 2^(levels-1)"};
+    if (ctx->stream != n->stream) n->stream = ctx->stream;
+}
+
+// normalise a batch of FP64 right-hand sides into a.x; norms into n->d_scal[b]
+void load_inputs(mgnet* n, rte_ctx* ctx, const double* const* r, int B, Acts& a) {
+    const int64_t len = ctx->n;
+    check(cudaMemsetAsync(n->d_scal, 0, 64 * sizeof(double), n->stream), "memset");
+    for (int b = 0; b < B; ++b) {
+        k_double_norm<<<grid_for(len), 256, 0, n->stream>>>(r[b], len, n->d_scal + b);
+    }
+    k_sqrt_inplace<<<1, 64, 0, n->stream>>>(n->d_scal, B);
+    for (int b = 0; b < B; ++b)
+        k_normalise_in<<<grid_for(len), 256, 0, n->stream>>>(r[b], len, n->d_scal + b, a.x + (size_t)b * len);
+    check(cudaGetLastError(), "load_inputs");
+}
+
+// loss = mean_b ||x_b - B psi_b|| / ||x_b|| ; a.gpsi = its gradient
+double loss_and_seed(mgnet* n, rte_ctx* ctx, Acts& a, int B) {
+    const int64_t len = ctx->n;
+    double* sums = n->d_scal + 32;
+    check(cudaMemsetAsync(sums, 0, 2 * B * sizeof(double), n->stream), "memset");
+    for (int b = 0; b < B; ++b) {
+        const float* psi = a.psi + (size_t)b * len;
+        const float* x = a.x + (size_t)b * len;
+        launch_response_apply(ctx, psi, false, a.wloss, false);            // B psi
+        k_sub_f<<<grid_for(len), 256, 0, n->stream>>>(x, a.wloss, len, a.rloss + 0);
+        k_norms2<<<grid_for(len), 256, 0, n->stream>>>(a.rloss, x, len, sums + 2 * b);
+        launch_response_apply_t(ctx, a.rloss, a.gpsi + (size_t)b * len, a.scr);   // B^T res
+    }
+    check(cudaMemcpyAsync(n->h_scal, sums, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, n->stream), "d2h");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    double loss = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double nr = std::sqrt(n->h_scal[2 * b]), nx = std::sqrt(n->h_scal[2 * b + 1]);
+        loss += nr / nx / B;
+        const float scale = (float)(nr > 0 ? -1.0 / (nr * nx * B) : 0.0);
+        nn::scale_copy(a.gpsi + (size_t)b * len, a.gpsi + (size_t)b * len, scale, len, n->stream);
+    }
+    return loss;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ solver hooks
+void mgnet_prepare(mgnet* net, rte_ctx* ctx) {
+    check_ctx(net, ctx);
+    features(net, ctx, false);
+}
+
+void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
+    check_ctx(net, ctx);
+    ProfScope ps(ctx, K_MGNET, 0.0, 0);
+    Features& F = features(net, ctx, false);
+    Acts a = workspace(net, 2, ctx->I);
+    const double* rv[1] = {v};
+    load_inputs(net, ctx, rv, 1, a);
+    forward(net, F, a, 1, ctx->I);
+    k_scale_out<<<grid_for(ctx->n), 256, 0, net->stream>>>(a.psi, ctx->n, net->d_scal, z);
+    check(cudaGetLastError(), "k_scale_out");
 }
 
 }  // namespace rte
+
+using namespace rte;
+
+#define MG_GUARD_BEGIN try {
+#define MG_GUARD_END(net)                                                                        \
+    }                                                                                            \
+    catch (const CudaError& e) { rte_status s = cuda_status(nullptr, e.code, e.where); if (net) net->err = rte_last_error(nullptr); return s; } \
+    catch (const StatusError& e) { set_error(nullptr, e.msg); if (net) net->err = e.msg; return e.code; } \
+    catch (const std::bad_alloc&) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; } \
+    catch (const std::out_of_range&) { set_error(nullptr, "unknown parameter"); return RTE_EINVAL; }
+
+extern "C" {
+
+RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** out) {
+    if (!cfg || !out) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    *out = nullptr;
+    if (cfg->M < 4 || cfg->M % 4 || cfg->levels < 1 || cfg->levels > 8 || cfg->c0 < 1 || cfg->cmax < cfg->c0 ||
+        cfg->cc < 1 || cfg->ccmax < cfg->cc || cfg->cc > cfg->c0 || cfg->ccmax > cfg->cmax) {
+        set_error(nullptr, "bad network configuration (need cc <= c0, ccmax <= cmax)");
+        return RTE_EINVAL;
+    }
+    mgnet* n = new (std::nothrow) mgnet();
+    if (!n) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; }
+    n->M = cfg->M; n->L = cfg->levels; n->c0 = cfg->c0; n->cmax = cfg->cmax;
+    n->cc = cfg->cc; n->ccmax = cfg->ccmax;
+    n->stream = static_cast<cudaStream_t>(stream);
+    MG_GUARD_BEGIN
+    build_params(n);
+    check(cudaMalloc(&n->p, n->np * 4 * 4), "cudaMalloc (parameters)");
+    n->g = n->p + n->np;
+    n->m = n->g + n->np;
+    n->v = n->m + n->np;
+    check(cudaMemsetAsync(n->p, 0, n->np * 16, n->stream), "memset");
+    check(cudaMalloc(&n->d_scal, 128 * sizeof(double)), "cudaMalloc");
+    check(cudaMallocHost(&n->h_scal, 128 * sizeof(double)), "cudaMallocHost");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    *out = n;
+    return RTE_OK;
+    }
+    catch (...) {
+        mgnet_destroy(n);
+        set_error(nullptr, "mgnet_create failed");
+        return RTE_ENOMEM;
+    }
+}
+
+RTE_API void mgnet_destroy(mgnet* n) {
+    if (!n) return;
+    cudaStreamSynchronize(n->stream);
+    for (auto& kv : n->feats)
+        if (kv.second.block) cudaFree(kv.second.block);
+    if (n->ws) cudaFree(n->ws);
+    if (n->p) cudaFree(n->p);
+    if (n->d_scal) cudaFree(n->d_scal);
+    if (n->h_scal) cudaFreeHost(n->h_scal);
+    delete n;
+}
+
+RTE_API int64_t mgnet_param_count(const mgnet* n) { return n ? (int64_t)n->np : -1; }
+
+RTE_API rte_status mgnet_set_params(mgnet* n, const float* host, int64_t count) {
+    if (!n || !host || count != (int64_t)n->np) { set_error(nullptr, "bad argument"); return RTE_EINVAL; }
+    MG_GUARD_BEGIN
+    check(cudaMemcpyAsync(n->p, host, n->np * 4, cudaMemcpyHostToDevice, n->stream), "h2d");
+    check(cudaMemsetAsync(n->m, 0, n->np * 8, n->stream), "memset");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    n->step = 0;
+    ++n->version;
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+RTE_API rte_status mgnet_get_params(mgnet* n, float* host, int64_t count) {
+    if (!n || !host || count != (int64_t)n->np) { set_error(nullptr, "bad argument"); return RTE_EINVAL; }
+    MG_GUARD_BEGIN
+    check(cudaMemcpyAsync(host, n->p, n->np * 4, cudaMemcpyDeviceToHost, n->stream), "d2h");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+RTE_API rte_status mgnet_precond(mgnet* n, rte_ctx* ctx, const double* r_dev, float* z_dev) {
+    if (!n || !ctx || !r_dev || !z_dev) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    MG_GUARD_BEGIN
+    mgnet_precondition(n, ctx, r_dev, z_dev);
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+RTE_API rte_status mgnet_apply(mgnet* n, rte_ctx* ctx, const double* r_dev, double* z_dev) {
+    if (!n || !ctx || !r_dev || !z_dev) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    MG_GUARD_BEGIN
+    Acts a = workspace(n, 2, ctx->I);
+    mgnet_precondition(n, ctx, r_dev, a.gtmp);
+    launch_block_apply(ctx, false, a.gtmp, false, z_dev, true);
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+static rte_status loss_grad_impl(mgnet* n, rte_ctx* ctx, const double* const* r_dev, int batch,
+                                 double* loss_out) {
+    if (!n || !ctx || !r_dev || batch < 1 || batch > 16) {
+        set_error(nullptr, "bad argument (batch in [1, 16])");
+        return RTE_EINVAL;
+    }
+    MG_GUARD_BEGIN
+    check_ctx(n, ctx);
+    for (int b = 0; b < batch; ++b)
+        if (!r_dev[b]) throw StatusError{RTE_EINVAL, "NULL sample"};
+    Features& F = features(n, ctx, true);
+    const int Bw = batch < 2 ? 2 : batch;
+    Acts a = workspace(n, Bw, ctx->I);
+    load_inputs(n, ctx, r_dev, batch, a);
+    forward(n, F, a, batch, ctx->I);
+    const double loss = loss_and_seed(n, ctx, a, batch);
+    check(cudaMemsetAsync(n->g, 0, n->np * 4, n->stream), "memset");
+    backward(n, F, a, ctx, batch, ctx->I);
+    if (loss_out) *loss_out = loss;
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+RTE_API rte_status mgnet_loss_grad(mgnet* n, rte_ctx* ctx, const double* const* r_dev, int batch,
+                                   double* loss_out, float* grad_host) {
+    rte_status st = loss_grad_impl(n, ctx, r_dev, batch, loss_out);
+    if (st != RTE_OK || !grad_host) return st;
+    MG_GUARD_BEGIN
+    check(cudaMemcpyAsync(grad_host, n->g, n->np * 4, cudaMemcpyDeviceToHost, n->stream), "d2h");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+RTE_API rte_status mgnet_train_step(mgnet* n, rte_ctx* ctx, const double* const* r_dev, int batch,
+                                    double lr, double* loss_out) {
+    rte_status st = loss_grad_impl(n, ctx, r_dev, batch, loss_out);
+    if (st != RTE_OK) return st;
+    MG_GUARD_BEGIN
+    ++n->step;
+    nn::adam(n->p, n->g, n->m, n->v, n->np, (float)lr, n->step, n->stream);
+    ++n->version;
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+// File format: "MGNET001", int32 M, levels, c0, cmax, cc, ccmax, int64 count,
+// count float32 parameters, uint32 checksum (sum of the 32-bit words).
+RTE_API rte_status mgnet_save(mgnet* n, const char* path) {
+    if (!n || !path) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    MG_GUARD_BEGIN
+    std::vector<float> h(n->np);
+    check(cudaMemcpyAsync(h.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost, n->stream), "d2h");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) throw StatusError{RTE_EINVAL, "cannot open file for writing"};
+    const int32_t hdr[6] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax};
+    const int64_t cnt = (int64_t)n->np;
+    uint32_t sum = 0;
+    for (size_t i = 0; i < n->np; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
+    bool ok = std::fwrite("MGNET001", 1, 8, f) == 8 && std::fwrite(hdr, 4, 6, f) == 6 &&
+              std::fwrite(&cnt, 8, 1, f) == 1 && std::fwrite(h.data(), 4, n->np, f) == n->np &&
+              std::fwrite(&sum, 4, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) throw StatusError{RTE_EINVAL, "write failed"};
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
+RTE_API rte_status mgnet_load(mgnet* n, const char* path) {
+    if (!n || !path) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    MG_GUARD_BEGIN
+    FILE* f = std::fopen(path, "rb");
+    if (!f) throw StatusError{RTE_EINVAL, "cannot open file"};
+    char magic[8];
+    int32_t hdr[6];
+    int64_t cnt = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MGNET001", 8) == 0 &&
+              std::fread(hdr, 4, 6, f) == 6 && std::fread(&cnt, 8, 1, f) == 1;
+    const int32_t want[6] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax};
+    ok = ok && std::memcmp(hdr, want, sizeof(want)) == 0 && cnt == (int64_t)n->np;
+    std::vector<float> h(ok ? n->np : 0);
+    uint32_t sum = 0, stored = 0;
+    ok = ok && std::fread(h.data(), 4, n->np, f) == n->np && std::fread(&stored, 4, 1, f) == 1;
+    std::fclose(f);
+    if (ok)
+        for (size_t i = 0; i < n->np; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
+    if (!ok || sum != stored) throw StatusError{RTE_EINVAL, "not a matching MGNET001 file or bad checksum"};
+    return mgnet_set_params(n, h.data(), cnt);
+    MG_GUARD_END(n)
+}
+
+}  // extern "C"

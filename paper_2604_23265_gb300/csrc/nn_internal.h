@@ -1,0 +1,88 @@
+// Internal interface of the network kernels (nn_kernels.cu).
+#pragma once
+
+#include "rte_internal.h"
+
+namespace rte {
+namespace nn {
+
+constexpr int kMaxTaps = 16;
+
+// Taps of a gather convolution: input pixel (S gy + dy[t], S gx + dx[t]),
+// weight offset wi[t] inside the kernel window.
+struct Taps {
+    int T = 0;
+    int dy[kMaxTaps] = {};
+    int dx[kMaxTaps] = {};
+    int wi[kMaxTaps] = {};
+    int dymin = 0, dymax = 0, dxmin = 0, dxmax = 0;
+    void finish() {
+        dymin = dxmin = 1 << 20;
+        dymax = dxmax = -(1 << 20);
+        for (int t = 0; t < T; ++t) {
+            dymin = dy[t] < dymin ? dy[t] : dymin;
+            dymax = dy[t] > dymax ? dy[t] : dymax;
+            dxmin = dx[t] < dxmin ? dx[t] : dxmin;
+            dxmax = dx[t] > dxmax ? dx[t] : dxmax;
+        }
+    }
+};
+
+struct ConvArgs {
+    const float* x = nullptr;        // [B][Ci][Hi][Wi]
+    int B = 1, Ci = 0, Hi = 0, Wi = 0;
+    const float* w = nullptr;        // w[(o so + i si) KK + wi]
+    int so = 0, si = 0, KK = 1;
+    int Co = 0;
+    int Hg = 0, Wg = 0, S = 1;       // class grid and input stride
+    int OS = 1, OY0 = 0, OX0 = 0;    // output placement
+    float* y = nullptr;              // [B][Co][Ho][Wo]
+    int Ho = 0, Wo = 0;
+    const float* bias = nullptr;     // per output channel
+    float cst = 0.f;
+    float* raw = nullptr;            // stores acc (+bias +cst) before gating
+    const float* gate = nullptr;     // [B][Co][Ho][Wo], or [Co][Ho][Wo] if gate_bcast
+    int gate_bcast = 0;
+    const float* mask = nullptr;     // keep where mask > 0
+    float sign = 1.f;
+    const float* base = nullptr;     // added after sign
+    int accumulate = 0;              // y += ...
+    int relu_in = 0;                 // ReLU applied to x on load
+    Taps tp;
+};
+
+struct WgradArgs {
+    const float* g = nullptr;        // [B][Co][Hgo][Wgo] (gradient of the output)
+    int B = 1, Co = 0, Hgo = 0, Wgo = 0;
+    int Hg = 0, Wg = 0, OS = 1, OY0 = 0, OX0 = 0;
+    const float* x = nullptr;        // [B][Ci][Hi][Wi]
+    int Ci = 0, Hi = 0, Wi = 0, S = 1;
+    int relu_in = 0;
+    float* dw = nullptr;             // accumulated: dw[(o so + i si) KK + wi]
+    int so = 0, si = 0, KK = 1;
+    Taps tp;
+};
+
+void conv(const ConvArgs& a, cudaStream_t st);
+void wgrad(const WgradArgs& a, cudaStream_t st);
+void bn_stats(const float* x, int B, int C, int HW, float* mean, float* invstd, cudaStream_t st);
+void bn_relu(const float* x, int B, int C, int HW, const float* mean, const float* invstd,
+             const float* gamma, const float* beta, float* y, cudaStream_t st);
+void bn_relu_bwd(const float* x, const float* y, const float* g, int B, int C, int HW,
+                 const float* mean, const float* invstd, const float* gamma, float* dgamma,
+                 float* dbeta, float* dx, cudaStream_t st);
+// out[b] = sign g[b] gate ; dgate += sum_b sign g[b] raw[b]   (gate shared by the B samples)
+void gate_bwd(const float* g, const float* gate, const float* raw, float sign, int B, size_t chw,
+              float* out, float* dgate, cudaStream_t st);
+// y = x (+)= ...: small helpers
+void scale_copy(float* y, const float* x, float alpha, size_t n, cudaStream_t st);
+void axpy(float* y, const float* x, float alpha, size_t n, cudaStream_t st);
+void channel_sum(const float* g, int B, int C, int HW, float* out, cudaStream_t st);
+void adam(float* p, const float* g, float* m, float* v, size_t n, float lr, int step, cudaStream_t st);
+
+Taps taps_conv(int k, int pad);
+Taps taps_conv_flipped(int k, int pad);
+Taps taps_parity(int k, int py, int px);
+
+}  // namespace nn
+}  // namespace rte

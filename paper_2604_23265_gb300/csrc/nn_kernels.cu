@@ -1,0 +1,440 @@
+// Network kernels of the MgNet preconditioner (FP32 on CUDA cores).
+//
+// One gather convolution kernel serves every convolution of the V-cycle and
+// its backward pass.  A convolution is given as a tap table: for output
+// pixel (gy, gx) of a "class grid" and tap t, the input pixel is
+// (S gy + dy_t, S gx + dx_t) and the weight is w[(o so + i si) KK + wi_t].
+//   3x3 stride 1 / stride 2 / 1x1 convolutions: one class grid = the output.
+//   Transposed 4x4 stride 2 (prolongation) and the backward data of the
+//   stride-2 restriction: four parity classes, each a small convolution on the
+//   coarse grid whose results land at (2 gy + py, 2 gx + px).
+//   Backward data of a convolution: flipped taps and swapped weight strides.
+// The epilogue fuses what the V-cycle applies to a convolution result:
+//   v = acc (+ bias[o]) (+ cst); raw = v; v *= gate; v *= mask > 0;
+//   v = sign v (+ base) (+ y);  y = v.
+// Weight gradients use the same tap tables (k_wgrad).
+#include "nn_internal.h"
+
+namespace rte {
+namespace nn {
+namespace {
+
+constexpr int kTileCo = 64;      // output channels per CTA
+constexpr int kTileG = 8;        // 8 x 8 class-grid pixels per CTA
+constexpr int kChunk = 8;        // input channels staged per pass
+constexpr int kMaxPatch = 20;    // staged patch side (7 S + taps span)
+
+__global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
+    __shared__ float xs[kChunk][kMaxPatch][kMaxPatch + 1];
+    __shared__ __align__(16) float ws[kChunk][kMaxTaps][kTileCo];
+    const int tid = threadIdx.x;
+    const int tilesx = (a.Wg + kTileG - 1) / kTileG;
+    const int gy0 = (blockIdx.x / tilesx) * kTileG, gx0 = (blockIdx.x % tilesx) * kTileG;
+    const int co0 = blockIdx.y * kTileCo;
+    const int b = blockIdx.z;
+    const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
+    const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
+    const int tco = tid >> 4, tpx = tid & 15;
+    const int r = tpx >> 1, c0 = (tpx & 1) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[p][j] = 0.f;
+    const float* xb = a.x + (size_t)b * a.Ci * a.Hi * a.Wi;
+    for (int ci0 = 0; ci0 < a.Ci; ci0 += kChunk) {
+        for (int e = tid; e < kChunk * PY * PX; e += 256) {
+            const int ci = e / (PY * PX), rem = e - ci * PY * PX;
+            const int yy = rem / PX, xx = rem - yy * PX;
+            const int iy = a.S * gy0 + a.tp.dymin + yy, ix = a.S * gx0 + a.tp.dxmin + xx;
+            float v = 0.f;
+            if (ci0 + ci < a.Ci && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi) {
+                v = xb[((size_t)(ci0 + ci) * a.Hi + iy) * a.Wi + ix];
+                if (a.relu_in) v = fmaxf(v, 0.f);
+            }
+            xs[ci][yy][xx] = v;
+        }
+        for (int e = tid; e < kChunk * a.tp.T * kTileCo; e += 256) {
+            const int ci = e / (a.tp.T * kTileCo), rem = e - ci * a.tp.T * kTileCo;
+            const int t = rem / kTileCo, co = rem - t * kTileCo;
+            float v = 0.f;
+            if (ci0 + ci < a.Ci && co0 + co < a.Co)
+                v = a.w[((size_t)(co0 + co) * a.so + (size_t)(ci0 + ci) * a.si) * a.KK + a.tp.wi[t]];
+            ws[ci][t][co] = v;
+        }
+        __syncthreads();
+        const int nci = min(kChunk, a.Ci - ci0);
+        for (int ci = 0; ci < nci; ++ci) {
+            for (int t = 0; t < a.tp.T; ++t) {
+                const int yy = a.S * r + a.tp.dy[t] - a.tp.dymin;
+                const int xx0 = a.S * c0 + a.tp.dx[t] - a.tp.dxmin;
+                float xv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xv[j] = xs[ci][yy][xx0 + a.S * j];
+                const float4 wv = *reinterpret_cast<const float4*>(&ws[ci][t][tco * 4]);
+                const float wa[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[p][j] = fmaf(wa[p], xv[j], acc[p][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int co = co0 + tco * 4 + p;
+        if (co >= a.Co) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gy = gy0 + r, gx = gx0 + c0 + j;
+            if (gy >= a.Hg || gx >= a.Wg) continue;
+            const int oy = a.OS * gy + a.OY0, ox = a.OS * gx + a.OX0;
+            const size_t idx = (((size_t)b * a.Co + co) * a.Ho + oy) * a.Wo + ox;
+            float v = acc[p][j];
+            if (a.bias) v += a.bias[co];
+            v += a.cst;
+            if (a.raw) a.raw[idx] = v;
+            if (a.gate)
+                v *= a.gate[a.gate_bcast ? (((size_t)co * a.Ho + oy) * a.Wo + ox) : idx];
+            if (a.mask && !(a.mask[idx] > 0.f)) v = 0.f;
+            v *= a.sign;
+            if (a.base) v += a.base[idx];
+            if (a.accumulate) v += a.y[idx];
+            a.y[idx] = v;
+        }
+    }
+}
+
+// dW[(o so + i si) KK + wi_t] += sum_{b, gy, gx} G[b][o][OS gy + OY0][OS gx + OX0]
+//                                      * X[b][i][S gy + dy_t][S gx + dx_t]
+// CTA: 16 o x 16 i over an 8 x 8 class-grid tile of one batch entry.
+__global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
+    __shared__ float gs[16][kTileG * kTileG];
+    __shared__ float xs[16][kMaxPatch][kMaxPatch + 1];
+    const int tid = threadIdx.x;
+    const int tilesx = (a.Wg + kTileG - 1) / kTileG;
+    const int gy0 = (blockIdx.x / tilesx) * kTileG, gx0 = (blockIdx.x % tilesx) * kTileG;
+    const int otiles = (a.Co + 15) / 16;
+    const int o0 = (blockIdx.y % otiles) * 16, i0 = (blockIdx.y / otiles) * 16;
+    const int b = blockIdx.z;
+    const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
+    const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
+    for (int e = tid; e < 16 * kTileG * kTileG; e += 256) {
+        const int o = e / (kTileG * kTileG), p = e - o * kTileG * kTileG;
+        const int gy = gy0 + p / kTileG, gx = gx0 + p % kTileG;
+        float v = 0.f;
+        if (o0 + o < a.Co && gy < a.Hg && gx < a.Wg)
+            v = a.g[(((size_t)b * a.Co + o0 + o) * a.Hgo + a.OS * gy + a.OY0) * a.Wgo + a.OS * gx + a.OX0];
+        gs[o][p] = v;
+    }
+    for (int e = tid; e < 16 * PY * PX; e += 256) {
+        const int i = e / (PY * PX), rem = e - i * PY * PX;
+        const int yy = rem / PX, xx = rem - yy * PX;
+        const int iy = a.S * gy0 + a.tp.dymin + yy, ix = a.S * gx0 + a.tp.dxmin + xx;
+        float v = 0.f;
+        if (i0 + i < a.Ci && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi) {
+            v = a.x[(((size_t)b * a.Ci + i0 + i) * a.Hi + iy) * a.Wi + ix];
+            if (a.relu_in) v = fmaxf(v, 0.f);
+        }
+        xs[i][yy][xx] = v;
+    }
+    __syncthreads();
+    const int o = tid >> 4, i = tid & 15;
+    if (o0 + o >= a.Co || i0 + i >= a.Ci) return;
+    for (int t = 0; t < a.tp.T; ++t) {
+        float acc = 0.f;
+        for (int p = 0; p < kTileG * kTileG; ++p) {
+            const int py = p / kTileG, px = p - py * kTileG;
+            acc = fmaf(gs[o][p], xs[i][a.S * py + a.tp.dy[t] - a.tp.dymin][a.S * px + a.tp.dx[t] - a.tp.dxmin], acc);
+        }
+        atomicAdd(&a.dw[((size_t)(o0 + o) * a.so + (size_t)(i0 + i) * a.si) * a.KK + a.tp.wi[t]], acc);
+    }
+}
+
+// Per-channel statistics over (B, H, W): mean and 1/sqrt(var + eps) (biased
+// variance, two passes in FP64).
+__global__ void k_bn_stats(const float* __restrict__ x, int B, int C, int HW, float eps,
+                           float* __restrict__ mean, float* __restrict__ invstd) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int e = threadIdx.x; e < B * HW; e += blockDim.x) {
+        const int b = e / HW, p = e - b * HW;
+        s += x[((size_t)b * C + c) * HW + p];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        red[0] = t / ((double)B * HW);
+    }
+    __syncthreads();
+    const double mu = red[0];
+    __syncthreads();
+    double v = 0.0;
+    for (int e = threadIdx.x; e < B * HW; e += blockDim.x) {
+        const int b = e / HW, p = e - b * HW;
+        const double d = x[((size_t)b * C + c) * HW + p] - mu;
+        v += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        mean[c] = (float)mu;
+        invstd[c] = (float)(1.0 / sqrt(t / ((double)B * HW) + (double)eps));
+    }
+}
+
+// y = ReLU(gamma (x - mean) invstd + beta)
+__global__ void k_bn_relu(const float* __restrict__ x, int B, int C, int HW,
+                          const float* __restrict__ mean, const float* __restrict__ invstd,
+                          const float* __restrict__ gamma, const float* __restrict__ beta,
+                          float* __restrict__ y) {
+    const size_t n = (size_t)B * C * HW;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)((e / HW) % C);
+        const float v = gamma[c] * (x[e] - mean[c]) * invstd[c] + beta[c];
+        y[e] = fmaxf(v, 0.f);
+    }
+}
+
+// Backward of y = ReLU(BN(x)): per channel sums S1 = sum g', S2 = sum g' xh
+// with g' = g [y > 0]; dgamma += S2, dbeta += S1; then
+// dx = gamma invstd / cnt (cnt g' - S1 - xh S2).
+__global__ void k_bn_relu_bwd(const float* __restrict__ x, const float* __restrict__ y,
+                              const float* __restrict__ g, int B, int C, int HW,
+                              const float* __restrict__ mean, const float* __restrict__ invstd,
+                              const float* __restrict__ gamma, float* __restrict__ dgamma,
+                              float* __restrict__ dbeta, float* __restrict__ dx) {
+    __shared__ double r1[32], r2[32];
+    const int c = blockIdx.x;
+    const float mu = mean[c], is = invstd[c];
+    double s1 = 0.0, s2 = 0.0;
+    for (int e = threadIdx.x; e < B * HW; e += blockDim.x) {
+        const int b = e / HW, p = e - b * HW;
+        const size_t idx = ((size_t)b * C + c) * HW + p;
+        const float gp = y[idx] > 0.f ? g[idx] : 0.f;
+        const float xh = (x[idx] - mu) * is;
+        s1 += gp;
+        s2 += (double)gp * xh;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = s1; r2[threadIdx.x >> 5] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t1 += r1[w]; t2 += r2[w]; }
+        r1[0] = t1;
+        r2[0] = t2;
+        dgamma[c] += (float)t2;
+        dbeta[c] += (float)t1;
+    }
+    __syncthreads();
+    const double S1 = r1[0], S2 = r2[0];
+    const double cnt = (double)B * HW;
+    for (int e = threadIdx.x; e < B * HW; e += blockDim.x) {
+        const int b = e / HW, p = e - b * HW;
+        const size_t idx = ((size_t)b * C + c) * HW + p;
+        const float gp = y[idx] > 0.f ? g[idx] : 0.f;
+        const double xh = ((double)x[idx] - mu) * is;
+        dx[idx] = (float)((double)gamma[c] * is / cnt * (cnt * gp - S1 - xh * S2));
+    }
+}
+
+// backward of v = sign raw * gate with one gate shared by B samples:
+// out[b] = sign g[b] gate ; dgate += sum_b sign g[b] raw[b]
+__global__ void k_gate_bwd(const float* __restrict__ g, const float* __restrict__ gate,
+                           const float* __restrict__ raw, float sign, int B, size_t chw,
+                           float* __restrict__ out, float* __restrict__ dgate) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < chw; e += (size_t)gridDim.x * blockDim.x) {
+        const float ge = gate[e];
+        float acc = 0.f;
+        for (int b = 0; b < B; ++b) {
+            const float gv = sign * g[(size_t)b * chw + e];
+            out[(size_t)b * chw + e] = gv * ge;
+            acc = fmaf(gv, raw[(size_t)b * chw + e], acc);
+        }
+        dgate[e] += acc;
+    }
+}
+
+__global__ void k_scale_copy(float* __restrict__ y, const float* __restrict__ x, float alpha, size_t n) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = alpha * x[e];
+}
+
+__global__ void k_axpy_f(float* __restrict__ y, const float* __restrict__ x, float alpha, size_t n) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        y[e] += alpha * x[e];
+}
+
+// per-channel sum over (B, H, W) into out[c] (+=): gradient of a head bias
+__global__ void k_channel_sum(const float* __restrict__ g, int B, int C, int HW, float* __restrict__ out) {
+    __shared__ float red[32];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int e = threadIdx.x; e < B * HW; e += blockDim.x) {
+        const int b = e / HW, p = e - b * HW;
+        s += g[((size_t)b * C + c) * HW + p];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[c] += t;
+    }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[e];
+        const float mi = b1 * m[e] + (1.f - b1) * gi;
+        const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+        m[e] = mi;
+        v[e] = vi;
+        p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+int ew_blocks(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+void conv(const ConvArgs& a, cudaStream_t st) {
+    if (a.tp.T > kMaxTaps) throw StatusError{RTE_EINVAL, "too many taps"};
+    const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
+    const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
+    if (PY > kMaxPatch || PX > kMaxPatch) throw StatusError{RTE_EINVAL, "patch too large"};
+    const int tiles = ((a.Hg + kTileG - 1) / kTileG) * ((a.Wg + kTileG - 1) / kTileG);
+    dim3 grid(tiles, (a.Co + kTileCo - 1) / kTileCo, a.B);
+    k_conv<<<grid, 256, 0, st>>>(a);
+    check(cudaGetLastError(), "k_conv");
+}
+
+void wgrad(const WgradArgs& a, cudaStream_t st) {
+    const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
+    const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
+    if (PY > kMaxPatch || PX > kMaxPatch || a.tp.T > kMaxTaps)
+        throw StatusError{RTE_EINVAL, "wgrad tile too large"};
+    const int tiles = ((a.Hg + kTileG - 1) / kTileG) * ((a.Wg + kTileG - 1) / kTileG);
+    dim3 grid(tiles, ((a.Co + 15) / 16) * ((a.Ci + 15) / 16), a.B);
+    k_wgrad<<<grid, 256, 0, st>>>(a);
+    check(cudaGetLastError(), "k_wgrad");
+}
+
+void bn_stats(const float* x, int B, int C, int HW, float* mean, float* invstd, cudaStream_t st) {
+    k_bn_stats<<<C, 256, 0, st>>>(x, B, C, HW, 1e-5f, mean, invstd);
+    check(cudaGetLastError(), "k_bn_stats");
+}
+
+void bn_relu(const float* x, int B, int C, int HW, const float* mean, const float* invstd,
+             const float* gamma, const float* beta, float* y, cudaStream_t st) {
+    const size_t n = (size_t)B * C * HW;
+    k_bn_relu<<<ew_blocks(n), 256, 0, st>>>(x, B, C, HW, mean, invstd, gamma, beta, y);
+    check(cudaGetLastError(), "k_bn_relu");
+}
+
+void bn_relu_bwd(const float* x, const float* y, const float* g, int B, int C, int HW,
+                 const float* mean, const float* invstd, const float* gamma, float* dgamma,
+                 float* dbeta, float* dx, cudaStream_t st) {
+    k_bn_relu_bwd<<<C, 256, 0, st>>>(x, y, g, B, C, HW, mean, invstd, gamma, dgamma, dbeta, dx);
+    check(cudaGetLastError(), "k_bn_relu_bwd");
+}
+
+void gate_bwd(const float* g, const float* gate, const float* raw, float sign, int B, size_t chw,
+              float* out, float* dgate, cudaStream_t st) {
+    k_gate_bwd<<<ew_blocks(chw), 256, 0, st>>>(g, gate, raw, sign, B, chw, out, dgate);
+    check(cudaGetLastError(), "k_gate_bwd");
+}
+
+void scale_copy(float* y, const float* x, float alpha, size_t n, cudaStream_t st) {
+    k_scale_copy<<<ew_blocks(n), 256, 0, st>>>(y, x, alpha, n);
+    check(cudaGetLastError(), "k_scale_copy");
+}
+
+void axpy(float* y, const float* x, float alpha, size_t n, cudaStream_t st) {
+    k_axpy_f<<<ew_blocks(n), 256, 0, st>>>(y, x, alpha, n);
+    check(cudaGetLastError(), "k_axpy_f");
+}
+
+void channel_sum(const float* g, int B, int C, int HW, float* out, cudaStream_t st) {
+    k_channel_sum<<<C, 256, 0, st>>>(g, B, C, HW, out);
+    check(cudaGetLastError(), "k_channel_sum");
+}
+
+void adam(float* p, const float* g, float* m, float* v, size_t n, float lr, int step, cudaStream_t st) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    k_adam<<<ew_blocks(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
+    check(cudaGetLastError(), "k_adam");
+}
+
+// ---------------------------------------------------------------- tap tables
+Taps taps_conv(int k, int pad) {
+    Taps t{};
+    t.T = k * k;
+    for (int ky = 0; ky < k; ++ky)
+        for (int kx = 0; kx < k; ++kx) {
+            const int q = ky * k + kx;
+            t.dy[q] = ky - pad;
+            t.dx[q] = kx - pad;
+            t.wi[q] = q;
+        }
+    t.finish();
+    return t;
+}
+
+Taps taps_conv_flipped(int k, int pad) {
+    Taps t{};
+    t.T = k * k;
+    for (int ky = 0; ky < k; ++ky)
+        for (int kx = 0; kx < k; ++kx) {
+            const int q = ky * k + kx;
+            t.dy[q] = pad - ky;
+            t.dx[q] = pad - kx;
+            t.wi[q] = q;
+        }
+    t.finish();
+    return t;
+}
+
+// Scatter of a stride-2 kernel of size k (pad 1) onto fine-grid parity
+// class (py, px): fine pixel 2 gy + py receives coarse pixel gy + d from
+// kernel row ky when 2 (gy + d) + ky - 1 = 2 gy + py, i.e. ky = py + 1 - 2 d.
+Taps taps_parity(int k, int py, int px) {
+    Taps t{};
+    t.T = 0;
+    for (int ky = 0; ky < k; ++ky) {
+        if (((py + 1 - ky) & 1) != 0) continue;
+        const int dy = (py + 1 - ky) / 2;
+        for (int kx = 0; kx < k; ++kx) {
+            if (((px + 1 - kx) & 1) != 0) continue;
+            const int dx = (px + 1 - kx) / 2;
+            t.dy[t.T] = dy;
+            t.dx[t.T] = dx;
+            t.wi[t.T] = ky * k + kx;
+            ++t.T;
+        }
+    }
+    t.finish();
+    return t;
+}
+
+}  // namespace nn
+}  // namespace rte

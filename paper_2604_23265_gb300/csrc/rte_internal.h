@@ -47,6 +47,7 @@ struct rte_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     int num_sms = 0;
+    uint64_t uid = 0;                // unique per context (cache key for network features)
 
     // host copies of the set-up tables
     std::vector<double> xi_h;        // [nmat][2M]
@@ -65,6 +66,7 @@ struct rte_ctx {
     int* rowinfo = nullptr;          // [4][M]: j >= 0 incoming row j of face f, -(j+1) outgoing
     int* rowdir = nullptr;           // [2M] direction of each row slot
     double* inflow = nullptr;        // [4][I][M]
+    float* coef_in = nullptr;        // [4][N] CoeffNet inputs: log sigma_T, log sigma_a, log eps, log tau
     double* b = nullptr;             // [n]
     double* Dt = nullptr;            // [N][2M][2M], Dt[c][j][i] = D_c[i][j]  (FP64)
     float* Rt = nullptr;             // [N][2M][2M], Rt[c][i][row] = R_c[row][i] (FP32)
@@ -122,6 +124,7 @@ void launch_apply(rte_ctx* ctx, bool f64, const void* x, void* y, bool y_is_doub
 void launch_apply_adjoint(rte_ctx* ctx, bool f64, const void* y, void* x);
 void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi);
 void launch_rhs(rte_ctx* ctx);
+void launch_coef_inputs(rte_ctx* ctx, const double* sT, const double* sa, const double* eps);
 
 // block kernels (blocks.cu) ------------------------------------------------
 // builds G_C for every cell, inverts it into ctx->Dt (FP64) and forms the
@@ -134,6 +137,8 @@ void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_d
 // space, R in FP32); v, w float or double; uses trace_out as scratch
 void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* w,
                            bool w_is_double);
+// w = (A D)^T u = u - R^T P u (float; scratch holds n floats)
+void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scratch);
 
 // krylov kernels (krylov.cu) -----------------------------------------------
 // h[0..k) = V^T w (deterministic, last-block reduction into h)

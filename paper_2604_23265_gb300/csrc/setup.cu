@@ -7,6 +7,7 @@
 // Everything proportional to the grid (b, the per-cell blocks and their
 // inverses) is built on the device.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -441,6 +442,16 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     ctx->Dt = static_cast<double*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(double)));
     ctx->Rt = static_cast<float*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(float)));
     launch_rhs(ctx);
+    {
+        std::vector<double> eh(N);
+        for (int c = 0; c < N; ++c) eh[c] = eps_is_scalar ? eps[0] : eps[c];
+        std::vector<double> sTh(sigma_T, sigma_T + N), sah(sigma_a, sigma_a + N);
+        double* dsT = upload(ctx, sTh);
+        double* dsa = upload(ctx, sah);
+        double* de = upload(ctx, eh);
+        ctx->coef_in = static_cast<float*>(dev_alloc(ctx, (size_t)4 * N * sizeof(float)));
+        launch_coef_inputs(ctx, dsT, dsa, de);
+    }
     int* sing = reinterpret_cast<int*>(ctx->scal + kScal - 1);
     launch_build_invert(ctx, sing);
     int sing_h = 0;
@@ -492,6 +503,8 @@ RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
     ctx->n = (int64_t)2 * ctx->M * ctx->N;
     ctx->g = g;
     ctx->stream = static_cast<cudaStream_t>(stream);
+    static std::atomic<uint64_t> next_uid{1};
+    ctx->uid = next_uid.fetch_add(1);
     rte_status st = RTE_OK;
     try {
         build(ctx, sigma_T, sigma_a, q, eps, eps_is_scalar, inflow);

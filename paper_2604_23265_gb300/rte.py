@@ -86,6 +86,17 @@ SIGNATURES = {
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
     "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
     "rte_profile": (_I, [_P, _I]),
+    "mgnet_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
+    "mgnet_destroy": (None, [_P]),
+    "mgnet_param_count": (ctypes.c_int64, [_P]),
+    "mgnet_set_params": (_I, [_P, _P, ctypes.c_int64]),
+    "mgnet_get_params": (_I, [_P, _P, ctypes.c_int64]),
+    "mgnet_precond": (_I, [_P, _P, _P, _P]),
+    "mgnet_apply": (_I, [_P, _P, _P, _P]),
+    "mgnet_train_step": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(_D)]),
+    "mgnet_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D), _P]),
+    "mgnet_save": (_I, [_P, ctypes.c_char_p]),
+    "mgnet_load": (_I, [_P, ctypes.c_char_p]),
     "rte_profile_read": (_I, [_P, ctypes.POINTER(KernelStat), _I]),
 }
 
@@ -142,6 +153,98 @@ def eigenbasis(M, g, one_minus_gamma, axis):
     _check(load().rte_eigenbasis(int(M), float(g), float(one_minus_gamma), int(axis),
                                  xi.ctypes.data_as(_P), L.ctypes.data_as(_P)))
     return xi, L
+
+
+class MgNetConfig(ctypes.Structure):
+    _fields_ = [("M", _I), ("levels", _I), ("c0", _I), ("cmax", _I), ("cc", _I), ("ccmax", _I)]
+
+
+class MgNet:
+    """The learned preconditioner (mgnet_*); weights as one float32 vector in
+    the order of ``workloads.param_shapes``."""
+
+    def __init__(self, shape, stream=None):
+        cfg = MgNetConfig(shape.M, shape.levels, shape.c0, shape.cmax, shape.cc, shape.ccmax)
+        out = ctypes.c_void_p()
+        _check(load().mgnet_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(out)))
+        self.ptr = out
+        self.shape = shape
+        self.count = int(load().mgnet_param_count(self.ptr))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().mgnet_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def flatten(params, shape):
+        from . import workloads
+        return np.concatenate([np.asarray(params[name], np.float64).ravel()
+                               for name, _ in workloads.param_shapes(shape)]).astype(np.float32)
+
+    @staticmethod
+    def unflatten(flat, shape):
+        from . import workloads
+        out, o = {}, 0
+        for name, shp in workloads.param_shapes(shape):
+            k = int(np.prod(shp))
+            out[name] = np.asarray(flat[o:o + k], np.float64).reshape(shp)
+            o += k
+        return out
+
+    def set_params(self, params):
+        flat = params if isinstance(params, np.ndarray) else self.flatten(params, self.shape)
+        flat = np.ascontiguousarray(flat, np.float32)
+        _check(load().mgnet_set_params(self.ptr, flat.ctypes.data_as(_P), flat.size))
+
+    def get_params(self):
+        flat = np.zeros(self.count, np.float32)
+        _check(load().mgnet_get_params(self.ptr, flat.ctypes.data_as(_P), flat.size))
+        return flat
+
+    def precond(self, ctx, r, z):
+        import torch
+        _check(load().mgnet_precond(self.ptr, ctx.ptr, _dev(r, torch.float64, ctx.n),
+                                    _dev(z, torch.float32, ctx.n)))
+        return z
+
+    def apply(self, ctx, r, z):
+        import torch
+        _check(load().mgnet_apply(self.ptr, ctx.ptr, _dev(r, torch.float64, ctx.n),
+                                  _dev(z, torch.float64, ctx.n)))
+        return z
+
+    def _ptrs(self, ctx, rs):
+        import torch
+        arr = (_P * len(rs))(*[_dev(r, torch.float64, ctx.n).value for r in rs])
+        return arr
+
+    def train_step(self, ctx, rs, lr):
+        loss = ctypes.c_double()
+        arr = self._ptrs(ctx, rs)
+        _check(load().mgnet_train_step(self.ptr, ctx.ptr, ctypes.cast(arr, _P), len(rs), float(lr),
+                                       ctypes.byref(loss)))
+        return loss.value
+
+    def loss_grad(self, ctx, rs):
+        loss = ctypes.c_double()
+        g = np.zeros(self.count, np.float32)
+        arr = self._ptrs(ctx, rs)
+        _check(load().mgnet_loss_grad(self.ptr, ctx.ptr, ctypes.cast(arr, _P), len(rs),
+                                      ctypes.byref(loss), g.ctypes.data_as(_P)))
+        return loss.value, g
+
+    def save(self, path):
+        _check(load().mgnet_save(self.ptr, str(path).encode()))
+
+    def load(self, path):
+        _check(load().mgnet_load(self.ptr, str(path).encode()))
 
 
 class Context:

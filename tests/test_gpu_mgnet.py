@@ -1,0 +1,95 @@
+"""GPU parity of the MgNet preconditioner against the FP64 oracle (same seeded
+weights and inputs): forward, loss, every parameter's gradient, training and
+the MgNet-preconditioned solve.  FP32 network arithmetic: relative L2 bars of
+1e-4 (outputs) and 2e-3 (gradients, sums over up to 65k products)."""
+import numpy as np
+import pytest
+
+from oracle import krylov, mgnet as OM, tfps
+from paper_2604_23265_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def _setup(I=16, M=8, levels=3, seed=0, proj=0.5, c0=8, cmax=16, cc=4, ccmax=8):
+    from paper_2604_23265_gb300 import rte
+    shape = W.NetShape(M=M, levels=levels, c0=c0, cmax=cmax, cc=cc, ccmax=ccmax)
+    params = W.init_params(shape, seed=seed, proj_scale=proj)
+    # round the weights to float32 so both sides use identical values
+    params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
+    md = W.grf_diffusive(seed + 3, I=I, M=M, eps=1e-2)
+    ctx = rte.Context.from_medium(md)
+    net = rte.MgNet(shape)
+    net.set_params(params)
+    p = tfps.Problem(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow)
+    return rte, shape, params, md, ctx, net, p
+
+
+@pytest.mark.parametrize("I,M,levels", [(16, 8, 3), (24, 4, 2), (32, 16, 4), (8, 8, 1)])
+def test_forward_matches_oracle(lib, I, M, levels):
+    rte, shape, params, md, ctx, net, p = _setup(I=I, M=M, levels=levels)
+    r = W.random_vector(ctx.n, 7)
+    z = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
+    net.precond(ctx, torch.tensor(r, device="cuda"), z)
+    ref = OM.apply_net(params, shape, OM.coeff_inputs(md), r)
+    assert _rel(z.cpu().numpy(), ref) <= 1e-4
+    za = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    net.apply(ctx, torch.tensor(r, device="cuda"), za)
+    refa = tfps.block_apply(p.block_inverse(), ref.reshape(2 * M, -1)).ravel()
+    assert _rel(za.cpu().numpy(), refa) <= 1e-4 * np.linalg.cond(p.blocks()).max() ** 0.5 + 1e-4
+
+
+@pytest.mark.parametrize("levels,batch", [(1, 1), (2, 3), (3, 2)])
+def test_loss_and_gradients_match_oracle(lib, levels, batch):
+    rte, shape, params, md, ctx, net, p = _setup(I=16, M=8, levels=levels, proj=0.3)
+    rs = [W.random_vector(ctx.n, 20 + b) for b in range(batch)]
+    loss, g = net.loss_grad(ctx, [torch.tensor(r, device="cuda") for r in rs])
+    D = p.block_inverse()
+    cx = OM.coeff_inputs(md)
+    lref, gref = OM.loss_and_grad(params, shape, [p] * batch, [D] * batch, [cx] * batch, rs)
+    assert abs(loss - lref) <= 1e-5 * lref
+    G = rte.MgNet.unflatten(g, shape)
+    for k in gref:
+        scale = max(np.linalg.norm(gref[k]), 1e-3 * max(np.linalg.norm(v) for v in gref.values()))
+        assert np.linalg.norm(G[k] - gref[k]) <= 2e-3 * scale, k
+
+
+def test_training_reduces_loss(lib):
+    rte, shape, params, md, ctx, net, p = _setup(I=16, M=8, levels=3, proj=0.0)
+    rs = [torch.tensor(W.random_vector(ctx.n, 40 + b), device="cuda") for b in range(4)]
+    first = net.train_step(ctx, rs, 3e-3)
+    for _ in range(60):
+        last = net.train_step(ctx, rs, 3e-3)
+    assert last < 0.9 * first
+
+
+def test_mgnet_preconditioned_solve(lib):
+    """FGMRES with a network close to the identity (small projection) converges
+    to 1e-10 and the solution matches the oracle's dense LU solution."""
+    rte, shape, params, md, ctx, net, p = _setup(I=16, M=8, levels=3, proj=0.02)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, pc=net, tol=1e-10, restart=40, stall_ratio=10.0)
+    assert info["converged"], info
+    xl = krylov.dense_solve(p.assemble(), p.rhs().ravel())
+    psi = torch.zeros(md.M * md.I * md.I, dtype=torch.float64, device="cuda")
+    ctx.reconstruct(x, psi)
+    ref = p.reconstruct(xl.reshape(2 * md.M, -1)).ravel()
+    assert _rel(psi.cpu().numpy(), ref) <= 1e-7
+
+
+def test_save_load_roundtrip(lib, tmp_path):
+    rte, shape, params, md, ctx, net, p = _setup()
+    net.save(tmp_path / "w.bin")
+    net2 = rte.MgNet(shape)
+    net2.load(tmp_path / "w.bin")
+    np.testing.assert_array_equal(net.get_params(), net2.get_params())
+    raw = bytearray((tmp_path / "w.bin").read_bytes())
+    raw[100] ^= 0xFF
+    (tmp_path / "bad.bin").write_bytes(bytes(raw))
+    with pytest.raises(rte.RteError):
+        net2.load(tmp_path / "bad.bin")
