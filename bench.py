@@ -168,7 +168,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    md = W.grf_diffusive(seed=rank)
+    md = W.grf_diffusive(seed=rank, I=args.size, M=args.dirs)
     stream = torch.cuda.current_stream()
     ctx = rte.Context.from_medium(md, stream=stream)
     x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
@@ -211,7 +211,7 @@ def run_ours(args):
     psi_host = torch.empty(md.M * md.I * md.I, dtype=torch.float64).pin_memory()
     d2h = psi_host.numel() * 8
     e2e_times = []
-    for _ in range(args.steps):
+    for _ in range(0 if args.no_e2e else args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = rte.Context(md.I, md.M, hs[0], hs[1], hs[2], hs[3], md.g, hs[4], stream=stream)
@@ -224,8 +224,8 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
         c2.close()
         converged = converged and bool(i2["converged"])
-    e2e_s = _max_over_ranks(world, sum(e2e_times))
-    e2e_value = (args.steps * world / e2e_s) if converged else 0.0
+    e2e_s = _max_over_ranks(world, sum(e2e_times)) if e2e_times else float("nan")
+    e2e_value = (args.steps * world / e2e_s) if (converged and e2e_times) else 0.0
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -246,6 +246,9 @@ def run_ours(args):
                     for k, v in prof.items() if v[0]},
         "clocks": clocks,
     }
+    if (args.size, args.dirs) != (256, 64):
+        out["config"]["workload"] = f"profiling case {args.size}x{args.size}, M={args.dirs} (not the benchmark)"
+        out["config"]["I"], out["config"]["M"] = args.size, args.dirs
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(md, iters)
     if rank == 0:
@@ -289,6 +292,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=20000,
                     help="iteration count used to project the oracle's per-iteration time")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")
+    ap.add_argument("--dirs", type=int, default=64, help="profiling only: directions")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -67,50 +67,61 @@ __device__ void block_reduce_finish(double (&acc)[KMAX], int K, double* __restri
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Chunked streaming layout: a block owns chunks of kChunk = 4 * kT consecutive
-// elements; lane l of warp w holds elements base + 2l + {0,1} and
-// base + 64 + 2l + {0,1} of its 128-element slice (two 16-byte loads per
-// vector), so every load instruction of a warp covers 512 contiguous bytes.
-constexpr int kChunk = 4 * kT;
+// Chunked streaming layout: a block owns chunks of kChunk = 8 * kT consecutive
+// elements; lane l of warp w holds elements base + 2l + {0,1} + 64 q, q = 0..3,
+// of its 256-element slice (four 16-byte loads per vector), so every load
+// instruction of a warp covers 512 contiguous bytes.  Only the last chunk
+// needs bounds checks.
+constexpr int kChunk = 8 * kT;
 
 struct Slice {
-    double v[4];
+    double v[8];
 };
 
 __device__ __forceinline__ int64_t slice_base(int64_t chunk) {
-    return chunk * kChunk + (int64_t)(threadIdx.x >> 5) * 128 + 2 * (threadIdx.x & 31);
+    return chunk * kChunk + (int64_t)(threadIdx.x >> 5) * 256 + 2 * (threadIdx.x & 31);
 }
 
+template <bool TAIL>
 __device__ __forceinline__ Slice load_slice(const double* __restrict__ p, int64_t base, int64_t n) {
     Slice s;
-    if (base + 65 < n) {
-        const double2 a = *reinterpret_cast<const double2*>(p + base);
-        const double2 b = *reinterpret_cast<const double2*>(p + base + 64);
-        s.v[0] = a.x; s.v[1] = a.y; s.v[2] = b.x; s.v[3] = b.y;
-    } else {
-        s.v[0] = base < n ? p[base] : 0.0;
-        s.v[1] = base + 1 < n ? p[base + 1] : 0.0;
-        s.v[2] = base + 64 < n ? p[base + 64] : 0.0;
-        s.v[3] = base + 65 < n ? p[base + 65] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + 64 * q;
+        if (!TAIL || i + 1 < n) {
+            const double2 a = *reinterpret_cast<const double2*>(p + i);
+            s.v[2 * q] = a.x;
+            s.v[2 * q + 1] = a.y;
+        } else {
+            s.v[2 * q] = i < n ? p[i] : 0.0;
+            s.v[2 * q + 1] = 0.0;
+        }
     }
     return s;
 }
 
+template <bool TAIL>
 __device__ __forceinline__ void store_slice(double* __restrict__ p, int64_t base, int64_t n,
                                             const Slice& s) {
-    if (base + 65 < n) {
-        *reinterpret_cast<double2*>(p + base) = make_double2(s.v[0], s.v[1]);
-        *reinterpret_cast<double2*>(p + base + 64) = make_double2(s.v[2], s.v[3]);
-    } else {
-        if (base < n) p[base] = s.v[0];
-        if (base + 1 < n) p[base + 1] = s.v[1];
-        if (base + 64 < n) p[base + 64] = s.v[2];
-        if (base + 65 < n) p[base + 65] = s.v[3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + 64 * q;
+        if (!TAIL || i + 1 < n) {
+            *reinterpret_cast<double2*>(p + i) = make_double2(s.v[2 * q], s.v[2 * q + 1]);
+        } else if (i < n) {
+            p[i] = s.v[2 * q];
+        }
     }
 }
 
 __device__ __forceinline__ double slice_dot(const Slice& a, const Slice& b) {
-    return fma(a.v[0], b.v[0], fma(a.v[1], b.v[1], fma(a.v[2], b.v[2], a.v[3] * b.v[3])));
+    double t0 = a.v[0] * b.v[0], t1 = a.v[1] * b.v[1];
+#pragma unroll
+    for (int e = 2; e < 8; e += 2) {
+        t0 = fma(a.v[e], b.v[e], t0);
+        t1 = fma(a.v[e + 1], b.v[e + 1], t1);
+    }
+    return t0 + t1;
 }
 
 // Every thread accumulates its own partial dot products in shared memory,
@@ -144,30 +155,74 @@ __device__ void finish_dots(const double* s_part, int K, double* partials, unsig
 }
 
 // h[k] = V[k] . w for k < K
+template <bool TAIL>
+__device__ __forceinline__ void mdot_chunk(const double* __restrict__ V, int K, int64_t n,
+                                           const double* __restrict__ w, int64_t base,
+                                           double* s_part) {
+    const int tid = threadIdx.x;
+    const Slice ws = load_slice<TAIL>(w, base, n);
+    const double* vk = V;
+    int k = 0;
+    for (; k + 2 <= K; k += 2, vk += 2 * n) {
+        const Slice v0 = load_slice<TAIL>(vk, base, n);
+        const Slice v1 = load_slice<TAIL>(vk + n, base, n);
+        s_part[(k + 0) * kT + tid] += slice_dot(v0, ws);
+        s_part[(k + 1) * kT + tid] += slice_dot(v1, ws);
+    }
+    if (k < K) s_part[k * kT + tid] += slice_dot(load_slice<TAIL>(vk, base, n), ws);
+}
+
 __global__ void __launch_bounds__(kT) k_mdot(const double* __restrict__ V, int K, int64_t n,
                                              const double* __restrict__ w, double* partials,
                                              unsigned* counter, double* h) {
     extern __shared__ double s_part[];          // [K][kT]
     const int tid = threadIdx.x;
     for (int k = 0; k < K; ++k) s_part[k * kT + tid] = 0.0;
-    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const int64_t full = n / kChunk, nchunks = (n + kChunk - 1) / kChunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int64_t base = slice_base(ch);
-        const Slice ws = load_slice(w, base, n);
-        int k = 0;
-        for (; k + 4 <= K; k += 4) {
-            const Slice v0 = load_slice(V + (size_t)(k + 0) * n, base, n);
-            const Slice v1 = load_slice(V + (size_t)(k + 1) * n, base, n);
-            const Slice v2 = load_slice(V + (size_t)(k + 2) * n, base, n);
-            const Slice v3 = load_slice(V + (size_t)(k + 3) * n, base, n);
-            s_part[(k + 0) * kT + tid] += slice_dot(v0, ws);
-            s_part[(k + 1) * kT + tid] += slice_dot(v1, ws);
-            s_part[(k + 2) * kT + tid] += slice_dot(v2, ws);
-            s_part[(k + 3) * kT + tid] += slice_dot(v3, ws);
-        }
-        for (; k < K; ++k) s_part[k * kT + tid] += slice_dot(load_slice(V + (size_t)k * n, base, n), ws);
+        if (ch < full)
+            mdot_chunk<false>(V, K, n, w, slice_base(ch), s_part);
+        else
+            mdot_chunk<true>(V, K, n, w, slice_base(ch), s_part);
     }
     finish_dots(s_part, K, partials, counter, h);
+}
+
+// w <- w - sum_k V[k] h1[k] on one chunk; then (DOTS) s_part[k] += V[k] . w
+template <bool TAIL, bool DOTS>
+__device__ __forceinline__ Slice update_chunk(const double* __restrict__ V, int K, int64_t n,
+                                              double* __restrict__ w, const double* sh,
+                                              int64_t base, double* s_part) {
+    const int tid = threadIdx.x;
+    Slice ws = load_slice<TAIL>(w, base, n);
+    const double* vk = V;
+    int k = 0;
+    for (; k + 2 <= K; k += 2, vk += 2 * n) {
+        const Slice v0 = load_slice<TAIL>(vk, base, n);
+        const Slice v1 = load_slice<TAIL>(vk + n, base, n);
+        const double h0 = sh[k], h1 = sh[k + 1];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ws.v[e] = fma(-h1, v1.v[e], fma(-h0, v0.v[e], ws.v[e]));
+    }
+    if (k < K) {
+        const Slice v0 = load_slice<TAIL>(vk, base, n);
+        const double h0 = sh[k];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ws.v[e] = fma(-h0, v0.v[e], ws.v[e]);
+    }
+    store_slice<TAIL>(w, base, n, ws);
+    if (DOTS) {
+        vk = V;
+        k = 0;
+        for (; k + 2 <= K; k += 2, vk += 2 * n) {
+            const Slice v0 = load_slice<TAIL>(vk, base, n);
+            const Slice v1 = load_slice<TAIL>(vk + n, base, n);
+            s_part[(k + 0) * kT + tid] += slice_dot(v0, ws);
+            s_part[(k + 1) * kT + tid] += slice_dot(v1, ws);
+        }
+        if (k < K) s_part[k * kT + tid] += slice_dot(load_slice<TAIL>(vk, base, n), ws);
+    }
+    return ws;
 }
 
 // w <- w - sum_k V[k] h1[k]; then h2[k] = V[k] . w   (V re-read from cache)
@@ -182,43 +237,12 @@ __global__ void __launch_bounds__(kT) k_update_dot(const double* __restrict__ V,
     for (int k = tid; k < K; k += blockDim.x) sh[k] = h1[k];
     for (int k = 0; k < K; ++k) s_part[k * kT + tid] = 0.0;
     __syncthreads();
-    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const int64_t full = n / kChunk, nchunks = (n + kChunk - 1) / kChunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int64_t base = slice_base(ch);
-        Slice ws = load_slice(w, base, n);
-        int k = 0;
-        for (; k + 4 <= K; k += 4) {
-            const Slice v0 = load_slice(V + (size_t)(k + 0) * n, base, n);
-            const Slice v1 = load_slice(V + (size_t)(k + 1) * n, base, n);
-            const Slice v2 = load_slice(V + (size_t)(k + 2) * n, base, n);
-            const Slice v3 = load_slice(V + (size_t)(k + 3) * n, base, n);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                double t = ws.v[e];
-                t = fma(-sh[k], v0.v[e], t);
-                t = fma(-sh[k + 1], v1.v[e], t);
-                t = fma(-sh[k + 2], v2.v[e], t);
-                ws.v[e] = fma(-sh[k + 3], v3.v[e], t);
-            }
-        }
-        for (; k < K; ++k) {
-            const Slice v = load_slice(V + (size_t)k * n, base, n);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) ws.v[e] = fma(-sh[k], v.v[e], ws.v[e]);
-        }
-        store_slice(w, base, n, ws);
-        k = 0;
-        for (; k + 4 <= K; k += 4) {
-            const Slice v0 = load_slice(V + (size_t)(k + 0) * n, base, n);
-            const Slice v1 = load_slice(V + (size_t)(k + 1) * n, base, n);
-            const Slice v2 = load_slice(V + (size_t)(k + 2) * n, base, n);
-            const Slice v3 = load_slice(V + (size_t)(k + 3) * n, base, n);
-            s_part[(k + 0) * kT + tid] += slice_dot(v0, ws);
-            s_part[(k + 1) * kT + tid] += slice_dot(v1, ws);
-            s_part[(k + 2) * kT + tid] += slice_dot(v2, ws);
-            s_part[(k + 3) * kT + tid] += slice_dot(v3, ws);
-        }
-        for (; k < K; ++k) s_part[k * kT + tid] += slice_dot(load_slice(V + (size_t)k * n, base, n), ws);
+        if (ch < full)
+            update_chunk<false, true>(V, K, n, w, sh, slice_base(ch), s_part);
+        else
+            update_chunk<true, true>(V, K, n, w, sh, slice_base(ch), s_part);
     }
     finish_dots(s_part, K, partials, counter, h2);
 }
@@ -234,17 +258,13 @@ __global__ void __launch_bounds__(kT) k_update_norm(const double* __restrict__ V
     for (int k = threadIdx.x; k < K; k += blockDim.x) sh[k] = h2[k];
     __syncthreads();
     double acc[1] = {0.0};
-    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const int64_t full = n / kChunk, nchunks = (n + kChunk - 1) / kChunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int64_t base = slice_base(ch);
-        Slice ws = load_slice(w, base, n);
-        for (int k = 0; k < K; ++k) {
-            const Slice v = load_slice(V + (size_t)k * n, base, n);
-            const double hk = sh[k];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) ws.v[e] = fma(-hk, v.v[e], ws.v[e]);
-        }
-        store_slice(w, base, n, ws);
+        Slice ws;
+        if (ch < full)
+            ws = update_chunk<false, false>(V, K, n, w, sh, slice_base(ch), nullptr);
+        else
+            ws = update_chunk<true, false>(V, K, n, w, sh, slice_base(ch), nullptr);
         acc[0] += slice_dot(ws, ws);
     }
     // out[K] = ||w||; block 0 also writes out[k] = h1[k] + h2[k]
