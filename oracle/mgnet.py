@@ -15,7 +15,9 @@ Readings of the paper (Sec. 3.1-3.4, silent or ambiguous there):
   operator and solution-operator encodings a = 1 + head, ainv = 1 + head
   (width of the MgNet level), so an untrained net gates by one.
 * MgNet (Sec. 3.3): lift 1x1 (2M -> C_0); smoothing
-  u <- u + (B_l * ReLU(f - (A_l * u) o a_l)) o ainv_l with 3x3 convs A_l, B_l;
+  u <- u + (B_l * act(f - (A_l * u) o a_l)) o ainv_l with 3x3 convs A_l, B_l;
+  act is the identity by default (Sec. 3.3 names convolutional smoothers
+  and no activation; the operator they approximate is linear) or ReLU;
   restriction f_{l+1} = R_l * (f_l - (A_l * u_l) o a_l), 3x3 stride 2;
   prolongation u_l <- u_l + P_l *^T u_{l+1}, transposed 4x4 stride 2; one
   pre- and one post-smoothing step per level (two on the coarsest); width
@@ -220,7 +222,8 @@ def forward(params, shape, coeff_x, x):
             tt = f[l]
         else:
             tt = t.sub(f[l], t.mul(t.conv(ul, P[f"A{l}.w"], 1, 1), a[l]))
-        corr = t.mul(t.conv(t.relu(tt), P[f"B{l}.w"], 1, 1), ai[l])
+        inner = t.relu(tt) if shape.act == "relu" else tt
+        corr = t.mul(t.conv(inner, P[f"B{l}.w"], 1, 1), ai[l])
         return corr if ul is None else t.add(ul, corr)
 
     for l in range(L - 1):

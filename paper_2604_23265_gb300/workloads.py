@@ -194,6 +194,7 @@ class NetShape:
     cc: int = 8
     ccmax: int = 32
     cin: int = 4
+    act: str = "linear"      # smoother activation: "linear" or "relu"
 
     def width(self, l):
         return min(self.c0 * 2 ** l, self.cmax)
@@ -226,9 +227,10 @@ def param_shapes(s: NetShape):
     return out
 
 
-def init_params(s: NetShape, seed: int = 0, proj_scale: float = 0.0):
+def init_params(s: NetShape, seed: int = 0, proj_scale: float = 0.0, vcycle_scale: float = 1.0):
     """He-style normal weights, BN gamma = 1, beta = 0, head biases 0; the
-    projection starts at proj_scale (0: the network returns its input)."""
+    projection starts at proj_scale (0: the network returns its input) and the
+    V-cycle convolutions (A, B, R, P) are multiplied by vcycle_scale."""
     rng = np.random.default_rng(seed)
     params = {}
     for name, shape in param_shapes(s):
@@ -245,5 +247,7 @@ def init_params(s: NetShape, seed: int = 0, proj_scale: float = 0.0):
                 v = v * 0.1
             if name == "proj.w":
                 v = v * proj_scale
+            if name[0] in "ABRP":
+                v = v * vcycle_scale
         params[name] = v.astype(np.float64)
     return params

@@ -36,8 +36,8 @@ def test_P11_transposed_conv_is_adjoint(k, s, p, H):
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-def _small(levels=2, batch=2, seed=0, proj=0.3):
-    shape = W.NetShape(M=4, levels=levels, c0=4, cmax=8, cc=4, ccmax=8)
+def _small(levels=2, batch=2, seed=0, proj=0.3, act="linear"):
+    shape = W.NetShape(M=4, levels=levels, c0=4, cmax=8, cc=4, ccmax=8, act=act)
     params = W.init_params(shape, seed=seed, proj_scale=proj)
     meds = [W.polynomial_diffusion(s, I=8, M=4) for s in range(batch)]
     probs = [tfps.Problem(m.I, m.M, m.sigma_T, m.sigma_a, m.q, m.eps, m.g, m.inflow) for m in meds]
@@ -47,14 +47,15 @@ def _small(levels=2, batch=2, seed=0, proj=0.3):
     return shape, params, probs, Ds, cx, rs
 
 
-@pytest.mark.parametrize("levels", [1, 2, 3])
-def test_P16_gradients_match_finite_differences(levels):
-    shape, params, probs, Ds, cx, rs = _small(levels=levels)
+@pytest.mark.parametrize("levels,act", [(1, "linear"), (2, "linear"), (3, "linear"), (2, "relu"),
+                                        (3, "relu")])
+def test_P16_gradients_match_finite_differences(levels, act):
+    shape, params, probs, Ds, cx, rs = _small(levels=levels, act=act)
     loss, grads = mgnet.loss_and_grad(params, shape, probs, Ds, cx, rs)
     rng = np.random.default_rng(5)
     for trial in range(3):
         d = {k: rng.standard_normal(v.shape) for k, v in params.items()}
-        h = 1e-6
+        h = 1e-7
         lp = mgnet.loss_and_grad({k: v + h * d[k] for k, v in params.items()}, shape, probs, Ds, cx, rs)[0]
         lm = mgnet.loss_and_grad({k: v - h * d[k] for k, v in params.items()}, shape, probs, Ds, cx, rs)[0]
         fd = (lp - lm) / (2 * h)
