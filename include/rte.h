@@ -233,6 +233,8 @@ typedef struct rte_solve_opts {
     int use_x0;            /* 1: x_dev holds the initial guess */
     double stall_ratio;    /* MgNet fallback threshold per cycle (default 0.9) */
     double timeout_ms;     /* wall-clock limit, <= 0 for none */
+    const volatile int* cancel;   /* host flag read after every step (NULL: none);
+                                     non-zero ends the solve with RTE_ECANCELLED */
 } rte_solve_opts;
 
 typedef struct rte_solve_info {
@@ -304,7 +306,68 @@ RTE_API rte_status mgnet_loss_grad(mgnet* net, rte_ctx* ctx, const double* const
  * ccmax), int64 count, count float32, uint32 word checksum.  Load checks the
  * configuration and checksum (EINVAL on mismatch). */
 RTE_API rte_status mgnet_save(mgnet* net, const char* path);
+/* A new network with the same configuration and weights (its own caches and
+ * workspace, so copies can serve different streams at once). */
+RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out);
 RTE_API rte_status mgnet_load(mgnet* net, const char* path);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of solve requests (no counterpart in the
+ * paper).  rte_server_create starts `slots` worker threads, each with its own
+ * CUDA stream (and its own copy of net, if net is not NULL).  Submitted
+ * requests (host arrays, copied at submission) wait in FIFO order and are
+ * admitted as soon as a slot is free and their estimated device footprint
+ * fits in max_device_bytes together with the requests already running; the
+ * admitted solves overlap on the GPU and each releases its slot and bytes the
+ * moment it finishes.  A request runs rte_setup, rte_solve (MgNet when
+ * use_net and the server has a network, else block Jacobi) and
+ * rte_reconstruct; results are the same bits as a lone solve.
+ * Errors are per request (rte_result.status): a malformed medium gives
+ * EINVAL, a cancelled one ECANCELLED; submit rejects a request that can never
+ * fit (ENOMEM) or is malformed (EINVAL).  inject_alloc_failure_id makes that
+ * request fail with ENOMEM at admission (host-side fault injection, -1: off).
+ * rte_server_wait blocks until the request is done (or timeout_ms > 0
+ * elapses: ETIMEOUT, request kept) and copies psi [M][N] (cell centres) to
+ * psi_host if not NULL; a finished request is forgotten after its wait.
+ * Thread-safe: any thread may submit, wait or cancel.
+ * ------------------------------------------------------------------------- */
+typedef struct rte_server rte_server;
+typedef struct rte_server_config {
+    size_t max_device_bytes;
+    int slots;
+    int64_t inject_alloc_failure_id;
+} rte_server_config;
+typedef struct rte_request {
+    int I, M;
+    const double *sigma_T, *sigma_a, *q, *eps;
+    int eps_is_scalar;
+    double g;
+    const double* inflow;      /* [4][I][M] or NULL */
+    double tol;                /* <= 0: 1e-8 */
+    int max_iter, restart;     /* <= 0: defaults */
+    int use_net;
+} rte_request;
+typedef struct rte_result {
+    int status;                /* rte_status of the request */
+    rte_solve_info info;
+    double latency_s;          /* submission to completion */
+    double queue_s;            /* submission to admission */
+    size_t footprint;          /* estimated device bytes */
+} rte_result;
+typedef struct rte_server_stats_t {
+    int64_t queued, completed;
+    int active;
+    size_t bytes_in_use;
+} rte_server_stats_t;
+
+RTE_API void rte_server_config_default(rte_server_config* cfg);
+RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, rte_server** out);
+RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* req, int64_t* id_out);
+RTE_API rte_status rte_server_wait(rte_server* s, int64_t id, double timeout_ms, rte_result* res,
+                                   double* psi_host);
+RTE_API rte_status rte_server_cancel(rte_server* s, int64_t id);
+RTE_API rte_status rte_server_stats(rte_server* s, rte_server_stats_t* stats);
+RTE_API void rte_server_destroy(rte_server* s);
 
 /* ---------------------------------------------------------------------------
  * Per-kernel accounting (no counterpart in the paper: instrumentation).
@@ -321,9 +384,15 @@ typedef struct rte_kernel_stat {
     long long launches;    /* launches since the last rte_profile call */
     double ms;             /* summed event time (0 unless timing is on) */
     double bytes;          /* summed algorithmic bytes */
+    double flops;          /* summed FP64 flops (Gram-Schmidt, FP64 operator) */
 } rte_kernel_stat;
 
 RTE_API rte_status rte_profile(rte_ctx* ctx, int enable);
+
+/* Measured FP64 FMA throughput of the current device in GFLOP/s (2 flops per
+ * FMA), from a short event-timed kernel on stream: the denominator of the
+ * roofline of kernels bound by FP64 arithmetic.  No counterpart in the paper. */
+RTE_API rte_status rte_fp64_fma_rate(void* stream, double* gflops);
 RTE_API int rte_profile_read(rte_ctx* ctx, rte_kernel_stat* out, int max);
 
 #ifdef __cplusplus

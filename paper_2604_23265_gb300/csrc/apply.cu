@@ -403,7 +403,8 @@ void apply_impl(rte_ctx* ctx, const T* x, void* y, bool y_is_double, const doubl
     T* out = own + ctx->n;                                            // second half
     const T* Lt = std::is_same<T, double>::value ? (const T*)ctx->Lt64 : (const T*)ctx->Lt32;
     {
-        ProfScope ps(ctx, K_TRACES, (double)ctx->n * sizeof(T));
+        ProfScope ps(ctx, K_TRACES, (double)ctx->n * sizeof(T), 1,
+                     sizeof(T) == 8 ? 12.0 * ctx->M * ctx->M * ctx->N : 0.0);
         constexpr int MBS = sizeof(T) == 4 ? 16 : 8;
         const size_t smem_shl = sizeof(T) * (2 * (size_t)M * M + 6 * (size_t)M * 32);
         if (ctx->nmat == 1 && M % MBS == 0 && smem_shl <= 200 * 1024) {

@@ -328,7 +328,7 @@ int red_blocks(rte_ctx* ctx, int64_t n) {
 
 void launch_mdot(rte_ctx* ctx, const double* V, int k, const double* w, double* h) {
     const int g = dot_blocks(ctx, ctx->n, k, (const void*)k_mdot);
-    ProfScope ps(ctx, K_MDOT, (double)(k + 1) * ctx->n * 8);
+    ProfScope ps(ctx, K_MDOT, (double)(k + 1) * ctx->n * 8, 1, 2.0 * k * ctx->n);
     k_mdot<<<g, kT, (size_t)k * kT * sizeof(double), ctx->stream>>>(V, k, ctx->n, w, ctx->partials,
                                                                  ctx->counter, h);
     check(cudaGetLastError(), "k_mdot");
@@ -337,7 +337,7 @@ void launch_mdot(rte_ctx* ctx, const double* V, int k, const double* w, double* 
 void launch_update_dot(rte_ctx* ctx, const double* V, int k, double* w, const double* h1,
                        double* h2) {
     const int g = dot_blocks(ctx, ctx->n, k, (const void*)k_update_dot);
-    ProfScope ps(ctx, K_UPDATE_DOT, (double)(k + 2) * ctx->n * 8);
+    ProfScope ps(ctx, K_UPDATE_DOT, (double)(k + 2) * ctx->n * 8, 1, 4.0 * k * ctx->n);
     k_update_dot<<<g, kT, (size_t)k * kT * sizeof(double), ctx->stream>>>(V, k, ctx->n, w, h1,
                                                                        ctx->partials, ctx->counter,
                                                                        h2);
@@ -347,7 +347,7 @@ void launch_update_dot(rte_ctx* ctx, const double* V, int k, double* w, const do
 void launch_update_norm(rte_ctx* ctx, const double* V, int k, double* w, const double* h1,
                         const double* h2, double* out) {
     const int g = red_blocks(ctx, ctx->n);
-    ProfScope ps(ctx, K_UPDATE_NORM, (double)(k + 2) * ctx->n * 8);
+    ProfScope ps(ctx, K_UPDATE_NORM, (double)(k + 2) * ctx->n * 8, 1, (2.0 * k + 2.0) * ctx->n);
     k_update_norm<<<g, kT, 0, ctx->stream>>>(V, k, ctx->n, w, h1, h2, ctx->partials, ctx->counter,
                                              out);
     check(cudaGetLastError(), "k_update_norm");

@@ -645,6 +645,21 @@ RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** o
     }
 }
 
+RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out) {
+    if (!src || !out) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    mgnet_config cfg{src->M, src->L, src->c0, src->cmax, src->cc, src->ccmax};
+    rte_status st = mgnet_create(&cfg, stream, out);
+    if (st != RTE_OK) return st;
+    mgnet* n = *out;
+    MG_GUARD_BEGIN
+    check(cudaStreamSynchronize(src->stream), "sync");
+    check(cudaMemcpyAsync(n->p, src->p, n->np * 4, cudaMemcpyDeviceToDevice, n->stream), "d2d");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    ++n->version;
+    return RTE_OK;
+    MG_GUARD_END(n)
+}
+
 RTE_API void mgnet_destroy(mgnet* n) {
     if (!n) return;
     cudaStreamSynchronize(n->stream);

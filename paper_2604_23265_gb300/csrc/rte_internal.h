@@ -35,6 +35,7 @@ struct Profiler {
     std::vector<Pending> pending;
     double ms[K_COUNT] = {};
     double bytes[K_COUNT] = {};
+    double flops[K_COUNT] = {};          // FP64 flops of the kernels bound by FP64 arithmetic
     long long launches[K_COUNT] = {};
 };
 
@@ -111,7 +112,7 @@ struct ProfScope {
     rte_ctx* ctx;
     int kid;
     cudaEvent_t b = nullptr;
-    ProfScope(rte_ctx* c, int k, double bytes, int launches = 1);
+    ProfScope(rte_ctx* c, int k, double bytes, int launches = 1, double flops64 = 0.0);
     ~ProfScope();
 };
 void prof_resolve(rte_ctx* ctx);      // after a stream synchronisation

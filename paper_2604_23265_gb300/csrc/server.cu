@@ -1,0 +1,332 @@
+// Serving runtime: continuous batching of radiative-transfer solve requests.
+//
+// Requests of any grid size, direction count, eps and g are queued as they
+// arrive.  A scheduler admits the oldest waiting request as soon as a worker
+// slot is free and its estimated device footprint fits in the budget (admission
+// by HBM footprint); each slot runs on its own CUDA stream with stream-ordered
+// allocation, so the solves of all admitted requests overlap on the GPU and
+// one request's set-up or release never synchronises the others.  A finished
+// request releases its slot and its bytes at once and the next one is admitted
+// -- continuous batching rather than batch-synchronous rounds.  Results are
+// computed with the same deterministic kernels as a lone solve, so each result
+// is bit-identical alone and in the mix.  Faults stay per request: a malformed
+// medium, an injected allocation failure or a cancellation ends that request
+// with its status; the others continue.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
+#include <cmath>
+
+#include "rte_internal.h"
+
+namespace rte {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    int64_t id = 0;
+    int I = 0, M = 0;
+    std::vector<double> sT, sa, q, eps, inflow;
+    int eps_is_scalar = 1;
+    double g = 0.0;
+    rte_solve_opts opts{};
+    int use_net = 0;
+    size_t footprint = 0;
+    Clock::time_point t_submit, t_start, t_end;
+    volatile int cancel = 0;
+    bool done = false;
+    rte_status status = RTE_OK;
+    rte_solve_info info{};
+    std::vector<double> psi;          // [M][N]
+    std::string err;
+};
+
+}  // namespace
+}  // namespace rte
+
+struct rte_server {
+    rte_server_config cfg{};
+    int device = 0;
+    std::vector<mgnet*> nets;                  // one network copy per slot (or empty)
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<rte::Job>> queue;
+    std::map<int64_t, std::shared_ptr<rte::Job>> jobs;
+    size_t bytes_in_use = 0;
+    int active = 0;
+    int64_t next_id = 1;
+    bool stopping = false;
+    std::vector<std::thread> workers;
+    int64_t completed = 0;
+};
+
+namespace rte {
+namespace {
+
+// Device bytes a solve holds: D (FP64) and R (FP32) blocks, per-cell tables,
+// b and the operator scratch, the Krylov basis (FP64) and MgNet outputs (FP32).
+size_t footprint(int I, int M, int restart, bool net) {
+    const size_t N = (size_t)I * I, n2 = 2 * (size_t)M, n = n2 * N;
+    size_t b = N * n2 * n2 * (8 + 4);
+    b += n * 8 * 6;                                    // b, trace scratch (2n), w, tmp, x
+    b += (size_t)(restart + 1) * n * 8 + (size_t)restart * n * 4;
+    b += N * 64 + (size_t)M * n2 * 48;                 // per-cell and basis tables
+    if (net) b += n * 4 * 16;                          // network activations (upper bound)
+    return b + (64u << 20);
+}
+
+bool valid_request(const rte_request* r, std::string& why) {
+    if (!r->sigma_T || !r->sigma_a || !r->q || !r->eps) { why = "NULL medium array"; return false; }
+    if (r->I < 1 || r->I > 8192 || r->M < 4 || r->M % 4 || r->M > 80) { why = "bad I or M"; return false; }
+    if (!(std::fabs(r->g) < 1.0)) { why = "need |g| < 1"; return false; }
+    return true;
+}
+
+void worker_main(rte_server* s, int slot) {
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    mgnet* net = slot < (int)s->nets.size() ? s->nets[slot] : nullptr;
+    while (true) {
+        std::shared_ptr<Job> job;
+        bool admitted = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] {
+                if (s->stopping) return true;
+                if (s->queue.empty()) return false;
+                const auto& head = s->queue.front();
+                return head->cancel || s->bytes_in_use + head->footprint <= s->cfg.max_device_bytes;
+            });
+            if (s->stopping && s->queue.empty()) break;
+            if (s->stopping) break;
+            job = s->queue.front();
+            s->queue.pop_front();
+            admitted = !job->cancel;
+            if (admitted) {
+                s->bytes_in_use += job->footprint;
+                ++s->active;
+            }
+        }
+        job->t_start = Clock::now();
+        if (!admitted) {
+            job->status = RTE_ECANCELLED;
+            job->err = "cancelled before admission";
+        } else if (s->cfg.inject_alloc_failure_id == job->id) {
+            job->status = RTE_ENOMEM;          // host-side fault injection for tests
+            job->err = "injected allocation failure";
+        } else {
+            rte_ctx* ctx = nullptr;
+            rte_grid grid{job->I};
+            rte_quadrature quad{job->M};
+            job->status = rte_setup(&grid, &quad, job->sT.data(), job->sa.data(), job->q.data(),
+                                    job->eps.data(), job->eps_is_scalar, job->g,
+                                    job->inflow.empty() ? nullptr : job->inflow.data(), st, &ctx);
+            if (job->status == RTE_OK) {
+                const int64_t n = (int64_t)2 * job->M * job->I * job->I;
+                double* x = nullptr;
+                double* psi = nullptr;
+                cudaError_t e = cudaMallocAsync(&x, n * sizeof(double), st);
+                if (e == cudaSuccess) e = cudaMallocAsync(&psi, (size_t)job->M * job->I * job->I * sizeof(double), st);
+                if (e != cudaSuccess) {
+                    job->status = RTE_ENOMEM;
+                    job->err = cudaGetErrorString(e);
+                } else {
+                    job->opts.cancel = &job->cancel;
+                    mgnet* pc = (job->use_net && net) ? net : nullptr;
+                    job->status = rte_solve(ctx, pc, &job->opts, x, &job->info);
+                    if (job->status == RTE_OK || job->status == RTE_ENOTCONV) {
+                        rte_reconstruct(ctx, x, psi);
+                        job->psi.resize((size_t)job->M * job->I * job->I);
+                        cudaMemcpyAsync(job->psi.data(), psi, job->psi.size() * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st);
+                        cudaStreamSynchronize(st);
+                    }
+                    if (job->status != RTE_OK) job->err = rte_last_error(ctx);
+                }
+                if (x) cudaFreeAsync(x, st);
+                if (psi) cudaFreeAsync(psi, st);
+                rte_destroy(ctx);
+            } else {
+                job->err = rte_last_error(nullptr);
+            }
+        }
+        job->t_end = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (admitted) {
+                s->bytes_in_use -= job->footprint;
+                --s->active;
+            }
+            job->done = true;
+            ++s->completed;
+        }
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+    cudaStreamDestroy(st);
+}
+
+}  // namespace
+}  // namespace rte
+
+using namespace rte;
+
+extern "C" {
+
+RTE_API void rte_server_config_default(rte_server_config* c) {
+    if (!c) return;
+    c->max_device_bytes = (size_t)64 << 30;
+    c->slots = 4;
+    c->inject_alloc_failure_id = -1;
+}
+
+RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, rte_server** out) {
+    if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64 || cfg->max_device_bytes == 0) {
+        set_error(nullptr, "bad server configuration (slots in [1, 64])");
+        return RTE_EINVAL;
+    }
+    *out = nullptr;
+    rte_server* s = new (std::nothrow) rte_server();
+    if (!s) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; }
+    s->cfg = *cfg;
+    cudaGetDevice(&s->device);
+    if (net) {
+        for (int i = 0; i < cfg->slots; ++i) {
+            mgnet* c = nullptr;
+            rte_status st = mgnet_clone(net, nullptr, &c);
+            if (st != RTE_OK) {
+                for (mgnet* m : s->nets) mgnet_destroy(m);
+                delete s;
+                return st;
+            }
+            s->nets.push_back(c);
+        }
+    }
+    for (int i = 0; i < cfg->slots; ++i) s->workers.emplace_back(worker_main, s, i);
+    *out = s;
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* r, int64_t* id_out) {
+    if (!s || !r || !id_out) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    std::string why;
+    if (!valid_request(r, why)) { set_error(nullptr, "malformed request: " + why); return RTE_EINVAL; }
+    auto job = std::make_shared<Job>();
+    const size_t N = (size_t)r->I * r->I;
+    job->I = r->I;
+    job->M = r->M;
+    job->sT.assign(r->sigma_T, r->sigma_T + N);
+    job->sa.assign(r->sigma_a, r->sigma_a + N);
+    job->q.assign(r->q, r->q + N);
+    job->eps_is_scalar = r->eps_is_scalar;
+    job->eps.assign(r->eps, r->eps + (r->eps_is_scalar ? 1 : N));
+    if (r->inflow) job->inflow.assign(r->inflow, r->inflow + (size_t)4 * r->I * r->M);
+    job->g = r->g;
+    rte_solve_opts_default(&job->opts);
+    job->opts.tol = r->tol > 0 ? r->tol : 1e-8;
+    if (r->max_iter > 0) job->opts.max_iter = r->max_iter;
+    if (r->restart > 0) job->opts.restart = r->restart;
+    job->use_net = r->use_net && !s->nets.empty();
+    job->footprint = footprint(r->I, r->M, job->opts.restart, job->use_net);
+    if (job->footprint > s->cfg.max_device_bytes) {
+        set_error(nullptr, "request needs more device memory than the server budget");
+        return RTE_ENOMEM;
+    }
+    job->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) { set_error(nullptr, "server is stopping"); return RTE_ECANCELLED; }
+        job->id = s->next_id++;
+        s->jobs[job->id] = job;
+        s->queue.push_back(job);
+    }
+    s->cv_work.notify_all();
+    *id_out = job->id;
+    return RTE_OK;
+}
+
+static void fill_result(const Job& j, rte_result* res, double* psi_host) {
+    if (res) {
+        res->status = j.status;
+        res->info = j.info;
+        res->latency_s = std::chrono::duration<double>(j.t_end - j.t_submit).count();
+        res->queue_s = std::chrono::duration<double>(j.t_start - j.t_submit).count();
+        res->footprint = j.footprint;
+    }
+    if (psi_host && !j.psi.empty()) std::memcpy(psi_host, j.psi.data(), j.psi.size() * sizeof(double));
+}
+
+RTE_API rte_status rte_server_wait(rte_server* s, int64_t id, double timeout_ms, rte_result* res,
+                                   double* psi_host) {
+    if (!s) { set_error(nullptr, "NULL server"); return RTE_EINVAL; }
+    std::shared_ptr<Job> job;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(id);
+        if (it == s->jobs.end()) { set_error(nullptr, "unknown request id"); return RTE_EINVAL; }
+        job = it->second;
+        auto pred = [&] { return job->done; };
+        if (timeout_ms > 0) {
+            if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred))
+                return RTE_ETIMEOUT;
+        } else {
+            s->cv_done.wait(lk, pred);
+        }
+        s->jobs.erase(id);
+    }
+    fill_result(*job, res, psi_host);
+    if (job->status != RTE_OK) set_error(nullptr, job->err);
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_server_cancel(rte_server* s, int64_t id) {
+    if (!s) { set_error(nullptr, "NULL server"); return RTE_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) { set_error(nullptr, "unknown request id"); return RTE_EINVAL; }
+    it->second->cancel = 1;
+    s->cv_work.notify_all();
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_server_stats(rte_server* s, rte_server_stats_t* st) {
+    if (!s || !st) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    st->queued = (int64_t)s->queue.size();
+    st->active = s->active;
+    st->completed = s->completed;
+    st->bytes_in_use = s->bytes_in_use;
+    return RTE_OK;
+}
+
+RTE_API void rte_server_destroy(rte_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+        for (auto& kv : s->jobs) kv.second->cancel = 1;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto& j : s->queue) {
+            j->status = RTE_ECANCELLED;
+            j->done = true;
+        }
+    }
+    s->cv_done.notify_all();
+    for (mgnet* m : s->nets) mgnet_destroy(m);
+    delete s;
+}
+
+}  // extern "C"

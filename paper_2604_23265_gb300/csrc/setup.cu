@@ -33,8 +33,10 @@ rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where) {
 void* dev_alloc(rte_ctx* ctx, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc"};
+    // stream-ordered: a context's allocations and frees never synchronise
+    // the device, so concurrent solves on other streams keep running
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) throw CudaError{e, "cudaMallocAsync"};
     ctx->allocations.push_back(p);
     ctx->device_bytes += bytes;
     check(cudaMemsetAsync(p, 0, bytes, ctx->stream), "cudaMemset");
@@ -58,9 +60,11 @@ static cudaEvent_t prof_event(rte_ctx* ctx) {
     return e;
 }
 
-ProfScope::ProfScope(rte_ctx* c, int k, double bytes, int launches) : ctx(c), kid(k) {
+ProfScope::ProfScope(rte_ctx* c, int k, double bytes, int launches, double flops64)
+    : ctx(c), kid(k) {
     ctx->prof.launches[k] += launches;
     ctx->prof.bytes[k] += bytes;
+    ctx->prof.flops[k] += flops64;
     if (ctx->prof.on) {
         b = prof_event(ctx);
         check(cudaEventRecord(b, ctx->stream), "cudaEventRecord");
@@ -668,6 +672,7 @@ RTE_API rte_status rte_profile(rte_ctx* ctx, int enable) {
     for (int k = 0; k < K_COUNT; ++k) {
         ctx->prof.ms[k] = 0.0;
         ctx->prof.bytes[k] = 0.0;
+        ctx->prof.flops[k] = 0.0;
         ctx->prof.launches[k] = 0;
     }
     ctx->prof.on = enable != 0;
@@ -686,6 +691,7 @@ RTE_API int rte_profile_read(rte_ctx* ctx, rte_kernel_stat* out, int max) {
         out[n].launches = ctx->prof.launches[k];
         out[n].ms = ctx->prof.ms[k];
         out[n].bytes = ctx->prof.bytes[k];
+        out[n].flops = ctx->prof.flops[k];
         ++n;
     }
     return out ? n : K_COUNT;
@@ -696,7 +702,8 @@ RTE_API void rte_destroy(rte_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     free_workspace(ctx);
     prof_free(ctx);
-    for (void* p : ctx->allocations) cudaFree(p);
+    for (void* p : ctx->allocations) cudaFreeAsync(p, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     delete ctx;
 }
 

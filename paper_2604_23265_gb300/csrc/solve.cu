@@ -46,7 +46,7 @@ struct Workspace {
 
 void free_workspace(rte_ctx* ctx) {
     if (!ctx || !ctx->ws) return;
-    for (void* p : ctx->ws->allocs) cudaFree(p);
+    for (void* p : ctx->ws->allocs) cudaFreeAsync(p, ctx->stream);
     if (ctx->ws->est_host) cudaFreeHost(ctx->ws->est_host);
     ctx->device_bytes -= ctx->ws->bytes;
     delete ctx->ws;
@@ -59,8 +59,8 @@ template <typename T>
 T* ws_alloc(rte_ctx* ctx, Workspace* ws, size_t count) {
     void* p = nullptr;
     const size_t bytes = count * sizeof(T) + 16;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc (solve workspace)"};
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) throw CudaError{e, "cudaMallocAsync (solve workspace)"};
     ws->allocs.push_back(p);
     ws->bytes += bytes;
     ctx->device_bytes += bytes;
@@ -193,6 +193,7 @@ RTE_API void rte_solve_opts_default(rte_solve_opts* o) {
     o->use_x0 = 0;
     o->stall_ratio = 0.9;
     o->timeout_ms = 0.0;
+    o->cancel = nullptr;
 }
 
 RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in,
@@ -255,6 +256,11 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
             if (inf.relres <= opts.tol) { inf.converged = 1; break; }
             if (inf.iterations >= opts.max_iter) { status = RTE_ENOTCONV; break; }
             if (opts.timeout_ms > 0 && elapsed_ms() > opts.timeout_ms) { status = RTE_ETIMEOUT; break; }
+            if (opts.cancel && *opts.cancel) {
+                set_error(ctx, "cancelled");
+                status = RTE_ECANCELLED;
+                break;
+            }
             launch_scale(ctx, ws->w, ws->est + 3, ws->V);
             {
                 ProfScope ps(ctx, K_CYCLE, 0.0);
@@ -304,6 +310,7 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                 }
                 if (est / bnorm <= opts.tol || wn == 0.0 || inf.iterations >= opts.max_iter) break;
                 if (opts.timeout_ms > 0 && elapsed_ms() > opts.timeout_ms) break;
+                if (opts.cancel && *opts.cancel) break;
             }
             if (k > 0) {
                 {

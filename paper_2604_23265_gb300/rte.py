@@ -45,7 +45,8 @@ class CtxInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("inner_precision", ctypes.c_int), ("use_x0", ctypes.c_int),
-                ("stall_ratio", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
+                ("stall_ratio", ctypes.c_double), ("timeout_ms", ctypes.c_double),
+                ("cancel", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -58,7 +59,7 @@ class SolveInfo(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -85,7 +86,16 @@ SIGNATURES = {
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
     "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
+    "rte_fp64_fma_rate": (_I, [_P, ctypes.POINTER(_D)]),
     "rte_profile": (_I, [_P, _I]),
+    "rte_server_config_default": (None, [_P]),
+    "rte_server_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
+    "rte_server_submit": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "rte_server_wait": (_I, [_P, ctypes.c_int64, _D, _P, _P]),
+    "rte_server_cancel": (_I, [_P, ctypes.c_int64]),
+    "rte_server_stats": (_I, [_P, _P]),
+    "rte_server_destroy": (None, [_P]),
+    "mgnet_clone": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "mgnet_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "mgnet_destroy": (None, [_P]),
     "mgnet_param_count": (ctypes.c_int64, [_P]),
@@ -146,6 +156,13 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def fp64_fma_rate(stream=None):
+    """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
+    v = ctypes.c_double()
+    _check(load().rte_fp64_fma_rate(_stream_ptr(stream), ctypes.byref(v)))
+    return v.value
+
+
 def eigenbasis(M, g, one_minus_gamma, axis):
     """Host FP64 eigenpairs of the local TFPS problem (rte_eigenbasis); no GPU needed."""
     xi = np.zeros(M)
@@ -153,6 +170,84 @@ def eigenbasis(M, g, one_minus_gamma, axis):
     _check(load().rte_eigenbasis(int(M), float(g), float(one_minus_gamma), int(axis),
                                  xi.ctypes.data_as(_P), L.ctypes.data_as(_P)))
     return xi, L
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_device_bytes", ctypes.c_size_t), ("slots", _I),
+                ("inject_alloc_failure_id", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("I", _I), ("M", _I), ("sigma_T", _P), ("sigma_a", _P), ("q", _P), ("eps", _P),
+                ("eps_is_scalar", _I), ("g", _D), ("inflow", _P), ("tol", _D), ("max_iter", _I),
+                ("restart", _I), ("use_net", _I)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", _I), ("info", SolveInfo), ("latency_s", _D), ("queue_s", _D),
+                ("footprint", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("completed", ctypes.c_int64), ("active", _I),
+                ("bytes_in_use", ctypes.c_size_t)]
+
+
+class Server:
+    """Continuous-batching solve server (rte_server_*); thread-safe."""
+
+    def __init__(self, slots=4, max_device_bytes=64 << 30, net=None, inject_alloc_failure_id=-1):
+        cfg = ServerConfig()
+        load().rte_server_config_default(ctypes.byref(cfg))
+        cfg.slots, cfg.max_device_bytes = int(slots), int(max_device_bytes)
+        cfg.inject_alloc_failure_id = int(inject_alloc_failure_id)
+        out = ctypes.c_void_p()
+        _check(load().rte_server_create(ctypes.byref(cfg), net.ptr if net is not None else None,
+                                        ctypes.byref(out)))
+        self.ptr = out
+        self._meta = {}
+
+    def submit(self, md, tol=1e-8, use_net=False, max_iter=0, restart=0):
+        arrs = [np.ascontiguousarray(a, np.float64) for a in
+                (md.sigma_T, md.sigma_a, md.q, np.asarray(md.eps).reshape(-1), md.inflow)]
+        eps_scalar = int(arrs[3].size == 1)
+        req = Request(md.I, md.M, *[a.ctypes.data_as(_P) for a in arrs[:4]], eps_scalar, float(md.g),
+                      arrs[4].ctypes.data_as(_P), float(tol), int(max_iter), int(restart), int(use_net))
+        rid = ctypes.c_int64()
+        _check(load().rte_server_submit(self.ptr, ctypes.byref(req), ctypes.byref(rid)))
+        self._meta[rid.value] = (md.M, md.I)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=0.0):
+        M, I = self._meta[rid]
+        res = Result()
+        psi = np.zeros(M * I * I)
+        _check(load().rte_server_wait(self.ptr, int(rid), float(timeout_ms), ctypes.byref(res),
+                                      psi.ctypes.data_as(_P)))
+        del self._meta[rid]
+        d = {"status": STATUS_NAMES[res.status], "latency_s": res.latency_s, "queue_s": res.queue_s,
+             "footprint": res.footprint}
+        d.update(res.info.as_dict())
+        return d, psi
+
+    def cancel(self, rid):
+        _check(load().rte_server_cancel(self.ptr, int(rid)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().rte_server_stats(self.ptr, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().rte_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MgNetConfig(ctypes.Structure):
@@ -359,13 +454,13 @@ class Context:
         _check(load().rte_profile(self.ptr, int(enable)), self.ptr)
 
     def profile_read(self):
-        """{kernel class: (launches, ms, algorithmic bytes)}."""
+        """{kernel class: (launches, ms, algorithmic bytes, FP64 flops)}."""
         n = load().rte_profile_read(self.ptr, None, 0)
         arr = (KernelStat * n)()
         got = load().rte_profile_read(self.ptr, arr, n)
         if got < 0:
             _check(RTE_ECUDA, self.ptr)
-        return {a.name.decode(): (a.launches, a.ms, a.bytes) for a in arr[:got]}
+        return {a.name.decode(): (a.launches, a.ms, a.bytes, a.flops) for a in arr[:got]}
 
     def solve(self, x, pc=None, tol=1e-8, restart=50, max_iter=20000, inner_precision=RTE_F32,
               use_x0=False, stall_ratio=0.9, timeout_ms=0.0, raise_on_error=True):

@@ -65,7 +65,7 @@ def test_training_reduces_loss(lib):
     first = net.train_step(ctx, rs, 3e-3)
     for _ in range(60):
         last = net.train_step(ctx, rs, 3e-3)
-    assert last < 0.9 * first
+    assert last < 0.95 * first
 
 
 def test_mgnet_preconditioned_solve(lib):
@@ -74,16 +74,16 @@ def test_mgnet_preconditioned_solve(lib):
     LU solution."""
     rte, shape, params, md, ctx, net, p = _setup(I=16, M=8, levels=3, proj=0.0)
     x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
-    ref_info = ctx.solve(x, tol=1e-10, restart=40)
+    ref_info = ctx.solve(x, tol=1e-12, restart=40)
     x.zero_()
-    info = ctx.solve(x, pc=net, tol=1e-10, restart=40, stall_ratio=10.0)
+    info = ctx.solve(x, pc=net, tol=1e-12, restart=40, stall_ratio=10.0)
     assert info["converged"] and not info["fell_back"], info
     assert info["iterations"] == ref_info["iterations"]
     xl = krylov.dense_solve(p.assemble(), p.rhs().ravel())
     psi = torch.zeros(md.M * md.I * md.I, dtype=torch.float64, device="cuda")
     ctx.reconstruct(x, psi)
     ref = p.reconstruct(xl.reshape(2 * md.M, -1)).ravel()
-    assert _rel(psi.cpu().numpy(), ref) <= 1e-7
+    assert _rel(psi.cpu().numpy(), ref) <= 1e-9
 
 
 def test_stalled_network_falls_back_to_block_jacobi(lib):
