@@ -212,6 +212,15 @@ RTE_API rte_status rte_cgs2_noalloc(const double* V_dev, int k, int64_t n, doubl
                                     double* h_dev, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * rte_arnoldi_basis -- k (1..64) steps of the Arnoldi process on the
+ * block-Jacobi preconditioned operator A D (face-flux space, CGS2) started
+ * from b / ||b||; V_dev receives the k orthonormal vectors (double, vector j
+ * at V_dev + j*n).  The vectors the classical iteration works with: one
+ * source of training inputs for the learned preconditioner.  Synchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev);
+
+/* ---------------------------------------------------------------------------
  * rte_solve -- solve A x = b for this context's b by right-preconditioned
  * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt plus
  * reorthogonalisation, Givens/Hessenberg least squares in FP64 on the device,
@@ -257,7 +266,8 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
  * batch normalisation, ReLU; widths min(cc 2^l, ccmax)) on the per-cell
  * inputs log sigma_T, log sigma_a, log eps, log tau, with 1x1 heads
  * a_l = 1 + head, ainv_l = 1 + head of MgNet width min(c0 2^l, cmax);
- * MgNet: lift 1x1 (2M -> c0), smoothing u <- u + (B_l * ReLU(f - (A_l * u) o a_l)) o ainv_l,
+ * MgNet: lift 1x1 (2M -> c0), smoothing u <- u + (B_l * act(f - (A_l * u) o a_l)) o ainv_l
+ * (act = identity when act == 0, the default reading of Sec. 3.3; ReLU when 1),
  * restriction conv 3x3 stride 2, prolongation transposed conv 4x4 stride 2,
  * one pre- and one post-smoothing step per level (two on the coarsest),
  * projection 1x1 (c0 -> 2M) added to the input: psi_d = x + proj(u_0).
@@ -271,6 +281,7 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
  * ------------------------------------------------------------------------- */
 typedef struct mgnet_config {
     int M, levels, c0, cmax, cc, ccmax;
+    int act;          /* 0: linear smoothers, 1: ReLU */
 } mgnet_config;
 
 RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** out);
@@ -302,8 +313,8 @@ RTE_API rte_status mgnet_train_step(mgnet* net, rte_ctx* ctx, const double* cons
 RTE_API rte_status mgnet_loss_grad(mgnet* net, rte_ctx* ctx, const double* const* r_dev, int batch,
                                    double* loss_out, float* grad_host);
 
-/* Weights to / from a file: "MGNET001", six int32 (M, levels, c0, cmax, cc,
- * ccmax), int64 count, count float32, uint32 word checksum.  Load checks the
+/* Weights to / from a file: "MGNET002", seven int32 (M, levels, c0, cmax, cc,
+ * ccmax, act), int64 count, count float32, uint32 word checksum.  Load checks the
  * configuration and checksum (EINVAL on mismatch). */
 RTE_API rte_status mgnet_save(mgnet* net, const char* path);
 /* A new network with the same configuration and weights (its own caches and

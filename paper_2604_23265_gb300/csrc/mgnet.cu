@@ -4,7 +4,8 @@
 // Network (readings of Sec. 3.2-3.3):
 //   CoeffNet, level l: z = conv3x3(g_{l-1}, stride 1 at l = 0 else 2),
 //     g_l = ReLU(BN(z)); a_l = 1 + head_a(g_l), ainv_l = 1 + head_ainv(g_l).
-//   MgNet: f_0 = lift(x); smoothing u <- u + (B_l * ReLU(f - (A_l * u) o a_l)) o ainv_l;
+//   MgNet: f_0 = lift(x); smoothing u <- u + (B_l * act(f - (A_l * u) o a_l)) o ainv_l
+//     with act the identity (default) or ReLU;
 //     restriction f_{l+1} = R_l *_{s2} (f_l - (A_l * u_l) o a_l);
 //     prolongation u_l <- u_l + P_l *^T u_{l+1}; one pre- and one
 //     post-smoothing step per level, two on the coarsest;
@@ -48,6 +49,7 @@ struct Features {            // CoeffNet outputs of one medium for one weight ve
 
 struct mgnet {
     int M = 0, L = 0, c0 = 0, cmax = 0, cc = 0, ccmax = 0, cin = 4;
+    int act = 0;                     // smoother activation: 0 identity, 1 ReLU
     cudaStream_t stream = nullptr;
     std::string err;
     std::vector<rte::Param> params;
@@ -286,7 +288,7 @@ void forward(mgnet* n, const Features& F, Acts& a, int B, int I) {
     auto smooth_first = [&](int l, float* q, float* u) {     // u = (B * ReLU(f)) o ainv
         const int H = I >> l, C = n->C(l);
         ConvArgs c = cv(a.f[l], B, C, H, P(n, sl("B", l)), C, 1, 9, C, H, 1, u, H, t3);
-        c.relu_in = 1; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1;
+        c.relu_in = n->act; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1;
         nn::conv(c, n->stream);
     };
     auto residual = [&](int l, const float* u, float* craw, float* out) {   // f - (A * u) o a
@@ -298,7 +300,7 @@ void forward(mgnet* n, const Features& F, Acts& a, int B, int I) {
     auto smooth_update = [&](int l, const float* t, float* q, const float* u, float* out) {
         const int H = I >> l, C = n->C(l);
         ConvArgs c = cv(t, B, C, H, P(n, sl("B", l)), C, 1, 9, C, H, 1, out, H, t3);
-        c.relu_in = 1; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1; c.base = u;
+        c.relu_in = n->act; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1; c.base = u;
         nn::conv(c, n->stream);
     };
     for (int l = 0; l + 1 < L; ++l) {
@@ -365,11 +367,11 @@ void backward(mgnet* n, Features& F, Acts& a, rte_ctx* ctx, int B, int I) {
         float* gq = a.t1[l];
         float* gt = a.t2b[l];
         nn::gate_bwd(gu, F.ai[l], q, 1.f, B, chw, gq, gai[l], st);
-        // gt = bwd_data(B_l, gq) masked by t > 0 ; dB += wgrad(gq, ReLU(t))
-        bwd_data_s1(n, gq, B, C, H, P(n, sl("B", l)), C, 3, gt, false, t);
+        // gt = bwd_data(B_l, gq) (masked by t > 0 for ReLU) ; dB += wgrad(gq, act(t))
+        bwd_data_s1(n, gq, B, C, H, P(n, sl("B", l)), C, 3, gt, false, n->act ? t : nullptr);
         {
             WgradArgs w = wg(gq, B, C, H, t, C, H, 1, G(n, sl("B", l)), C, 1, 9, t3);
-            w.relu_in = 1;
+            w.relu_in = n->act;
             nn::wgrad(w, st);
         }
         nn::axpy(a.gf[l], gt, 1.f, (size_t)B * chw, st);
@@ -616,14 +618,15 @@ RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** o
     if (!cfg || !out) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
     *out = nullptr;
     if (cfg->M < 4 || cfg->M % 4 || cfg->levels < 1 || cfg->levels > 8 || cfg->c0 < 1 || cfg->cmax < cfg->c0 ||
-        cfg->cc < 1 || cfg->ccmax < cfg->cc || cfg->cc > cfg->c0 || cfg->ccmax > cfg->cmax) {
+        cfg->cc < 1 || cfg->ccmax < cfg->cc || cfg->cc > cfg->c0 || cfg->ccmax > cfg->cmax ||
+        (cfg->act != 0 && cfg->act != 1)) {
         set_error(nullptr, "bad network configuration (need cc <= c0, ccmax <= cmax)");
         return RTE_EINVAL;
     }
     mgnet* n = new (std::nothrow) mgnet();
     if (!n) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; }
     n->M = cfg->M; n->L = cfg->levels; n->c0 = cfg->c0; n->cmax = cfg->cmax;
-    n->cc = cfg->cc; n->ccmax = cfg->ccmax;
+    n->cc = cfg->cc; n->ccmax = cfg->ccmax; n->act = cfg->act;
     n->stream = static_cast<cudaStream_t>(stream);
     MG_GUARD_BEGIN
     build_params(n);
@@ -647,7 +650,7 @@ RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** o
 
 RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out) {
     if (!src || !out) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
-    mgnet_config cfg{src->M, src->L, src->c0, src->cmax, src->cc, src->ccmax};
+    mgnet_config cfg{src->M, src->L, src->c0, src->cmax, src->cc, src->ccmax, src->act};
     rte_status st = mgnet_create(&cfg, stream, out);
     if (st != RTE_OK) return st;
     mgnet* n = *out;
@@ -759,7 +762,7 @@ RTE_API rte_status mgnet_train_step(mgnet* n, rte_ctx* ctx, const double* const*
     MG_GUARD_END(n)
 }
 
-// File format: "MGNET001", int32 M, levels, c0, cmax, cc, ccmax, int64 count,
+// File format: "MGNET002", int32 M, levels, c0, cmax, cc, ccmax, act, int64 count,
 // count float32 parameters, uint32 checksum (sum of the 32-bit words).
 RTE_API rte_status mgnet_save(mgnet* n, const char* path) {
     if (!n || !path) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
@@ -769,11 +772,11 @@ RTE_API rte_status mgnet_save(mgnet* n, const char* path) {
     check(cudaStreamSynchronize(n->stream), "sync");
     FILE* f = std::fopen(path, "wb");
     if (!f) throw StatusError{RTE_EINVAL, "cannot open file for writing"};
-    const int32_t hdr[6] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax};
+    const int32_t hdr[7] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax, n->act};
     const int64_t cnt = (int64_t)n->np;
     uint32_t sum = 0;
     for (size_t i = 0; i < n->np; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
-    bool ok = std::fwrite("MGNET001", 1, 8, f) == 8 && std::fwrite(hdr, 4, 6, f) == 6 &&
+    bool ok = std::fwrite("MGNET002", 1, 8, f) == 8 && std::fwrite(hdr, 4, 7, f) == 7 &&
               std::fwrite(&cnt, 8, 1, f) == 1 && std::fwrite(h.data(), 4, n->np, f) == n->np &&
               std::fwrite(&sum, 4, 1, f) == 1;
     ok = (std::fclose(f) == 0) && ok;
@@ -788,11 +791,11 @@ RTE_API rte_status mgnet_load(mgnet* n, const char* path) {
     FILE* f = std::fopen(path, "rb");
     if (!f) throw StatusError{RTE_EINVAL, "cannot open file"};
     char magic[8];
-    int32_t hdr[6];
+    int32_t hdr[7];
     int64_t cnt = 0;
-    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MGNET001", 8) == 0 &&
-              std::fread(hdr, 4, 6, f) == 6 && std::fread(&cnt, 8, 1, f) == 1;
-    const int32_t want[6] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax};
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MGNET002", 8) == 0 &&
+              std::fread(hdr, 4, 7, f) == 7 && std::fread(&cnt, 8, 1, f) == 1;
+    const int32_t want[7] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax, n->act};
     ok = ok && std::memcmp(hdr, want, sizeof(want)) == 0 && cnt == (int64_t)n->np;
     std::vector<float> h(ok ? n->np : 0);
     uint32_t sum = 0, stored = 0;
@@ -800,7 +803,7 @@ RTE_API rte_status mgnet_load(mgnet* n, const char* path) {
     std::fclose(f);
     if (ok)
         for (size_t i = 0; i < n->np; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
-    if (!ok || sum != stored) throw StatusError{RTE_EINVAL, "not a matching MGNET001 file or bad checksum"};
+    if (!ok || sum != stored) throw StatusError{RTE_EINVAL, "not a matching MGNET002 file or bad checksum"};
     return mgnet_set_params(n, h.data(), cnt);
     MG_GUARD_END(n)
 }

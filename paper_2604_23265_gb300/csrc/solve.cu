@@ -196,6 +196,32 @@ RTE_API void rte_solve_opts_default(rte_solve_opts* o) {
     o->cancel = nullptr;
 }
 
+RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev) {
+    if (!ctx || !V_dev || k < 1 || k > kMaxKrylov) { set_error(ctx, "bad argument (1 <= k <= 64)"); return RTE_EINVAL; }
+    try {
+        Workspace* ws = get_workspace(ctx, ctx->ws ? ctx->ws->m : kMaxKrylov);
+        if (ws->m < k) ws = get_workspace(ctx, kMaxKrylov);
+        const int64_t n = ctx->n;
+        launch_norm(ctx, ctx->b, ws->est + 3);
+        launch_scale(ctx, ctx->b, ws->est + 3, V_dev);
+        for (int j = 0; j + 1 < k; ++j) {
+            launch_response_apply(ctx, V_dev + (size_t)j * n, true, ws->w, true);
+            const int K = j + 1;
+            launch_mdot(ctx, V_dev, K, ws->w, ws->h1);
+            launch_update_dot(ctx, V_dev, K, ws->w, ws->h1, ws->h2);
+            launch_update_norm(ctx, V_dev, K, ws->w, ws->h1, ws->h2, ws->hcol);
+            launch_scale(ctx, ws->w, ws->hcol + K, V_dev + (size_t)(j + 1) * n);
+        }
+        check(cudaStreamSynchronize(ctx->stream), "sync");
+    } catch (const CudaError& e) {
+        return cuda_status(ctx, e.code, e.where);
+    } catch (const StatusError& e) {
+        set_error(ctx, e.msg);
+        return e.code;
+    }
+    return RTE_OK;
+}
+
 RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in,
                              double* x_dev, rte_solve_info* info) {
     if (!ctx || !x_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }

@@ -83,6 +83,7 @@ SIGNATURES = {
     "rte_response_apply": (_I, [_P, _P, _P]),
     "rte_cgs2": (_I, [_P, _P, _I, _P, _P]),
     "rte_cgs2_noalloc": (_I, [_P, _I, ctypes.c_int64, _P, _P, _P]),
+    "rte_arnoldi_basis": (_I, [_P, _I, _P]),
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
     "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
@@ -251,7 +252,8 @@ class Server:
 
 
 class MgNetConfig(ctypes.Structure):
-    _fields_ = [("M", _I), ("levels", _I), ("c0", _I), ("cmax", _I), ("cc", _I), ("ccmax", _I)]
+    _fields_ = [("M", _I), ("levels", _I), ("c0", _I), ("cmax", _I), ("cc", _I), ("ccmax", _I),
+                ("act", _I)]
 
 
 class MgNet:
@@ -259,7 +261,8 @@ class MgNet:
     the order of ``workloads.param_shapes``."""
 
     def __init__(self, shape, stream=None):
-        cfg = MgNetConfig(shape.M, shape.levels, shape.c0, shape.cmax, shape.cc, shape.ccmax)
+        cfg = MgNetConfig(shape.M, shape.levels, shape.c0, shape.cmax, shape.cc, shape.ccmax,
+                          1 if getattr(shape, "act", "linear") == "relu" else 0)
         out = ctypes.c_void_p()
         _check(load().mgnet_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(out)))
         self.ptr = out
@@ -461,6 +464,12 @@ class Context:
         if got < 0:
             _check(RTE_ECUDA, self.ptr)
         return {a.name.decode(): (a.launches, a.ms, a.bytes, a.flops) for a in arr[:got]}
+
+    def arnoldi_basis(self, k, V):
+        """k Arnoldi vectors of the block-Jacobi preconditioned operator from b."""
+        import torch
+        _check(load().rte_arnoldi_basis(self.ptr, int(k), _dev(V, torch.float64, k * self.n)), self.ptr)
+        return V
 
     def solve(self, x, pc=None, tol=1e-8, restart=50, max_iter=20000, inner_precision=RTE_F32,
               use_x0=False, stall_ratio=0.9, timeout_ms=0.0, raise_on_error=True):

@@ -61,11 +61,12 @@ def test_loss_and_gradients_match_oracle(lib, levels, batch):
 
 def test_training_reduces_loss(lib):
     rte, shape, params, md, ctx, net, p = _setup(I=16, M=8, levels=3, proj=0.0)
+    net.set_params(W.init_params(shape, seed=0, proj_scale=0.0, vcycle_scale=0.5))
     rs = [torch.tensor(W.random_vector(ctx.n, 40 + b), device="cuda") for b in range(4)]
     first = net.train_step(ctx, rs, 3e-3)
-    for _ in range(60):
+    for _ in range(100):
         last = net.train_step(ctx, rs, 3e-3)
-    assert last < 0.95 * first
+    assert last < 0.8 * first
 
 
 def test_mgnet_preconditioned_solve(lib):
@@ -83,7 +84,9 @@ def test_mgnet_preconditioned_solve(lib):
     psi = torch.zeros(md.M * md.I * md.I, dtype=torch.float64, device="cuda")
     ctx.reconstruct(x, psi)
     ref = p.reconstruct(xl.reshape(2 * md.M, -1)).ravel()
-    assert _rel(psi.cpu().numpy(), ref) <= 1e-9
+    assert _rel(psi.cpu().numpy(), ref) <= 1e-6          # cond(A) x tol on this medium
+    r = p.rhs().ravel() - p.apply(x.cpu().numpy().reshape(2 * md.M, -1)).ravel()
+    assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 2e-12
 
 
 def test_stalled_network_falls_back_to_block_jacobi(lib):
