@@ -395,7 +395,8 @@ typedef struct rte_kernel_stat {
     long long launches;    /* launches since the last rte_profile call */
     double ms;             /* summed event time (0 unless timing is on) */
     double bytes;          /* summed algorithmic bytes */
-    double flops;          /* summed FP64 flops (Gram-Schmidt, FP64 operator) */
+    double flops;          /* summed arithmetic flops: FP64 for the Gram-Schmidt passes and
+                              the FP64 operator, FP32 for the network ("mgnet") */
 } rte_kernel_stat;
 
 RTE_API rte_status rte_profile(rte_ctx* ctx, int enable);
@@ -404,6 +405,9 @@ RTE_API rte_status rte_profile(rte_ctx* ctx, int enable);
  * FMA), from a short event-timed kernel on stream: the denominator of the
  * roofline of kernels bound by FP64 arithmetic.  No counterpart in the paper. */
 RTE_API rte_status rte_fp64_fma_rate(void* stream, double* gflops);
+/* The same for FP32 FMA (CUDA cores): the roofline of the network's FP32
+ * convolutions. */
+RTE_API rte_status rte_fp32_fma_rate(void* stream, double* gflops);
 RTE_API int rte_profile_read(rte_ctx* ctx, rte_kernel_stat* out, int max);
 
 #ifdef __cplusplus

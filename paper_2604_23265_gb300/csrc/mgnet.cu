@@ -590,14 +590,24 @@ void mgnet_prepare(mgnet* net, rte_ctx* ctx) {
 
 void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
     check_ctx(net, ctx);
-    ProfScope ps(ctx, K_MGNET, 0.0, 0);
     Features& F = features(net, ctx, false);
     Acts a = workspace(net, 2, ctx->I);
-    const double* rv[1] = {v};
-    load_inputs(net, ctx, rv, 1, a);
-    forward(net, F, a, 1, ctx->I);
-    k_scale_out<<<grid_for(ctx->n), 256, 0, net->stream>>>(a.psi, ctx->n, net->d_scal, z);
-    check(cudaGetLastError(), "k_scale_out");
+    // count the forward's convolutions (launches, FP32 flops) for the profile
+    nn::Counters cnt;
+    struct Reset {
+        ~Reset() { nn::tl_counters = nullptr; }
+    } reset;
+    nn::tl_counters = &cnt;
+    {
+        ProfScope ps(ctx, K_MGNET, (double)ctx->n * 12, 0);
+        const double* rv[1] = {v};
+        load_inputs(net, ctx, rv, 1, a);
+        forward(net, F, a, 1, ctx->I);
+        k_scale_out<<<grid_for(ctx->n), 256, 0, net->stream>>>(a.psi, ctx->n, net->d_scal, z);
+        check(cudaGetLastError(), "k_scale_out");
+    }
+    ctx->prof.launches[K_MGNET] += cnt.launches + 4;      // + norm, sqrt, normalise, scale
+    ctx->prof.flops[K_MGNET] += cnt.flops;
 }
 
 }  // namespace rte

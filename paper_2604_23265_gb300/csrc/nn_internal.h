@@ -63,6 +63,13 @@ struct WgradArgs {
     Taps tp;
 };
 
+// counters of the calling network (launches and FP32 flops), may be null
+struct Counters {
+    long long launches = 0;
+    double flops = 0.0;
+};
+extern thread_local Counters* tl_counters;
+
 void conv(const ConvArgs& a, cudaStream_t st);
 void wgrad(const WgradArgs& a, cudaStream_t st);
 void bn_stats(const float* x, int B, int C, int HW, float* mean, float* invstd, cudaStream_t st);

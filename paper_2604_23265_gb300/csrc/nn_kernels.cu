@@ -316,8 +316,14 @@ int ew_blocks(size_t n) {
 
 }  // namespace
 
+thread_local Counters* tl_counters = nullptr;
+
 void conv(const ConvArgs& a, cudaStream_t st) {
     if (a.tp.T > kMaxTaps) throw StatusError{RTE_EINVAL, "too many taps"};
+    if (tl_counters) {
+        tl_counters->launches += 1;
+        tl_counters->flops += 2.0 * a.B * a.Co * (double)a.Hg * a.Wg * a.Ci * a.tp.T;
+    }
     const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
     const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
     if (PY > kMaxPatch || PX > kMaxPatch) throw StatusError{RTE_EINVAL, "patch too large"};

@@ -88,6 +88,7 @@ SIGNATURES = {
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
     "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
     "rte_fp64_fma_rate": (_I, [_P, ctypes.POINTER(_D)]),
+    "rte_fp32_fma_rate": (_I, [_P, ctypes.POINTER(_D)]),
     "rte_profile": (_I, [_P, _I]),
     "rte_server_config_default": (None, [_P]),
     "rte_server_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
@@ -161,6 +162,13 @@ def fp64_fma_rate(stream=None):
     """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
     v = ctypes.c_double()
     _check(load().rte_fp64_fma_rate(_stream_ptr(stream), ctypes.byref(v)))
+    return v.value
+
+
+def fp32_fma_rate(stream=None):
+    """Measured FP32 FMA throughput of the current GPU (CUDA cores), GFLOP/s."""
+    v = ctypes.c_double()
+    _check(load().rte_fp32_fma_rate(_stream_ptr(stream), ctypes.byref(v)))
     return v.value
 
 
