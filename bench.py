@@ -195,6 +195,31 @@ def _roofline(rte, stream, prof):
     return roof, kernels
 
 
+def run_precond_only(args):
+    """Profiling mode: apply an (untrained) network args.precond_only times to a
+    unit vector of the workload; prints the mean time per application."""
+    import torch
+    from paper_2604_23265_gb300 import rte, train
+    torch.cuda.set_device(0)
+    md = W.grf_diffusive(seed=0, I=args.size, M=args.dirs)
+    ctx = rte.Context.from_medium(md)
+    net = rte.MgNet(train.default_shape(md.M, md.I))
+    net.set_params(W.init_params(net.shape, seed=0, proj_scale=0.01, vcycle_scale=0.5))
+    v = torch.tensor(W.random_vector(ctx.n, 1), device="cuda")
+    v /= v.norm()
+    z = torch.empty(ctx.n, dtype=torch.float32, device="cuda")
+    net.precond(ctx, v, z)                      # features and workspace
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.precond_only):
+        net.precond(ctx, v, z)
+    ev1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "precond_only", "I": md.I, "M": md.M, "levels": net.shape.levels,
+                      "ms_per_application": ev0.elapsed_time(ev1) / args.precond_only}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_2604_23265_gb300 import rte, train
@@ -355,12 +380,16 @@ def main():
     ap.add_argument("--train-steps", type=int, default=600)
     ap.add_argument("--train-media", type=int, default=4)
     ap.add_argument("--no-bj", action="store_true", help="skip the block-Jacobi comparison solve")
+    ap.add_argument("--precond-only", type=int, default=0,
+                    help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")
     ap.add_argument("--dirs", type=int, default=64, help="profiling only: directions")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.precond_only > 0:
+        run_precond_only(args)
     else:
         run_ours(args)
 

@@ -22,20 +22,28 @@ namespace {
 constexpr int kTileCo = 64;      // output channels per CTA
 constexpr int kTileG = 8;        // 8 x 8 class-grid pixels per CTA
 constexpr int kChunk = 8;        // input channels staged per pass
-constexpr int kMaxPatch = 20;    // staged patch side (7 S + taps span)
+constexpr int kMaxPatch = 20;    // staged patch side of the weight-gradient tile
+constexpr int kSmallGrid = 4096; // class grids up to this many pixels use k_conv_small
 
+// CTA tile: TCO output channels x (TW x TH) class-grid pixels, TCO * TW * TH =
+// 4096 outputs; each of the 256 threads computes 4 channels x 4 pixels of a
+// row.  TCO follows the layer's output width (16, 32 or 64) so that narrow
+// layers do not idle most of the tile.
+template <int TCO, int TW, int TH>
 __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
-    __shared__ float xs[kChunk][kMaxPatch][kMaxPatch + 1];
-    __shared__ __align__(16) float ws[kChunk][kMaxTaps][kTileCo];
+    constexpr int PYM = (TH - 1) * 2 + 4, PXM = (TW - 1) * 2 + 4;   // largest staged patch
+    __shared__ float xs[kChunk][PYM][PXM + 1];
+    __shared__ __align__(16) float ws[kChunk][kMaxTaps][TCO];
     const int tid = threadIdx.x;
-    const int tilesx = (a.Wg + kTileG - 1) / kTileG;
-    const int gy0 = (blockIdx.x / tilesx) * kTileG, gx0 = (blockIdx.x % tilesx) * kTileG;
-    const int co0 = blockIdx.y * kTileCo;
+    const int tilesx = (a.Wg + TW - 1) / TW;
+    const int gy0 = (blockIdx.x / tilesx) * TH, gx0 = (blockIdx.x % tilesx) * TW;
+    const int co0 = blockIdx.y * TCO;
     const int b = blockIdx.z;
-    const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
-    const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
-    const int tco = tid >> 4, tpx = tid & 15;
-    const int r = tpx >> 1, c0 = (tpx & 1) * 4;
+    const int PY = (TH - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
+    const int PX = (TW - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
+    constexpr int GROUPS = TW * TH / 4;          // pixel groups of 4 along a row
+    const int tco = tid / GROUPS, tpx = tid % GROUPS;
+    const int r = tpx / (TW / 4), c0 = (tpx % (TW / 4)) * 4;
     float acc[4][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -54,9 +62,9 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
             }
             xs[ci][yy][xx] = v;
         }
-        for (int e = tid; e < kChunk * a.tp.T * kTileCo; e += 256) {
-            const int ci = e / (a.tp.T * kTileCo), rem = e - ci * a.tp.T * kTileCo;
-            const int t = rem / kTileCo, co = rem - t * kTileCo;
+        for (int e = tid; e < kChunk * a.tp.T * TCO; e += 256) {
+            const int ci = e / (a.tp.T * TCO), rem = e - ci * a.tp.T * TCO;
+            const int t = rem / TCO, co = rem - t * TCO;
             float v = 0.f;
             if (ci0 + ci < a.Ci && co0 + co < a.Co)
                 v = a.w[((size_t)(co0 + co) * a.so + (size_t)(ci0 + ci) * a.si) * a.KK + a.tp.wi[t]];
@@ -104,6 +112,46 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
             a.y[idx] = v;
         }
     }
+}
+
+// Small class grids (coarse V-cycle levels): one output per thread, so even an
+// 8 x 8 grid with 64 channels spreads over 16 CTAs instead of one.  Threads of
+// a warp share the output channel (weights broadcast) and cover consecutive
+// pixels (coalesced inputs, reused through L1 by the neighbouring taps).
+__global__ void __launch_bounds__(256) k_conv_small(ConvArgs a) {
+    const int64_t total = (int64_t)a.B * a.Co * a.Hg * a.Wg;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int gx = (int)(e % a.Wg);
+    const int gy = (int)((e / a.Wg) % a.Hg);
+    const int co = (int)((e / ((int64_t)a.Wg * a.Hg)) % a.Co);
+    const int b = (int)(e / ((int64_t)a.Wg * a.Hg * a.Co));
+    const float* xb = a.x + (size_t)b * a.Ci * a.Hi * a.Wi;
+    float acc = 0.f;
+    for (int t = 0; t < a.tp.T; ++t) {
+        const int iy = a.S * gy + a.tp.dy[t], ix = a.S * gx + a.tp.dx[t];
+        if (iy < 0 || iy >= a.Hi || ix < 0 || ix >= a.Wi) continue;
+        const float* xp = xb + (size_t)iy * a.Wi + ix;
+        const float* wp = a.w + (size_t)co * a.so * a.KK + a.tp.wi[t];
+        const size_t xs = (size_t)a.Hi * a.Wi, wstep = (size_t)a.si * a.KK;
+        if (a.relu_in) {
+            for (int ci = 0; ci < a.Ci; ++ci) acc = fmaf(__ldg(wp + ci * wstep), fmaxf(__ldg(xp + ci * xs), 0.f), acc);
+        } else {
+            for (int ci = 0; ci < a.Ci; ++ci) acc = fmaf(__ldg(wp + ci * wstep), __ldg(xp + ci * xs), acc);
+        }
+    }
+    const int oy = a.OS * gy + a.OY0, ox = a.OS * gx + a.OX0;
+    const size_t idx = (((size_t)b * a.Co + co) * a.Ho + oy) * a.Wo + ox;
+    float v = acc;
+    if (a.bias) v += a.bias[co];
+    v += a.cst;
+    if (a.raw) a.raw[idx] = v;
+    if (a.gate) v *= a.gate[a.gate_bcast ? (((size_t)co * a.Ho + oy) * a.Wo + ox) : idx];
+    if (a.mask && !(a.mask[idx] > 0.f)) v = 0.f;
+    v *= a.sign;
+    if (a.base) v += a.base[idx];
+    if (a.accumulate) v += a.y[idx];
+    a.y[idx] = v;
 }
 
 // dW[(o so + i si) KK + wi_t] += sum_{b, gy, gx} G[b][o][OS gy + OY0][OS gx + OX0]
@@ -320,16 +368,26 @@ thread_local Counters* tl_counters = nullptr;
 
 void conv(const ConvArgs& a, cudaStream_t st) {
     if (a.tp.T > kMaxTaps) throw StatusError{RTE_EINVAL, "too many taps"};
+    if (a.S < 1 || a.S > 2 || a.tp.dymax - a.tp.dymin > 3 || a.tp.dxmax - a.tp.dxmin > 3)
+        throw StatusError{RTE_EINVAL, "convolution stride or tap span too large"};
     if (tl_counters) {
         tl_counters->launches += 1;
         tl_counters->flops += 2.0 * a.B * a.Co * (double)a.Hg * a.Wg * a.Ci * a.tp.T;
     }
-    const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
-    const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
-    if (PY > kMaxPatch || PX > kMaxPatch) throw StatusError{RTE_EINVAL, "patch too large"};
-    const int tiles = ((a.Hg + kTileG - 1) / kTileG) * ((a.Wg + kTileG - 1) / kTileG);
-    dim3 grid(tiles, (a.Co + kTileCo - 1) / kTileCo, a.B);
-    k_conv<<<grid, 256, 0, st>>>(a);
+    auto launch = [&](auto kern, int tco, int tw, int th) {
+        const int tiles = ((a.Hg + th - 1) / th) * ((a.Wg + tw - 1) / tw);
+        dim3 grid(tiles, (a.Co + tco - 1) / tco, a.B);
+        kern<<<grid, 256, 0, st>>>(a);
+    };
+    if ((int64_t)a.Hg * a.Wg <= kSmallGrid) {
+        const int64_t total = (int64_t)a.B * a.Co * a.Hg * a.Wg;
+        k_conv_small<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
+    } else if (a.Co <= 16)
+        launch(k_conv<16, 16, 16>, 16, 16, 16);
+    else if (a.Co <= 32)
+        launch(k_conv<32, 16, 8>, 32, 16, 8);
+    else
+        launch(k_conv<64, 8, 8>, 64, 8, 8);
     check(cudaGetLastError(), "k_conv");
 }
 
