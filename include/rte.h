@@ -287,6 +287,22 @@ typedef struct mgnet_config {
 RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** out);
 RTE_API void mgnet_destroy(mgnet* net);
 RTE_API int64_t mgnet_param_count(const mgnet* net);
+
+/* Arithmetic of the V-cycle convolutions when the network preconditions
+ * (mgnet_precond, mgnet_apply, rte_solve); training always uses FP32.
+ *   MGNET_BF16: tcgen05 tensor cores, BF16 operands (weights and gathered
+ *               activations rounded to nearest even), FP32 accumulation and
+ *               FP32 epilogue / storage (default);
+ *   MGNET_FP32: FP32 FMA on the CUDA cores.
+ * The CoeffNet features are FP32 in both.  EINVAL for another value. */
+typedef enum mgnet_precision { MGNET_FP32 = 0, MGNET_BF16 = 1 } mgnet_precision;
+RTE_API rte_status mgnet_set_precision(mgnet* net, int precision);
+RTE_API int mgnet_get_precision(const mgnet* net);
+
+/* 1 if a bounded wait inside a tensor-core network kernel expired since the
+ * last reset (that launch wrote NaN outputs), else 0; reset != 0 clears the
+ * flag.  Synchronises with the device.  Returns -1 if the flag cannot be read. */
+RTE_API int mgnet_kernel_status(int reset);
 /* Host float32 [count] in the order above; set also resets the Adam state. */
 RTE_API rte_status mgnet_set_params(mgnet* net, const float* host, int64_t count);
 RTE_API rte_status mgnet_get_params(mgnet* net, float* host, int64_t count);

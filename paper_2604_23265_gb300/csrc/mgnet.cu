@@ -50,6 +50,13 @@ struct Features {            // CoeffNet outputs of one medium for one weight ve
 struct mgnet {
     int M = 0, L = 0, c0 = 0, cmax = 0, cc = 0, ccmax = 0, cin = 4;
     int act = 0;                     // smoother activation: 0 identity, 1 ReLU
+    int prec = 1;                    // inference convolutions: 0 FP32 CUDA cores, 1 BF16 tensor cores
+    // tensor-core inference path: BF16 C8 activations, packed weights
+    void* tc_ws = nullptr;
+    size_t tc_ws_bytes = 0;
+    void* tcw = nullptr;
+    size_t tcw_bytes = 0;
+    uint64_t tcw_version = ~0ull;
     cudaStream_t stream = nullptr;
     std::string err;
     std::vector<rte::Param> params;
@@ -280,35 +287,39 @@ Features& features(mgnet* n, rte_ctx* ctx, bool force) {
 }
 
 // ------------------------------------------------------------------ forward
-// x must already hold the normalised inputs [B][2M][I][I]; writes a.psi.
-void forward(mgnet* n, const Features& F, Acts& a, int B, int I) {
+// FP32 forward (CUDA cores). x must already hold the normalised inputs
+// [B][2M][I][I]; writes a.psi.  keep: store the pre-gate values the backward
+// pass needs (training).
+void forward(mgnet* n, const Features& F, Acts& a, int B, int I, bool keep) {
     const int L = n->L, M2 = 2 * n->M;
     const Taps t3 = nn::taps_conv(3, 1), t1 = nn::taps_conv(1, 0);
-    nn::conv(cv(a.x, B, M2, I, P(n, "lift.w"), M2, 1, 1, n->C(0), I, 1, a.f[0], I, t1), n->stream);
+    auto conv = [&](const ConvArgs& c) { nn::conv(c, n->stream); };
+    auto kept = [&](float* q) { return keep ? q : nullptr; };
+    conv(cv(a.x, B, M2, I, P(n, "lift.w"), M2, 1, 1, n->C(0), I, 1, a.f[0], I, t1));
     auto smooth_first = [&](int l, float* q, float* u) {     // u = (B * ReLU(f)) o ainv
         const int H = I >> l, C = n->C(l);
         ConvArgs c = cv(a.f[l], B, C, H, P(n, sl("B", l)), C, 1, 9, C, H, 1, u, H, t3);
-        c.relu_in = n->act; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1;
-        nn::conv(c, n->stream);
+        c.relu_in = n->act; c.raw = kept(q); c.gate = F.ai[l]; c.gate_bcast = 1;
+        conv(c);
     };
     auto residual = [&](int l, const float* u, float* craw, float* out) {   // f - (A * u) o a
         const int H = I >> l, C = n->C(l);
         ConvArgs c = cv(u, B, C, H, P(n, sl("A", l)), C, 1, 9, C, H, 1, out, H, t3);
-        c.raw = craw; c.gate = F.a[l]; c.gate_bcast = 1; c.sign = -1.f; c.base = a.f[l];
-        nn::conv(c, n->stream);
+        c.raw = kept(craw); c.gate = F.a[l]; c.gate_bcast = 1; c.sign = -1.f; c.base = a.f[l];
+        conv(c);
     };
     auto smooth_update = [&](int l, const float* t, float* q, const float* u, float* out) {
         const int H = I >> l, C = n->C(l);
         ConvArgs c = cv(t, B, C, H, P(n, sl("B", l)), C, 1, 9, C, H, 1, out, H, t3);
-        c.relu_in = n->act; c.raw = q; c.gate = F.ai[l]; c.gate_bcast = 1; c.base = u;
-        nn::conv(c, n->stream);
+        c.relu_in = n->act; c.raw = kept(q); c.gate = F.ai[l]; c.gate_bcast = 1; c.base = u;
+        conv(c);
     };
     for (int l = 0; l + 1 < L; ++l) {
         const int H = I >> l;
         smooth_first(l, a.qpre[l], a.upre[l]);
         residual(l, a.upre[l], a.cdown[l], a.res[l]);
-        nn::conv(cv(a.res[l], B, n->C(l), H, P(n, sl("R", l)), n->C(l), 1, 9, n->C(l + 1), H / 2, 2,
-                    a.f[l + 1], H / 2, t3), n->stream);
+        conv(cv(a.res[l], B, n->C(l), H, P(n, sl("R", l)), n->C(l), 1, 9, n->C(l + 1), H / 2, 2,
+                a.f[l + 1], H / 2, t3));
     }
     smooth_first(L - 1, a.q1, a.u1);
     residual(L - 1, a.u1, a.c2, a.t2);
@@ -316,14 +327,14 @@ void forward(mgnet* n, const Features& F, Acts& a, int B, int I) {
     float* uup = a.u2;
     for (int l = L - 2; l >= 0; --l) {
         const int H = I >> l;
-        const size_t e = level_elems(n, B, I, l);
-        check(cudaMemcpyAsync(a.umid[l], a.upre[l], e * 4, cudaMemcpyDeviceToDevice, n->stream), "copy");
+        // u_mid = u_pre + P *^T u_coarse: each fine pixel belongs to exactly one
+        // parity class, so every class adds u_pre to its own pixels
         for (int py = 0; py < 2; ++py)
             for (int px = 0; px < 2; ++px) {
                 ConvArgs c = cv(uup, B, n->C(l + 1), H / 2, P(n, sl("P", l)), 1, n->C(l), 16, n->C(l),
                                 H / 2, 1, a.umid[l], H, nn::taps_parity(4, py, px));
-                c.OS = 2; c.OY0 = py; c.OX0 = px; c.accumulate = 1;
-                nn::conv(c, n->stream);
+                c.OS = 2; c.OY0 = py; c.OX0 = px; c.base = a.upre[l];
+                conv(c);
             }
         residual(l, a.umid[l], a.cpost[l], a.tpost[l]);
         smooth_update(l, a.tpost[l], a.qpost[l], a.umid[l], a.uout[l]);
@@ -331,7 +342,158 @@ void forward(mgnet* n, const Features& F, Acts& a, int B, int I) {
     }
     ConvArgs c = cv(uup, B, n->C(0), I, P(n, "proj.w"), n->C(0), 1, 1, M2, I, 1, a.psi, I, t1);
     c.base = a.x;
-    nn::conv(c, n->stream);
+    conv(c);
+}
+
+// ------------------------------------------------------------------ tensor-core forward
+// Inference forward on the tensor cores (conv_tc.cu): the same layers as
+// forward(), BF16 C8 activations, FP32 accumulation and gating.  Every layer of
+// the V-cycle is linear or ReLU without bias and the gates depend on the medium
+// only, so the network is positively homogeneous, rms(r) Net(r / rms(r)) =
+// Net(r): the input is fed unnormalised and z = r + proj(u) is written directly.
+struct TcActs {
+    std::vector<void*> f, upre, res, umid, tpost, uout;
+    void *u1 = nullptr, *t2 = nullptr, *u2 = nullptr;
+};
+
+size_t c8_bytes(int C, int H) { return (((size_t)(C + 7) / 8) * H * H * 16 + 255) & ~(size_t)255; }
+
+TcActs tc_workspace(mgnet* n, int I) {
+    const int L = n->L;
+    size_t need = 0;
+    for (int l = 0; l < L; ++l) need += 6 * c8_bytes(n->C(l), I >> l);
+    need += 3 * c8_bytes(n->C(L - 1), I >> (L - 1));
+    if (!n->tc_ws || n->tc_ws_bytes < need) {
+        if (n->tc_ws) cudaFree(n->tc_ws);
+        n->tc_ws = nullptr;
+        check(cudaMalloc(&n->tc_ws, need), "cudaMalloc (tensor-core workspace)");
+        n->tc_ws_bytes = need;
+    }
+    char* p = static_cast<char*>(n->tc_ws);
+    auto take = [&](int C, int H) { void* r = p; p += c8_bytes(C, H); return r; };
+    TcActs A;
+    for (int l = 0; l < L; ++l) {
+        const int C = n->C(l), H = I >> l;
+        A.f.push_back(take(C, H));
+        A.upre.push_back(take(C, H));
+        A.res.push_back(take(C, H));
+        A.umid.push_back(take(C, H));
+        A.tpost.push_back(take(C, H));
+        A.uout.push_back(take(C, H));
+    }
+    const int C = n->C(L - 1), H = I >> (L - 1);
+    A.u1 = take(C, H);
+    A.t2 = take(C, H);
+    A.u2 = take(C, H);
+    return A;
+}
+
+enum class TcMode { Plan, Pack, Run };
+
+// Plan: returns the packed-weight bytes; Pack: packs then runs; Run: runs.
+size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z, TcMode mode) {
+    const int L = n->L, M2 = 2 * n->M;
+    const Taps t3 = nn::taps_conv(3, 1), t1 = nn::taps_conv(1, 0);
+    TcActs A;
+    if (mode != TcMode::Plan) A = tc_workspace(n, I);
+    size_t cursor = 0;
+    auto run = [&](nn::TcConv c, const char* wname, int so, int si, int KK, const Taps& tp) {
+        const size_t bytes = nn::tc_weight_bytes(tp.T, c.Ci, c.Co);
+        void* dst = static_cast<char*>(n->tcw) + cursor;
+        cursor += bytes;
+        if (mode == TcMode::Plan) return;
+        if (mode == TcMode::Pack) nn::tc_pack(P(n, wname), so, si, KK, tp, c.Ci, c.Co, dst, n->stream);
+        c.w = dst;
+        c.T = tp.T;
+        for (int t = 0; t < tp.T; ++t) {
+            c.dy[t] = tp.dy[t];
+            c.dx[t] = tp.dx[t];
+        }
+        nn::tc_conv(c, n->stream);
+    };
+    auto conv = [&](const void* x8, int Ci, int Hi, int Co, int Hg, int S, void* y8, int Ho) {
+        nn::TcConv c;
+        c.x8 = x8; c.B = 1; c.Ci = Ci; c.Hi = Hi; c.Wi = Hi;
+        c.Co = Co; c.Hg = Hg; c.Wg = Hg; c.S = S;
+        c.y8 = y8; c.Ho = Ho; c.Wo = Ho;
+        return c;
+    };
+    {   // lift: FP64 Krylov vector -> f_0
+        nn::TcConv c = conv(nullptr, M2, I, n->C(0), I, 1, A.f.empty() ? nullptr : A.f[0], I);
+        c.x64 = r;
+        run(c, "lift.w", M2, 1, 1, t1);
+    }
+    auto smooth_first = [&](int l, void* u) {            // u = (B * act(f)) o ainv
+        const int H = I >> l, C = n->C(l);
+        nn::TcConv c = conv(A.f.empty() ? nullptr : A.f[l], C, H, C, H, 1, u, H);
+        c.relu_in = n->act;
+        c.gate = F ? F->ai[l] : nullptr;
+        run(c, sl("B", l).c_str(), C, 1, 9, t3);
+    };
+    auto residual = [&](int l, const void* u, void* out) {   // f - (A * u) o a
+        const int H = I >> l, C = n->C(l);
+        nn::TcConv c = conv(u, C, H, C, H, 1, out, H);
+        c.gate = F ? F->a[l] : nullptr;
+        c.sign = -1.f;
+        c.base8 = A.f.empty() ? nullptr : A.f[l];
+        run(c, sl("A", l).c_str(), C, 1, 9, t3);
+    };
+    auto smooth_update = [&](int l, const void* t, const void* u, void* out) {   // u + (B * act(t)) o ainv
+        const int H = I >> l, C = n->C(l);
+        nn::TcConv c = conv(t, C, H, C, H, 1, out, H);
+        c.relu_in = n->act;
+        c.gate = F ? F->ai[l] : nullptr;
+        c.base8 = u;
+        run(c, sl("B", l).c_str(), C, 1, 9, t3);
+    };
+    auto at = [&](std::vector<void*>& v, int l) { return v.empty() ? nullptr : v[l]; };
+    for (int l = 0; l + 1 < L; ++l) {
+        const int H = I >> l;
+        smooth_first(l, at(A.upre, l));
+        residual(l, at(A.upre, l), at(A.res, l));
+        run(conv(at(A.res, l), n->C(l), H, n->C(l + 1), H / 2, 2, at(A.f, l + 1), H / 2), sl("R", l).c_str(),
+            n->C(l), 1, 9, t3);
+    }
+    smooth_first(L - 1, A.u1);
+    residual(L - 1, A.u1, A.t2);
+    smooth_update(L - 1, A.t2, A.u1, A.u2);
+    const void* uup = A.u2;
+    for (int l = L - 2; l >= 0; --l) {
+        const int H = I >> l;
+        for (int py = 0; py < 2; ++py)
+            for (int px = 0; px < 2; ++px) {      // u_mid = u_pre + P *^T u_coarse, one parity class each
+                nn::TcConv c = conv(uup, n->C(l + 1), H / 2, n->C(l), H / 2, 1, at(A.umid, l), H);
+                c.OS = 2; c.OY0 = py; c.OX0 = px;
+                c.base8 = at(A.upre, l);
+                run(c, sl("P", l).c_str(), 1, n->C(l), 16, nn::taps_parity(4, py, px));
+            }
+        residual(l, at(A.umid, l), at(A.tpost, l));
+        smooth_update(l, at(A.tpost, l), at(A.umid, l), at(A.uout, l));
+        uup = at(A.uout, l);
+    }
+    {   // z = r + proj(u_0), FP32 [2M][I][I]
+        nn::TcConv c = conv(uup, n->C(0), I, M2, I, 1, nullptr, I);
+        c.y32 = z;
+        c.base64 = r;
+        run(c, "proj.w", n->C(0), 1, 1, t1);
+    }
+    return cursor;
+}
+
+void tc_precondition(mgnet* n, const Features& F, rte_ctx* ctx, const double* v, float* z) {
+    if (n->tcw_version != n->version) {
+        const size_t need = tc_forward(n, nullptr, ctx->I, nullptr, nullptr, TcMode::Plan);
+        if (!n->tcw || n->tcw_bytes < need) {
+            if (n->tcw) cudaFree(n->tcw);
+            n->tcw = nullptr;
+            check(cudaMalloc(&n->tcw, need), "cudaMalloc (packed weights)");
+            n->tcw_bytes = need;
+        }
+        tc_forward(n, &F, ctx->I, v, z, TcMode::Pack);
+        n->tcw_version = n->version;
+    } else {
+        tc_forward(n, &F, ctx->I, v, z, TcMode::Run);
+    }
 }
 
 // ------------------------------------------------------------------ backward
@@ -591,22 +753,26 @@ void mgnet_prepare(mgnet* net, rte_ctx* ctx) {
 void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
     check_ctx(net, ctx);
     Features& F = features(net, ctx, false);
-    Acts a = workspace(net, 2, ctx->I);
     // count the forward's convolutions (launches, FP32 flops) for the profile
     nn::Counters cnt;
     struct Reset {
         ~Reset() { nn::tl_counters = nullptr; }
     } reset;
     nn::tl_counters = &cnt;
-    {
+    if (net->prec == MGNET_BF16) {
         ProfScope ps(ctx, K_MGNET, (double)ctx->n * 12, 0);
+        tc_precondition(net, F, ctx, v, z);
+    } else {
+        ProfScope ps(ctx, K_MGNET, (double)ctx->n * 12, 0);
+        Acts a = workspace(net, 2, ctx->I);
         const double* rv[1] = {v};
         load_inputs(net, ctx, rv, 1, a);
-        forward(net, F, a, 1, ctx->I);
+        forward(net, F, a, 1, ctx->I, false);
         k_scale_out<<<grid_for(ctx->n), 256, 0, net->stream>>>(a.psi, ctx->n, net->d_scal, z);
         check(cudaGetLastError(), "k_scale_out");
+        cnt.launches += 4;                                // norm, sqrt, normalise, scale
     }
-    ctx->prof.launches[K_MGNET] += cnt.launches + 4;      // + norm, sqrt, normalise, scale
+    ctx->prof.launches[K_MGNET] += cnt.launches;
     ctx->prof.flops[K_MGNET] += cnt.flops;
 }
 
@@ -667,6 +833,7 @@ RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out) {
     MG_GUARD_BEGIN
     check(cudaStreamSynchronize(src->stream), "sync");
     check(cudaMemcpyAsync(n->p, src->p, n->np * 4, cudaMemcpyDeviceToDevice, n->stream), "d2d");
+    n->prec = src->prec;
     check(cudaStreamSynchronize(n->stream), "sync");
     ++n->version;
     return RTE_OK;
@@ -679,6 +846,8 @@ RTE_API void mgnet_destroy(mgnet* n) {
     for (auto& kv : n->feats)
         if (kv.second.block) cudaFree(kv.second.block);
     if (n->ws) cudaFree(n->ws);
+    if (n->tc_ws) cudaFree(n->tc_ws);
+    if (n->tcw) cudaFree(n->tcw);
     if (n->p) cudaFree(n->p);
     if (n->d_scal) cudaFree(n->d_scal);
     if (n->h_scal) cudaFreeHost(n->h_scal);
@@ -686,6 +855,25 @@ RTE_API void mgnet_destroy(mgnet* n) {
 }
 
 RTE_API int64_t mgnet_param_count(const mgnet* n) { return n ? (int64_t)n->np : -1; }
+
+RTE_API rte_status mgnet_set_precision(mgnet* n, int precision) {
+    if (!n || (precision != MGNET_FP32 && precision != MGNET_BF16)) {
+        set_error(nullptr, "bad argument (precision MGNET_FP32 or MGNET_BF16)");
+        return RTE_EINVAL;
+    }
+    n->prec = precision;
+    return RTE_OK;
+}
+
+RTE_API int mgnet_get_precision(const mgnet* n) { return n ? n->prec : -1; }
+
+RTE_API int mgnet_kernel_status(int reset) {
+    try {
+        return nn::conv_tc_status(reset != 0);
+    } catch (...) {
+        return -1;
+    }
+}
 
 RTE_API rte_status mgnet_set_params(mgnet* n, const float* host, int64_t count) {
     if (!n || !host || count != (int64_t)n->np) { set_error(nullptr, "bad argument"); return RTE_EINVAL; }
@@ -740,7 +928,7 @@ static rte_status loss_grad_impl(mgnet* n, rte_ctx* ctx, const double* const* r_
     const int Bw = batch < 2 ? 2 : batch;
     Acts a = workspace(n, Bw, ctx->I);
     load_inputs(n, ctx, r_dev, batch, a);
-    forward(n, F, a, batch, ctx->I);
+    forward(n, F, a, batch, ctx->I, true);
     const double loss = loss_and_seed(n, ctx, a, batch);
     check(cudaMemsetAsync(n->g, 0, n->np * 4, n->stream), "memset");
     backward(n, F, a, ctx, batch, ctx->I);

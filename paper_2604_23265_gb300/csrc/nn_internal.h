@@ -71,6 +71,37 @@ struct Counters {
 extern thread_local Counters* tl_counters;
 
 void conv(const ConvArgs& a, cudaStream_t st);
+// Tensor-core (tcgen05) gather convolution of the inference forward pass
+// (conv_tc.cu): BF16 operands, FP32 accumulation.  Activations are BF16 in the
+// channel-chunked layout C8 = [B][ceil(C/8)][H][W][8] (16-byte aligned);
+// weights are packed by tc_pack.  Output pixel (OS gy + OY0, OS gx + OX0) of
+// class-grid pixel (gy, gx) receives
+//   v = sign (sum_t sum_i X[b][i][S gy + dy_t][S gx + dx_t] W[t][i][o]) gate[o] (+ base)
+struct TcConv {
+    const void* x8 = nullptr;        // BF16 C8 input, or
+    const double* x64 = nullptr;     // FP64 [B][Ci][Hi][Wi] input (converted on load)
+    int B = 1, Ci = 0, Hi = 0, Wi = 0;
+    int relu_in = 0;                 // ReLU applied to the gathered input
+    const void* w = nullptr;         // packed weights (tc_pack, tc_weight_bytes(T, Ci, Co))
+    int Co = 0;
+    int Hg = 0, Wg = 0, S = 1;       // class grid and input stride
+    int OS = 1, OY0 = 0, OX0 = 0;    // output placement
+    int Ho = 0, Wo = 0;
+    int T = 0;
+    int dy[kMaxTaps] = {}, dx[kMaxTaps] = {};
+    const float* gate = nullptr;     // FP32 [Co][Ho][Wo], shared by the batch
+    float sign = 1.f;
+    const void* base8 = nullptr;     // BF16 C8 of the output's shape, or
+    const double* base64 = nullptr;  // FP64 [B][Co][Ho][Wo]
+    void* y8 = nullptr;              // BF16 C8 output, or
+    float* y32 = nullptr;            // FP32 [B][Co][Ho][Wo] output
+};
+size_t tc_weight_bytes(int T, int Ci, int Co);
+// packs W[t][i][o] = w[(o so + i si) KK + wi_t] into dst (tc_weight_bytes)
+void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int Co, void* dst, cudaStream_t st);
+void tc_conv(const TcConv& a, cudaStream_t st);
+// 1 once a bounded wait of the tensor-core kernel expired (reset on request).
+int conv_tc_status(bool reset);
 void wgrad(const WgradArgs& a, cudaStream_t st);
 void bn_stats(const float* x, int B, int C, int HW, float* mean, float* invstd, cudaStream_t st);
 void bn_relu(const float* x, int B, int C, int HW, const float* mean, const float* invstd,

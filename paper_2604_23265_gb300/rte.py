@@ -101,6 +101,9 @@ SIGNATURES = {
     "mgnet_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "mgnet_destroy": (None, [_P]),
     "mgnet_param_count": (ctypes.c_int64, [_P]),
+    "mgnet_set_precision": (_I, [_P, _I]),
+    "mgnet_get_precision": (_I, [_P]),
+    "mgnet_kernel_status": (_I, [_I]),
     "mgnet_set_params": (_I, [_P, _P, ctypes.c_int64]),
     "mgnet_get_params": (_I, [_P, _P, ctypes.c_int64]),
     "mgnet_precond": (_I, [_P, _P, _P, _P]),
@@ -308,6 +311,23 @@ class MgNet:
         flat = params if isinstance(params, np.ndarray) else self.flatten(params, self.shape)
         flat = np.ascontiguousarray(flat, np.float32)
         _check(load().mgnet_set_params(self.ptr, flat.ctypes.data_as(_P), flat.size))
+
+    FP32, BF16 = 0, 1
+
+    @property
+    def precision(self):
+        """Convolution arithmetic when preconditioning: MgNet.BF16 (tensor
+        cores, default) or MgNet.FP32 (CUDA cores)."""
+        return int(load().mgnet_get_precision(self.ptr))
+
+    @precision.setter
+    def precision(self, value):
+        _check(load().mgnet_set_precision(self.ptr, int(value)))
+
+    @staticmethod
+    def kernel_status(reset=True):
+        """1 if a bounded wait of a tensor-core network kernel expired."""
+        return int(load().mgnet_kernel_status(1 if reset else 0))
 
     def get_params(self):
         flat = np.zeros(self.count, np.float32)

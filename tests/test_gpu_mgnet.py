@@ -1,7 +1,8 @@
 """GPU parity of the MgNet preconditioner against the FP64 oracle (same seeded
 weights and inputs): forward, loss, every parameter's gradient, training and
 the MgNet-preconditioned solve.  FP32 network arithmetic: relative L2 bars of
-1e-4 (outputs) and 2e-3 (gradients, sums over up to 65k products)."""
+1e-4 (outputs) and 2e-3 (gradients, sums over up to 65k products); the
+tensor-core forward (BF16 operands): 2e-2."""
 import numpy as np
 import pytest
 
@@ -16,9 +17,9 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
-def _setup(I=16, M=8, levels=3, seed=0, proj=0.5, c0=8, cmax=16, cc=4, ccmax=8):
+def _setup(I=16, M=8, levels=3, seed=0, proj=0.5, c0=8, cmax=16, cc=4, ccmax=8, act="linear"):
     from paper_2604_23265_gb300 import rte
-    shape = W.NetShape(M=M, levels=levels, c0=c0, cmax=cmax, cc=cc, ccmax=ccmax)
+    shape = W.NetShape(M=M, levels=levels, c0=c0, cmax=cmax, cc=cc, ccmax=ccmax, act=act)
     params = W.init_params(shape, seed=seed, proj_scale=proj)
     # round the weights to float32 so both sides use identical values
     params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
@@ -33,6 +34,7 @@ def _setup(I=16, M=8, levels=3, seed=0, proj=0.5, c0=8, cmax=16, cc=4, ccmax=8):
 @pytest.mark.parametrize("I,M,levels", [(16, 8, 3), (24, 4, 2), (32, 16, 4), (8, 8, 1)])
 def test_forward_matches_oracle(lib, I, M, levels):
     rte, shape, params, md, ctx, net, p = _setup(I=I, M=M, levels=levels)
+    net.precision = rte.MgNet.FP32
     r = W.random_vector(ctx.n, 7)
     z = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
     net.precond(ctx, torch.tensor(r, device="cuda"), z)
@@ -42,6 +44,45 @@ def test_forward_matches_oracle(lib, I, M, levels):
     net.apply(ctx, torch.tensor(r, device="cuda"), za)
     refa = tfps.block_apply(p.block_inverse(), ref.reshape(2 * M, -1)).ravel()
     assert _rel(za.cpu().numpy(), refa) <= 1e-4 * np.linalg.cond(p.blocks()).max() ** 0.5 + 1e-4
+
+
+# Tensor-core (BF16 operands, FP32 accumulation) forward against the FP64
+# oracle under identical weights: relative L2 <= 2e-2 on the output and on the
+# network's own part z - r (psi_d - x).  The shapes cover input channels that
+# are not a multiple of 16 (2M = 8), output channels below 16 (c0 = 8), one to
+# three pipeline stages, 128-pixel tiles with a ragged tail (24 x 24, 8 x 8
+# coarse grids), 64-channel levels (72 KB of weights per CTA), and a 128-wide
+# lift / projection (M = 64, 128 TMEM columns), and ReLU smoothers.
+@pytest.mark.parametrize("I,M,levels,c0,cmax,act", [(16, 8, 3, 8, 16, "linear"), (24, 4, 2, 8, 16, "linear"),
+                                                    (32, 16, 4, 16, 64, "linear"), (8, 8, 1, 8, 16, "linear"),
+                                                    (64, 64, 4, 16, 64, "linear"), (40, 20, 2, 24, 48, "linear"),
+                                                    (32, 8, 3, 16, 32, "relu")])
+def test_tensor_core_forward_matches_oracle(lib, I, M, levels, c0, cmax, act):
+    rte, shape, params, md, ctx, net, p = _setup(I=I, M=M, levels=levels, c0=c0, cmax=cmax,
+                                                 cc=4, ccmax=8, act=act)
+    assert net.precision == rte.MgNet.BF16
+    r = W.random_vector(ctx.n, 7)
+    z = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
+    net.precond(ctx, torch.tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rte.MgNet.kernel_status() == 0
+    ref = OM.apply_net(params, shape, OM.coeff_inputs(md), r)
+    zc = z.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(zc))
+    assert _rel(zc, ref) <= 2e-2
+    assert _rel(zc - r, ref - r) <= 2e-2
+    # and against the FP32 CUDA-core path of the same network
+    net.precision = rte.MgNet.FP32
+    z32 = torch.zeros_like(z)
+    net.precond(ctx, torch.tensor(r, device="cuda"), z32)
+    assert _rel(zc - r, z32.cpu().numpy() - r) <= 2e-2
+
+
+def test_precision_switch_rejects_unknown_value(lib):
+    rte, shape, params, md, ctx, net, p = _setup(I=8, M=8, levels=1)
+    with pytest.raises(rte.RteError):
+        net.precision = 2
+    assert net.precision == rte.MgNet.BF16
 
 
 @pytest.mark.parametrize("levels,batch", [(1, 1), (2, 3), (3, 2)])
@@ -87,6 +128,20 @@ def test_mgnet_preconditioned_solve(lib):
     assert _rel(psi.cpu().numpy(), ref) <= 1e-6          # cond(A) x tol on this medium
     r = p.rhs().ravel() - p.apply(x.cpu().numpy().reshape(2 * md.M, -1)).ravel()
     assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 2e-12
+
+
+def test_tensor_core_network_solve_reaches_tolerance(lib):
+    """A non-trivial network on the tensor cores preconditions a solve to a
+    true FP64 relative residual of 1e-10 (flexible GMRES absorbs the BF16
+    rounding of the preconditioner)."""
+    rte, shape, params, md, ctx, net, p = _setup(I=32, M=8, levels=3, proj=0.05)
+    net.set_params(W.init_params(shape, seed=1, proj_scale=0.05, vcycle_scale=0.5))
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, pc=net, tol=1e-10, restart=40, stall_ratio=10.0)
+    assert info["converged"] and not info["fell_back"], info
+    assert rte.MgNet.kernel_status() == 0
+    r = p.rhs().ravel() - p.apply(x.cpu().numpy().reshape(2 * md.M, -1)).ravel()
+    assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 1e-10
 
 
 def test_stalled_network_falls_back_to_block_jacobi(lib):
