@@ -16,11 +16,17 @@
 //
 // Shared memory: the layer's weights, packed once per weight version into the
 // MMA layout (tc_pack) and copied by one bulk async copy, then a ring of NS
-// stages of the gathered tile, one tap per stage.  Every thread issues the
-// cp.async of tap t, then waits for its own copies of tap t - 1, fences them
-// into the async proxy and meets the others at a barrier, after which one
-// thread issues tap t - 1's MMAs and commits them to the stage's mbarrier; tap
-// t + NS - 1 waits on that barrier before reusing the stage.  Operands use the
+// stages of the gathered tile, one tap per stage.  When every tap fits (up to
+// 64 input channels with 3 x 3 taps) all gathers are in flight at once and the
+// MMAs follow one wait.  Otherwise every thread issues the cp.async of tap t,
+// waits for its own copies of tap t - 1, fences them into the async proxy and
+// meets the others at a barrier, after which one thread issues tap t - 1's
+// MMAs and commits them to the stage's mbarrier; tap t + NS - 1 waits on that
+// barrier before reusing the stage.  Launched with programmatic dependent
+// launch, a layer allocates its tensor memory and copies its weights while the
+// previous layer finishes, and waits for it only before the gather; a layer
+// signals its dependents only after its last output store (the signal is what
+// makes those stores visible to them).  Operands use the
 // no-swizzle K-major canonical layout with 8 x 16-byte core matrices stored
 // row-group-major (byte (g KC + kc) 128 + (r mod 8) 16 for row 8 g + r mod 8,
 // channel chunk kc; KC chunks per row): leading (K) byte offset 128, stride
@@ -195,6 +201,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             "l"(a.w), "r"(wbytes), "r"(saddr(&w_bar))
             : "memory");
     }
+    // the inputs are the previous layer's outputs: wait for that grid (its
+    // writes before its trigger are visible after this)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // this thread gathers row r, channel chunks kc = half, half + 2, ...
     const int r = tid & (kRows - 1), half = tid >> 7;
     const int64_t p = p0 + r;
@@ -240,12 +249,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         cp_async_commit();
     };
-    // after this thread's copies of tap u have landed: ReLU them if asked,
-    // hand them to the async proxy, then one thread issues the tap's MMAs
-    bool ok = true;
-    auto finish = [&](int u, bool last) {
-        const int s = u % NS;
-        if (last) cp_async_wait<0>(); else cp_async_wait<1>();
+    // ReLU of this thread's own (landed) rows of stage s
+    auto relu_stage = [&](int s) {
         if (!F64IN && a.relu_in) {
             const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
             for (int kc = half; kc < KC; kc += 2) {
@@ -264,31 +269,63 @@ __global__ void __launch_bounds__(kThreads, 1)
                              : "memory");
             }
         }
+    };
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Npad >> 3) << 17) |
+                           ((uint32_t)(kRows >> 4) << 24);
+    auto issue = [&](int u) {       // one thread: the MMAs of tap u
+        const int s = u % NS;
+        for (int j = 0; j < KC / 2; ++j) {
+            const uint64_t ad = sdesc(xbase + s * stage_bytes + 2 * j * 128, 128, KC * 128);
+            const uint64_t bd = sdesc(wbase + u * tap_bytes + 2 * j * 128, 128, KC * 128);
+            tc_mma(tmem, ad, bd, idesc, (u > 0 || j > 0) ? 1u : 0u);
+        }
+    };
+    // after this thread's copies of tap u have landed: ReLU them if asked,
+    // hand them to the async proxy, then one thread issues the tap's MMAs
+    bool ok = true;
+    auto finish = [&](int u, bool last) {
+        const int s = u % NS;
+        if (last) cp_async_wait<0>(); else cp_async_wait<1>();
+        relu_stage(s);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             if (u == 0 && !mbar_wait(&w_bar, 0)) ok = false;
             if (ok) {
                 tc_fence_after();
-                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Npad >> 3) << 17) |
-                                       ((uint32_t)(kRows >> 4) << 24);
-                for (int j = 0; j < KC / 2; ++j) {
-                    const uint64_t ad = sdesc(xbase + s * stage_bytes + 2 * j * 128, 128, KC * 128);
-                    const uint64_t bd = sdesc(wbase + u * tap_bytes + 2 * j * 128, 128, KC * 128);
-                    tc_mma(tmem, ad, bd, idesc, (u > 0 || j > 0) ? 1u : 0u);
-                }
+                issue(u);
             }
             tc_commit(&mma_bar[s]);
         }
     };
-    for (int t = 0; t < T; ++t) {
-        const int s = t % NS;
-        if (t >= NS && !mbar_wait(&mma_bar[s], (unsigned)((t / NS) - 1) & 1u)) ok = false;
-        gather(t, s);
-        if (t > 0) finish(t - 1, false);
+    if (NS == T) {
+        // every tap has its own stage: all gathers in flight at once, one
+        // wait, then all MMAs back to back
+        for (int t = 0; t < T; ++t) gather(t, t);
+        cp_async_wait<0>();
+        for (int t = 0; t < T; ++t) relu_stage(t);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (!mbar_wait(&w_bar, 0)) ok = false;
+            if (ok) {
+                tc_fence_after();
+                for (int t = 0; t < T; ++t) issue(t);
+            }
+            tc_commit(&mma_bar[0]);
+        }
+        if (!mbar_wait(&mma_bar[0], 0)) ok = false;
+    } else {
+        // ring of NS stages: the gather of tap t overlaps the MMAs of tap t - 1
+        for (int t = 0; t < T; ++t) {
+            const int s = t % NS;
+            if (t >= NS && !mbar_wait(&mma_bar[s], (unsigned)((t / NS) - 1) & 1u)) ok = false;
+            gather(t, s);
+            if (t > 0) finish(t - 1, false);
+        }
+        finish(T - 1, true);
+        if (!mbar_wait(&mma_bar[(T - 1) % NS], (unsigned)((T - 1) / NS) & 1u)) ok = false;
     }
-    finish(T - 1, true);
-    if (!mbar_wait(&mma_bar[(T - 1) % NS], (unsigned)((T - 1) / NS) & 1u)) ok = false;
     if (tid == 0 && !mbar_wait(&w_bar, 0)) ok = false;   // weights landed even if no MMA ran
     tc_fence_after();
     if (!ok) {
@@ -351,8 +388,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     }
+    // every output of this CTA is written: the next layer may launch (its
+    // CTAs may wait in tcgen05.alloc until this CTA releases its columns)
     tc_fence_before();
     __syncthreads();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
@@ -428,21 +468,32 @@ const KernelLimits<F64IN>& limits() {
 }
 
 template <bool F64IN>
-void launch(const TcConv& a, cudaStream_t st) {
+void launch(const TcConv& a, bool pdl, cudaStream_t st) {
     const int T = a.T;
     const int KC = chunks_kc(a.Ci), Npad = pad_n(a.Co);
-    const int NS = T < kMaxStages ? T : kMaxStages;
     int k = 0;
     while ((32 << k) < Npad) ++k;
     const uint32_t ncols = 32u << k;
     const KernelLimits<F64IN>& L = limits<F64IN>();
-    size_t smem = (size_t)T * Npad * KC * 16 + (size_t)NS * KC * 2048;
+    const size_t wbytes = (size_t)T * Npad * KC * 16, stage = (size_t)KC * 2048;
+    // every tap resident if it fits, else a ring of kMaxStages stages
+    int NS = T;
+    if (wbytes + NS * stage > L.max_dyn) NS = T < kMaxStages ? T : kMaxStages;
+    size_t smem = wbytes + NS * stage;
     if (smem < L.floor_bytes[k]) smem = L.floor_bytes[k];
     if (smem > L.max_dyn) throw StatusError{RTE_EINVAL, "tensor-core convolution: tile exceeds shared memory"};
     const int64_t total = (int64_t)a.B * a.Hg * a.Wg;
-    const unsigned grid = (unsigned)((total + kRows - 1) / kRows);
-    k_conv_tc<F64IN><<<grid, kThreads, smem, st>>>(a, KC, Npad, NS, ncols);
-    check(cudaGetLastError(), "k_conv_tc");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((total + kRows - 1) / kRows));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    check(cudaLaunchKernelEx(&cfg, k_conv_tc<F64IN>, a, KC, Npad, NS, ncols), "k_conv_tc");
 }
 
 }  // namespace
@@ -456,7 +507,7 @@ void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int
     check(cudaGetLastError(), "k_tc_pack");
 }
 
-void tc_conv(const TcConv& a, cudaStream_t st) {
+void tc_conv(const TcConv& a, bool pdl, cudaStream_t st) {
     if (a.T < 1 || a.T > kMaxTaps || a.S < 1 || a.S > 2 || a.Ci < 1 || a.Co < 1 || !a.w ||
         (!a.x8) == (!a.x64) || (!a.y8) == (!a.y32))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: bad arguments"};
@@ -470,9 +521,9 @@ void tc_conv(const TcConv& a, cudaStream_t st) {
         tl_counters->flops += 2.0 * a.B * a.Co * (double)a.Hg * a.Wg * a.Ci * a.T;
     }
     if (a.x64)
-        launch<true>(a, st);
+        launch<true>(a, pdl, st);
     else
-        launch<false>(a, st);
+        launch<false>(a, pdl, st);
 }
 
 int conv_tc_status(bool reset) {

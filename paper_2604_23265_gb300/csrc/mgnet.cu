@@ -409,7 +409,7 @@ size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z,
             c.dy[t] = tp.dy[t];
             c.dx[t] = tp.dx[t];
         }
-        nn::tc_conv(c, n->stream);
+        nn::tc_conv(c, mode == TcMode::Run, n->stream);
     };
     auto conv = [&](const void* x8, int Ci, int Hi, int Co, int Hg, int S, void* y8, int Ho) {
         nn::TcConv c;

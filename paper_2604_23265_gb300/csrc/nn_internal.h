@@ -99,7 +99,9 @@ struct TcConv {
 size_t tc_weight_bytes(int T, int Ci, int Co);
 // packs W[t][i][o] = w[(o so + i si) KK + wi_t] into dst (tc_weight_bytes)
 void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int Co, void* dst, cudaStream_t st);
-void tc_conv(const TcConv& a, cudaStream_t st);
+// pdl: programmatic dependent launch (the weights must not be written by the
+// previous kernel in the stream)
+void tc_conv(const TcConv& a, bool pdl, cudaStream_t st);
 // 1 once a bounded wait of the tensor-core kernel expired (reset on request).
 int conv_tc_status(bool reset);
 void wgrad(const WgradArgs& a, cudaStream_t st);

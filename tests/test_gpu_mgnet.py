@@ -78,6 +78,22 @@ def test_tensor_core_forward_matches_oracle(lib, I, M, levels, c0, cmax, act):
     assert _rel(zc - r, z32.cpu().numpy() - r) <= 2e-2
 
 
+def test_tensor_core_repeated_applications_are_identical(lib):
+    """The first application packs the weights; later ones chain the layers by
+    programmatic dependent launch.  Every application gives the same bits."""
+    rte, shape, params, md, ctx, net, p = _setup(I=32, M=8, levels=3, c0=16, cmax=32)
+    r = torch.tensor(W.random_vector(ctx.n, 5), device="cuda")
+    outs = []
+    for k in range(4):
+        z = torch.full((ctx.n,), float("nan"), dtype=torch.float32, device="cuda")
+        net.precond(ctx, r, z)
+        outs.append(z.cpu().numpy())
+    assert rte.MgNet.kernel_status() == 0
+    assert np.all(np.isfinite(outs[0]))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
 def test_precision_switch_rejects_unknown_value(lib):
     rte, shape, params, md, ctx, net, p = _setup(I=8, M=8, levels=1)
     with pytest.raises(rte.RteError):
