@@ -216,6 +216,58 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const uint32_t row_off = (uint32_t)((r >> 3) * KC) * 128 + (uint32_t)(r & 7) * 16;
 
+    // epilogue row of this thread (warp w reads TMEM lanes 32 (w mod 4) ...;
+    // the two warps on the same lanes take alternate 16-column blocks)
+    const int quad = warp & 3, first_c16 = warp >> 2;
+    const int64_t pe = p0 + quad * 32 + (tid & 31);
+    int oy = 0, ox = 0, eb = 0;
+    if (pe < total) {
+        const int egx = (int)(pe % a.Wg), egy = (int)((pe / a.Wg) % a.Hg);
+        eb = (int)(pe / ((int64_t)a.Wg * a.Hg));
+        oy = a.OS * egy + a.OY0;
+        ox = a.OS * egx + a.OX0;
+    }
+    const size_t oplane = (size_t)a.Ho * a.Wo;
+    const size_t opix = (size_t)oy * a.Wo + ox;
+    const int KCo = (a.Co + 7) / 8;
+    // gate and base of a 16-column block (read-only in this kernel)
+    auto load_epi = [&](int c16, float (&g)[16], float (&bb)[16]) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            g[i] = 1.f;
+            bb[i] = 0.f;
+        }
+        if (pe >= total) return;
+        if (a.gate) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int co = c16 * 16 + i;
+                if (co < a.Co) g[i] = __ldg(a.gate + (size_t)co * oplane + opix);
+            }
+        }
+        if (a.base8) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kc = c16 * 2 + h;
+                if (kc < KCo) {
+                    float t8[8];
+                    unpack8(__ldg(reinterpret_cast<const uint4*>(a.base8) + ((size_t)eb * KCo + kc) * oplane + opix),
+                            t8);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) bb[h * 8 + i] = t8[i];
+                }
+            }
+        } else if (a.base64) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int co = c16 * 16 + i;
+                if (co < a.Co) bb[i] = (float)__ldg(a.base64 + ((size_t)eb * a.Co + co) * oplane + opix);
+            }
+        }
+    };
+    float eg[16], eb8[16];
+    if (first_c16 < Npad / 16) load_epi(first_c16, eg, eb8);
+
     auto gather = [&](int t, int s) {
         const int iy = a.S * gy + a.dy[t], ix = a.S * gx + a.dx[t];
         const bool in = live && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
@@ -335,57 +387,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     ok = fail == 0;
 
-    // epilogue
-    const int quad = warp & 3;
-    const int row = quad * 32 + (tid & 31);
-    const int64_t pe = p0 + row;
-    int oy = 0, ox = 0, eb = 0;
-    if (pe < total) {
-        const int egx = (int)(pe % a.Wg), egy = (int)((pe / a.Wg) % a.Hg);
-        eb = (int)(pe / ((int64_t)a.Wg * a.Hg));
-        oy = a.OS * egy + a.OY0;
-        ox = a.OS * egx + a.OX0;
-    }
-    const size_t oplane = (size_t)a.Ho * a.Wo;
-    const size_t opix = (size_t)oy * a.Wo + ox;
-    const int KCo = (a.Co + 7) / 8;
+    // epilogue: block c16 of 16 columns; the operands of the next block are
+    // loaded before the current one is stored, so each thread has one round
+    // trip in flight per block instead of one per element
     const float nanv = __int_as_float(0x7fc00000);
-    for (int c16 = warp >> 2; c16 < Npad / 16; c16 += 2) {
+    for (int c16 = first_c16; c16 < Npad / 16; c16 += 2) {
         float acc[16];
         tc_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c16 * 16), acc);
-        if (pe >= total) continue;
+        float gn[16], bn[16];
+        if (c16 + 2 < Npad / 16) load_epi(c16 + 2, gn, bn);
+        if (pe < total) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int kc = c16 * 2 + h;
-            if (kc >= KCo) break;
-            float v[8], base[8];
-            if (a.base8) {
-                const uint4 u = reinterpret_cast<const uint4*>(a.base8)[((size_t)eb * KCo + kc) * oplane + opix];
-                unpack8(u, base);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int co = kc * 8 + i;
-                float x = 0.f;
-                if (co < a.Co) {
-                    x = acc[h * 8 + i];
-                    if (a.gate) x *= __ldg(a.gate + (size_t)co * oplane + opix);
-                    x *= a.sign;
-                    if (a.base8) x += base[i];
-                    if (a.base64) x += (float)__ldg(a.base64 + ((size_t)eb * a.Co + co) * oplane + opix);
-                    if (!ok) x = nanv;
-                }
-                v[i] = x;
-            }
-            if (a.y8) {
-                reinterpret_cast<uint4*>(a.y8)[((size_t)eb * KCo + kc) * oplane + opix] = pack8(v);
-            } else {
+            for (int h = 0; h < 2; ++h) {
+                const int kc = c16 * 2 + h;
+                if (kc >= KCo) break;
+                float v[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int co = kc * 8 + i;
-                    if (co < a.Co) a.y32[((size_t)eb * a.Co + co) * oplane + opix] = v[i];
+                    const float x = a.sign * (acc[h * 8 + i] * eg[h * 8 + i]) + eb8[h * 8 + i];
+                    v[i] = co < a.Co ? (ok ? x : nanv) : 0.f;
+                }
+                if (a.y8) {
+                    reinterpret_cast<uint4*>(a.y8)[((size_t)eb * KCo + kc) * oplane + opix] = pack8(v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int co = kc * 8 + i;
+                        if (co < a.Co) a.y32[((size_t)eb * a.Co + co) * oplane + opix] = v[i];
+                    }
                 }
             }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            eg[i] = gn[i];
+            eb8[i] = bn[i];
         }
     }
     // every output of this CTA is written: the next layer may launch (its
