@@ -3,40 +3,45 @@
 //
 // Implicit GEMM over tap tables:
 //   D[p][o] = sum_t sum_i X[b][i][S gy_p + dy_t][S gx_p + dx_t] W[t][i][o]
-// with M = 128 class-grid pixels per CTA (pixel r of the tile owns TMEM lane
-// r), N = output channels rounded up to 16 (TMEM columns), and one MMA of
-// K = 16 input channels per (tap, channel pair group).
+// with M = 128 class-grid pixels per CTA (pixel row m of the tile owns TMEM
+// lane m), N = output channels rounded up to 16 (TMEM columns), and one MMA of
+// K = 16 input channels per (tap, channel pair).
 //
 // Activations between the layers are BF16 in a channel-chunked layout
 // "C8" = [B][ceil(C/8)][H][W][8]: the 8 channels of one pixel are one 16-byte
-// row of an MMA core matrix, so gathering tap t of the tile is one 16-byte
-// cp.async per (pixel, chunk), zero-filled outside the image.  The first layer
-// (lift) reads the FP64 Krylov vector [2M][I][I] directly and converts; the
-// last (projection) writes FP32 [2M][I][I].
+// row of an MMA core matrix.  Both operands use the no-swizzle K-major
+// canonical layout (8 rows x 16 bytes per core matrix).
 //
-// Shared memory: the layer's weights, packed once per weight version into the
-// MMA layout (tc_pack) and copied by one bulk async copy, then a ring of NS
-// stages of the gathered tile, one tap per stage.  When every tap fits (up to
-// 64 input channels with 3 x 3 taps) all gathers are in flight at once and the
-// MMAs follow one wait.  Otherwise every thread issues the cp.async of tap t,
-// waits for its own copies of tap t - 1, fences them into the async proxy and
-// meets the others at a barrier, after which one thread issues tap t - 1's
-// MMAs and commits them to the stage's mbarrier; tap t + NS - 1 waits on that
-// barrier before reusing the stage.  Launched with programmatic dependent
-// launch, a layer allocates its tensor memory and copies its weights while the
-// previous layer finishes, and waits for it only before the gather; a layer
-// signals its dependents only after its last output store (the signal is what
-// makes those stores visible to them).  Operands use the
-// no-swizzle K-major canonical layout with 8 x 16-byte core matrices stored
-// row-group-major (byte (g KC + kc) 128 + (r mod 8) 16 for row 8 g + r mod 8,
-// channel chunk kc; KC chunks per row): leading (K) byte offset 128, stride
-// (M/N) byte offset 128 KC.
+// Input staging, by layer:
+//  * halo (stride-1 taps within +-1: the 3 x 3 smoothers, the four parity
+//    classes of the transposed prolongation, the 1 x 1 projection): one TMA
+//    tensor load brings the tile's rows with a one-pixel halo, [KC][BH][BW]
+//    x 16 bytes, zero outside the image.  The tile is R rows x SW columns of
+//    the class grid (SW = min(W, 128), BW = SW + 2, BH = R + 2) and MMA row m
+//    is halo pixel (m / BW + 1, m mod BW + 1), so the A operand of tap
+//    (dy, dx) is the same buffer shifted by dy BW + dx rows: no copy per tap.
+//    Rows with m mod BW >= SW are computed and discarded.
+//  * gather (the stride-2 restriction): tap t of the tile is one 16-byte
+//    cp.async per (pixel, chunk), all taps in flight at once when they fit in
+//    shared memory, else a ring of three stages overlapping the MMAs.
+//  * FP64 (the lift from the Krylov vector [2M][I][I]): loaded and converted
+//    by the threads.
+// The weights of a layer are packed once per weight version into the MMA
+// layout (tc_pack) and arrive by one bulk async copy.
+//
+// The four parity classes of a transposed convolution run as one launch
+// (blockIdx.y = class, each with its own taps, weights and output offset).
+// Layers are chained by programmatic dependent launch: a layer allocates its
+// tensor memory and copies its weights while the previous layer finishes,
+// waits for it only before touching activations, and signals its dependents
+// after its last store (the signal is what makes those stores visible).
 //
 // The epilogue reads the accumulators back with tcgen05.ld (warp w sees lanes
 // 32 (w mod 4) ...; the two warps on the same lanes take alternate 16-column
 // blocks) and applies v = sign (acc o gate) (+ base) before the store.
 // Every wait is bounded: on expiry the CTA records the failure in a device
 // flag, writes NaN outputs, releases its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <mutex>
@@ -52,6 +57,8 @@ constexpr int kThreads = 256;
 constexpr int kMaxStages = 3;
 constexpr long long kSpinLimit = 1ll << 24;
 
+enum Mode { kGather = 0, kF64 = 1, kHalo = 2 };
+
 __device__ int g_tc_status;          // 1 once a bounded wait expired
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -66,6 +73,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
@@ -137,6 +149,16 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// TMA tiled load of a 4-D box into shared memory, completion on an mbarrier
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -155,94 +177,139 @@ __device__ __forceinline__ void unpack8(uint4 u, float (&v)[8]) {
     }
 }
 
+// ReLU of the BF16 pairs of 16 bytes of shared memory
+__device__ __forceinline__ void relu16(uint32_t addr) {
+    uint32_t w[4];
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                 : "r"(addr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {      // clear negative halves
+        const uint32_t lo = (w[i] & 0x8000u) ? 0u : (w[i] & 0xFFFFu);
+        const uint32_t hi = (w[i] & 0x80000000u) ? 0u : (w[i] & 0xFFFF0000u);
+        w[i] = lo | hi;
+    }
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+}
+
+// Geometry of one launch (host computed).
 // KC: channel chunks of 8 per MMA row (even); Npad: output channels rounded
-// up to 16; NS: stages; ncols: allocated TMEM columns (power of two >= Npad).
-// F64IN: the input is FP64 [B][Ci][Hi][Wi] (converted while gathering),
-// otherwise BF16 C8.
-template <bool F64IN>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_conv_tc(const __grid_constant__ TcConv a, int KC, int Npad, int NS, uint32_t ncols) {
-    extern __shared__ __align__(128) unsigned char smem[];
+// up to 16; NS: stages (gather modes); ncols: TMEM columns (power of two >=
+// Npad); halo mode: tile SW x R class-grid pixels, halo box BW x BH, tiles_x
+// tiles across the width, tiles_y down the height; xoff: byte offset of the
+// input staging area (1024-aligned).
+struct Geo {
+    int KC, Npad, NS;
+    uint32_t ncols;
+    int SW, R, BW, BH, tiles_x, tiles_y;
+    uint32_t xoff;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__ TcConv a, const Geo g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mma_bar[kMaxStages];
-    __shared__ __align__(8) uint64_t w_bar;
+    __shared__ __align__(8) uint64_t w_bar, x_bar;
     __shared__ uint32_t tslot;
     __shared__ int fail;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int T = a.T;
+    const int KC = g.KC, Npad = g.Npad, NS = g.NS;
+    const int T = a.T, cls = blockIdx.y;
     const uint32_t tap_bytes = (uint32_t)Npad * KC * 16;
     const uint32_t stage_bytes = (uint32_t)KC * 2048;
     const uint32_t wbytes = (uint32_t)T * tap_bytes;
-    const uint32_t wbase = saddr(smem), xbase = wbase + wbytes;
-    const int64_t total = (int64_t)a.B * a.Hg * a.Wg;
-    const int64_t p0 = (int64_t)blockIdx.x * kRows;
+    const uint32_t wbase = saddr(smem), xbase = wbase + g.xoff;
     const int KCi = (a.Ci + 7) / 8;
+    const int OY0 = a.oy0[cls], OX0 = a.ox0[cls];
+
+    // tile of this CTA: halo mode, rows y0 .. y0 + R - 1, columns x0 .. x0 + SW - 1
+    // of batch entry tb; gather modes, 128 consecutive pixels from p0
+    int tb = 0, y0 = 0, x0 = 0;
+    int64_t p0 = 0;
+    const int64_t total = (int64_t)a.B * a.Hg * a.Wg;
+    if (MODE == kHalo) {
+        int q = blockIdx.x;
+        const int tx = q % g.tiles_x;
+        q /= g.tiles_x;
+        const int ty = q % g.tiles_y;
+        tb = q / g.tiles_y;
+        y0 = ty * g.R;
+        x0 = tx * g.SW;
+    } else {
+        p0 = (int64_t)blockIdx.x * kRows;
+    }
+    // class-grid pixel of MMA row m (false: no output there)
+    auto pixel = [&](int m, int& b, int& gy, int& gx) -> bool {
+        if (MODE == kHalo) {
+            const int yy = m / g.BW, xx = m - yy * g.BW;
+            b = tb;
+            gy = y0 + yy;
+            gx = x0 + xx;
+            return xx < g.SW && yy < g.R && gy < a.Hg && gx < a.Wg;
+        }
+        const int64_t p = p0 + m;
+        if (p >= total) return false;
+        gx = (int)(p % a.Wg);
+        gy = (int)((p / a.Wg) % a.Hg);
+        b = (int)(p / ((int64_t)a.Wg * a.Hg));
+        return true;
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tslot)),
-                     "r"(ncols)
+                     "r"(g.ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         fail = 0;
-        for (int s = 0; s < NS; ++s) mbar_init(&mma_bar[s], 1);
+        for (int s = 0; s < kMaxStages; ++s) mbar_init(&mma_bar[s], 1);
         mbar_init(&w_bar, 1);
+        mbar_init(&x_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    if (tid == 0) {      // packed weights: one bulk copy tracked by w_bar
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&w_bar)), "r"(wbytes)
-                     : "memory");
+    if (tid == 0) {      // this class's packed weights: one bulk copy tracked by w_bar
+        mbar_expect(&w_bar, wbytes);
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(wbase),
-            "l"(a.w), "r"(wbytes), "r"(saddr(&w_bar))
+            "l"(static_cast<const char*>(a.w) + (size_t)cls * wbytes), "r"(wbytes), "r"(saddr(&w_bar))
             : "memory");
     }
     // the inputs are the previous layer's outputs: wait for that grid (its
     // writes before its trigger are visible after this)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // this thread gathers row r, channel chunks kc = half, half + 2, ...
-    const int r = tid & (kRows - 1), half = tid >> 7;
-    const int64_t p = p0 + r;
-    const bool live = p < total;
-    int gx = 0, gy = 0, b = 0;
-    if (live) {
-        gx = (int)(p % a.Wg);
-        gy = (int)((p / a.Wg) % a.Hg);
-        b = (int)(p / ((int64_t)a.Wg * a.Hg));
+    if (MODE == kHalo && tid == 0) {
+        mbar_expect(&x_bar, (uint32_t)KCi * g.BH * g.BW * 16);
+        tma_load_4d(xbase, &a.tmap, 0, x0 - 1, y0 - 1, tb * KCi, &x_bar);
     }
-    const uint32_t row_off = (uint32_t)((r >> 3) * KC) * 128 + (uint32_t)(r & 7) * 16;
 
     // epilogue row of this thread (warp w reads TMEM lanes 32 (w mod 4) ...;
     // the two warps on the same lanes take alternate 16-column blocks)
     const int quad = warp & 3, first_c16 = warp >> 2;
-    const int64_t pe = p0 + quad * 32 + (tid & 31);
-    int oy = 0, ox = 0, eb = 0;
-    if (pe < total) {
-        const int egx = (int)(pe % a.Wg), egy = (int)((pe / a.Wg) % a.Hg);
-        eb = (int)(pe / ((int64_t)a.Wg * a.Hg));
-        oy = a.OS * egy + a.OY0;
-        ox = a.OS * egx + a.OX0;
-    }
+    int eb = 0, egy = 0, egx = 0;
+    const bool elive = pixel(quad * 32 + (tid & 31), eb, egy, egx);
+    const int oy = a.OS * egy + OY0, ox = a.OS * egx + OX0;
     const size_t oplane = (size_t)a.Ho * a.Wo;
-    const size_t opix = (size_t)oy * a.Wo + ox;
+    const size_t opix = elive ? (size_t)oy * a.Wo + ox : 0;
     const int KCo = (a.Co + 7) / 8;
     // gate and base of a 16-column block (read-only in this kernel)
-    auto load_epi = [&](int c16, float (&g)[16], float (&bb)[16]) {
+    auto load_epi = [&](int c16, float (&gt)[16], float (&bb)[16]) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            g[i] = 1.f;
+            gt[i] = 1.f;
             bb[i] = 0.f;
         }
-        if (pe >= total) return;
+        if (!elive) return;
         if (a.gate) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int co = c16 * 16 + i;
-                if (co < a.Co) g[i] = __ldg(a.gate + (size_t)co * oplane + opix);
+                if (co < a.Co) gt[i] = __ldg(a.gate + (size_t)co * oplane + opix);
             }
         }
         if (a.base8) {
@@ -268,117 +335,142 @@ __global__ void __launch_bounds__(kThreads, 1)
     float eg[16], eb8[16];
     if (first_c16 < Npad / 16) load_epi(first_c16, eg, eb8);
 
-    auto gather = [&](int t, int s) {
-        const int iy = a.S * gy + a.dy[t], ix = a.S * gx + a.dx[t];
-        const bool in = live && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
-        const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
-        if constexpr (F64IN) {
-            const size_t plane = (size_t)a.Hi * a.Wi;
-            const double* xp = a.x64 + (size_t)b * a.Ci * plane + (in ? (size_t)iy * a.Wi + ix : 0);
-#pragma unroll 4
-            for (int kc = half; kc < KC; kc += 2) {
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int ci = kc * 8 + j;
-                    const float x = (in && ci < a.Ci) ? (float)__ldg(xp + (size_t)ci * plane) : 0.f;
-                    v[j] = a.relu_in ? fmaxf(x, 0.f) : x;
-                }
-                const uint4 pk = pack8(v);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + kc * 128), "r"(pk.x),
-                             "r"(pk.y), "r"(pk.z), "r"(pk.w)
-                             : "memory");
-            }
-        } else {
-            const uint4* xp = reinterpret_cast<const uint4*>(a.x8);
-            const size_t plane = (size_t)a.Hi * a.Wi;
-            const size_t pix = in ? (size_t)iy * a.Wi + ix : 0;
-            for (int kc = half; kc < KC; kc += 2) {
-                const bool ok = in && kc < KCi;
-                const uint4* src = ok ? xp + ((size_t)b * KCi + kc) * plane + pix : xp;
-                cp_async16(dst + kc * 128, src, ok ? 16u : 0u);
-            }
-        }
-        cp_async_commit();
-    };
-    // ReLU of this thread's own (landed) rows of stage s
-    auto relu_stage = [&](int s) {
-        if (!F64IN && a.relu_in) {
-            const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
-            for (int kc = half; kc < KC; kc += 2) {
-                uint32_t w[4];
-                asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                             : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-                             : "r"(dst + kc * 128));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {      // ReLU of two BF16: clear negative halves
-                    const uint32_t lo = (w[i] & 0x8000u) ? 0u : (w[i] & 0xFFFFu);
-                    const uint32_t hi = (w[i] & 0x80000000u) ? 0u : (w[i] & 0xFFFF0000u);
-                    w[i] = lo | hi;
-                }
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + kc * 128), "r"(w[0]),
-                             "r"(w[1]), "r"(w[2]), "r"(w[3])
-                             : "memory");
-            }
-        }
-    };
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Npad >> 3) << 17) |
                            ((uint32_t)(kRows >> 4) << 24);
-    auto issue = [&](int u) {       // one thread: the MMAs of tap u
-        const int s = u % NS;
-        for (int j = 0; j < KC / 2; ++j) {
-            const uint64_t ad = sdesc(xbase + s * stage_bytes + 2 * j * 128, 128, KC * 128);
-            const uint64_t bd = sdesc(wbase + u * tap_bytes + 2 * j * 128, 128, KC * 128);
-            tc_mma(tmem, ad, bd, idesc, (u > 0 || j > 0) ? 1u : 0u);
-        }
-    };
-    // after this thread's copies of tap u have landed: ReLU them if asked,
-    // hand them to the async proxy, then one thread issues the tap's MMAs
     bool ok = true;
-    auto finish = [&](int u, bool last) {
-        const int s = u % NS;
-        if (last) cp_async_wait<0>(); else cp_async_wait<1>();
-        relu_stage(s);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            if (u == 0 && !mbar_wait(&w_bar, 0)) ok = false;
-            if (ok) {
-                tc_fence_after();
-                issue(u);
-            }
-            tc_commit(&mma_bar[s]);
+
+    if (MODE == kHalo) {
+        // the halo is written by the async proxy and read by it: only ReLU
+        // or the zero chunk of an odd channel count touch it from the threads
+        const uint32_t plane_bytes = (uint32_t)g.BH * g.BW * 16;
+        if (a.relu_in || KC > KCi) {
+            if (!mbar_wait(&x_bar, 0)) ok = false;
+            if (a.relu_in)
+                for (uint32_t o = tid * 16; o < (uint32_t)KCi * plane_bytes; o += kThreads * 16) relu16(xbase + o);
+            for (uint32_t o = KCi * plane_bytes + tid * 16; o < (uint32_t)KC * plane_bytes; o += kThreads * 16)
+                asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(xbase + o), "r"(0u) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
         }
-    };
-    if (NS == T) {
-        // every tap has its own stage: all gathers in flight at once, one
-        // wait, then all MMAs back to back
-        for (int t = 0; t < T; ++t) gather(t, t);
-        cp_async_wait<0>();
-        for (int t = 0; t < T; ++t) relu_stage(t);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
         if (tid == 0) {
-            if (!mbar_wait(&w_bar, 0)) ok = false;
+            if (!mbar_wait(&w_bar, 0) || !mbar_wait(&x_bar, 0)) ok = false;
             if (ok) {
                 tc_fence_after();
-                for (int t = 0; t < T; ++t) issue(t);
+                for (int t = 0; t < T; ++t) {
+                    const int tt = cls * T + t;
+                    const uint32_t shift = (uint32_t)((1 + a.dy[tt]) * g.BW + (1 + a.dx[tt])) * 16;
+                    for (int j = 0; j < KC / 2; ++j) {
+                        const uint64_t ad = sdesc(xbase + 2 * j * plane_bytes + shift, plane_bytes, 128);
+                        const uint64_t bd = sdesc(wbase + t * tap_bytes + 2 * j * 128, 128, KC * 128);
+                        tc_mma(tmem, ad, bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
+                    }
+                }
             }
             tc_commit(&mma_bar[0]);
         }
         if (!mbar_wait(&mma_bar[0], 0)) ok = false;
     } else {
-        // ring of NS stages: the gather of tap t overlaps the MMAs of tap t - 1
-        for (int t = 0; t < T; ++t) {
-            const int s = t % NS;
-            if (t >= NS && !mbar_wait(&mma_bar[s], (unsigned)((t / NS) - 1) & 1u)) ok = false;
-            gather(t, s);
-            if (t > 0) finish(t - 1, false);
+        // this thread gathers row r, channel chunks kc = half, half + 2, ...
+        const int r = tid & (kRows - 1), half = tid >> 7;
+        int b = 0, gy = 0, gx = 0;
+        const bool live = pixel(r, b, gy, gx);
+        const uint32_t row_off = (uint32_t)((r >> 3) * KC) * 128 + (uint32_t)(r & 7) * 16;
+        auto gather = [&](int t, int s) {
+            const int tt = cls * T + t;
+            const int iy = a.S * gy + a.dy[tt], ix = a.S * gx + a.dx[tt];
+            const bool in = live && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+            const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
+            const size_t plane = (size_t)a.Hi * a.Wi;
+            if (MODE == kF64) {
+                const double* xp = a.x64 + (size_t)b * a.Ci * plane + (in ? (size_t)iy * a.Wi + ix : 0);
+#pragma unroll 4
+                for (int kc = half; kc < KC; kc += 2) {
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int ci = kc * 8 + j;
+                        const float x = (in && ci < a.Ci) ? (float)__ldg(xp + (size_t)ci * plane) : 0.f;
+                        v[j] = a.relu_in ? fmaxf(x, 0.f) : x;
+                    }
+                    const uint4 pk = pack8(v);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + kc * 128), "r"(pk.x),
+                                 "r"(pk.y), "r"(pk.z), "r"(pk.w)
+                                 : "memory");
+                }
+            } else {
+                const uint4* xp = reinterpret_cast<const uint4*>(a.x8);
+                const size_t pix = in ? (size_t)iy * a.Wi + ix : 0;
+                for (int kc = half; kc < KC; kc += 2) {
+                    const bool okc = in && kc < KCi;
+                    const uint4* src = okc ? xp + ((size_t)b * KCi + kc) * plane + pix : xp;
+                    cp_async16(dst + kc * 128, src, okc ? 16u : 0u);
+                }
+            }
+            cp_async_commit();
+        };
+        // ReLU of this thread's own (landed) rows of stage s
+        auto relu_stage = [&](int s) {
+            if (MODE == kGather && a.relu_in) {
+                const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
+                for (int kc = half; kc < KC; kc += 2) relu16(dst + kc * 128);
+            }
+        };
+        auto issue = [&](int u) {       // one thread: the MMAs of tap u
+            const int s = u % NS;
+            for (int j = 0; j < KC / 2; ++j) {
+                const uint64_t ad = sdesc(xbase + s * stage_bytes + 2 * j * 128, 128, KC * 128);
+                const uint64_t bd = sdesc(wbase + u * tap_bytes + 2 * j * 128, 128, KC * 128);
+                tc_mma(tmem, ad, bd, idesc, (u > 0 || j > 0) ? 1u : 0u);
+            }
+        };
+        // after this thread's copies of tap u have landed: ReLU them if asked,
+        // hand them to the async proxy, then one thread issues the tap's MMAs
+        auto finish = [&](int u, bool last) {
+            const int s = u % NS;
+            if (last) cp_async_wait<0>(); else cp_async_wait<1>();
+            relu_stage(s);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                if (u == 0 && !mbar_wait(&w_bar, 0)) ok = false;
+                if (ok) {
+                    tc_fence_after();
+                    issue(u);
+                }
+                tc_commit(&mma_bar[s]);
+            }
+        };
+        if (NS == T) {
+            // every tap has its own stage: all gathers in flight at once, one
+            // wait, then all MMAs back to back
+            for (int t = 0; t < T; ++t) gather(t, t);
+            cp_async_wait<0>();
+            for (int t = 0; t < T; ++t) relu_stage(t);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                if (!mbar_wait(&w_bar, 0)) ok = false;
+                if (ok) {
+                    tc_fence_after();
+                    for (int t = 0; t < T; ++t) issue(t);
+                }
+                tc_commit(&mma_bar[0]);
+            }
+            if (!mbar_wait(&mma_bar[0], 0)) ok = false;
+        } else {
+            // ring of NS stages: the gather of tap t overlaps the MMAs of tap t - 1
+            for (int t = 0; t < T; ++t) {
+                const int s = t % NS;
+                if (t >= NS && !mbar_wait(&mma_bar[s], (unsigned)((t / NS) - 1) & 1u)) ok = false;
+                gather(t, s);
+                if (t > 0) finish(t - 1, false);
+            }
+            finish(T - 1, true);
+            if (!mbar_wait(&mma_bar[(T - 1) % NS], (unsigned)((T - 1) / NS) & 1u)) ok = false;
         }
-        finish(T - 1, true);
-        if (!mbar_wait(&mma_bar[(T - 1) % NS], (unsigned)((T - 1) / NS) & 1u)) ok = false;
     }
-    if (tid == 0 && !mbar_wait(&w_bar, 0)) ok = false;   // weights landed even if no MMA ran
+    if (tid == 0 && !mbar_wait(&w_bar, 0)) ok = false;   // the weight copy has landed in every case
+    if (MODE == kHalo && tid == 0 && !mbar_wait(&x_bar, 0)) ok = false;
     tc_fence_after();
     if (!ok) {
         fail = 1;
@@ -396,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c16 * 16), acc);
         float gn[16], bn[16];
         if (c16 + 2 < Npad / 16) load_epi(c16 + 2, gn, bn);
-        if (pe < total) {
+        if (elive) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int kc = c16 * 2 + h;
@@ -432,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.ncols) : "memory");
     }
 }
 
@@ -463,7 +555,6 @@ __global__ void k_tc_pack(const float* __restrict__ w, int so, int si, int KK, T
 int chunks_kc(int Ci) { return ((Ci + 15) / 16) * 2; }
 int pad_n(int Co) { return ((Co + 15) / 16) * 16; }
 
-template <bool F64IN>
 struct KernelLimits {
     size_t max_dyn = 0;
     size_t floor_bytes[4] = {0, 0, 0, 0};   // by TMEM columns 32, 64, 128, 256
@@ -473,9 +564,9 @@ struct KernelLimits {
 // per TMEM column count, the least dynamic shared memory that keeps the
 // resident CTAs of one SM within the 512 TMEM columns (a CTA would otherwise
 // wait in tcgen05.alloc).
-template <bool F64IN>
-const KernelLimits<F64IN>& limits() {
-    static KernelLimits<F64IN> L;
+template <int MODE>
+const KernelLimits& limits() {
+    static KernelLimits L;
     static std::once_flag once;
     std::call_once(once, [] {
         int dev = 0, optin = 0, per_sm = 0;
@@ -483,17 +574,16 @@ const KernelLimits<F64IN>& limits() {
         check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attribute");
         check(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev), "attribute");
         cudaFuncAttributes fa{};
-        check(cudaFuncGetAttributes(&fa, k_conv_tc<F64IN>), "cudaFuncGetAttributes");
+        check(cudaFuncGetAttributes(&fa, k_conv_tc<MODE>), "cudaFuncGetAttributes");
         L.max_dyn = (size_t)optin - fa.sharedSizeBytes;
-        check(cudaFuncSetAttribute(k_conv_tc<F64IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.max_dyn),
+        check(cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.max_dyn),
               "cudaFuncSetAttribute");
         for (int k = 0; k < 4; ++k) {
             const int allowed = 512 / (32 << k);
             size_t s = 0;
             for (;;) {
                 int nb = 0;
-                check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_tc<F64IN>, kThreads, s),
-                      "occupancy");
+                check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_conv_tc<MODE>, kThreads, s), "occupancy");
                 if (nb <= allowed) break;
                 s = s == 0 ? (size_t)per_sm / (allowed + 1) : s + 4096;
                 if (s > L.max_dyn) throw StatusError{RTE_EINVAL, "cannot bound tensor-core occupancy"};
@@ -504,24 +594,38 @@ const KernelLimits<F64IN>& limits() {
     return L;
 }
 
-template <bool F64IN>
-void launch(const TcConv& a, bool pdl, cudaStream_t st) {
-    const int T = a.T;
-    const int KC = chunks_kc(a.Ci), Npad = pad_n(a.Co);
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, reached through the runtime (no libcuda link)
+EncodeTiled encoder() {
+    static EncodeTiled fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        check(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q),
+              "cudaGetDriverEntryPointByVersion");
+        if (q != cudaDriverEntryPointSuccess || !p)
+            throw StatusError{RTE_ECUDA, "cuTensorMapEncodeTiled is not available"};
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+template <int MODE>
+void launch(const TcConv& a, Geo g, size_t stage_area, bool pdl, unsigned grid_x, cudaStream_t st) {
+    g.ncols = 32;
+    while (g.ncols < (uint32_t)g.Npad) g.ncols <<= 1;
     int k = 0;
-    while ((32 << k) < Npad) ++k;
-    const uint32_t ncols = 32u << k;
-    const KernelLimits<F64IN>& L = limits<F64IN>();
-    const size_t wbytes = (size_t)T * Npad * KC * 16, stage = (size_t)KC * 2048;
-    // every tap resident if it fits, else a ring of kMaxStages stages
-    int NS = T;
-    if (wbytes + NS * stage > L.max_dyn) NS = T < kMaxStages ? T : kMaxStages;
-    size_t smem = wbytes + NS * stage;
+    while ((32u << k) < g.ncols) ++k;
+    const KernelLimits& L = limits<MODE>();
+    const size_t wbytes = (size_t)a.T * g.Npad * g.KC * 16;
+    g.xoff = (uint32_t)((wbytes + 1023) & ~(size_t)1023);
+    size_t smem = g.xoff + stage_area;
     if (smem < L.floor_bytes[k]) smem = L.floor_bytes[k];
     if (smem > L.max_dyn) throw StatusError{RTE_EINVAL, "tensor-core convolution: tile exceeds shared memory"};
-    const int64_t total = (int64_t)a.B * a.Hg * a.Wg;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((total + kRows - 1) / kRows));
+    cfg.gridDim = dim3(grid_x, (unsigned)a.classes);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -530,7 +634,7 @@ void launch(const TcConv& a, bool pdl, cudaStream_t st) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    check(cudaLaunchKernelEx(&cfg, k_conv_tc<F64IN>, a, KC, Npad, NS, ncols), "k_conv_tc");
+    check(cudaLaunchKernelEx(&cfg, k_conv_tc<MODE>, a, g), "k_conv_tc");
 }
 
 }  // namespace
@@ -544,23 +648,63 @@ void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int
     check(cudaGetLastError(), "k_tc_pack");
 }
 
-void tc_conv(const TcConv& a, bool pdl, cudaStream_t st) {
-    if (a.T < 1 || a.T > kMaxTaps || a.S < 1 || a.S > 2 || a.Ci < 1 || a.Co < 1 || !a.w ||
-        (!a.x8) == (!a.x64) || (!a.y8) == (!a.y32))
+void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
+    TcConv a = in;
+    if (a.T < 1 || a.classes < 1 || a.classes > 4 || a.T * a.classes > kMaxTaps || a.S < 1 || a.S > 2 ||
+        a.Ci < 1 || a.Co < 1 || !a.w || (!a.x8) == (!a.x64) || (!a.y8) == (!a.y32))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: bad arguments"};
     if (pad_n(a.Co) > 256) throw StatusError{RTE_EINVAL, "tensor-core convolution: more than 256 output channels"};
     if (reinterpret_cast<uintptr_t>(a.w) % 16 || (a.x8 && reinterpret_cast<uintptr_t>(a.x8) % 16) ||
         (a.y8 && reinterpret_cast<uintptr_t>(a.y8) % 16) || (a.base8 && reinterpret_cast<uintptr_t>(a.base8) % 16))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: buffers must be 16-byte aligned"};
-    if ((int64_t)a.B * a.Hg * a.Wg == 0) return;
+    const int64_t total = (int64_t)a.B * a.Hg * a.Wg;
+    if (total == 0) return;
     if (tl_counters) {
         tl_counters->launches += 1;
-        tl_counters->flops += 2.0 * a.B * a.Co * (double)a.Hg * a.Wg * a.Ci * a.T;
+        tl_counters->flops += 2.0 * a.B * a.Co * (double)a.Hg * a.Wg * a.Ci * a.T * a.classes;
     }
-    if (a.x64)
-        launch<true>(a, pdl, st);
-    else
-        launch<false>(a, pdl, st);
+    Geo g{};
+    g.KC = chunks_kc(a.Ci);
+    g.Npad = pad_n(a.Co);
+    const int T = a.T;
+    if (a.x64) {
+        g.NS = T;
+        launch<kF64>(a, g, (size_t)T * g.KC * 2048, pdl, (unsigned)((total + kRows - 1) / kRows), st);
+        return;
+    }
+    bool halo = a.S == 1 && a.Hg == a.Hi && a.Wg == a.Wi;
+    for (int t = 0; t < T * a.classes; ++t)
+        halo = halo && a.dy[t] >= -1 && a.dy[t] <= 1 && a.dx[t] >= -1 && a.dx[t] <= 1;
+    if (halo) {
+        g.SW = a.Wg < kRows ? a.Wg : kRows;
+        g.BW = g.SW + 2;
+        g.R = (kRows - g.SW) / g.BW + 1;
+        if (g.R > a.Hg) g.R = a.Hg;
+        g.BH = g.R + 2;
+        g.tiles_x = (a.Wg + g.SW - 1) / g.SW;
+        g.tiles_y = (a.Hg + g.R - 1) / g.R;
+        g.NS = 1;
+        const int KCi = (a.Ci + 7) / 8;
+        const cuuint64_t dims[4] = {8, (cuuint64_t)a.Wi, (cuuint64_t)a.Hi, (cuuint64_t)a.B * KCi};
+        const cuuint64_t strides[3] = {16, (cuuint64_t)a.Wi * 16, (cuuint64_t)a.Hi * a.Wi * 16};
+        const cuuint32_t box[4] = {8, (cuuint32_t)g.BW, (cuuint32_t)g.BH, (cuuint32_t)KCi};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUresult cr = encoder()(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(a.x8), dims,
+                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) throw StatusError{RTE_ECUDA, "cuTensorMapEncodeTiled failed"};
+        // halo planes plus the rows the discarded MMA rows of the last plane read
+        const size_t area = (size_t)g.KC * g.BH * g.BW * 16 + (size_t)(2 * g.BW + 130) * 16;
+        const unsigned tiles = (unsigned)(g.tiles_x * g.tiles_y * a.B);
+        launch<kHalo>(a, g, area, pdl, tiles, st);
+        return;
+    }
+    // every tap resident if it fits, else a ring of kMaxStages stages
+    const size_t wbytes = (size_t)T * g.Npad * g.KC * 16, stage = (size_t)g.KC * 2048;
+    g.NS = T;
+    if (((wbytes + 1023) & ~(size_t)1023) + T * stage > limits<kGather>().max_dyn)
+        g.NS = T < kMaxStages ? T : kMaxStages;
+    launch<kGather>(a, g, (size_t)g.NS * stage, pdl, (unsigned)((total + kRows - 1) / kRows), st);
 }
 
 int conv_tc_status(bool reset) {

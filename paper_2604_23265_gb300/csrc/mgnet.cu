@@ -404,7 +404,7 @@ size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z,
         if (mode == TcMode::Plan) return;
         if (mode == TcMode::Pack) nn::tc_pack(P(n, wname), so, si, KK, tp, c.Ci, c.Co, dst, n->stream);
         c.w = dst;
-        c.T = tp.T;
+        c.T = tp.T / c.classes;
         for (int t = 0; t < tp.T; ++t) {
             c.dy[t] = tp.dy[t];
             c.dx[t] = tp.dx[t];
@@ -460,13 +460,26 @@ size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z,
     const void* uup = A.u2;
     for (int l = L - 2; l >= 0; --l) {
         const int H = I >> l;
-        for (int py = 0; py < 2; ++py)
-            for (int px = 0; px < 2; ++px) {      // u_mid = u_pre + P *^T u_coarse, one parity class each
-                nn::TcConv c = conv(uup, n->C(l + 1), H / 2, n->C(l), H / 2, 1, at(A.umid, l), H);
-                c.OS = 2; c.OY0 = py; c.OX0 = px;
-                c.base8 = at(A.upre, l);
-                run(c, sl("P", l).c_str(), 1, n->C(l), 16, nn::taps_parity(4, py, px));
+        {   // u_mid = u_pre + P *^T u_coarse: the four parity classes in one launch
+            nn::TcConv c = conv(uup, n->C(l + 1), H / 2, n->C(l), H / 2, 1, at(A.umid, l), H);
+            c.OS = 2;
+            c.classes = 4;
+            c.base8 = at(A.upre, l);
+            Taps all{};
+            for (int q = 0; q < 4; ++q) {
+                const Taps tq = nn::taps_parity(4, q / 2, q % 2);
+                c.oy0[q] = q / 2;
+                c.ox0[q] = q % 2;
+                for (int t = 0; t < tq.T; ++t) {
+                    all.dy[all.T] = tq.dy[t];
+                    all.dx[all.T] = tq.dx[t];
+                    all.wi[all.T] = tq.wi[t];
+                    ++all.T;
+                }
             }
+            all.finish();
+            run(c, sl("P", l).c_str(), 1, n->C(l), 16, all);
+        }
         residual(l, at(A.umid, l), at(A.tpost, l));
         smooth_update(l, at(A.tpost, l), at(A.umid, l), at(A.uout, l));
         uup = at(A.uout, l);

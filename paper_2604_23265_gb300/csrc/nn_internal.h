@@ -1,6 +1,8 @@
 // Internal interface of the network kernels (nn_kernels.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "rte_internal.h"
 
 namespace rte {
@@ -74,21 +76,24 @@ void conv(const ConvArgs& a, cudaStream_t st);
 // Tensor-core (tcgen05) gather convolution of the inference forward pass
 // (conv_tc.cu): BF16 operands, FP32 accumulation.  Activations are BF16 in the
 // channel-chunked layout C8 = [B][ceil(C/8)][H][W][8] (16-byte aligned);
-// weights are packed by tc_pack.  Output pixel (OS gy + OY0, OS gx + OX0) of
-// class-grid pixel (gy, gx) receives
+// weights are packed by tc_pack.  Output pixel (OS gy + oy0, OS gx + ox0) of
+// class-grid pixel (gy, gx) of a class receives
 //   v = sign (sum_t sum_i X[b][i][S gy + dy_t][S gx + dx_t] W[t][i][o]) gate[o] (+ base)
 struct TcConv {
+    CUtensorMap tmap;                // filled by tc_conv (TMA halo loads of x8)
     const void* x8 = nullptr;        // BF16 C8 input, or
     const double* x64 = nullptr;     // FP64 [B][Ci][Hi][Wi] input (converted on load)
     int B = 1, Ci = 0, Hi = 0, Wi = 0;
     int relu_in = 0;                 // ReLU applied to the gathered input
-    const void* w = nullptr;         // packed weights (tc_pack, tc_weight_bytes(T, Ci, Co))
+    const void* w = nullptr;         // packed weights (tc_pack, classes x tc_weight_bytes(T, Ci, Co))
     int Co = 0;
     int Hg = 0, Wg = 0, S = 1;       // class grid and input stride
-    int OS = 1, OY0 = 0, OX0 = 0;    // output placement
+    int OS = 1;                      // output placement OS g + (oy0, ox0)[class]
     int Ho = 0, Wo = 0;
-    int T = 0;
+    int T = 0;                       // taps per class
+    int classes = 1;                 // class c uses taps c T .. c T + T - 1
     int dy[kMaxTaps] = {}, dx[kMaxTaps] = {};
+    int oy0[4] = {}, ox0[4] = {};
     const float* gate = nullptr;     // FP32 [Co][Ho][Wo], shared by the batch
     float sign = 1.f;
     const void* base8 = nullptr;     // BF16 C8 of the output's shape, or
