@@ -27,7 +27,7 @@
 //  * FP64 (the lift from the Krylov vector [2M][I][I]): loaded and converted
 //    by the threads.
 // The weights of a layer are packed once per weight version into the MMA
-// layout (tc_pack) and arrive by one bulk async copy.
+// layout (tc_pack) and arrive by bulk async copies of 8 KB.
 //
 // The four parity classes of a transposed convolution run as one launch
 // (blockIdx.y = class, each with its own taps, weights and output offset).
@@ -193,6 +193,17 @@ __device__ __forceinline__ void relu16(uint32_t addr) {
                  : "memory");
 }
 
+// Issues the MMAs of one accumulation (the first overwrites the accumulator).
+struct Chain {
+    uint32_t d;
+    uint32_t acc = 0;
+    __device__ explicit Chain(uint32_t tmem) : d(tmem) {}
+    __device__ __forceinline__ void mma(uint64_t ad, uint64_t bd, uint32_t idesc) {
+        tc_mma(d, ad, bd, idesc, acc);
+        acc = 1;
+    }
+};
+
 // Geometry of one launch (host computed).
 // KC: channel chunks of 8 per MMA row (even); Npad: output channels rounded
 // up to 16; NS: stages (gather modes); ncols: TMEM columns (power of two >=
@@ -273,12 +284,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    if (tid == 0) {      // this class's packed weights: one bulk copy tracked by w_bar
+    if (tid == 0) {      // this class's packed weights: bulk copies of 8 KB tracked by w_bar
         mbar_expect(&w_bar, wbytes);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(wbase),
-            "l"(static_cast<const char*>(a.w) + (size_t)cls * wbytes), "r"(wbytes), "r"(saddr(&w_bar))
-            : "memory");
+        const char* src = static_cast<const char*>(a.w) + (size_t)cls * wbytes;
+        for (uint32_t off = 0; off < wbytes; off += 8192) {
+            const uint32_t n = wbytes - off < 8192 ? wbytes - off : 8192;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    wbase + off),
+                "l"(src + off), "r"(n), "r"(saddr(&w_bar))
+                : "memory");
+        }
     }
     // the inputs are the previous layer's outputs: wait for that grid (its
     // writes before its trigger are visible after this)
@@ -356,14 +372,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
             if (!mbar_wait(&w_bar, 0) || !mbar_wait(&x_bar, 0)) ok = false;
             if (ok) {
                 tc_fence_after();
+                // descriptors differ only in the start-address field (bits 0-13,
+                // no carry below 256 KB), so each MMA costs two adds
+                const uint64_t a0 = sdesc(xbase, plane_bytes, 128), b0 = sdesc(wbase, 128, KC * 128);
+                const uint64_t astep = (2 * plane_bytes) >> 4;
+                Chain chain(tmem);
                 for (int t = 0; t < T; ++t) {
                     const int tt = cls * T + t;
-                    const uint32_t shift = (uint32_t)((1 + a.dy[tt]) * g.BW + (1 + a.dx[tt])) * 16;
-                    for (int j = 0; j < KC / 2; ++j) {
-                        const uint64_t ad = sdesc(xbase + 2 * j * plane_bytes + shift, plane_bytes, 128);
-                        const uint64_t bd = sdesc(wbase + t * tap_bytes + 2 * j * 128, 128, KC * 128);
-                        tc_mma(tmem, ad, bd, idesc, (t > 0 || j > 0) ? 1u : 0u);
-                    }
+                    uint64_t ad = a0 + (((1 + a.dy[tt]) * g.BW + (1 + a.dx[tt])) & 0xFFFF);
+                    uint64_t bd = b0 + ((t * tap_bytes) >> 4);
+                    for (int j = 0; j < KC / 2; ++j, ad += astep, bd += 16) chain.mma(ad, bd, idesc);
                 }
             }
             tc_commit(&mma_bar[0]);
@@ -415,13 +433,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                 for (int kc = half; kc < KC; kc += 2) relu16(dst + kc * 128);
             }
         };
+        Chain chain(tmem);               // used by thread 0 only
         auto issue = [&](int u) {       // one thread: the MMAs of tap u
-            const int s = u % NS;
-            for (int j = 0; j < KC / 2; ++j) {
-                const uint64_t ad = sdesc(xbase + s * stage_bytes + 2 * j * 128, 128, KC * 128);
-                const uint64_t bd = sdesc(wbase + u * tap_bytes + 2 * j * 128, 128, KC * 128);
-                tc_mma(tmem, ad, bd, idesc, (u > 0 || j > 0) ? 1u : 0u);
-            }
+            uint64_t ad = sdesc(xbase + (u % NS) * stage_bytes, 128, KC * 128);
+            uint64_t bd = sdesc(wbase + u * tap_bytes, 128, KC * 128);
+            for (int j = 0; j < KC / 2; ++j, ad += 16, bd += 16) chain.mma(ad, bd, idesc);
         };
         // after this thread's copies of tap u have landed: ReLU them if asked,
         // hand them to the async proxy, then one thread issues the tap's MMAs

@@ -38,8 +38,9 @@ struct Workspace {
     double* h1 = nullptr;     // [m+1]
     double* h2 = nullptr;     // [m+1]
     double* hcol = nullptr;   // [m+2]
+    double* zero = nullptr;   // [m+1] zeros
     double* est = nullptr;    // [4] device status: est, beta, bnorm
-    double* est_host = nullptr;   // pinned [4]
+    double* est_host = nullptr;   // pinned [4 + m + 2]: est, ..., then a Hessenberg column
     std::vector<void*> allocs;
     size_t bytes = 0;
 };
@@ -87,9 +88,32 @@ Workspace* get_workspace(rte_ctx* ctx, int m) {
     ws->h1 = ws_alloc<double>(ctx, ws, m + 1);
     ws->h2 = ws_alloc<double>(ctx, ws, m + 1);
     ws->hcol = ws_alloc<double>(ctx, ws, m + 2);
+    ws->zero = ws_alloc<double>(ctx, ws, m + 1);
     ws->est = ws_alloc<double>(ctx, ws, 4);
-    check(cudaMallocHost(&ws->est_host, 4 * sizeof(double)), "cudaMallocHost");
+    check(cudaMallocHost(&ws->est_host, (4 + m + 2) * sizeof(double)), "cudaMallocHost");
     return ws;
+}
+
+// Orthogonalises w against V[0..K) (orthonormal), leaving ws->hcol = [h, ||w||]
+// with w - V h the projected vector (still unnormalised in w).  Classical
+// Gram-Schmidt with selective reorthogonalisation: a second projection only
+// when the first removed more than half of w's squared length, i.e. when
+// ||w - V h1|| < ||h1|| (the "twice is enough" test with threshold 1/sqrt 2 on
+// ||w_after|| / ||w_before||, ||w_before||^2 = ||w_after||^2 + ||h1||^2 for
+// orthonormal V).  Returns true if the second projection ran.
+bool orthogonalise(rte_ctx* ctx, Workspace* ws, const double* V, int K) {
+    launch_mdot(ctx, V, K, ws->w, ws->h1);                                // h1 = V^T w
+    launch_update_norm(ctx, V, K, ws->w, ws->zero, ws->h1, ws->hcol);    // w -= V h1, ||w||
+    double* hc = ws->est_host + 4;
+    check(cudaMemcpyAsync(hc, ws->hcol, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+          "d2h hcol");
+    check(cudaStreamSynchronize(ctx->stream), "orthogonalise sync");
+    double hh = 0.0;
+    for (int k = 0; k < K; ++k) hh += hc[k] * hc[k];
+    if (!(hc[K] * hc[K] < hh)) return false;
+    launch_mdot(ctx, V, K, ws->w, ws->h2);                                // h2 = V^T w
+    launch_update_norm(ctx, V, K, ws->w, ws->h1, ws->h2, ws->hcol);      // w -= V h2; h = h1 + h2
+    return true;
 }
 
 // Start of a cycle: g = (beta, 0, ...), H = 0.
@@ -207,9 +231,7 @@ RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev) {
         for (int j = 0; j + 1 < k; ++j) {
             launch_response_apply(ctx, V_dev + (size_t)j * n, true, ws->w, true);
             const int K = j + 1;
-            launch_mdot(ctx, V_dev, K, ws->w, ws->h1);
-            launch_update_dot(ctx, V_dev, K, ws->w, ws->h1, ws->h2);
-            launch_update_norm(ctx, V_dev, K, ws->w, ws->h1, ws->h2, ws->hcol);
+            orthogonalise(ctx, ws, V_dev, K);
             launch_scale(ctx, ws->w, ws->hcol + K, V_dev + (size_t)(j + 1) * n);
         }
         check(cudaStreamSynchronize(ctx->stream), "sync");
@@ -312,9 +334,7 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                     launch_apply(ctx, true, ws->tmp, ws->w, true, nullptr);
                 }
                 const int K = j + 1;
-                launch_mdot(ctx, ws->V, K, ws->w, ws->h1);
-                launch_update_dot(ctx, ws->V, K, ws->w, ws->h1, ws->h2);
-                launch_update_norm(ctx, ws->V, K, ws->w, ws->h1, ws->h2, ws->hcol);
+                if (orthogonalise(ctx, ws, ws->V, K)) ++inf.reorth;
                 launch_scale(ctx, ws->w, ws->hcol + K, ws->V + (size_t)(j + 1) * n);
                 {
                     ProfScope ps(ctx, K_GIVENS, 0.0);
