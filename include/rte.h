@@ -222,10 +222,8 @@ RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev);
 
 /* ---------------------------------------------------------------------------
  * rte_solve -- solve A x = b for this context's b by right-preconditioned
- * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt and
- * selective reorthogonalisation (a second projection whenever the first
- * removed more than half of the vector's squared length), Givens/Hessenberg
- * least squares in FP64 on the device,
+ * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt plus
+ * reorthogonalisation, Givens/Hessenberg least squares in FP64 on the device,
  * inner operator applies in opts->inner_precision, and the true residual
  * ||b - A x|| / ||b|| recomputed in FP64 at the end of every cycle decides
  * convergence.  pc: NULL = block Jacobi (Sec. 4); else the MgNet
@@ -255,7 +253,6 @@ typedef struct rte_solve_info {
     int fell_back;         /* 1 if MgNet was replaced by block Jacobi */
     double relres;         /* final true relative residual (FP64) */
     double seconds;        /* wall time of the call */
-    int reorth;            /* Arnoldi steps that needed the second Gram-Schmidt projection */
 } rte_solve_info;
 
 RTE_API void rte_solve_opts_default(rte_solve_opts* opts);

@@ -51,8 +51,7 @@ class SolveOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
-                ("fell_back", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("reorth", ctypes.c_int)]
+                ("fell_back", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -171,23 +171,15 @@ def test_cgs2_projection(lib, k):
 
 @pytest.mark.parametrize("k", [8, 40, 64])
 def test_arnoldi_basis_is_orthonormal(lib, k):
-    """Arnoldi with classical Gram-Schmidt and selective reorthogonalisation
-    keeps V^T V = I to 1e-12 (pin P15), on the diffusive medium where the
-    Krylov vectors are nearly dependent."""
+    """Arnoldi with classical Gram-Schmidt and reorthogonalisation keeps
+    V^T V = I to 1e-12 (pin P15), on the diffusive medium where the Krylov
+    vectors are nearly dependent."""
     md = W.grf_diffusive(seed=2, I=24, M=8, eps=1e-3)
     ctx = _gpu(md)
     V = torch.zeros(k * ctx.n, dtype=torch.float64, device="cuda")
     ctx.arnoldi_basis(k, V)
     Vm = V.cpu().numpy().reshape(k, ctx.n)
     assert np.abs(Vm @ Vm.T - np.eye(k)).max() <= 1e-12
-
-
-def test_solve_reports_reorthogonalisations(lib):
-    md = _generic(16, 8, 4)
-    ctx = _gpu(md)
-    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
-    info = ctx.solve(x, tol=1e-10, restart=30)
-    assert info["converged"] and 0 <= info["reorth"] <= info["iterations"]
 
 
 @pytest.mark.parametrize("I,M,seed", [(9, 4, 0), (13, 8, 1), (16, 8, 2), (1, 8, 5)])
