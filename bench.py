@@ -334,12 +334,70 @@ def run_ours(args):
         out["config"]["I"], out["config"]["M"] = args.size, args.dirs
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(md, bj["iterations"] if bj else iters)
+    ctx.close()
+    if rank == 0 and world == 1 and args.serve > 0:
+        out["serving"] = serving_leg(args.serve)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+SERVE_WORKLOAD = ("Poisson arrivals of mixed solve requests: I in {32, 64, 128}, M in {8, 16}, "
+                  "eps log-uniform in [1e-2, 1], g uniform in [0, 0.9], GRF media; FGMRES(50) with "
+                  "block Jacobi to rel-res 1e-8; 4 slots")
+
+
+def serving_leg(n_req, seed=11):
+    """Continuous-batching server under Poisson arrivals (a reduced instance of
+    the serving workload): p50 / p99 latency and solves/s.  The arrival rate is
+    half the capacity estimated from three requests served one at a time."""
+    import threading
+    from paper_2604_23265_gb300 import rte
+    media = [W.mixed_instance(seed * 1000 + i, grids=(32, 64, 128), dirs=(8, 16), eps_range=(1e-2, 1.0),
+                              g_range=(0.0, 0.9)) for i in range(n_req)]
+    slots = 4
+    srv = rte.Server(slots=slots, max_device_bytes=64 << 30)
+    try:
+        t0 = time.perf_counter()
+        for md in media[:3]:
+            res, _ = srv.wait(srv.submit(md, tol=1e-8, max_iter=4000))
+        service = (time.perf_counter() - t0) / 3
+        rate = 0.5 * slots / service
+        rng = np.random.default_rng(seed)
+        gaps = rng.exponential(1.0 / rate, n_req)
+        ids = [None] * n_req
+        start = time.perf_counter()
+
+        def feeder():
+            t = start
+            for i, md in enumerate(media):
+                t += gaps[i]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids[i] = srv.submit(md, tol=1e-8, max_iter=4000)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        lat, queue, ok = [], [], 0
+        for i in range(n_req):
+            while ids[i] is None:
+                time.sleep(0.0005)
+            res, _ = srv.wait(ids[i])
+            lat.append(res["latency_s"])
+            queue.append(res["queue_s"])
+            ok += res["status"] == "OK"
+        th.join()
+        span = time.perf_counter() - start
+    finally:
+        srv.close()
+    lat = np.asarray(lat)
+    return {"workload": SERVE_WORKLOAD, "requests": n_req, "completed_ok": int(ok), "slots": slots,
+            "arrival_rate_per_s": rate, "single_request_service_s": service,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_queue_s": float(np.mean(queue)), "solves_per_s": n_req / span}
 
 
 def run_reference(args):
@@ -383,6 +441,8 @@ def main():
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", type=int, default=24,
+                    help="requests of the serving leg (p50/p99 latency); 0 skips it")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")
     ap.add_argument("--dirs", type=int, default=64, help="profiling only: directions")
     args = ap.parse_args()

@@ -221,6 +221,34 @@ RTE_API rte_status rte_cgs2_noalloc(const double* V_dev, int k, int64_t n, doubl
 RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev);
 
 /* ---------------------------------------------------------------------------
+ * ATFPS filter of the loss (Sec. 2.3; Eqs. def_V_delta,
+ * 2DAdaptiveTFPS_continuity_cond, 2DAdaptiveTFPS_boundary_cond, loss_delta).
+ *
+ * rte_atfps_setup builds, on the device, the selection (basis function k of
+ * cell c kept iff exp(-|xi_k| tau_c / 2) > delta) and for every interface the
+ * projections onto its kept coordinates: the kept functions centred at the
+ * interface (lower/left cell first, each group in ascending |xi|) are
+ * orthonormalised (QR with positive R diagonal), the dropped ones follow,
+ * every column is scaled to max-norm one, and the first s rows of the inverse
+ * of that basis are kept.  Interior interfaces use the midpoint jump over all
+ * M directions; boundary faces the M/2 incoming components.  Interfaces are
+ * ordered: interior vertical (row-major), interior horizontal, per row the
+ * west and east boundary faces, per column the south and north ones.
+ * delta in [0, 1).  rows_out (may be NULL): number of kept coordinates R.
+ * ESINGULAR if an interface basis is numerically singular (pivot below 1e-12
+ * of its unit max-norm columns).  Replaces a previous filter.  Synchronous.
+ *
+ * rte_atfps_mask: host uint8 [2M][N] copy of the selection (1 = kept).
+ * rte_atfps_apply: out = F y, y double [n] indexed like the rows of A, out
+ * double [R] (device).  rte_atfps_apply_t: y = F^T r (device).  EINVAL
+ * without a filter.  Asynchronous on the context's stream.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_atfps_setup(rte_ctx* ctx, double delta, int64_t* rows_out);
+RTE_API rte_status rte_atfps_mask(rte_ctx* ctx, unsigned char* mask_host);
+RTE_API rte_status rte_atfps_apply(rte_ctx* ctx, const double* y_dev, double* out_dev);
+RTE_API rte_status rte_atfps_apply_t(rte_ctx* ctx, const double* r_dev, double* y_dev);
+
+/* ---------------------------------------------------------------------------
  * rte_solve -- solve A x = b for this context's b by right-preconditioned
  * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt plus
  * reorthogonalisation, Givens/Hessenberg least squares in FP64 on the device,
@@ -298,6 +326,16 @@ RTE_API int64_t mgnet_param_count(const mgnet* net);
 typedef enum mgnet_precision { MGNET_FP32 = 0, MGNET_BF16 = 1 } mgnet_precision;
 RTE_API rte_status mgnet_set_precision(mgnet* net, int precision);
 RTE_API int mgnet_get_precision(const mgnet* net);
+
+/* Loss of mgnet_train_step / mgnet_loss_grad:
+ *   MGNET_LOSS_PLAIN: Eq. loss in face-flux space, ||x - A D psi_d|| / ||x|| (default);
+ *   MGNET_LOSS_FILTERED: Eq. loss_delta, ||F (A (mask o D psi_d) - x)|| / ||x||
+ *     with the context's ATFPS filter (rte_atfps_setup; EINVAL at the step
+ *     without one), A applied in FP64.
+ * EINVAL for another value. */
+typedef enum mgnet_loss { MGNET_LOSS_PLAIN = 0, MGNET_LOSS_FILTERED = 1 } mgnet_loss;
+RTE_API rte_status mgnet_set_loss(mgnet* net, int kind);
+RTE_API int mgnet_get_loss(const mgnet* net);
 
 /* 1 if a bounded wait inside a tensor-core network kernel expired since the
  * last reset (that launch wrote NaN outputs), else 0; reset != 0 clears the

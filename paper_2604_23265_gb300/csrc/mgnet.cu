@@ -51,6 +51,9 @@ struct mgnet {
     int M = 0, L = 0, c0 = 0, cmax = 0, cc = 0, ccmax = 0, cin = 4;
     int act = 0;                     // smoother activation: 0 identity, 1 ReLU
     int prec = 1;                    // inference convolutions: 0 FP32 CUDA cores, 1 BF16 tensor cores
+    int loss = 0;                    // training loss: 0 plain (Eq. loss), 1 ATFPS-filtered (Eq. loss_delta)
+    void* lscr = nullptr;            // scratch of the filtered loss
+    size_t lscr_bytes = 0;
     // tensor-core inference path: BF16 C8 activations, packed weights
     void* tc_ws = nullptr;
     size_t tc_ws_bytes = 0;
@@ -680,6 +683,35 @@ __global__ void k_norms2(const float* __restrict__ a, const float* __restrict__ 
     }
 }
 
+// y -= x
+__global__ void k_sub_from_d(double* __restrict__ y, const float* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] -= (double)x[i];
+}
+
+// out[0] += ||a||^2 (double), out[1] += ||b||^2 (float)
+__global__ void k_sumsq_df(const double* __restrict__ a, int64_t na, const float* __restrict__ b, int64_t nb,
+                           double* __restrict__ out) {
+    __shared__ double ra[32], rb[32];
+    double sa = 0.0, sb = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride) sa = fma(a[i], a[i], sa);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride)
+        sb += (double)b[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = sa; rb[threadIdx.x >> 5] = sb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += ra[w]; tb += rb[w]; }
+        atomicAdd(out, ta);
+        atomicAdd(out + 1, tb);
+    }
+}
+
 __global__ void k_sub_f(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
                         float* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -730,8 +762,55 @@ void load_inputs(mgnet* n, rte_ctx* ctx, const double* const* r, int B, Acts& a)
     check(cudaGetLastError(), "load_inputs");
 }
 
+// Eq. loss_delta: loss = mean_b ||F (A (mask o D psi_b) - x_b)|| / ||x_b||, A in
+// FP64; a.gpsi = its gradient D^T (mask o A^T F^T res_b) / (||res_b|| ||x_b|| B).
+double loss_and_seed_filtered(mgnet* n, rte_ctx* ctx, Acts& a, int B) {
+    const int64_t len = ctx->n, R = atfps_rows(ctx);
+    if (R < 0) throw StatusError{RTE_EINVAL, "the filtered loss needs rte_atfps_setup on the context"};
+    const size_t need = (4 * (size_t)len + (size_t)B * (R + 1)) * sizeof(double) + 1024;
+    if (!n->lscr || n->lscr_bytes < need) {
+        if (n->lscr) cudaFree(n->lscr);
+        n->lscr = nullptr;
+        check(cudaMalloc(&n->lscr, need), "cudaMalloc (filtered loss scratch)");
+        n->lscr_bytes = need;
+    }
+    double* alpha = static_cast<double*>(n->lscr);
+    double* y = alpha + len;
+    double* u = y + len;
+    double* galpha = u + len;
+    double* res = galpha + len;          // [B][R]
+    double* sums = n->d_scal + 32;
+    check(cudaMemsetAsync(sums, 0, 2 * B * sizeof(double), n->stream), "memset");
+    for (int b = 0; b < B; ++b) {
+        const float* psi = a.psi + (size_t)b * len;
+        const float* x = a.x + (size_t)b * len;
+        launch_block_apply(ctx, false, psi, false, alpha, true);            // D psi
+        atfps_mask_mul(ctx, alpha);                                          // D_delta psi
+        launch_apply(ctx, true, alpha, y, true, nullptr);                   // A alpha
+        k_sub_from_d<<<grid_for(len), 256, 0, n->stream>>>(y, x, len);
+        atfps_apply(ctx, y, res + (size_t)b * R);
+        k_sumsq_df<<<grid_for(len), 256, 0, n->stream>>>(res + (size_t)b * R, R, x, len, sums + 2 * b);
+    }
+    check(cudaGetLastError(), "filtered loss");
+    check(cudaMemcpyAsync(n->h_scal, sums, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, n->stream), "d2h");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    double loss = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double nr = std::sqrt(n->h_scal[2 * b]), nx = std::sqrt(n->h_scal[2 * b + 1]);
+        loss += nr / nx / B;
+        float* g = a.gpsi + (size_t)b * len;
+        atfps_apply_t(ctx, res + (size_t)b * R, u);                          // F^T res
+        launch_apply_adjoint(ctx, true, u, galpha);                          // A^T
+        atfps_mask_mul(ctx, galpha);
+        launch_block_apply(ctx, true, galpha, true, g, false);               // D^T
+        nn::scale_copy(g, g, (float)(nr > 0 ? 1.0 / (nr * nx * B) : 0.0), len, n->stream);
+    }
+    return loss;
+}
+
 // loss = mean_b ||x_b - B psi_b|| / ||x_b|| ; a.gpsi = its gradient
 double loss_and_seed(mgnet* n, rte_ctx* ctx, Acts& a, int B) {
+    if (n->loss == MGNET_LOSS_FILTERED) return loss_and_seed_filtered(n, ctx, a, B);
     const int64_t len = ctx->n;
     double* sums = n->d_scal + 32;
     check(cudaMemsetAsync(sums, 0, 2 * B * sizeof(double), n->stream), "memset");
@@ -847,6 +926,7 @@ RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out) {
     check(cudaStreamSynchronize(src->stream), "sync");
     check(cudaMemcpyAsync(n->p, src->p, n->np * 4, cudaMemcpyDeviceToDevice, n->stream), "d2d");
     n->prec = src->prec;
+    n->loss = src->loss;
     check(cudaStreamSynchronize(n->stream), "sync");
     ++n->version;
     return RTE_OK;
@@ -861,6 +941,7 @@ RTE_API void mgnet_destroy(mgnet* n) {
     if (n->ws) cudaFree(n->ws);
     if (n->tc_ws) cudaFree(n->tc_ws);
     if (n->tcw) cudaFree(n->tcw);
+    if (n->lscr) cudaFree(n->lscr);
     if (n->p) cudaFree(n->p);
     if (n->d_scal) cudaFree(n->d_scal);
     if (n->h_scal) cudaFreeHost(n->h_scal);
@@ -879,6 +960,17 @@ RTE_API rte_status mgnet_set_precision(mgnet* n, int precision) {
 }
 
 RTE_API int mgnet_get_precision(const mgnet* n) { return n ? n->prec : -1; }
+
+RTE_API rte_status mgnet_set_loss(mgnet* n, int kind) {
+    if (!n || (kind != MGNET_LOSS_PLAIN && kind != MGNET_LOSS_FILTERED)) {
+        set_error(nullptr, "bad argument (MGNET_LOSS_PLAIN or MGNET_LOSS_FILTERED)");
+        return RTE_EINVAL;
+    }
+    n->loss = kind;
+    return RTE_OK;
+}
+
+RTE_API int mgnet_get_loss(const mgnet* n) { return n ? n->loss : -1; }
 
 RTE_API int mgnet_kernel_status(int reset) {
     try {

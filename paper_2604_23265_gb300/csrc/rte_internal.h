@@ -16,6 +16,7 @@ constexpr int kRedThreads = 256;    // block size of the reduction kernels
 constexpr int kScal = 256;          // small device scalars per context
 
 struct Workspace;                   // Krylov buffers of rte_solve (solve.cu)
+struct Atfps;                       // ATFPS loss filter of a context (atfps.cu)
 
 // Kernel classes counted (always) and timed (when profiling is on).
 enum KernelId {
@@ -81,6 +82,7 @@ struct rte_ctx {
 
     size_t device_bytes = 0;
     rte::Workspace* ws = nullptr;
+    rte::Atfps* atfps = nullptr;
     rte::Profiler prof;
     std::vector<void*> allocations;
 };
@@ -126,6 +128,17 @@ void launch_apply_adjoint(rte_ctx* ctx, bool f64, const void* y, void* x);
 void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi);
 void launch_rhs(rte_ctx* ctx);
 void launch_coef_inputs(rte_ctx* ctx, const double* sT, const double* sa, const double* eps);
+
+// ATFPS loss filter (atfps.cu) -----------------------------------------------
+void atfps_setup(rte_ctx* ctx, double delta);
+void atfps_free(rte_ctx* ctx);
+// out [rows] = F y, y [n] indexed like the rows of A
+void atfps_apply(rte_ctx* ctx, const double* y, double* out);
+// y [n] = F^T r
+void atfps_apply_t(rte_ctx* ctx, const double* r, double* y);
+// x [n] (TFPS coefficients, [2M][N]) *= selection mask
+void atfps_mask_mul(rte_ctx* ctx, double* x);
+int64_t atfps_rows(const rte_ctx* ctx);   // -1 without a filter
 
 // block kernels (blocks.cu) ------------------------------------------------
 // builds G_C for every cell, inverts it into ctx->Dt (FP64) and forms the

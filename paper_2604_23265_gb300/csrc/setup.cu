@@ -701,6 +701,7 @@ RTE_API void rte_destroy(rte_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     free_workspace(ctx);
+    atfps_free(ctx);
     prof_free(ctx);
     for (void* p : ctx->allocations) cudaFreeAsync(p, ctx->stream);
     cudaStreamSynchronize(ctx->stream);

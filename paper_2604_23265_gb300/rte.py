@@ -102,6 +102,12 @@ SIGNATURES = {
     "mgnet_destroy": (None, [_P]),
     "mgnet_param_count": (ctypes.c_int64, [_P]),
     "mgnet_set_precision": (_I, [_P, _I]),
+    "mgnet_set_loss": (_I, [_P, _I]),
+    "mgnet_get_loss": (_I, [_P]),
+    "rte_atfps_setup": (_I, [_P, _D, ctypes.POINTER(ctypes.c_int64)]),
+    "rte_atfps_mask": (_I, [_P, _P]),
+    "rte_atfps_apply": (_I, [_P, _P, _P]),
+    "rte_atfps_apply_t": (_I, [_P, _P, _P]),
     "mgnet_get_precision": (_I, [_P]),
     "mgnet_kernel_status": (_I, [_I]),
     "mgnet_set_params": (_I, [_P, _P, ctypes.c_int64]),
@@ -324,6 +330,18 @@ class MgNet:
     def precision(self, value):
         _check(load().mgnet_set_precision(self.ptr, int(value)))
 
+    PLAIN, FILTERED = 0, 1
+
+    @property
+    def loss(self):
+        """Training loss: MgNet.PLAIN (Eq. loss) or MgNet.FILTERED (Eq. loss_delta,
+        needs Context.atfps_setup on the training contexts)."""
+        return int(load().mgnet_get_loss(self.ptr))
+
+    @loss.setter
+    def loss(self, value):
+        _check(load().mgnet_set_loss(self.ptr, int(value)))
+
     @staticmethod
     def kernel_status(reset=True):
         """1 if a bounded wait of a tensor-core network kernel expired."""
@@ -492,6 +510,31 @@ class Context:
         if got < 0:
             _check(RTE_ECUDA, self.ptr)
         return {a.name.decode(): (a.launches, a.ms, a.bytes, a.flops) for a in arr[:got]}
+
+    def atfps_setup(self, delta):
+        """ATFPS filter of the loss (Sec. 2.3); returns the number of kept coordinates."""
+        rows = ctypes.c_int64()
+        _check(load().rte_atfps_setup(self.ptr, float(delta), ctypes.byref(rows)), self.ptr)
+        self.atfps_rows = rows.value
+        return rows.value
+
+    def atfps_mask(self):
+        """Selection [2M][N] (1 = kept) of the current filter."""
+        m = np.zeros(2 * self.M * self.I * self.I, np.uint8)
+        _check(load().rte_atfps_mask(self.ptr, m.ctypes.data_as(_P)), self.ptr)
+        return m.reshape(2 * self.M, self.I * self.I)
+
+    def atfps_apply(self, y, out):
+        import torch
+        _check(load().rte_atfps_apply(self.ptr, _dev(y, torch.float64, self.n),
+                                      _dev(out, torch.float64, self.atfps_rows)), self.ptr)
+        return out
+
+    def atfps_apply_t(self, r, y):
+        import torch
+        _check(load().rte_atfps_apply_t(self.ptr, _dev(r, torch.float64, self.atfps_rows),
+                                        _dev(y, torch.float64, self.n)), self.ptr)
+        return y
 
     def arnoldi_basis(self, k, V):
         """k Arnoldi vectors of the block-Jacobi preconditioned operator from b."""
