@@ -683,6 +683,12 @@ __global__ void k_norms2(const float* __restrict__ a, const float* __restrict__ 
     }
 }
 
+// y = (float) (s x)
+__global__ void k_scale_to_f(const double* __restrict__ x, double s, float* __restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)(s * x[i]);
+}
+
 // y -= x
 __global__ void k_sub_from_d(double* __restrict__ y, const float* __restrict__ x, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -802,8 +808,9 @@ double loss_and_seed_filtered(mgnet* n, rte_ctx* ctx, Acts& a, int B) {
         atfps_apply_t(ctx, res + (size_t)b * R, u);                          // F^T res
         launch_apply_adjoint(ctx, true, u, galpha);                          // A^T
         atfps_mask_mul(ctx, galpha);
-        launch_block_apply(ctx, true, galpha, true, g, false);               // D^T
-        nn::scale_copy(g, g, (float)(nr > 0 ? 1.0 / (nr * nx * B) : 0.0), len, n->stream);
+        launch_block_apply(ctx, true, galpha, true, alpha, true);            // D^T
+        k_scale_to_f<<<grid_for(len), 256, 0, n->stream>>>(alpha, nr > 0 ? 1.0 / (nr * nx * B) : 0.0, g, len);
+        check(cudaGetLastError(), "k_scale_to_f");
     }
     return loss;
 }
