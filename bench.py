@@ -237,7 +237,7 @@ def run_ours(args):
         # same distribution (seeds 101..), never on the benchmark medium
         media = [W.grf_diffusive(seed=101 + i, I=I, M=M) for i in range(args.train_media)]
         net, tctx, losses, train_s = train.train_for(media, steps=args.train_steps, batch=8,
-                                                     lr0=3e-3, seed=0)
+                                                     lr0=3e-3, seed=0, loss=args.loss, delta=args.delta)
         for c in tctx:
             c.close()
         train_loss = float(np.mean(losses[-20:]))
@@ -323,7 +323,8 @@ def run_ours(args):
         "clocks": clocks,
     }
     if net is not None:
-        out["mgnet"] = {"train_seconds": train_s, "train_media": args.train_media,
+        out["mgnet"] = {"loss": args.loss, "delta": args.delta if args.loss == "filtered" else None,
+                        "train_seconds": train_s, "train_media": args.train_media,
                         "train_steps": args.train_steps, "final_loss": train_loss,
                         "levels": net.shape.levels, "params": net.count}
     if bj is not None:
@@ -441,6 +442,9 @@ def main():
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
+                    help="training loss of the network: Eq. loss or the ATFPS-filtered Eq. loss_delta")
+    ap.add_argument("--delta", type=float, default=1e-2, help="ATFPS selection threshold (filtered loss)")
     ap.add_argument("--serve", type=int, default=24,
                     help="requests of the serving leg (p50/p99 latency); 0 skips it")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")

@@ -1,9 +1,10 @@
 """Training of the MgNet preconditioner on the GPU (Sec. 3.4, Sec. 4.1).
 
 The network is trained with the library's own forward, backward and Adam
-kernels (``MgNet.train_step``) on the unfiltered physics-informed loss of
-Eq. loss, ||x - A D psi_d|| / ||x||, with the learning rate annealed by a
-cosine schedule (Sec. 4.1: initial rate 1e-3 there).
+kernels (``MgNet.train_step``) on the physics-informed loss of Eq. loss,
+||x - A D psi_d|| / ||x||, or on its ATFPS-filtered form (Eq. loss_delta,
+Sec. 2.3), with the learning rate annealed by a cosine schedule (Sec. 4.1:
+initial rate 1e-3 there).
 
 Training inputs are generated by the plain solver's own operators for each
 training medium:
@@ -70,15 +71,22 @@ def default_shape(M, I):
 
 
 def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_smooth=32, seed=0,
-              log=None):
-    """Create a network for the media's (I, M), generate inputs and train it.
-    Returns (net, contexts, losses, seconds)."""
+              log=None, loss="plain", delta=1e-2):
+    """Create a network for the media's (I, M), generate inputs and train it
+    with the plain loss (Eq. loss) or the ATFPS-filtered one (Eq. loss_delta,
+    selection threshold delta).  Returns (net, contexts, losses, seconds)."""
     I, M = media[0].I, media[0].M
     shape = shape or default_shape(M, I)
     net = rte.MgNet(shape)
     net.set_params(workloads.init_params(shape, seed=seed, proj_scale=0.0, vcycle_scale=0.5))
     t0 = time.time()
     ctxs = [rte.Context.from_medium(md) for md in media]
+    if loss == "filtered":
+        for c in ctxs:
+            c.atfps_setup(delta)
+        net.loss = rte.MgNet.FILTERED
+    elif loss != "plain":
+        raise ValueError("loss is 'plain' or 'filtered'")
     inputs = [training_inputs(c, md, n_krylov, n_smooth, seed + 17 * i)
               for i, (c, md) in enumerate(zip(ctxs, media))]
     losses = train(net, ctxs, inputs, steps, batch, lr0, seed, log)
