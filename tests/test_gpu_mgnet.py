@@ -94,6 +94,32 @@ def test_tensor_core_repeated_applications_are_identical(lib):
         np.testing.assert_array_equal(o, outs[0])
 
 
+def test_tensor_core_forward_at_full_size_matches_fp32_path(lib):
+    """At the benchmark size (256 x 256 cells, M = 64, 6 levels, widths 16-64)
+    the tensor-core network agrees with the FP32 CUDA-core path (itself at
+    parity with the oracle at small sizes) to the BF16 bar, on the network's
+    own part z - r."""
+    from paper_2604_23265_gb300 import rte, train
+    md = W.grf_diffusive(seed=0, I=256, M=64)
+    ctx = rte.Context.from_medium(md)
+    shape = train.default_shape(md.M, md.I)
+    net = rte.MgNet(shape)
+    net.set_params(W.init_params(shape, seed=2, proj_scale=0.05, vcycle_scale=0.5))
+    r = torch.tensor(W.random_vector(ctx.n, 3), device="cuda")
+    z16 = torch.zeros(ctx.n, dtype=torch.float32, device="cuda")
+    net.precond(ctx, r, z16)
+    net.precision = rte.MgNet.FP32
+    z32 = torch.zeros_like(z16)
+    net.precond(ctx, r, z32)
+    torch.cuda.synchronize()
+    assert rte.MgNet.kernel_status() == 0
+    rf = r.float()
+    d16, d32 = (z16 - rf).double(), (z32 - rf).double()
+    assert torch.isfinite(d16).all()
+    assert (torch.linalg.norm(d16 - d32) / torch.linalg.norm(d32)).item() <= 2e-2
+    ctx.close()
+
+
 def test_precision_switch_rejects_unknown_value(lib):
     rte, shape, params, md, ctx, net, p = _setup(I=8, M=8, levels=1)
     with pytest.raises(rte.RteError):
