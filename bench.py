@@ -236,7 +236,8 @@ def run_ours(args):
         # the network is trained before the timed region on other media of the
         # same distribution (seeds 101..), never on the benchmark medium
         media = [W.grf_diffusive(seed=101 + i, I=I, M=M) for i in range(args.train_media)]
-        net, tctx, losses, train_s = train.train_for(media, steps=args.train_steps, batch=8,
+        shape = train.default_shape(M, I, c0=args.c0, cmax=args.cmax)
+        net, tctx, losses, train_s = train.train_for(media, shape=shape, steps=args.train_steps, batch=8,
                                                      lr0=3e-3, seed=0, loss=args.loss, delta=args.delta)
         for c in tctx:
             c.close()
@@ -442,6 +443,8 @@ def main():
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--c0", type=int, default=16, help="network width at the finest level")
+    ap.add_argument("--cmax", type=int, default=64, help="largest network width")
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
                     help="training loss of the network: Eq. loss or the ATFPS-filtered Eq. loss_delta")
     ap.add_argument("--delta", type=float, default=1e-2, help="ATFPS selection threshold (filtered loss)")

@@ -63,11 +63,11 @@ def train(net, ctxs, inputs, steps=600, batch=8, lr0=3e-3, seed=0, log=None):
     return losses
 
 
-def default_shape(M, I):
+def default_shape(M, I, c0=16, cmax=64):
     """Network widths used for a grid of I x I cells with M directions: a
     V-cycle down to an 8 x 8 coarsest grid (at least one level)."""
     levels = max(1, int(round(math.log2(I))) - 2)
-    return workloads.NetShape(M=M, levels=levels, c0=16, cmax=64, cc=8, ccmax=32, act="linear")
+    return workloads.NetShape(M=M, levels=levels, c0=c0, cmax=cmax, cc=8, ccmax=32, act="linear")
 
 
 def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_smooth=32, seed=0,
