@@ -238,7 +238,8 @@ def run_ours(args):
         media = [W.grf_diffusive(seed=101 + i, I=I, M=M) for i in range(args.train_media)]
         shape = train.default_shape(M, I, c0=args.c0, cmax=args.cmax)
         net, tctx, losses, train_s = train.train_for(media, shape=shape, steps=args.train_steps, batch=8,
-                                                     lr0=3e-3, seed=0, loss=args.loss, delta=args.delta)
+                                                     lr0=3e-3, seed=args.train_seed, loss=args.loss,
+                                                     delta=args.delta)
         for c in tctx:
             c.close()
         train_loss = float(np.mean(losses[-20:]))
@@ -325,6 +326,7 @@ def run_ours(args):
     }
     if net is not None:
         out["mgnet"] = {"loss": args.loss, "delta": args.delta if args.loss == "filtered" else None,
+                        "train_seed": args.train_seed,
                         "train_seconds": train_s, "train_media": args.train_media,
                         "train_steps": args.train_steps, "final_loss": train_loss,
                         "levels": net.shape.levels, "params": net.count}
@@ -437,12 +439,13 @@ def main():
                          "(block-Jacobi FGMRES(50) on this workload, as measured on the GPU)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--pc", default="mgnet", choices=["mgnet", "bj"])
-    ap.add_argument("--train-steps", type=int, default=600)
-    ap.add_argument("--train-media", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--train-media", type=int, default=8)
     ap.add_argument("--no-bj", action="store_true", help="skip the block-Jacobi comparison solve")
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--train-seed", type=int, default=0, help="seed of the weights and input draws")
     ap.add_argument("--c0", type=int, default=16, help="network width at the finest level")
     ap.add_argument("--cmax", type=int, default=64, help="largest network width")
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
