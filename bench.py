@@ -341,6 +341,8 @@ def run_ours(args):
     ctx.close()
     if rank == 0 and world == 1 and args.serve > 0:
         out["serving"] = serving_leg(args.serve)
+    if rank == 0 and world == 1 and args.batch > 0:
+        out["batched"] = batched_leg(args.batch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -404,6 +406,43 @@ def serving_leg(n_req, seed=11):
             "mean_queue_s": float(np.mean(queue)), "solves_per_s": n_req / span}
 
 
+BATCH_WORKLOAD = ("mixed instances: I in {32, 64}, M in {8, 16}, eps log-uniform in [1e-2, 1], g uniform in "
+                  "[0, 0.8], GRF media; FGMRES(50) with block Jacobi to rel-res 1e-8")
+
+
+def batched_leg(count, seed=23):
+    """count solves of mixed small instances: one grouped call (shared launches
+    per Arnoldi round) against the same solves one after the other; both on
+    the device, set-up excluded, results compared bit for bit."""
+    import torch
+    from paper_2604_23265_gb300 import rte
+    media = [W.mixed_instance(seed * 1000 + i, grids=(32, 64), dirs=(8, 16), eps_range=(1e-2, 1.0),
+                              g_range=(0.0, 0.8)) for i in range(count)]
+    ctxs = [rte.Context.from_medium(md) for md in media]
+    xs1 = [torch.zeros(c.n, dtype=torch.float64, device="cuda") for c in ctxs]
+    xs2 = [torch.zeros(c.n, dtype=torch.float64, device="cuda") for c in ctxs]
+    for c, x in zip(ctxs, xs1):            # warm-up (workspaces)
+        c.solve(x, tol=1e-8, max_iter=5, raise_on_error=False)
+    rte.solve_group(ctxs, xs2, tol=1e-8, max_iter=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lone = [c.solve(x, tol=1e-8) for c, x in zip(ctxs, xs1)]
+    torch.cuda.synchronize()
+    t_lone = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    grp = rte.solve_group(ctxs, xs2, tol=1e-8)
+    torch.cuda.synchronize()
+    t_grp = time.perf_counter() - t0
+    same = all(a["iterations"] == b["iterations"] and torch.equal(x1, x2)
+               for a, b, x1, x2 in zip(lone, grp, xs1, xs2))
+    for c in ctxs:
+        c.close()
+    return {"workload": BATCH_WORKLOAD, "instances": count,
+            "grouped_solves_per_s": count / t_grp, "one_at_a_time_solves_per_s": count / t_lone,
+            "speedup": t_lone / t_grp, "iterations_total": int(sum(i["iterations"] for i in grp)),
+            "converged": all(i["converged"] for i in grp), "bit_identical_to_lone": bool(same)}
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores as the reference arm (bounded samples)."""
     world, rank, _ = _dist()
@@ -451,6 +490,8 @@ def main():
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
                     help="training loss of the network: Eq. loss or the ATFPS-filtered Eq. loss_delta")
     ap.add_argument("--delta", type=float, default=1e-2, help="ATFPS selection threshold (filtered loss)")
+    ap.add_argument("--batch", type=int, default=32,
+                    help="instances of the grouped-solve leg (shared launches); 0 skips it")
     ap.add_argument("--serve", type=int, default=24,
                     help="requests of the serving leg (p50/p99 latency); 0 skips it")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")

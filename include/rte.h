@@ -288,6 +288,26 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                              double* x_dev, rte_solve_info* info);
 
 /* ---------------------------------------------------------------------------
+ * rte_solve_group -- count (1..1024) solves of rte_solve advancing in
+ * lockstep: in every round each live solve takes one Arnoldi step, and the
+ * steps of all of them run as shared launches (inner operator w = B z and its
+ * neighbour gather, the three Gram-Schmidt passes, the scaling to v_{j+1},
+ * the Givens updates: six launches per round for the whole group, whatever
+ * the grids and direction counts), with one device-to-host read of all
+ * residual estimates.  Preconditioners (MgNet) and the cycle starts and ends
+ * run per solve.  Every solve keeps the block partition of its lone launches,
+ * so its result is bit-identical to rte_solve's.  ctxs: distinct contexts on
+ * one stream (EINVAL otherwise); pcs: NULL or one network (or NULL) per
+ * solve, on the same stream; x_dev[i]: double [n_i].  infos, statuses
+ * (may be NULL): per solve, as rte_solve would return them.  Returns RTE_OK
+ * unless the group itself failed (a CUDA error, an allocation), in which case
+ * every status carries that error.  Synchronous.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int count,
+                                   const rte_solve_opts* opts, double* const* x_dev,
+                                   rte_solve_info* infos, rte_status* statuses);
+
+/* ---------------------------------------------------------------------------
  * MgNet preconditioner (Sec. 3): CoeffNet + MgNet V-cycle in face-flux space.
  *
  * Network: CoeffNet levels l = 0..levels-1 (conv 3x3, stride 2 after level 0,

@@ -160,15 +160,13 @@ __global__ void __launch_bounds__(256) k_response(int M, const int* __restrict__
 // 256 threads = 256/G cells; r staged in shared memory; accumulation in the
 // matrix's precision.
 template <typename TD, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(256) k_block_apply(int M, int N, const TD* __restrict__ Xt,
-                                                     const TIN* __restrict__ r,
-                                                     TOUT* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char smb[];
+__device__ void block_apply_run(int M, int N, const TD* __restrict__ Xt, const TIN* __restrict__ r,
+                                TOUT* __restrict__ z, int bid, unsigned char* smb) {
     TD* rs = reinterpret_cast<TD*>(smb);
     const int n2 = 2 * M, G = n2 / 4;
     const int cells = blockDim.x / G;
     TD* zs = rs + n2 * cells;
-    const int c0 = blockIdx.x * cells;
+    const int c0 = bid * cells;
     for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
         const int j = e / cells, cc = e - j * cells;
         const int c = c0 + cc;
@@ -210,16 +208,23 @@ __global__ void __launch_bounds__(256) k_block_apply(int M, int N, const TD* __r
     }
 }
 
+template <typename TD, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256) k_block_apply(int M, int N, const TD* __restrict__ Xt,
+                                                     const TIN* __restrict__ r,
+                                                     TOUT* __restrict__ z) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    block_apply_run<TD, TIN, TOUT>(M, N, Xt, r, z, blockIdx.x, smb);
+}
+
 // w = v - P o: subtract the outgoing data o of the neighbour across each face
 // (o laid out like the rows: row (f, j) of cell C holds the value leaving C
 // through f in direction dirs[opp f][j]).  With o = R v this is w = A D v.
 template <typename TV, typename TO, typename TW>
-__global__ void k_gather(int I, int M, const TV* __restrict__ v, const TO* __restrict__ o,
-                         TW* __restrict__ w) {
+__device__ void gather_run(int I, int M, const TV* __restrict__ v, const TO* __restrict__ o, TW* __restrict__ w,
+                           int bid, int nb) {
     const int N = I * I, M2 = M / 2;
     const int64_t n = (int64_t)2 * M * N;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = (int64_t)bid * blockDim.x + threadIdx.x; e < n; e += (int64_t)nb * blockDim.x) {
         const int row = (int)(e / N);
         const int c = (int)(e - (int64_t)row * N);
         const int f = row / M2, j = row - f * M2;
@@ -233,6 +238,12 @@ __global__ void k_gather(int I, int M, const TV* __restrict__ v, const TO* __res
         if (nb >= 0) val -= (double)o[(int64_t)((f ^ 1) * M2 + j) * N + nb];
         w[e] = (TW)val;
     }
+}
+
+template <typename TV, typename TO, typename TW>
+__global__ void k_gather(int I, int M, const TV* __restrict__ v, const TO* __restrict__ o,
+                         TW* __restrict__ w) {
+    gather_run<TV, TO, TW>(I, M, v, o, w, blockIdx.x, gridDim.x);
 }
 
 // q = P u: every row (f, j) of cell C takes the neighbour's row (opp f, j)
@@ -436,6 +447,64 @@ void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scra
     ProfScope ps(ctx, K_RESPONSE_APPLY, (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * 12);
     k_response_t<<<blocks, threads, smem, ctx->stream>>>(M, ctx->N, ctx->Rt, u, scratch, w);
     check(cudaGetLastError(), "k_response_t");
+}
+
+namespace {
+template <int GroupItem::*START>
+__device__ int group_item_ba(const GroupItem* items, int count) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int i = 0;
+        while (i + 1 < count && items[i + 1].*START <= (int)blockIdx.x) ++i;
+        s_item = i;
+    }
+    __syncthreads();
+    return s_item;
+}
+
+__global__ void __launch_bounds__(256) k_block_apply_group(const GroupItem* __restrict__ items, int count) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    const GroupItem& it = items[group_item_ba<&GroupItem::b_ba>(items, count)];
+    const int bid = blockIdx.x - it.b_ba;
+    if (it.z_double)
+        block_apply_run<float, double, float>(it.M, it.N, it.Rt, static_cast<const double*>(it.z), it.o, bid, smb);
+    else
+        block_apply_run<float, float, float>(it.M, it.N, it.Rt, static_cast<const float*>(it.z), it.o, bid, smb);
+}
+
+__global__ void k_gather_group(const GroupItem* __restrict__ items, int count) {
+    const GroupItem& it = items[group_item_ba<&GroupItem::b_ga>(items, count)];
+    const int bid = blockIdx.x - it.b_ga;
+    if (it.z_double)
+        gather_run<double, float, double>(it.I, it.M, static_cast<const double*>(it.z), it.o, it.w, bid, it.n_ga);
+    else
+        gather_run<float, float, double>(it.I, it.M, static_cast<const float*>(it.z), it.o, it.w, bid, it.n_ga);
+}
+}  // namespace
+
+// the block counts a lone response apply of this context uses (block_apply_t
+// and launch_response_apply), so a grouped launch reproduces its arithmetic
+void group_response_geometry(rte_ctx* ctx, int* n_ba, int* n_ga, size_t* smem_ba) {
+    const int M = ctx->M, n2 = 2 * M, G = n2 / 4;
+    const int threads = G >= 256 ? G : (256 / G) * G;
+    if (threads != 256 && G < 256) {
+        // grouped blocks have 256 threads: the cells per block must be the same
+        if (256 / G != threads / G) throw StatusError{RTE_EINVAL, "grouped response apply: unsupported M"};
+    }
+    const int cells = threads / G;
+    *n_ba = (ctx->N + cells - 1) / cells;
+    *smem_ba = sizeof(float) * 2 * n2 * cells;
+    int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
+    *n_ga = (int)(want < cap ? want : cap);
+}
+
+void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba, int blocks_ga, size_t smem_ba,
+                           cudaStream_t st) {
+    check(cudaFuncSetAttribute(k_block_apply_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ba),
+          "grouped block apply smem");
+    k_block_apply_group<<<blocks_ba, 256, smem_ba, st>>>(items_dev, count);
+    k_gather_group<<<blocks_ga, 256, 0, st>>>(items_dev, count);
+    check(cudaGetLastError(), "grouped response apply");
 }
 
 void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* w,

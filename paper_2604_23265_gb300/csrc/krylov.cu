@@ -34,7 +34,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int KMAX>
 __device__ void block_reduce_finish(double (&acc)[KMAX], int K, double* __restrict__ partials,
                                     unsigned* __restrict__ counter, double* __restrict__ res,
-                                    bool sqrt_result) {
+                                    bool sqrt_result, int bid, int nb) {
     __shared__ double red[kT / 32][KMAX];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -49,18 +49,18 @@ __device__ void block_reduce_finish(double (&acc)[KMAX], int K, double* __restri
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][k];
-        partials[(size_t)blockIdx.x * KMAX + k] = s;
+        partials[(size_t)bid * KMAX + k] = s;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == nb - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     const int nw = blockDim.x >> 5;
     for (int k = warp; k < K; k += nw) {
         double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (size_t)b * KMAX + k);
+        for (int b = lane; b < nb; b += 32) s += __ldcg(partials + (size_t)b * KMAX + k);
         s = warp_sum(s);
         if (lane == 0) res[k] = sqrt_result ? sqrt(s) : s;
     }
@@ -128,7 +128,7 @@ __device__ __forceinline__ double slice_dot(const Slice& a, const Slice& b) {
 // s_part[k * kT + tid]; at the end the block reduces them (fixed order) and
 // hands the block sums to the last block.
 __device__ void finish_dots(const double* s_part, int K, double* partials, unsigned* counter,
-                            double* res) {
+                            double* res, int bid, int nb) {
     __shared__ bool s_last;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -137,17 +137,17 @@ __device__ void finish_dots(const double* s_part, int K, double* partials, unsig
 #pragma unroll
         for (int q = 0; q < kT / 32; ++q) t += s_part[k * kT + q * 32 + lane];
         t = warp_sum(t);
-        if (lane == 0) partials[(size_t)blockIdx.x * kMaxKrylov + k] = t;
+        if (lane == 0) partials[(size_t)bid * kMaxKrylov + k] = t;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == nb - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     for (int k = warp; k < K; k += kT / 32) {
         double t = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * kMaxKrylov + k);
+        for (int b = lane; b < nb; b += 32) t += __ldcg(partials + (size_t)b * kMaxKrylov + k);
         t = warp_sum(t);
         if (lane == 0) res[k] = t;
     }
@@ -172,20 +172,27 @@ __device__ __forceinline__ void mdot_chunk(const double* __restrict__ V, int K, 
     if (k < K) s_part[k * kT + tid] += slice_dot(load_slice<TAIL>(vk, base, n), ws);
 }
 
-__global__ void __launch_bounds__(kT) k_mdot(const double* __restrict__ V, int K, int64_t n,
-                                             const double* __restrict__ w, double* partials,
-                                             unsigned* counter, double* h) {
-    extern __shared__ double s_part[];          // [K][kT]
+// block bid of nb (a plain launch: blockIdx.x of gridDim.x; a grouped one: the
+// block's index within its instance's range)
+__device__ void mdot_run(const double* __restrict__ V, int K, int64_t n, const double* __restrict__ w,
+                         double* partials, unsigned* counter, double* h, int bid, int nb, double* s_part) {
     const int tid = threadIdx.x;
     for (int k = 0; k < K; ++k) s_part[k * kT + tid] = 0.0;
     const int64_t full = n / kChunk, nchunks = (n + kChunk - 1) / kChunk;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int64_t ch = bid; ch < nchunks; ch += nb) {
         if (ch < full)
             mdot_chunk<false>(V, K, n, w, slice_base(ch), s_part);
         else
             mdot_chunk<true>(V, K, n, w, slice_base(ch), s_part);
     }
-    finish_dots(s_part, K, partials, counter, h);
+    finish_dots(s_part, K, partials, counter, h, bid, nb);
+}
+
+__global__ void __launch_bounds__(kT) k_mdot(const double* __restrict__ V, int K, int64_t n,
+                                             const double* __restrict__ w, double* partials,
+                                             unsigned* counter, double* h) {
+    extern __shared__ double s_part[];          // [K][kT]
+    mdot_run(V, K, n, w, partials, counter, h, blockIdx.x, gridDim.x, s_part);
 }
 
 // w <- w - sum_k V[k] h1[k] on one chunk; then (DOTS) s_part[k] += V[k] . w
@@ -226,40 +233,43 @@ __device__ __forceinline__ Slice update_chunk(const double* __restrict__ V, int 
 }
 
 // w <- w - sum_k V[k] h1[k]; then h2[k] = V[k] . w   (V re-read from cache)
-__global__ void __launch_bounds__(kT) k_update_dot(const double* __restrict__ V, int K, int64_t n,
-                                                   double* __restrict__ w,
-                                                   const double* __restrict__ h1,
-                                                   double* partials, unsigned* counter,
-                                                   double* h2) {
-    extern __shared__ double s_part[];          // [K][kT]
+__device__ void update_dot_run(const double* __restrict__ V, int K, int64_t n, double* __restrict__ w,
+                               const double* __restrict__ h1, double* partials, unsigned* counter, double* h2,
+                               int bid, int nb, double* s_part) {
     __shared__ double sh[kMaxKrylov];
     const int tid = threadIdx.x;
     for (int k = tid; k < K; k += blockDim.x) sh[k] = h1[k];
     for (int k = 0; k < K; ++k) s_part[k * kT + tid] = 0.0;
     __syncthreads();
     const int64_t full = n / kChunk, nchunks = (n + kChunk - 1) / kChunk;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int64_t ch = bid; ch < nchunks; ch += nb) {
         if (ch < full)
             update_chunk<false, true>(V, K, n, w, sh, slice_base(ch), s_part);
         else
             update_chunk<true, true>(V, K, n, w, sh, slice_base(ch), s_part);
     }
-    finish_dots(s_part, K, partials, counter, h2);
+    finish_dots(s_part, K, partials, counter, h2, bid, nb);
+}
+
+__global__ void __launch_bounds__(kT) k_update_dot(const double* __restrict__ V, int K, int64_t n,
+                                                   double* __restrict__ w,
+                                                   const double* __restrict__ h1,
+                                                   double* partials, unsigned* counter,
+                                                   double* h2) {
+    extern __shared__ double s_part[];          // [K][kT]
+    update_dot_run(V, K, n, w, h1, partials, counter, h2, blockIdx.x, gridDim.x, s_part);
 }
 
 // w <- w - sum_k V[k] h2[k]; out[K] = ||w||; out[k] = h1[k] + h2[k]
-__global__ void __launch_bounds__(kT) k_update_norm(const double* __restrict__ V, int K, int64_t n,
-                                                    double* __restrict__ w,
-                                                    const double* __restrict__ h1,
-                                                    const double* __restrict__ h2,
-                                                    double* partials, unsigned* counter,
-                                                    double* out) {
+__device__ void update_norm_run(const double* __restrict__ V, int K, int64_t n, double* __restrict__ w,
+                                const double* __restrict__ h1, const double* __restrict__ h2, double* partials,
+                                unsigned* counter, double* out, int bid, int nb) {
     __shared__ double sh[kMaxKrylov];
     for (int k = threadIdx.x; k < K; k += blockDim.x) sh[k] = h2[k];
     __syncthreads();
     double acc[1] = {0.0};
     const int64_t full = n / kChunk, nchunks = (n + kChunk - 1) / kChunk;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int64_t ch = bid; ch < nchunks; ch += nb) {
         Slice ws;
         if (ch < full)
             ws = update_chunk<false, false>(V, K, n, w, sh, slice_base(ch), nullptr);
@@ -268,9 +278,18 @@ __global__ void __launch_bounds__(kT) k_update_norm(const double* __restrict__ V
         acc[0] += slice_dot(ws, ws);
     }
     // out[K] = ||w||; block 0 also writes out[k] = h1[k] + h2[k]
-    block_reduce_finish<1>(acc, 1, partials, counter, out + K, true);
-    if (blockIdx.x == 0)
+    block_reduce_finish<1>(acc, 1, partials, counter, out + K, true, bid, nb);
+    if (bid == 0)
         for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = h1[k] + h2[k];
+}
+
+__global__ void __launch_bounds__(kT) k_update_norm(const double* __restrict__ V, int K, int64_t n,
+                                                    double* __restrict__ w,
+                                                    const double* __restrict__ h1,
+                                                    const double* __restrict__ h2,
+                                                    double* partials, unsigned* counter,
+                                                    double* out) {
+    update_norm_run(V, K, n, w, h1, h2, partials, counter, out, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kT) k_norm(const double* __restrict__ x, int64_t n,
@@ -279,16 +298,20 @@ __global__ void __launch_bounds__(kT) k_norm(const double* __restrict__ x, int64
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         acc[0] = fma(x[i], x[i], acc[0]);
-    block_reduce_finish<1>(acc, 1, partials, counter, out, true);
+    block_reduce_finish<1>(acc, 1, partials, counter, out, true, blockIdx.x, gridDim.x);
+}
+
+__device__ void scale_run(const double* __restrict__ x, const double* __restrict__ s, int64_t n,
+                          double* __restrict__ y, int bid, int nb) {
+    const double v = s[0];
+    const double inv = (v != 0.0) ? 1.0 / v : 1.0;
+    for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb * blockDim.x)
+        y[i] = x[i] * inv;
 }
 
 __global__ void k_scale(const double* __restrict__ x, const double* __restrict__ s, int64_t n,
                         double* __restrict__ y) {
-    const double v = s[0];
-    const double inv = (v != 0.0) ? 1.0 / v : 1.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = x[i] * inv;
+    scale_run(x, s, n, y, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_combine_update(double* __restrict__ x, const float* __restrict__ Z, int K,
@@ -324,7 +347,66 @@ int red_blocks(rte_ctx* ctx, int64_t n) {
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+// the item whose block range [start, start + count) holds this block
+template <int GroupItem::*START>
+__device__ int group_item(const GroupItem* items, int count) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int i = 0;
+        while (i + 1 < count && items[i + 1].*START <= (int)blockIdx.x) ++i;
+        s_item = i;
+    }
+    __syncthreads();
+    return s_item;
+}
+
+__global__ void __launch_bounds__(kT) k_mdot_group(const GroupItem* __restrict__ items, int count) {
+    extern __shared__ double s_part[];
+    const GroupItem& it = items[group_item<&GroupItem::b_md>(items, count)];
+    mdot_run(it.V, it.K, it.n, it.w, it.partials, it.counter, it.h1, blockIdx.x - it.b_md, it.n_md, s_part);
+}
+
+__global__ void __launch_bounds__(kT) k_update_dot_group(const GroupItem* __restrict__ items, int count) {
+    extern __shared__ double s_part[];
+    const GroupItem& it = items[group_item<&GroupItem::b_ud>(items, count)];
+    update_dot_run(it.V, it.K, it.n, it.w, it.h1, it.partials, it.counter, it.h2, blockIdx.x - it.b_ud, it.n_ud,
+                   s_part);
+}
+
+__global__ void __launch_bounds__(kT) k_update_norm_group(const GroupItem* __restrict__ items, int count) {
+    const GroupItem& it = items[group_item<&GroupItem::b_rd>(items, count)];
+    update_norm_run(it.V, it.K, it.n, it.w, it.h1, it.h2, it.partials, it.counter, it.hcol, blockIdx.x - it.b_rd,
+                    it.n_rd);
+}
+
+__global__ void __launch_bounds__(kT) k_scale_group(const GroupItem* __restrict__ items, int count) {
+    const GroupItem& it = items[group_item<&GroupItem::b_rd>(items, count)];
+    scale_run(it.w, it.hcol + it.K, it.n, it.Vnext, blockIdx.x - it.b_rd, it.n_rd);
+}
+
 }  // namespace
+
+void group_ortho_geometry(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd) {
+    *n_md = dot_blocks(ctx, ctx->n, K, (const void*)k_mdot);
+    *n_ud = dot_blocks(ctx, ctx->n, K, (const void*)k_update_dot);
+    *n_rd = red_blocks(ctx, ctx->n);
+}
+
+void launch_group_orthogonalise(const GroupItem* items_dev, int count, int blocks_md, int blocks_ud,
+                                int blocks_rd, int kmax, cudaStream_t st) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const int smax = (int)(kMaxKrylov * kT * sizeof(double));
+        check(cudaFuncSetAttribute(k_mdot_group, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "smem");
+        check(cudaFuncSetAttribute(k_update_dot_group, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "smem");
+    });
+    const size_t smem = (size_t)kmax * kT * sizeof(double);
+    k_mdot_group<<<blocks_md, kT, smem, st>>>(items_dev, count);
+    k_update_dot_group<<<blocks_ud, kT, smem, st>>>(items_dev, count);
+    k_update_norm_group<<<blocks_rd, kT, 0, st>>>(items_dev, count);
+    k_scale_group<<<blocks_rd, kT, 0, st>>>(items_dev, count);
+    check(cudaGetLastError(), "grouped Gram-Schmidt");
+}
 
 void launch_mdot(rte_ctx* ctx, const double* V, int k, const double* w, double* h) {
     const int g = dot_blocks(ctx, ctx->n, k, (const void*)k_mdot);

@@ -129,6 +129,51 @@ void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi);
 void launch_rhs(rte_ctx* ctx);
 void launch_coef_inputs(rte_ctx* ctx, const double* sT, const double* sa, const double* eps);
 
+// grouped launches (rte_solve_group) ----------------------------------------
+// One instance of a grouped Arnoldi step: its vectors, reduction scratch and,
+// for every kernel of the step, the range of blocks it owns in the grouped
+// launch -- the same block count as its own launch would use, so the
+// instance's arithmetic (reduction order included) is that of a lone solve.
+struct GroupItem {
+    // inner operator w = z - P R z (z double or float), o = R z scratch
+    const float* Rt;
+    const void* z;
+    int z_double;
+    float* o;
+    int I, M, N;
+    int64_t n;
+    // Gram-Schmidt against V[0..K), new vector to Vnext
+    const double* V;
+    double* w;
+    double* h1;
+    double* h2;
+    double* hcol;
+    double* Vnext;
+    double* partials;
+    unsigned* counter;
+    int K;
+    // Givens on column j of the (m+1) x m Hessenberg matrix
+    int j, m;
+    double* H;
+    double* cs;
+    double* sn;
+    double* g;
+    double* est;             // the instance's own status (est, ||w||)
+    double* est_out;         // and a copy in the group's array
+    // block ranges: [b_x, b_x + n_x) of the grouped launch of kernel x
+    int b_ba, n_ba, b_ga, n_ga, b_md, n_md, b_ud, n_ud, b_rd, n_rd;
+};
+// w = z - P R z for every item (two grouped launches)
+void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba, int blocks_ga,
+                           size_t smem_ba, cudaStream_t st);
+// block counts and shared memory of one item's response apply / gather
+void group_response_geometry(rte_ctx* ctx, int* n_ba, int* n_ga, size_t* smem_ba);
+// CGS2 (three passes) and the scaling to Vnext for every item
+void launch_group_orthogonalise(const GroupItem* items_dev, int count, int blocks_md, int blocks_ud,
+                                int blocks_rd, int kmax, cudaStream_t st);
+// block counts of one item's Gram-Schmidt passes
+void group_ortho_geometry(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd);
+
 // ATFPS loss filter (atfps.cu) -----------------------------------------------
 void atfps_setup(rte_ctx* ctx, double delta);
 void atfps_free(rte_ctx* ctx);

@@ -111,9 +111,8 @@ __global__ void k_cycle_start(int m, const double* __restrict__ beta, double* H,
 }
 
 // Hessenberg column j: apply the previous rotations, make a new one, update g.
-__global__ void k_givens(int j, int m, const double* __restrict__ hcol, double* H, double* cs,
-                         double* sn, double* g, double* est) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void givens_run(int j, int m, const double* __restrict__ hcol, double* H, double* cs, double* sn,
+                           double* g, double* est) {
     double* col = H + (size_t)j * (m + 1);
     for (int i = 0; i <= j + 1; ++i) col[i] = hcol[i];
     for (int i = 0; i < j; ++i) {
@@ -136,6 +135,12 @@ __global__ void k_givens(int j, int m, const double* __restrict__ hcol, double* 
     g[j] = c * g[j];
     est[0] = fabs(g[j + 1]);
     est[1] = hcol[j + 1];         // ||w|| before normalisation (breakdown test)
+}
+
+__global__ void k_givens(int j, int m, const double* __restrict__ hcol, double* H, double* cs,
+                         double* sn, double* g, double* est) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    givens_run(j, m, hcol, H, cs, sn, g, est);
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k)  (upper triangular)
@@ -189,6 +194,180 @@ double read_scalar(rte_ctx* ctx, Workspace* ws, const double* dev) {
     return ws->est_host[0];
 }
 
+// Hessenberg column j: apply the previous rotations, make a new one, update
+// g; one block per item of a grouped Arnoldi step.
+__global__ void k_givens_group(const GroupItem* __restrict__ items) {
+    if (threadIdx.x != 0) return;
+    const GroupItem& it = items[blockIdx.x];
+    givens_run(it.j, it.m, it.hcol, it.H, it.cs, it.sn, it.g, it.est);
+    it.est_out[0] = it.est[0];
+    it.est_out[1] = it.est[1];
+}
+
+// One flexible-GMRES solve as a sequence of phases, so that several solves can
+// advance in lockstep with their Arnoldi steps in shared launches
+// (rte_solve_group); rte_solve runs the same phases for one solve.
+struct Solver {
+    rte_ctx* ctx = nullptr;
+    mgnet* pc = nullptr;
+    rte_solve_opts opts{};
+    double* x = nullptr;
+    rte_solve_info inf{};
+    rte_status status = RTE_OK;
+    Workspace* ws = nullptr;
+    int m = 0, gblk = 0;
+    int64_t n = 0;
+    double bnorm = 0.0, prev_res = -1.0;
+    bool use_net = false, first = true, cycle_net = false;
+    int j = 0, k = 0;                 // Arnoldi step in the cycle; columns for the cycle end
+    const void* zj = nullptr;
+    bool z_double = true;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    double elapsed_ms() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+
+    // workspace, initial guess, ||b||; false when there is nothing to solve
+    bool start() {
+        if (pc) mgnet_prepare(pc, ctx);
+        m = opts.restart;
+        ws = get_workspace(ctx, m);
+        n = ctx->n;
+        gblk = ctx->num_sms * 4;
+        if (!opts.use_x0) check(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->stream), "zero x");
+        launch_norm(ctx, ctx->b, ws->est + 2);
+        bnorm = read_scalar(ctx, ws, ws->est + 2);
+        if (bnorm == 0.0) {
+            check(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->stream), "zero x");
+            inf.converged = 1;
+            inf.relres = 0.0;
+            return false;
+        }
+        use_net = (pc != nullptr);
+        return true;
+    }
+
+    // true residual in FP64 and the decisions on it; false when the solve ends
+    bool cycle_begin() {
+        if (first && !opts.use_x0)
+            check(cudaMemcpyAsync(ws->w, ctx->b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+                  "r = b");
+        else
+            launch_apply(ctx, true, x, ws->w, true, ctx->b);
+        first = false;
+        launch_norm(ctx, ws->w, ws->est + 3);
+        const double beta = read_scalar(ctx, ws, ws->est + 3);
+        inf.relres = beta / bnorm;
+        if (!std::isfinite(beta)) {
+            set_error(ctx, "non-finite residual");
+            status = RTE_ESTALL;
+            return false;
+        }
+        if (use_net && prev_res > 0.0 && inf.relres > opts.stall_ratio * prev_res) {
+            use_net = false;          // the learned preconditioner stalled
+            inf.fell_back = 1;
+        }
+        prev_res = inf.relres;
+        if (inf.relres <= opts.tol) { inf.converged = 1; return false; }
+        if (inf.iterations >= opts.max_iter) { status = RTE_ENOTCONV; return false; }
+        if (opts.timeout_ms > 0 && elapsed_ms() > opts.timeout_ms) { status = RTE_ETIMEOUT; return false; }
+        if (opts.cancel && *opts.cancel) {
+            set_error(ctx, "cancelled");
+            status = RTE_ECANCELLED;
+            return false;
+        }
+        launch_scale(ctx, ws->w, ws->est + 3, ws->V);
+        {
+            ProfScope ps(ctx, K_CYCLE, 0.0);
+            k_cycle_start<<<1, 256, 0, ctx->stream>>>(m, ws->est + 3, ws->H, ws->g);
+            check(cudaGetLastError(), "k_cycle_start");
+        }
+        cycle_net = use_net;
+        j = 0;
+        k = 0;
+        return true;
+    }
+
+    // z_j: the network's output, or v_j itself (block Jacobi is inside B)
+    void precondition() {
+        const double* vj = ws->V + (size_t)j * n;
+        zj = vj;
+        z_double = true;
+        if (cycle_net) {
+            float* zf = ws->Z + (size_t)j * n;
+            mgnet_precondition(pc, ctx, vj, zf);
+            zj = zf;
+            z_double = false;
+        }
+    }
+
+    // w = B z_j
+    void inner_apply() {
+        if (opts.inner_precision == RTE_F32) {
+            launch_response_apply(ctx, zj, z_double, ws->w, true);
+        } else {
+            launch_block_apply(ctx, false, zj, z_double, ws->tmp, true);
+            launch_apply(ctx, true, ws->tmp, ws->w, true, nullptr);
+        }
+    }
+
+    // CGS2, v_{j+1}, Givens
+    void orthogonalise_step() {
+        const int K = j + 1;
+        orthogonalise(ctx, ws, ws->V, K);
+        launch_scale(ctx, ws->w, ws->hcol + K, ws->V + (size_t)(j + 1) * n);
+        ProfScope ps(ctx, K_GIVENS, 0.0);
+        k_givens<<<1, 32, 0, ctx->stream>>>(j, m, ws->hcol, ws->H, ws->cs, ws->sn, ws->g, ws->est);
+        check(cudaGetLastError(), "k_givens");
+    }
+
+    // after the step's residual estimate est and ||w|| wn were read: false
+    // when the cycle ends
+    bool after_step(double est, double wn) {
+        ++inf.iterations;
+        k = j + 1;
+        if (!std::isfinite(est)) {
+            if (use_net) { use_net = false; inf.fell_back = 1; }
+            k = j;           // drop the bad column
+            return false;
+        }
+        if (est / bnorm <= opts.tol || wn == 0.0 || inf.iterations >= opts.max_iter) return false;
+        if (opts.timeout_ms > 0 && elapsed_ms() > opts.timeout_ms) return false;
+        if (opts.cancel && *opts.cancel) return false;
+        return ++j < m;
+    }
+
+    // y = H^{-1} g, dy = Z y (or V y), alpha += D dy
+    void cycle_end() {
+        if (k > 0) {
+            {
+                ProfScope ps(ctx, K_BACKSUB, 0.0);
+                k_backsub<<<1, 32, 0, ctx->stream>>>(k, m, ws->H, ws->g, ws->y);
+                check(cudaGetLastError(), "k_backsub");
+            }
+            {
+                ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + (cycle_net ? 4 : 8) * k));
+                if (cycle_net)
+                    k_lincomb<float><<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
+                else
+                    k_lincomb<double><<<gblk, 256, 0, ctx->stream>>>(ws->V, k, n, ws->y, ws->tmp);
+                check(cudaGetLastError(), "k_lincomb");
+            }
+            launch_block_apply(ctx, false, ws->tmp, true, ws->w, true);   // D dy
+            ProfScope ps(ctx, K_XUPDATE, (double)n * 24);
+            k_axpy<<<gblk, 256, 0, ctx->stream>>>(x, ws->w, n);
+            check(cudaGetLastError(), "k_axpy");
+        }
+        ++inf.cycles;
+    }
+};
+
+bool valid_opts(const rte_solve_opts& o) {
+    return o.restart >= 1 && o.restart <= kMaxKrylov && o.tol > 0.0 && o.max_iter >= 0 &&
+           (o.inner_precision == RTE_F32 || o.inner_precision == RTE_F64);
+}
+
 }  // namespace
 }  // namespace rte
 
@@ -235,152 +414,191 @@ RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev) {
 RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in,
                              double* x_dev, rte_solve_info* info) {
     if (!ctx || !x_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
-    rte_solve_opts opts;
-    if (opts_in) opts = *opts_in; else rte_solve_opts_default(&opts);
-    if (opts.restart < 1 || opts.restart > kMaxKrylov || !(opts.tol > 0.0) || opts.max_iter < 0 ||
-        (opts.inner_precision != RTE_F32 && opts.inner_precision != RTE_F64)) {
+    Solver S;
+    S.ctx = ctx;
+    S.pc = pc;
+    S.x = x_dev;
+    if (opts_in) S.opts = *opts_in; else rte_solve_opts_default(&S.opts);
+    if (!valid_opts(S.opts)) {
         set_error(ctx, "bad solve options (restart in [1, 64], tol > 0)");
         return RTE_EINVAL;
     }
-    rte_solve_info inf{};
-    const auto t0 = std::chrono::steady_clock::now();
-    auto elapsed_ms = [&]() {
-        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    };
-    rte_status status = RTE_OK;
     try {
-        if (pc) mgnet_prepare(pc, ctx);
-        const int m = opts.restart;
-        Workspace* ws = get_workspace(ctx, m);
-        const int64_t n = ctx->n;
-        const int gblk = ctx->num_sms * 4;
-        if (!opts.use_x0) check(cudaMemsetAsync(x_dev, 0, n * sizeof(double), ctx->stream), "zero x");
-        launch_norm(ctx, ctx->b, ws->est + 2);
-        const double bnorm = read_scalar(ctx, ws, ws->est + 2);
-        if (bnorm == 0.0) {
-            check(cudaMemsetAsync(x_dev, 0, n * sizeof(double), ctx->stream), "zero x");
-            inf.converged = 1;
-            inf.relres = 0.0;
-            inf.seconds = elapsed_ms() * 1e-3;
-            if (info) *info = inf;
-            return RTE_OK;
-        }
-        bool use_net = (pc != nullptr);
-        double prev_res = -1.0;
-        bool first = true;
-        while (true) {
-            // true residual in FP64
-            if (first && !opts.use_x0)
-                check(cudaMemcpyAsync(ws->w, ctx->b, n * sizeof(double), cudaMemcpyDeviceToDevice,
-                                      ctx->stream), "r = b");
-            else
-                launch_apply(ctx, true, x_dev, ws->w, true, ctx->b);
-            first = false;
-            launch_norm(ctx, ws->w, ws->est + 3);
-            const double beta = read_scalar(ctx, ws, ws->est + 3);
-            inf.relres = beta / bnorm;
-            if (!std::isfinite(beta)) {
-                set_error(ctx, "non-finite residual");
-                status = RTE_ESTALL;
-                break;
+        if (S.start()) {
+            while (S.cycle_begin()) {
+                do {
+                    S.precondition();
+                    S.inner_apply();
+                    S.orthogonalise_step();
+                    check(cudaMemcpyAsync(S.ws->est_host, S.ws->est, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                          ctx->stream), "d2h est");
+                    check(cudaStreamSynchronize(ctx->stream), "step sync");
+                    prof_resolve(ctx);
+                } while (S.after_step(S.ws->est_host[0], S.ws->est_host[1]));
+                S.cycle_end();
             }
-            if (use_net && prev_res > 0.0 && inf.relres > opts.stall_ratio * prev_res) {
-                use_net = false;          // the learned preconditioner stalled
-                inf.fell_back = 1;
-            }
-            prev_res = inf.relres;
-            if (inf.relres <= opts.tol) { inf.converged = 1; break; }
-            if (inf.iterations >= opts.max_iter) { status = RTE_ENOTCONV; break; }
-            if (opts.timeout_ms > 0 && elapsed_ms() > opts.timeout_ms) { status = RTE_ETIMEOUT; break; }
-            if (opts.cancel && *opts.cancel) {
-                set_error(ctx, "cancelled");
-                status = RTE_ECANCELLED;
-                break;
-            }
-            launch_scale(ctx, ws->w, ws->est + 3, ws->V);
-            {
-                ProfScope ps(ctx, K_CYCLE, 0.0);
-                k_cycle_start<<<1, 256, 0, ctx->stream>>>(m, ws->est + 3, ws->H, ws->g);
-                check(cudaGetLastError(), "k_cycle_start");
-            }
-            const bool cycle_net = use_net;
-            int k = 0;
-            for (int j = 0; j < m; ++j) {
-                const double* vj = ws->V + (size_t)j * n;
-                const void* zj = vj;
-                bool z_double = true;
-                if (cycle_net) {
-                    float* zf = ws->Z + (size_t)j * n;
-                    mgnet_precondition(pc, ctx, vj, zf);
-                    zj = zf;
-                    z_double = false;
-                }
-                if (opts.inner_precision == RTE_F32) {
-                    launch_response_apply(ctx, zj, z_double, ws->w, true);
-                } else {
-                    launch_block_apply(ctx, false, zj, z_double, ws->tmp, true);
-                    launch_apply(ctx, true, ws->tmp, ws->w, true, nullptr);
-                }
-                const int K = j + 1;
-                orthogonalise(ctx, ws, ws->V, K);
-                launch_scale(ctx, ws->w, ws->hcol + K, ws->V + (size_t)(j + 1) * n);
-                {
-                    ProfScope ps(ctx, K_GIVENS, 0.0);
-                    k_givens<<<1, 32, 0, ctx->stream>>>(j, m, ws->hcol, ws->H, ws->cs, ws->sn,
-                                                         ws->g, ws->est);
-                    check(cudaGetLastError(), "k_givens");
-                }
-                check(cudaMemcpyAsync(ws->est_host, ws->est, 2 * sizeof(double),
-                                      cudaMemcpyDeviceToHost, ctx->stream), "d2h est");
-                check(cudaStreamSynchronize(ctx->stream), "step sync");
-                prof_resolve(ctx);
-                ++inf.iterations;
-                k = j + 1;
-                const double est = ws->est_host[0], wn = ws->est_host[1];
-                if (!std::isfinite(est)) {
-                    if (use_net) { use_net = false; inf.fell_back = 1; }
-                    k = j;           // drop the bad column
-                    break;
-                }
-                if (est / bnorm <= opts.tol || wn == 0.0 || inf.iterations >= opts.max_iter) break;
-                if (opts.timeout_ms > 0 && elapsed_ms() > opts.timeout_ms) break;
-                if (opts.cancel && *opts.cancel) break;
-            }
-            if (k > 0) {
-                {
-                    ProfScope ps(ctx, K_BACKSUB, 0.0);
-                    k_backsub<<<1, 32, 0, ctx->stream>>>(k, m, ws->H, ws->g, ws->y);
-                    check(cudaGetLastError(), "k_backsub");
-                }
-                {
-                    ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + (cycle_net ? 4 : 8) * k));
-                    if (cycle_net)
-                        k_lincomb<float><<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
-                    else
-                        k_lincomb<double><<<gblk, 256, 0, ctx->stream>>>(ws->V, k, n, ws->y, ws->tmp);
-                    check(cudaGetLastError(), "k_lincomb");
-                }
-                launch_block_apply(ctx, false, ws->tmp, true, ws->w, true);   // D dy
-                {
-                    ProfScope ps(ctx, K_XUPDATE, (double)n * 24);
-                    k_axpy<<<gblk, 256, 0, ctx->stream>>>(x_dev, ws->w, n);
-                    check(cudaGetLastError(), "k_axpy");
-                }
-            }
-            ++inf.cycles;
         }
     } catch (const CudaError& e) {
-        status = cuda_status(ctx, e.code, e.where);
+        S.status = cuda_status(ctx, e.code, e.where);
     } catch (const StatusError& e) {
         set_error(ctx, e.msg);
-        status = e.code;
+        S.status = e.code;
     } catch (const std::bad_alloc&) {
         set_error(ctx, "host allocation failed");
-        status = RTE_ENOMEM;
+        S.status = RTE_ENOMEM;
     }
-    inf.seconds = elapsed_ms() * 1e-3;
-    if (info) *info = inf;
-    return status;
+    S.inf.seconds = S.elapsed_ms() * 1e-3;
+    if (info) *info = S.inf;
+    return S.status;
+}
+
+RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int count,
+                                   const rte_solve_opts* opts_in, double* const* x_dev,
+                                   rte_solve_info* infos, rte_status* statuses) {
+    if (!ctxs || !x_dev || count < 1 || count > 1024) {
+        set_error(nullptr, "bad argument (1 <= count <= 1024)");
+        return RTE_EINVAL;
+    }
+    rte_solve_opts opts;
+    if (opts_in) opts = *opts_in; else rte_solve_opts_default(&opts);
+    if (!valid_opts(opts)) {
+        set_error(nullptr, "bad solve options (restart in [1, 64], tol > 0)");
+        return RTE_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i] || !x_dev[i]) { set_error(nullptr, "NULL context or solution"); return RTE_EINVAL; }
+        if (ctxs[i]->stream != ctxs[0]->stream) {
+            set_error(nullptr, "the contexts of a group must share one stream");
+            return RTE_EINVAL;
+        }
+        for (int q = 0; q < i; ++q)
+            if (ctxs[q] == ctxs[i]) { set_error(nullptr, "a context appears twice in the group"); return RTE_EINVAL; }
+    }
+    cudaStream_t st = ctxs[0]->stream;
+    enum Phase { kCycle, kStep, kDone };
+    std::vector<Solver> S(count);
+    std::vector<Phase> phase(count, kCycle);
+    GroupItem* items_h = nullptr;
+    GroupItem* items_d = nullptr;
+    double* est_h = nullptr;
+    double* est_d = nullptr;
+    rte_status fatal = RTE_OK;
+    std::string fatal_msg;
+    try {
+        check(cudaMallocHost(&items_h, count * sizeof(GroupItem)), "cudaMallocHost");
+        check(cudaMallocHost(&est_h, 2 * count * sizeof(double)), "cudaMallocHost");
+        check(cudaMallocAsync(&items_d, count * sizeof(GroupItem), st), "cudaMallocAsync");
+        check(cudaMallocAsync(&est_d, 2 * count * sizeof(double), st), "cudaMallocAsync");
+        for (int i = 0; i < count; ++i) {
+            S[i].ctx = ctxs[i];
+            S[i].pc = pcs ? pcs[i] : nullptr;
+            S[i].x = x_dev[i];
+            S[i].opts = opts;
+            if (!S[i].start()) phase[i] = kDone;
+        }
+        std::vector<int> live;
+        while (true) {
+            // cycle starts (true residual, decisions) one instance at a time
+            for (int i = 0; i < count; ++i)
+                if (phase[i] == kCycle) phase[i] = S[i].cycle_begin() ? kStep : kDone;
+            live.clear();
+            for (int i = 0; i < count; ++i)
+                if (phase[i] == kStep) live.push_back(i);
+            if (live.empty()) break;
+            // preconditioners (each network on its own launches)
+            for (int i : live) S[i].precondition();
+            // one grouped Arnoldi step over the live instances
+            int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, kmax = 1;
+            size_t smem_ba = 0;
+            for (size_t q = 0; q < live.size(); ++q) {
+                Solver& s = S[live[q]];
+                GroupItem& it = items_h[q];
+                rte_ctx* c = s.ctx;
+                const int K = s.j + 1;
+                int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0;
+                size_t sm = 0;
+                group_response_geometry(c, &nba, &nga, &sm);
+                group_ortho_geometry(c, K, &nmd, &nud, &nrd);
+                it.Rt = c->Rt;
+                it.z = s.zj;
+                it.z_double = s.z_double ? 1 : 0;
+                it.o = reinterpret_cast<float*>(c->trace_out);
+                it.I = c->I;
+                it.M = c->M;
+                it.N = c->N;
+                it.n = c->n;
+                it.V = s.ws->V;
+                it.w = s.ws->w;
+                it.h1 = s.ws->h1;
+                it.h2 = s.ws->h2;
+                it.hcol = s.ws->hcol;
+                it.Vnext = s.ws->V + (size_t)(s.j + 1) * s.n;
+                it.partials = c->partials;
+                it.counter = c->counter;
+                it.K = K;
+                it.j = s.j;
+                it.m = s.m;
+                it.H = s.ws->H;
+                it.cs = s.ws->cs;
+                it.sn = s.ws->sn;
+                it.g = s.ws->g;
+                it.est = s.ws->est;
+                it.est_out = est_d + 2 * q;
+                it.b_ba = ba; it.n_ba = nba; ba += nba;
+                it.b_ga = ga; it.n_ga = nga; ga += nga;
+                it.b_md = md; it.n_md = nmd; md += nmd;
+                it.b_ud = ud; it.n_ud = nud; ud += nud;
+                it.b_rd = rd; it.n_rd = nrd; rd += nrd;
+                kmax = K > kmax ? K : kmax;
+                smem_ba = sm > smem_ba ? sm : smem_ba;
+            }
+            const int nl = (int)live.size();
+            check(cudaMemcpyAsync(items_d, items_h, nl * sizeof(GroupItem), cudaMemcpyHostToDevice, st), "h2d items");
+            if (opts.inner_precision == RTE_F32) {
+                launch_group_response(items_d, nl, ba, ga, smem_ba, st);
+            } else {
+                for (int i : live) S[i].inner_apply();
+            }
+            launch_group_orthogonalise(items_d, nl, md, ud, rd, kmax, st);
+            k_givens_group<<<nl, 32, 0, st>>>(items_d);
+            check(cudaGetLastError(), "k_givens_group");
+            check(cudaMemcpyAsync(est_h, est_d, 2 * nl * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h est");
+            check(cudaStreamSynchronize(st), "group step sync");
+            for (int q = 0; q < nl; ++q) {
+                Solver& s = S[live[q]];
+                prof_resolve(s.ctx);
+                if (!s.after_step(est_h[2 * q], est_h[2 * q + 1])) {
+                    s.cycle_end();
+                    phase[live[q]] = kCycle;
+                }
+            }
+        }
+    } catch (const CudaError& e) {
+        fatal = cuda_status(nullptr, e.code, e.where);
+        fatal_msg = rte_last_error(nullptr);
+    } catch (const StatusError& e) {
+        fatal = e.code;
+        fatal_msg = e.msg;
+    } catch (const std::bad_alloc&) {
+        fatal = RTE_ENOMEM;
+        fatal_msg = "host allocation failed";
+    }
+    if (items_d) cudaFreeAsync(items_d, st);
+    if (est_d) cudaFreeAsync(est_d, st);
+    cudaStreamSynchronize(st);
+    if (items_h) cudaFreeHost(items_h);
+    if (est_h) cudaFreeHost(est_h);
+    for (int i = 0; i < count; ++i) {
+        S[i].inf.seconds = S[i].elapsed_ms() * 1e-3;
+        if (fatal != RTE_OK) S[i].status = fatal;
+        if (infos) infos[i] = S[i].inf;
+        if (statuses) statuses[i] = S[i].status;
+    }
+    if (fatal != RTE_OK) {
+        set_error(nullptr, fatal_msg);
+        return fatal;
+    }
+    return RTE_OK;
 }
 
 }  // extern "C"

@@ -102,6 +102,7 @@ SIGNATURES = {
     "mgnet_destroy": (None, [_P]),
     "mgnet_param_count": (ctypes.c_int64, [_P]),
     "mgnet_set_precision": (_I, [_P, _I]),
+    "rte_solve_group": (_I, [_P, _P, _I, _P, _P, _P, _P]),
     "mgnet_set_loss": (_I, [_P, _I]),
     "mgnet_get_loss": (_I, [_P]),
     "rte_atfps_setup": (_I, [_P, _D, ctypes.POINTER(ctypes.c_int64)]),
@@ -266,6 +267,32 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def solve_group(ctxs, xs, pcs=None, tol=1e-8, restart=50, max_iter=20000, inner_precision=RTE_F32,
+                use_x0=False, stall_ratio=0.9, timeout_ms=0.0):
+    """rte_solve_group: the solves of several contexts (one stream) in lockstep
+    with their Arnoldi steps in shared launches.  Returns one info dict (with
+    its "status") per solve."""
+    import torch
+    count = len(ctxs)
+    o = SolveOpts()
+    load().rte_solve_opts_default(ctypes.byref(o))
+    o.tol, o.restart, o.max_iter = float(tol), int(restart), int(max_iter)
+    o.inner_precision, o.use_x0 = int(inner_precision), int(use_x0)
+    o.stall_ratio, o.timeout_ms = float(stall_ratio), float(timeout_ms)
+    cp = (_P * count)(*[c.ptr for c in ctxs])
+    xp = (_P * count)(*[_dev(x, torch.float64, c.n) for c, x in zip(ctxs, xs)])
+    pp = (_P * count)(*[(p.ptr if p is not None else None) for p in (pcs or [None] * count)])
+    infos = (SolveInfo * count)()
+    sts = (ctypes.c_int * count)()
+    _check(load().rte_solve_group(cp, pp, count, ctypes.byref(o), xp, infos, sts))
+    out = []
+    for i in range(count):
+        d = infos[i].as_dict()
+        d["status"] = STATUS_NAMES[sts[i]]
+        out.append(d)
+    return out
 
 
 class MgNetConfig(ctypes.Structure):
