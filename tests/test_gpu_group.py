@@ -37,14 +37,19 @@ def test_group_is_bit_identical_to_lone_solves(lib, count, inner):
         assert i2["status"] == "OK" and i2["converged"], i2
         assert i2["iterations"] == i1["iterations"] and i2["cycles"] == i1["cycles"]
         assert torch.equal(x1, x2)
-    # and the solution is the oracle's (dense LU) on the smallest instance
+    # and the solution is the oracle's (dense LU) on the smallest instance:
+    # residual by the oracle's operator, and the angular flux at the cell centres
+    # (the coefficients themselves cancel heavily, so psi is compared, to
+    # cond(A) times the 1e-10 residual)
     i = int(np.argmin([md.I * md.M for md in media]))
     md = media[i]
     p = tfps.Problem(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow)
     xl = krylov.dense_solve(p.assemble(), p.rhs().ravel())
     r = p.rhs().ravel() - p.apply(xs[i].cpu().numpy().reshape(2 * md.M, -1)).ravel()
     assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 1e-10
-    assert np.linalg.norm(xs[i].cpu().numpy() - xl) <= 1e-6 * np.linalg.norm(xl)
+    psi = p.reconstruct(xs[i].cpu().numpy().reshape(2 * md.M, -1)).ravel()
+    psil = p.reconstruct(xl.reshape(2 * md.M, -1)).ravel()
+    assert np.linalg.norm(psi - psil) <= 1e-5 * np.linalg.norm(psil)
 
 
 def test_group_with_networks_and_early_endings(lib):
