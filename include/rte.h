@@ -415,12 +415,21 @@ RTE_API rte_status mgnet_load(mgnet* net, const char* path);
  * elapses: ETIMEOUT, request kept) and copies psi [M][N] (cell centres) to
  * psi_host if not NULL; a finished request is forgotten after its wait.
  * Thread-safe: any thread may submit, wait or cancel.
+ *
+ * grouped = 1: the admitted requests (up to `slots`, same footprint rule) run
+ * as one lockstep group on one stream: two threads set requests up, and one
+ * thread advances every running solve by one Arnoldi step per round with the
+ * steps of all of them in shared launches (as rte_solve_group); a request set
+ * up while others run joins at the next round, a finished one leaves at once
+ * (its bytes and slot go to the next waiting request).  Results are the same
+ * bits as a lone solve.  grouped = 0 (default): one stream per slot.
  * ------------------------------------------------------------------------- */
 typedef struct rte_server rte_server;
 typedef struct rte_server_config {
     size_t max_device_bytes;
     int slots;
     int64_t inject_alloc_failure_id;
+    int grouped;
 } rte_server_config;
 typedef struct rte_request {
     int I, M;

@@ -174,6 +174,20 @@ void launch_group_orthogonalise(const GroupItem* items_dev, int count, int block
 // block counts of one item's Gram-Schmidt passes
 void group_ortho_geometry(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd);
 
+// lockstep groups of solves (solve.cu), for the grouped server: a solve
+// (started on creation: workspace, initial guess, ||b||) and rounds over a set
+// of solves on one stream (cycle starts, then one Arnoldi step of every
+// stepping solve in shared launches).  Errors throw CudaError / StatusError.
+struct GroupSolve;
+struct GroupRounds;
+GroupSolve* group_solve_new(rte_ctx* ctx, mgnet* pc, const rte_solve_opts& opts, double* x);
+bool group_solve_done(const GroupSolve* g);
+void group_solve_result(const GroupSolve* g, rte_solve_info* info, rte_status* status);
+void group_solve_free(GroupSolve* g);
+GroupRounds* group_rounds_new(cudaStream_t st, int capacity);
+void group_rounds_step(GroupRounds* r, GroupSolve* const* set, int count);
+void group_rounds_free(GroupRounds* r);
+
 // ATFPS loss filter (atfps.cu) -----------------------------------------------
 void atfps_setup(rte_ctx* ctx, double delta);
 void atfps_free(rte_ctx* ctx);

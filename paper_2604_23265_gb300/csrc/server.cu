@@ -12,6 +12,13 @@
 // is bit-identical alone and in the mix.  Faults stay per request: a malformed
 // medium, an injected allocation failure or a cancellation ends that request
 // with its status; the others continue.
+//
+// Grouped mode: the admitted requests form one lockstep group on one stream.
+// Setup threads build each admitted request's context and vectors and hand it
+// to the group thread, which adds it to the group at the next round; every
+// round advances all running solves by one Arnoldi step in shared launches
+// (the rounds of rte_solve_group), and a solve that finishes is reconstructed,
+// copied out and released at once.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -47,6 +54,10 @@ struct Job {
     rte_solve_info info{};
     std::vector<double> psi;          // [M][N]
     std::string err;
+    // grouped mode: the request's context and vectors while it runs
+    rte_ctx* ctx = nullptr;
+    double* x = nullptr;
+    double* psi_dev = nullptr;
 };
 
 }  // namespace
@@ -66,6 +77,12 @@ struct rte_server {
     bool stopping = false;
     std::vector<std::thread> workers;
     int64_t completed = 0;
+    // grouped mode
+    cudaStream_t gst = nullptr;
+    mgnet* gnet = nullptr;
+    std::deque<std::shared_ptr<rte::Job>> setup_q;   // admitted, waiting for a setup thread
+    std::vector<std::shared_ptr<rte::Job>> ready;    // set up, waiting to join the group
+    std::condition_variable cv_setup, cv_group;
 };
 
 namespace rte {
@@ -175,6 +192,201 @@ void worker_main(rte_server* s, int slot) {
     cudaStreamDestroy(st);
 }
 
+// Releases a finished request (grouped mode): bytes, slot, completion.
+void finish_job(rte_server* s, const std::shared_ptr<Job>& job, bool admitted) {
+    job->t_end = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (admitted) {
+            s->bytes_in_use -= job->footprint;
+            --s->active;
+        }
+        job->done = true;
+        ++s->completed;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+// Grouped mode, admission: the oldest waiting request goes to the setup
+// threads when the group has a free slot and its footprint fits.
+void admit_main(rte_server* s) {
+    while (true) {
+        std::shared_ptr<Job> job;
+        bool admitted = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] {
+                if (s->stopping) return true;
+                if (s->queue.empty()) return false;
+                const auto& head = s->queue.front();
+                return head->cancel || (s->active < s->cfg.slots &&
+                                        s->bytes_in_use + head->footprint <= s->cfg.max_device_bytes);
+            });
+            if (s->stopping) break;
+            job = s->queue.front();
+            s->queue.pop_front();
+            admitted = !job->cancel;
+            if (admitted) {
+                s->bytes_in_use += job->footprint;
+                ++s->active;
+            }
+            job->t_start = Clock::now();
+            if (admitted) {
+                s->setup_q.push_back(job);
+                s->cv_setup.notify_one();
+                continue;
+            }
+        }
+        job->status = RTE_ECANCELLED;
+        job->err = "cancelled before admission";
+        finish_job(s, job, false);
+    }
+}
+
+// Grouped mode, set-up: context, solution and output vectors on the group's
+// stream, then hand-over to the group thread.
+void setup_main(rte_server* s) {
+    cudaSetDevice(s->device);
+    while (true) {
+        std::shared_ptr<Job> job;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_setup.wait(lk, [&] { return s->stopping || !s->setup_q.empty(); });
+            if (s->stopping) break;
+            job = s->setup_q.front();
+            s->setup_q.pop_front();
+        }
+        bool ok = false;
+        if (s->cfg.inject_alloc_failure_id == job->id) {
+            job->status = RTE_ENOMEM;          // host-side fault injection for tests
+            job->err = "injected allocation failure";
+        } else {
+            rte_grid grid{job->I};
+            rte_quadrature quad{job->M};
+            job->status = rte_setup(&grid, &quad, job->sT.data(), job->sa.data(), job->q.data(), job->eps.data(),
+                                    job->eps_is_scalar, job->g, job->inflow.empty() ? nullptr : job->inflow.data(),
+                                    s->gst, &job->ctx);
+            if (job->status == RTE_OK) {
+                const int64_t n = (int64_t)2 * job->M * job->I * job->I;
+                cudaError_t e = cudaMallocAsync(&job->x, n * sizeof(double), s->gst);
+                if (e == cudaSuccess)
+                    e = cudaMallocAsync(&job->psi_dev, (size_t)job->M * job->I * job->I * sizeof(double), s->gst);
+                if (e != cudaSuccess) {
+                    job->status = RTE_ENOMEM;
+                    job->err = cudaGetErrorString(e);
+                } else {
+                    ok = true;
+                }
+            } else {
+                job->err = rte_last_error(nullptr);
+            }
+        }
+        if (ok) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->ready.push_back(job);
+            s->cv_group.notify_one();
+        } else {
+            if (job->psi_dev) cudaFreeAsync(job->psi_dev, s->gst);
+            if (job->x) cudaFreeAsync(job->x, s->gst);
+            if (job->ctx) rte_destroy(job->ctx);
+            job->ctx = nullptr;
+            finish_job(s, job, true);
+        }
+    }
+}
+
+// reconstruct psi, copy it out, free the request's device state
+void complete_job(rte_server* s, const std::shared_ptr<Job>& job) {
+    if (job->status == RTE_OK || job->status == RTE_ENOTCONV) {
+        rte_reconstruct(job->ctx, job->x, job->psi_dev);
+        job->psi.resize((size_t)job->M * job->I * job->I);
+        cudaMemcpyAsync(job->psi.data(), job->psi_dev, job->psi.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        s->gst);
+        cudaStreamSynchronize(s->gst);
+    }
+    if (job->status != RTE_OK && job->err.empty()) job->err = rte_last_error(job->ctx);
+    cudaFreeAsync(job->x, s->gst);
+    cudaFreeAsync(job->psi_dev, s->gst);
+    rte_destroy(job->ctx);
+    job->ctx = nullptr;
+    finish_job(s, job, true);
+}
+
+// Grouped mode, the lockstep group: requests join between rounds and leave
+// when they finish.
+void group_main(rte_server* s) {
+    cudaSetDevice(s->device);
+    GroupRounds* rounds = nullptr;
+    std::vector<std::pair<std::shared_ptr<Job>, GroupSolve*>> live;
+    try {
+        rounds = group_rounds_new(s->gst, s->cfg.slots);
+        while (true) {
+            std::vector<std::shared_ptr<Job>> joining;
+            {
+                std::unique_lock<std::mutex> lk(s->mu);
+                if (live.empty())
+                    s->cv_group.wait(lk, [&] { return s->stopping || !s->ready.empty(); });
+                if (s->stopping) break;
+                joining.swap(s->ready);
+            }
+            for (auto& job : joining) {
+                job->opts.cancel = &job->cancel;
+                mgnet* pc = (job->use_net && s->gnet) ? s->gnet : nullptr;
+                try {
+                    live.emplace_back(job, group_solve_new(job->ctx, pc, job->opts, job->x));
+                } catch (const StatusError& e) {
+                    job->status = e.code;
+                    job->err = e.msg;
+                    complete_job(s, job);
+                } catch (const CudaError& e) {
+                    job->status = cuda_status(nullptr, e.code, e.where);
+                    job->err = e.where;
+                    complete_job(s, job);
+                }
+            }
+            std::vector<GroupSolve*> set;
+            for (auto& p : live) set.push_back(p.second);
+            group_rounds_step(rounds, set.data(), (int)set.size());
+            for (size_t i = 0; i < live.size();) {
+                if (group_solve_done(live[i].second)) {
+                    auto job = live[i].first;
+                    group_solve_result(live[i].second, &job->info, &job->status);
+                    group_solve_free(live[i].second);
+                    complete_job(s, job);
+                    live.erase(live.begin() + i);
+                } else {
+                    ++i;
+                }
+            }
+        }
+    } catch (const CudaError& e) {
+        const rte_status st = cuda_status(nullptr, e.code, e.where);
+        for (auto& p : live) {
+            p.first->status = st;
+            p.first->err = e.where;
+            group_solve_free(p.second);
+            complete_job(s, p.first);
+        }
+        live.clear();
+    } catch (const StatusError& e) {
+        for (auto& p : live) {
+            p.first->status = e.code;
+            p.first->err = e.msg;
+            group_solve_free(p.second);
+            complete_job(s, p.first);
+        }
+        live.clear();
+    }
+    for (auto& p : live) {             // stopping: cancelled mid-solve
+        p.first->status = RTE_ECANCELLED;
+        p.first->err = "server stopped";
+        group_solve_free(p.second);
+        complete_job(s, p.first);
+    }
+    if (rounds) group_rounds_free(rounds);
+}
+
 }  // namespace
 }  // namespace rte
 
@@ -187,6 +399,7 @@ RTE_API void rte_server_config_default(rte_server_config* c) {
     c->max_device_bytes = (size_t)64 << 30;
     c->slots = 4;
     c->inject_alloc_failure_id = -1;
+    c->grouped = 0;
 }
 
 RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, rte_server** out) {
@@ -199,6 +412,27 @@ RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, r
     if (!s) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; }
     s->cfg = *cfg;
     cudaGetDevice(&s->device);
+    if (cfg->grouped) {
+        if (cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            set_error(nullptr, "cudaStreamCreate failed");
+            return RTE_ECUDA;
+        }
+        if (net) {
+            rte_status st = mgnet_clone(net, s->gst, &s->gnet);
+            if (st != RTE_OK) {
+                cudaStreamDestroy(s->gst);
+                delete s;
+                return st;
+            }
+        }
+        s->workers.emplace_back(admit_main, s);
+        s->workers.emplace_back(setup_main, s);
+        s->workers.emplace_back(setup_main, s);
+        s->workers.emplace_back(group_main, s);
+        *out = s;
+        return RTE_OK;
+    }
     if (net) {
         for (int i = 0; i < cfg->slots; ++i) {
             mgnet* c = nullptr;
@@ -235,7 +469,7 @@ RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* r, int64_
     job->opts.tol = r->tol > 0 ? r->tol : 1e-8;
     if (r->max_iter > 0) job->opts.max_iter = r->max_iter;
     if (r->restart > 0) job->opts.restart = r->restart;
-    job->use_net = r->use_net && !s->nets.empty();
+    job->use_net = r->use_net && (!s->nets.empty() || s->gnet);
     job->footprint = footprint(r->I, r->M, job->opts.restart, job->use_net);
     if (job->footprint > s->cfg.max_device_bytes) {
         set_error(nullptr, "request needs more device memory than the server budget");
@@ -316,6 +550,8 @@ RTE_API void rte_server_destroy(rte_server* s) {
         for (auto& kv : s->jobs) kv.second->cancel = 1;
     }
     s->cv_work.notify_all();
+    s->cv_setup.notify_all();
+    s->cv_group.notify_all();
     for (auto& t : s->workers) t.join();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -326,6 +562,27 @@ RTE_API void rte_server_destroy(rte_server* s) {
     }
     s->cv_done.notify_all();
     for (mgnet* m : s->nets) mgnet_destroy(m);
+    {
+        // grouped mode: requests set up but never run
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto& j : s->ready) {
+            if (j->x) cudaFreeAsync(j->x, s->gst);
+            if (j->psi_dev) cudaFreeAsync(j->psi_dev, s->gst);
+            if (j->ctx) rte_destroy(j->ctx);
+            j->status = RTE_ECANCELLED;
+            j->done = true;
+        }
+        for (auto& j : s->setup_q) {
+            j->status = RTE_ECANCELLED;
+            j->done = true;
+        }
+    }
+    s->cv_done.notify_all();
+    if (s->gnet) mgnet_destroy(s->gnet);
+    if (s->gst) {
+        cudaStreamSynchronize(s->gst);
+        cudaStreamDestroy(s->gst);
+    }
     delete s;
 }
 

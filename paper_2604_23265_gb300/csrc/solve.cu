@@ -222,6 +222,7 @@ struct Solver {
     int j = 0, k = 0;                 // Arnoldi step in the cycle; columns for the cycle end
     const void* zj = nullptr;
     bool z_double = true;
+    int phase = 0;                    // grouped runs: 0 cycle start next, 1 stepping, 2 done
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
     double elapsed_ms() const {
@@ -363,12 +364,160 @@ struct Solver {
     }
 };
 
+// Lockstep rounds over a set of solves on one stream: the cycle starts of the
+// solves that need one, then one Arnoldi step of every stepping solve in
+// shared launches, one read of all residual estimates, and the per-solve
+// decisions (cycle ends included).
+struct GroupRunner {
+    enum { kCycle = 0, kStep = 1, kDone = 2 };
+    cudaStream_t st = nullptr;
+    int cap = 0;
+    GroupItem* items_h = nullptr;
+    GroupItem* items_d = nullptr;
+    double* est_h = nullptr;
+    double* est_d = nullptr;
+
+    GroupRunner(cudaStream_t s, int capacity) : st(s), cap(capacity) {
+        check(cudaMallocHost(&items_h, cap * sizeof(GroupItem)), "cudaMallocHost");
+        check(cudaMallocHost(&est_h, 2 * cap * sizeof(double)), "cudaMallocHost");
+        check(cudaMallocAsync(&items_d, cap * sizeof(GroupItem), st), "cudaMallocAsync");
+        check(cudaMallocAsync(&est_d, 2 * cap * sizeof(double), st), "cudaMallocAsync");
+    }
+    ~GroupRunner() {
+        if (items_d) cudaFreeAsync(items_d, st);
+        if (est_d) cudaFreeAsync(est_d, st);
+        cudaStreamSynchronize(st);
+        if (items_h) cudaFreeHost(items_h);
+        if (est_h) cudaFreeHost(est_h);
+    }
+
+    // one round; solves whose phase becomes kDone are finished
+    void round(const std::vector<Solver*>& set) {
+        for (Solver* s : set)
+            if (s->phase == kCycle) s->phase = s->cycle_begin() ? kStep : kDone;
+        std::vector<Solver*> live;
+        for (Solver* s : set)
+            if (s->phase == kStep) live.push_back(s);
+        if (live.empty()) return;
+        if ((int)live.size() > cap) throw StatusError{RTE_EINVAL, "group larger than its capacity"};
+        for (Solver* s : live) s->precondition();
+        int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, kmax = 1;
+        size_t smem_ba = 0;
+        bool f32 = true;
+        for (size_t q = 0; q < live.size(); ++q) {
+            Solver& s = *live[q];
+            GroupItem& it = items_h[q];
+            rte_ctx* c = s.ctx;
+            const int K = s.j + 1;
+            int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0;
+            size_t sm = 0;
+            group_response_geometry(c, &nba, &nga, &sm);
+            group_ortho_geometry(c, K, &nmd, &nud, &nrd);
+            f32 = f32 && s.opts.inner_precision == RTE_F32;
+            it.Rt = c->Rt;
+            it.z = s.zj;
+            it.z_double = s.z_double ? 1 : 0;
+            it.o = reinterpret_cast<float*>(c->trace_out);
+            it.I = c->I;
+            it.M = c->M;
+            it.N = c->N;
+            it.n = c->n;
+            it.V = s.ws->V;
+            it.w = s.ws->w;
+            it.h1 = s.ws->h1;
+            it.h2 = s.ws->h2;
+            it.hcol = s.ws->hcol;
+            it.Vnext = s.ws->V + (size_t)(s.j + 1) * s.n;
+            it.partials = c->partials;
+            it.counter = c->counter;
+            it.K = K;
+            it.j = s.j;
+            it.m = s.m;
+            it.H = s.ws->H;
+            it.cs = s.ws->cs;
+            it.sn = s.ws->sn;
+            it.g = s.ws->g;
+            it.est = s.ws->est;
+            it.est_out = est_d + 2 * q;
+            it.b_ba = ba; it.n_ba = nba; ba += nba;
+            it.b_ga = ga; it.n_ga = nga; ga += nga;
+            it.b_md = md; it.n_md = nmd; md += nmd;
+            it.b_ud = ud; it.n_ud = nud; ud += nud;
+            it.b_rd = rd; it.n_rd = nrd; rd += nrd;
+            kmax = K > kmax ? K : kmax;
+            smem_ba = sm > smem_ba ? sm : smem_ba;
+        }
+        const int nl = (int)live.size();
+        check(cudaMemcpyAsync(items_d, items_h, nl * sizeof(GroupItem), cudaMemcpyHostToDevice, st), "h2d items");
+        if (f32) {
+            launch_group_response(items_d, nl, ba, ga, smem_ba, st);
+        } else {
+            for (Solver* s : live) s->inner_apply();
+        }
+        launch_group_orthogonalise(items_d, nl, md, ud, rd, kmax, st);
+        k_givens_group<<<nl, 32, 0, st>>>(items_d);
+        check(cudaGetLastError(), "k_givens_group");
+        check(cudaMemcpyAsync(est_h, est_d, 2 * nl * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h est");
+        check(cudaStreamSynchronize(st), "group step sync");
+        for (int q = 0; q < nl; ++q) {
+            Solver& s = *live[q];
+            prof_resolve(s.ctx);
+            if (!s.after_step(est_h[2 * q], est_h[2 * q + 1])) {
+                s.cycle_end();
+                s.phase = kCycle;
+            }
+        }
+    }
+};
+
 bool valid_opts(const rte_solve_opts& o) {
     return o.restart >= 1 && o.restart <= kMaxKrylov && o.tol > 0.0 && o.max_iter >= 0 &&
            (o.inner_precision == RTE_F32 || o.inner_precision == RTE_F64);
 }
 
 }  // namespace
+
+struct GroupSolve : Solver {};
+struct GroupRounds : GroupRunner {
+    using GroupRunner::GroupRunner;
+};
+
+GroupSolve* group_solve_new(rte_ctx* ctx, mgnet* pc, const rte_solve_opts& opts, double* x) {
+    GroupSolve* g = new GroupSolve();
+    g->ctx = ctx;
+    g->pc = pc;
+    g->opts = opts;
+    g->x = x;
+    try {
+        g->phase = g->start() ? GroupRunner::kCycle : GroupRunner::kDone;
+    } catch (...) {
+        delete g;
+        throw;
+    }
+    return g;
+}
+
+bool group_solve_done(const GroupSolve* g) { return g->phase == GroupRunner::kDone; }
+
+void group_solve_result(const GroupSolve* g, rte_solve_info* info, rte_status* status) {
+    if (info) {
+        *info = g->inf;
+        info->seconds = g->elapsed_ms() * 1e-3;
+    }
+    if (status) *status = g->status;
+}
+
+void group_solve_free(GroupSolve* g) { delete g; }
+
+GroupRounds* group_rounds_new(cudaStream_t st, int capacity) { return new GroupRounds(st, capacity); }
+
+void group_rounds_step(GroupRounds* r, GroupSolve* const* set, int count) {
+    std::vector<Solver*> v(set, set + count);
+    r->round(v);
+}
+
+void group_rounds_free(GroupRounds* r) { delete r; }
+
 }  // namespace rte
 
 using namespace rte;
@@ -475,103 +624,25 @@ RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int 
             if (ctxs[q] == ctxs[i]) { set_error(nullptr, "a context appears twice in the group"); return RTE_EINVAL; }
     }
     cudaStream_t st = ctxs[0]->stream;
-    enum Phase { kCycle, kStep, kDone };
     std::vector<Solver> S(count);
-    std::vector<Phase> phase(count, kCycle);
-    GroupItem* items_h = nullptr;
-    GroupItem* items_d = nullptr;
-    double* est_h = nullptr;
-    double* est_d = nullptr;
     rte_status fatal = RTE_OK;
     std::string fatal_msg;
     try {
-        check(cudaMallocHost(&items_h, count * sizeof(GroupItem)), "cudaMallocHost");
-        check(cudaMallocHost(&est_h, 2 * count * sizeof(double)), "cudaMallocHost");
-        check(cudaMallocAsync(&items_d, count * sizeof(GroupItem), st), "cudaMallocAsync");
-        check(cudaMallocAsync(&est_d, 2 * count * sizeof(double), st), "cudaMallocAsync");
+        GroupRunner runner(st, count);
+        std::vector<Solver*> set;
         for (int i = 0; i < count; ++i) {
             S[i].ctx = ctxs[i];
             S[i].pc = pcs ? pcs[i] : nullptr;
             S[i].x = x_dev[i];
             S[i].opts = opts;
-            if (!S[i].start()) phase[i] = kDone;
+            S[i].phase = S[i].start() ? GroupRunner::kCycle : GroupRunner::kDone;
+            set.push_back(&S[i]);
         }
-        std::vector<int> live;
         while (true) {
-            // cycle starts (true residual, decisions) one instance at a time
-            for (int i = 0; i < count; ++i)
-                if (phase[i] == kCycle) phase[i] = S[i].cycle_begin() ? kStep : kDone;
-            live.clear();
-            for (int i = 0; i < count; ++i)
-                if (phase[i] == kStep) live.push_back(i);
-            if (live.empty()) break;
-            // preconditioners (each network on its own launches)
-            for (int i : live) S[i].precondition();
-            // one grouped Arnoldi step over the live instances
-            int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, kmax = 1;
-            size_t smem_ba = 0;
-            for (size_t q = 0; q < live.size(); ++q) {
-                Solver& s = S[live[q]];
-                GroupItem& it = items_h[q];
-                rte_ctx* c = s.ctx;
-                const int K = s.j + 1;
-                int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0;
-                size_t sm = 0;
-                group_response_geometry(c, &nba, &nga, &sm);
-                group_ortho_geometry(c, K, &nmd, &nud, &nrd);
-                it.Rt = c->Rt;
-                it.z = s.zj;
-                it.z_double = s.z_double ? 1 : 0;
-                it.o = reinterpret_cast<float*>(c->trace_out);
-                it.I = c->I;
-                it.M = c->M;
-                it.N = c->N;
-                it.n = c->n;
-                it.V = s.ws->V;
-                it.w = s.ws->w;
-                it.h1 = s.ws->h1;
-                it.h2 = s.ws->h2;
-                it.hcol = s.ws->hcol;
-                it.Vnext = s.ws->V + (size_t)(s.j + 1) * s.n;
-                it.partials = c->partials;
-                it.counter = c->counter;
-                it.K = K;
-                it.j = s.j;
-                it.m = s.m;
-                it.H = s.ws->H;
-                it.cs = s.ws->cs;
-                it.sn = s.ws->sn;
-                it.g = s.ws->g;
-                it.est = s.ws->est;
-                it.est_out = est_d + 2 * q;
-                it.b_ba = ba; it.n_ba = nba; ba += nba;
-                it.b_ga = ga; it.n_ga = nga; ga += nga;
-                it.b_md = md; it.n_md = nmd; md += nmd;
-                it.b_ud = ud; it.n_ud = nud; ud += nud;
-                it.b_rd = rd; it.n_rd = nrd; rd += nrd;
-                kmax = K > kmax ? K : kmax;
-                smem_ba = sm > smem_ba ? sm : smem_ba;
-            }
-            const int nl = (int)live.size();
-            check(cudaMemcpyAsync(items_d, items_h, nl * sizeof(GroupItem), cudaMemcpyHostToDevice, st), "h2d items");
-            if (opts.inner_precision == RTE_F32) {
-                launch_group_response(items_d, nl, ba, ga, smem_ba, st);
-            } else {
-                for (int i : live) S[i].inner_apply();
-            }
-            launch_group_orthogonalise(items_d, nl, md, ud, rd, kmax, st);
-            k_givens_group<<<nl, 32, 0, st>>>(items_d);
-            check(cudaGetLastError(), "k_givens_group");
-            check(cudaMemcpyAsync(est_h, est_d, 2 * nl * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h est");
-            check(cudaStreamSynchronize(st), "group step sync");
-            for (int q = 0; q < nl; ++q) {
-                Solver& s = S[live[q]];
-                prof_resolve(s.ctx);
-                if (!s.after_step(est_h[2 * q], est_h[2 * q + 1])) {
-                    s.cycle_end();
-                    phase[live[q]] = kCycle;
-                }
-            }
+            bool any = false;
+            for (Solver* s : set) any = any || s->phase != GroupRunner::kDone;
+            if (!any) break;
+            runner.round(set);
         }
     } catch (const CudaError& e) {
         fatal = cuda_status(nullptr, e.code, e.where);
@@ -583,11 +654,6 @@ RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int 
         fatal = RTE_ENOMEM;
         fatal_msg = "host allocation failed";
     }
-    if (items_d) cudaFreeAsync(items_d, st);
-    if (est_d) cudaFreeAsync(est_d, st);
-    cudaStreamSynchronize(st);
-    if (items_h) cudaFreeHost(items_h);
-    if (est_h) cudaFreeHost(est_h);
     for (int i = 0; i < count; ++i) {
         S[i].inf.seconds = S[i].elapsed_ms() * 1e-3;
         if (fatal != RTE_OK) S[i].status = fatal;

@@ -193,7 +193,7 @@ def eigenbasis(M, g, one_minus_gamma, axis):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_device_bytes", ctypes.c_size_t), ("slots", _I),
-                ("inject_alloc_failure_id", ctypes.c_int64)]
+                ("inject_alloc_failure_id", ctypes.c_int64), ("grouped", _I)]
 
 
 class Request(ctypes.Structure):
@@ -215,11 +215,12 @@ class ServerStats(ctypes.Structure):
 class Server:
     """Continuous-batching solve server (rte_server_*); thread-safe."""
 
-    def __init__(self, slots=4, max_device_bytes=64 << 30, net=None, inject_alloc_failure_id=-1):
+    def __init__(self, slots=4, max_device_bytes=64 << 30, net=None, inject_alloc_failure_id=-1, grouped=False):
         cfg = ServerConfig()
         load().rte_server_config_default(ctypes.byref(cfg))
         cfg.slots, cfg.max_device_bytes = int(slots), int(max_device_bytes)
         cfg.inject_alloc_failure_id = int(inject_alloc_failure_id)
+        cfg.grouped = 1 if grouped else 0
         out = ctypes.c_void_p()
         _check(load().rte_server_create(ctypes.byref(cfg), net.ptr if net is not None else None,
                                         ctypes.byref(out)))

@@ -1,5 +1,7 @@
-"""Continuous-batching server: every result is the same bits alone and in a
-mixed batch; admission by device footprint; faults stay per request."""
+"""Continuous-batching server, in both modes (one stream per slot, and the
+lockstep group whose Arnoldi steps share launches): every result is the same
+bits alone and in a mixed batch; admission by device footprint; faults stay
+per request."""
 import numpy as np
 import pytest
 
@@ -32,10 +34,11 @@ def _lone(md, tol=1e-8):
     return info, psi.cpu().numpy()
 
 
-def test_results_identical_alone_and_in_the_mix(lib):
+@pytest.mark.parametrize("grouped", [False, True])
+def test_results_identical_alone_and_in_the_mix(lib, grouped):
     from paper_2604_23265_gb300 import rte
     meds = _mix(10, seed=1)
-    srv = rte.Server(slots=4)
+    srv = rte.Server(slots=4, grouped=grouped)
     ids = [srv.submit(md) for md in meds]
     got = [srv.wait(i) for i in ids]
     srv.close()
@@ -46,24 +49,26 @@ def test_results_identical_alone_and_in_the_mix(lib):
         np.testing.assert_array_equal(psi, ref)
 
 
-def test_admission_by_footprint(lib):
+@pytest.mark.parametrize("grouped", [False, True])
+def test_admission_by_footprint(lib, grouped):
     from paper_2604_23265_gb300 import rte
     meds = _mix(6, seed=2)
     # a budget that holds about one request at a time: all still complete, later ones queue
-    srv = rte.Server(slots=4, max_device_bytes=int(1.5 * (96 << 20)))
+    srv = rte.Server(slots=4, max_device_bytes=int(1.5 * (96 << 20)), grouped=grouped)
     ids = [srv.submit(md) for md in meds]
     res = [srv.wait(i)[0] for i in ids]
     srv.close()
     assert all(r["status"] == "OK" for r in res)
     assert max(r["queue_s"] for r in res) > 0.0
-    tiny = rte.Server(slots=2, max_device_bytes=1 << 20)
+    tiny = rte.Server(slots=2, max_device_bytes=1 << 20, grouped=grouped)
     with pytest.raises(rte.RteError) as e:
         tiny.submit(meds[0])
     assert e.value.status == rte.RTE_ENOMEM
     tiny.close()
 
 
-def test_faults_stay_per_request(lib):
+@pytest.mark.parametrize("grouped", [False, True])
+def test_faults_stay_per_request(lib, grouped):
     from paper_2604_23265_gb300 import rte
     meds = _mix(5, seed=3)
     bad = W.grf_diffusive(7, I=16, M=8)
@@ -71,7 +76,7 @@ def test_faults_stay_per_request(lib):
     nan = W.grf_diffusive(8, I=16, M=8)
     nan.sigma_T = nan.sigma_T.copy()
     nan.sigma_T[5] = np.nan                          # NaN medium
-    srv = rte.Server(slots=3, inject_alloc_failure_id=2)
+    srv = rte.Server(slots=3, inject_alloc_failure_id=2, grouped=grouped)
     ids = [srv.submit(meds[0]), srv.submit(meds[1]), srv.submit(bad), srv.submit(nan),
            srv.submit(meds[2]), srv.submit(meds[3])]
     res = [srv.wait(i) for i in ids]
@@ -84,11 +89,12 @@ def test_faults_stay_per_request(lib):
         np.testing.assert_array_equal(res[k][1], _lone(md)[1])
 
 
-def test_cancellation(lib):
+@pytest.mark.parametrize("grouped", [False, True])
+def test_cancellation(lib, grouped):
     from paper_2604_23265_gb300 import rte
     slow = W.grf_diffusive(9, I=64, M=16, eps=1e-3)  # thousands of iterations
     quick = _mix(2, seed=4)
-    srv = rte.Server(slots=2)
+    srv = rte.Server(slots=2, grouped=grouped)
     i_slow = srv.submit(slow, tol=1e-12, max_iter=200000)
     i_q = [srv.submit(md) for md in quick]
     srv.cancel(i_slow)
