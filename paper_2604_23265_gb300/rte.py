@@ -247,6 +247,9 @@ class Server:
         del self._meta[rid]
         d = {"status": STATUS_NAMES[res.status], "latency_s": res.latency_s, "queue_s": res.queue_s,
              "footprint": res.footprint}
+        if res.status != RTE_OK:
+            msg = load().rte_last_error(None)
+            d["error"] = msg.decode() if msg else ""
         d.update(res.info.as_dict())
         return d, psi
 
