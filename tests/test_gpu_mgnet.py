@@ -52,11 +52,13 @@ def test_forward_matches_oracle(lib, I, M, levels):
 # are not a multiple of 16 (2M = 8), output channels below 16 (c0 = 8), one to
 # three pipeline stages, 128-pixel tiles with a ragged tail (24 x 24, 8 x 8
 # coarse grids), 64-channel levels (72 KB of weights per CTA), and a 128-wide
-# lift / projection (M = 64, 128 TMEM columns), and ReLU smoothers.
+# lift / projection (M = 64, 128 TMEM columns), the largest direction count
+# (M = 80: 160-wide lift input and projection, 256 TMEM columns), and ReLU
+# smoothers.
 @pytest.mark.parametrize("I,M,levels,c0,cmax,act", [(16, 8, 3, 8, 16, "linear"), (24, 4, 2, 8, 16, "linear"),
                                                     (32, 16, 4, 16, 64, "linear"), (8, 8, 1, 8, 16, "linear"),
                                                     (64, 64, 4, 16, 64, "linear"), (40, 20, 2, 24, 48, "linear"),
-                                                    (32, 8, 3, 16, 32, "relu")])
+                                                    (32, 8, 3, 16, 32, "relu"), (16, 80, 2, 16, 32, "linear")])
 def test_tensor_core_forward_matches_oracle(lib, I, M, levels, c0, cmax, act):
     rte, shape, params, md, ctx, net, p = _setup(I=I, M=M, levels=levels, c0=c0, cmax=cmax,
                                                  cc=4, ccmax=8, act=act)

@@ -39,7 +39,7 @@ def _generic(I, M, seed, eps=0.3, g=0.5, inflow=True):
     return W.Medium(I, M, sT, sa, q, np.full(N, eps), g, fl if fl is not None else W.zero_inflow(I, M))
 
 
-CASES = [(9, 4, 0), (13, 8, 1), (37, 16, 2), (20, 32, 3), (11, 64, 4), (1, 8, 5)]
+CASES = [(9, 4, 0), (13, 8, 1), (37, 16, 2), (20, 32, 3), (11, 64, 4), (1, 8, 5), (6, 80, 6)]
 
 
 @pytest.mark.parametrize("I,M,seed", CASES)
