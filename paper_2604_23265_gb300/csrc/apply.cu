@@ -410,16 +410,14 @@ void apply_impl(rte_ctx* ctx, const T* x, void* y, bool y_is_double, const doubl
         if (ctx->nmat == 1 && M % MBS == 0 && smem_shl <= 200 * 1024) {
             const int warps = M / MBS < 8 ? M / MBS : 8;
             auto kern = k_traces_shl<T, MBS>;
-            check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_shl), "traces smem");
+            raise_smem_limit((const void*)kern, (size_t)(smem_shl));
             kern<<<blocks, warps * 32, smem_shl, ctx->stream>>>(op_args(ctx), Lt, x, own, out);
         } else {
             const int MB = (M % 8 == 0) ? 8 : 4;
             const int warps = M / MB < 8 ? M / MB : 8;
             const size_t smem = sizeof(T) * 6 * M * 32;
             auto kern = (MB == 8) ? k_traces<T, 8> : k_traces<T, 4>;
-            check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                  "traces smem");
+            raise_smem_limit((const void*)kern, (size_t)(smem));
             kern<<<blocks, warps * 32, smem, ctx->stream>>>(op_args(ctx), Lt, x, own, out);
         }
         check(cudaGetLastError(), "k_traces");
@@ -443,8 +441,7 @@ void adjoint_impl(rte_ctx* ctx, const T* y, T* x) {
     const size_t smem = sizeof(T) * 4 * M * 32;
     const T* L = std::is_same<T, double>::value ? (const T*)ctx->L64 : (const T*)ctx->L32;
     auto kern = (MB == 8) ? k_adjoint<T, 8> : k_adjoint<T, 4>;
-    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-          "adjoint smem");
+    raise_smem_limit((const void*)kern, (size_t)(smem));
     ProfScope ps(ctx, K_ADJOINT, 2.0 * ctx->n * sizeof(T));
     kern<<<blocks, warps * 32, smem, ctx->stream>>>(op_args(ctx), L, y, x);
     check(cudaGetLastError(), "k_adjoint");
@@ -474,8 +471,7 @@ void launch_reconstruct(rte_ctx* ctx, const double* x, double* psi) {
     const int blocks = (ctx->N + kCellsPerBlock - 1) / kCellsPerBlock;
     const size_t smem = sizeof(double) * 2 * M * 32;
     auto kern = (MB == 8) ? k_reconstruct<8> : k_reconstruct<4>;
-    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-          "reconstruct smem");
+    raise_smem_limit((const void*)kern, (size_t)(smem));
     ProfScope ps(ctx, K_RECONSTRUCT, (double)ctx->n * 8 + (double)ctx->M * ctx->N * 8);
     kern<<<blocks, warps * 32, smem, ctx->stream>>>(op_args(ctx), ctx->Lt64, ctx->chis, x, psi);
     check(cudaGetLastError(), "k_reconstruct");

@@ -378,7 +378,7 @@ void atfps_setup(rte_ctx* ctx, double delta) {
     check(cudaMemcpyAsync(d_dirs, dirs.data(), dirs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
           "h2d");
     const size_t smem = (size_t)(2 * M * M + M) * sizeof(double);
-    check(cudaFuncSetAttribute(k_atfps_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
+    raise_smem_limit((const void*)k_atfps_build, (size_t)(smem));
     // a pivot below 1e-12 of the (unit max-norm) columns: cond(E) beyond ~1e12
     k_atfps_build<<<a->nif, kBuildThreads, smem, ctx->stream>>>(a->desc, a->off, d_ord, d_dirs, ctx->L64, ctx->mat,
                                                                 a->mask, M, N, 1e-12, a->proj, a->singular);

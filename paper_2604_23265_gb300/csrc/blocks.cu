@@ -357,8 +357,7 @@ __global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const doubl
 void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
     const int M = ctx->M, n2 = 2 * M;
     const size_t smem = sizeof(double) * ((size_t)n2 * (n2 + 1) + 3 * n2);
-    check(cudaFuncSetAttribute(k_build_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem), "build_invert smem");
+    raise_smem_limit((const void*)k_build_invert, (size_t)(smem));
     const int threads = n2 >= 64 ? 256 : 128;
     {
         ProfScope ps(ctx, K_INVERT, (double)ctx->N * n2 * n2 * 8);
@@ -368,8 +367,7 @@ void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
         check(cudaGetLastError(), "k_build_invert");
     }
     const size_t smem2 = sizeof(double) * ((size_t)n2 * (n2 + 1) + n2);
-    check(cudaFuncSetAttribute(k_response, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
-          "response smem");
+    raise_smem_limit((const void*)k_response, (size_t)(smem2));
     ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * n2 * n2 * 12);
     k_response<<<ctx->N, threads, smem2, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi, ctx->L64,
                                                         ctx->rowdir, ctx->Dt, ctx->Rt);
@@ -385,7 +383,7 @@ void block_apply_t(rte_ctx* ctx, const TD* X, const void* r, void* z, int kid, d
     const int blocks = (ctx->N + cells - 1) / cells;
     const size_t smem = sizeof(TD) * 2 * n2 * cells;
     auto kern = k_block_apply<TD, TIN, TOUT>;
-    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "ba");
+    raise_smem_limit((const void*)kern, (size_t)(smem));
     ProfScope ps(ctx, kid, bytes);
     kern<<<blocks, threads, smem, ctx->stream>>>(M, ctx->N, X, (const TIN*)r, (TOUT*)z);
     check(cudaGetLastError(), "k_block_apply");
@@ -414,13 +412,11 @@ void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_d
     const size_t smem = sizeof(double) * 2 * n2 * cells;
     ProfScope ps(ctx, K_BLOCK_T, bytes);
     if (r_is_double && z_is_double) {
-        check(cudaFuncSetAttribute(k_block_apply_t<double, double>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "bat");
+        raise_smem_limit((const void*)k_block_apply_t<double, double>, smem);
         k_block_apply_t<double, double><<<blocks, threads, smem, ctx->stream>>>(
             M, ctx->N, ctx->Dt, (const double*)r, (double*)z);
     } else if (!r_is_double && !z_is_double) {
-        check(cudaFuncSetAttribute(k_block_apply_t<float, float>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "bat");
+        raise_smem_limit((const void*)k_block_apply_t<float, float>, smem);
         k_block_apply_t<float, float><<<blocks, threads, smem, ctx->stream>>>(
             M, ctx->N, ctx->Dt, (const float*)r, (float*)z);
     } else {
@@ -442,8 +438,7 @@ void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scra
     const int cells = threads / G;
     const int blocks = (ctx->N + cells - 1) / cells;
     const size_t smem = sizeof(float) * 2 * n2 * cells;
-    check(cudaFuncSetAttribute(k_response_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-          "response_t smem");
+    raise_smem_limit((const void*)k_response_t, (size_t)(smem));
     ProfScope ps(ctx, K_RESPONSE_APPLY, (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * 12);
     k_response_t<<<blocks, threads, smem, ctx->stream>>>(M, ctx->N, ctx->Rt, u, scratch, w);
     check(cudaGetLastError(), "k_response_t");
@@ -500,8 +495,7 @@ void group_response_geometry(rte_ctx* ctx, int* n_ba, int* n_ga, size_t* smem_ba
 
 void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba, int blocks_ga, size_t smem_ba,
                            cudaStream_t st) {
-    check(cudaFuncSetAttribute(k_block_apply_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ba),
-          "grouped block apply smem");
+    raise_smem_limit((const void*)k_block_apply_group, (size_t)(smem_ba));
     k_block_apply_group<<<blocks_ba, 256, smem_ba, st>>>(items_dev, count);
     k_gather_group<<<blocks_ga, 256, 0, st>>>(items_dev, count);
     check(cudaGetLastError(), "grouped response apply");

@@ -331,8 +331,7 @@ __global__ void k_combine_update(double* __restrict__ x, const float* __restrict
 // resident blocks per SM as the shared memory allows (at most 4).
 int dot_blocks(rte_ctx* ctx, int64_t n, int K, const void* kern) {
     const size_t smem = (size_t)K * kT * sizeof(double);
-    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kMaxKrylov * kT * sizeof(double))), "dot smem");
+    raise_smem_limit((const void*)kern, (size_t)((kMaxKrylov * kT * sizeof(double))));
     int per_sm = 0;
     check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem), "occupancy");
     per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
@@ -397,8 +396,8 @@ void launch_group_orthogonalise(const GroupItem* items_dev, int count, int block
     static std::once_flag once;
     std::call_once(once, [] {
         const int smax = (int)(kMaxKrylov * kT * sizeof(double));
-        check(cudaFuncSetAttribute(k_mdot_group, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "smem");
-        check(cudaFuncSetAttribute(k_update_dot_group, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "smem");
+        raise_smem_limit((const void*)k_mdot_group, (size_t)(smax));
+        raise_smem_limit((const void*)k_update_dot_group, (size_t)(smax));
     });
     const size_t smem = (size_t)kmax * kT * sizeof(double);
     k_mdot_group<<<blocks_md, kT, smem, st>>>(items_dev, count);

@@ -107,6 +107,11 @@ inline void check(cudaError_t e, const char* where) {
     if (e != cudaSuccess) throw CudaError{e, where};
 }
 
+// Raises a kernel's dynamic shared memory limit to at least `bytes`, never
+// lowering it: concurrent callers (server threads, contexts of different M)
+// cannot shrink the limit under another thread's pending launch.
+void raise_smem_limit(const void* kern, size_t bytes);
+
 // profiling (setup.cu): wrap every launch of the library.
 // Counts the launch and its algorithmic bytes; with profiling on, brackets the
 // launch with events on the context's stream (resolved at sync points).

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 
 #include "rte_internal.h"
@@ -41,6 +42,17 @@ void* dev_alloc(rte_ctx* ctx, size_t bytes) {
     ctx->device_bytes += bytes;
     check(cudaMemsetAsync(p, 0, bytes, ctx->stream), "cudaMemset");
     return p;
+}
+
+void raise_smem_limit(const void* kern, size_t bytes) {
+    static std::mutex mu;
+    static std::map<const void*, size_t> limit;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[kern];
+    if (bytes <= cur) return;
+    check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+          "cudaFuncSetAttribute (dynamic shared memory)");
+    cur = bytes;
 }
 
 const char* const kKernelNames[K_COUNT] = {
