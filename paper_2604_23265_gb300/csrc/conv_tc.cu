@@ -321,11 +321,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
             bb[i] = 0.f;
         }
         if (!elive) return;
-        if (a.gate) {
+        if (a.gate || (a.batched && a.gate_b[0])) {
+            const float* gsrc = a.batched ? a.gate_b[eb] : a.gate;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int co = c16 * 16 + i;
-                if (co < a.Co) gt[i] = __ldg(a.gate + (size_t)co * oplane + opix);
+                if (co < a.Co) gt[i] = __ldg(gsrc + (size_t)co * oplane + opix);
             }
         }
         if (a.base8) {
@@ -340,11 +341,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                     for (int i = 0; i < 8; ++i) bb[h * 8 + i] = t8[i];
                 }
             }
-        } else if (a.base64) {
+        } else if (a.base64 || (a.batched && a.base64_b[0])) {
+            const double* bsrc = a.batched ? a.base64_b[eb] : a.base64 + (size_t)eb * a.Co * oplane;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int co = c16 * 16 + i;
-                if (co < a.Co) bb[i] = (float)__ldg(a.base64 + ((size_t)eb * a.Co + co) * oplane + opix);
+                if (co < a.Co) bb[i] = (float)__ldg(bsrc + (size_t)co * oplane + opix);
             }
         }
     };
@@ -400,7 +402,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
             const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
             const size_t plane = (size_t)a.Hi * a.Wi;
             if (MODE == kF64) {
-                const double* xp = a.x64 + (size_t)b * a.Ci * plane + (in ? (size_t)iy * a.Wi + ix : 0);
+                const double* xp = (a.batched ? a.x64_b[b] : a.x64 + (size_t)b * a.Ci * plane) +
+                                   (in ? (size_t)iy * a.Wi + ix : 0);
 #pragma unroll 4
                 for (int kc = half; kc < KC; kc += 2) {
                     float v[8];
@@ -519,10 +522,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
                 if (a.y8) {
                     reinterpret_cast<uint4*>(a.y8)[((size_t)eb * KCo + kc) * oplane + opix] = pack8(v);
                 } else {
+                    float* ysrc = a.batched ? a.y32_b[eb] : a.y32 + (size_t)eb * a.Co * oplane;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int co = kc * 8 + i;
-                        if (co < a.Co) a.y32[((size_t)eb * a.Co + co) * oplane + opix] = v[i];
+                        if (co < a.Co) ysrc[(size_t)co * oplane + opix] = v[i];
                     }
                 }
             }
@@ -667,7 +671,8 @@ void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int
 void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
     TcConv a = in;
     if (a.T < 1 || a.classes < 1 || a.classes > 4 || a.T * a.classes > kMaxTaps || a.S < 1 || a.S > 2 ||
-        a.Ci < 1 || a.Co < 1 || !a.w || (!a.x8) == (!a.x64) || (!a.y8) == (!a.y32))
+        a.Ci < 1 || a.Co < 1 || !a.w || (!a.x8) == (!(a.x64 || (a.batched && a.x64_b[0]))) ||
+        (!a.y8) == (!(a.y32 || (a.batched && a.y32_b[0]))) || (a.batched && a.B > kTcMaxBatch))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: bad arguments"};
     if (pad_n(a.Co) > 256) throw StatusError{RTE_EINVAL, "tensor-core convolution: more than 256 output channels"};
     if (reinterpret_cast<uintptr_t>(a.w) % 16 || (a.x8 && reinterpret_cast<uintptr_t>(a.x8) % 16) ||
@@ -683,7 +688,7 @@ void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
     g.KC = chunks_kc(a.Ci);
     g.Npad = pad_n(a.Co);
     const int T = a.T;
-    if (a.x64) {
+    if (a.x64 || (a.batched && a.x64_b[0])) {
         g.NS = T;
         launch<kF64>(a, g, (size_t)T * g.KC * 2048, pdl, (unsigned)((total + kRows - 1) / kRows), st);
         return;

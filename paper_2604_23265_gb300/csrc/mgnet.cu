@@ -361,11 +361,11 @@ struct TcActs {
 
 size_t c8_bytes(int C, int H) { return (((size_t)(C + 7) / 8) * H * H * 16 + 255) & ~(size_t)255; }
 
-TcActs tc_workspace(mgnet* n, int I) {
+TcActs tc_workspace(mgnet* n, int I, int B) {
     const int L = n->L;
     size_t need = 0;
-    for (int l = 0; l < L; ++l) need += 6 * c8_bytes(n->C(l), I >> l);
-    need += 3 * c8_bytes(n->C(L - 1), I >> (L - 1));
+    for (int l = 0; l < L; ++l) need += 6 * B * c8_bytes(n->C(l), I >> l);
+    need += 3 * B * c8_bytes(n->C(L - 1), I >> (L - 1));
     if (!n->tc_ws || n->tc_ws_bytes < need) {
         if (n->tc_ws) cudaFree(n->tc_ws);
         n->tc_ws = nullptr;
@@ -373,7 +373,7 @@ TcActs tc_workspace(mgnet* n, int I) {
         n->tc_ws_bytes = need;
     }
     char* p = static_cast<char*>(n->tc_ws);
-    auto take = [&](int C, int H) { void* r = p; p += c8_bytes(C, H); return r; };
+    auto take = [&](int C, int H) { void* r = p; p += B * c8_bytes(C, H); return r; };
     TcActs A;
     for (int l = 0; l < L; ++l) {
         const int C = n->C(l), H = I >> l;
@@ -393,12 +393,26 @@ TcActs tc_workspace(mgnet* n, int I) {
 
 enum class TcMode { Plan, Pack, Run };
 
+// The samples of one tensor-core forward: B solves of one grid size, each
+// with its input r, output z and medium (features F).
+struct TcSamples {
+    int B = 1;
+    const Features* F[nn::kTcMaxBatch] = {};
+    const double* r[nn::kTcMaxBatch] = {};
+    float* z[nn::kTcMaxBatch] = {};
+};
+
 // Plan: returns the packed-weight bytes; Pack: packs then runs; Run: runs.
-size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z, TcMode mode) {
-    const int L = n->L, M2 = 2 * n->M;
+// Every sample's output is the same bits as a forward of it alone.
+size_t tc_forward(mgnet* n, const TcSamples& S, int I, TcMode mode) {
+    const int L = n->L, M2 = 2 * n->M, B = S.B;
     const Taps t3 = nn::taps_conv(3, 1), t1 = nn::taps_conv(1, 0);
     TcActs A;
-    if (mode != TcMode::Plan) A = tc_workspace(n, I);
+    if (mode != TcMode::Plan) A = tc_workspace(n, I, B);
+    auto gates = [&](nn::TcConv& c, int l, bool inverse) {
+        for (int b = 0; b < B; ++b)
+            c.gate_b[b] = S.F[b] ? (inverse ? S.F[b]->ai[l] : S.F[b]->a[l]) : nullptr;
+    };
     size_t cursor = 0;
     auto run = [&](nn::TcConv c, const char* wname, int so, int si, int KK, const Taps& tp) {
         const size_t bytes = nn::tc_weight_bytes(tp.T, c.Ci, c.Co);
@@ -414,29 +428,30 @@ size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z,
         }
         nn::tc_conv(c, mode == TcMode::Run, n->stream);
     };
-    auto conv = [&](const void* x8, int Ci, int Hi, int Co, int Hg, int S, void* y8, int Ho) {
+    auto conv = [&](const void* x8, int Ci, int Hi, int Co, int Hg, int stride, void* y8, int Ho) {
         nn::TcConv c;
-        c.x8 = x8; c.B = 1; c.Ci = Ci; c.Hi = Hi; c.Wi = Hi;
-        c.Co = Co; c.Hg = Hg; c.Wg = Hg; c.S = S;
+        c.x8 = x8; c.B = B; c.Ci = Ci; c.Hi = Hi; c.Wi = Hi;
+        c.Co = Co; c.Hg = Hg; c.Wg = Hg; c.S = stride;
         c.y8 = y8; c.Ho = Ho; c.Wo = Ho;
+        c.batched = 1;
         return c;
     };
-    {   // lift: FP64 Krylov vector -> f_0
+    {   // lift: FP64 Krylov vectors -> f_0
         nn::TcConv c = conv(nullptr, M2, I, n->C(0), I, 1, A.f.empty() ? nullptr : A.f[0], I);
-        c.x64 = r;
+        for (int b = 0; b < B; ++b) c.x64_b[b] = S.r[b];
         run(c, "lift.w", M2, 1, 1, t1);
     }
     auto smooth_first = [&](int l, void* u) {            // u = (B * act(f)) o ainv
         const int H = I >> l, C = n->C(l);
         nn::TcConv c = conv(A.f.empty() ? nullptr : A.f[l], C, H, C, H, 1, u, H);
         c.relu_in = n->act;
-        c.gate = F ? F->ai[l] : nullptr;
+        gates(c, l, true);
         run(c, sl("B", l).c_str(), C, 1, 9, t3);
     };
     auto residual = [&](int l, const void* u, void* out) {   // f - (A * u) o a
         const int H = I >> l, C = n->C(l);
         nn::TcConv c = conv(u, C, H, C, H, 1, out, H);
-        c.gate = F ? F->a[l] : nullptr;
+        gates(c, l, false);
         c.sign = -1.f;
         c.base8 = A.f.empty() ? nullptr : A.f[l];
         run(c, sl("A", l).c_str(), C, 1, 9, t3);
@@ -445,7 +460,7 @@ size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z,
         const int H = I >> l, C = n->C(l);
         nn::TcConv c = conv(t, C, H, C, H, 1, out, H);
         c.relu_in = n->act;
-        c.gate = F ? F->ai[l] : nullptr;
+        gates(c, l, true);
         c.base8 = u;
         run(c, sl("B", l).c_str(), C, 1, 9, t3);
     };
@@ -489,26 +504,28 @@ size_t tc_forward(mgnet* n, const Features* F, int I, const double* r, float* z,
     }
     {   // z = r + proj(u_0), FP32 [2M][I][I]
         nn::TcConv c = conv(uup, n->C(0), I, M2, I, 1, nullptr, I);
-        c.y32 = z;
-        c.base64 = r;
+        for (int b = 0; b < B; ++b) {
+            c.y32_b[b] = S.z[b];
+            c.base64_b[b] = S.r[b];
+        }
         run(c, "proj.w", n->C(0), 1, 1, t1);
     }
     return cursor;
 }
 
-void tc_precondition(mgnet* n, const Features& F, rte_ctx* ctx, const double* v, float* z) {
+void tc_precondition(mgnet* n, const TcSamples& S, int I) {
     if (n->tcw_version != n->version) {
-        const size_t need = tc_forward(n, nullptr, ctx->I, nullptr, nullptr, TcMode::Plan);
+        const size_t need = tc_forward(n, TcSamples{}, I, TcMode::Plan);
         if (!n->tcw || n->tcw_bytes < need) {
             if (n->tcw) cudaFree(n->tcw);
             n->tcw = nullptr;
             check(cudaMalloc(&n->tcw, need), "cudaMalloc (packed weights)");
             n->tcw_bytes = need;
         }
-        tc_forward(n, &F, ctx->I, v, z, TcMode::Pack);
+        tc_forward(n, S, I, TcMode::Pack);
         n->tcw_version = n->version;
     } else {
-        tc_forward(n, &F, ctx->I, v, z, TcMode::Run);
+        tc_forward(n, S, I, TcMode::Run);
     }
 }
 
@@ -860,7 +877,11 @@ void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
     nn::tl_counters = &cnt;
     if (net->prec == MGNET_BF16) {
         ProfScope ps(ctx, K_MGNET, (double)ctx->n * 12, 0);
-        tc_precondition(net, F, ctx, v, z);
+        TcSamples S;
+        S.F[0] = &F;
+        S.r[0] = v;
+        S.z[0] = z;
+        tc_precondition(net, S, ctx->I);
     } else {
         ProfScope ps(ctx, K_MGNET, (double)ctx->n * 12, 0);
         Acts a = workspace(net, 2, ctx->I);
@@ -873,6 +894,29 @@ void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
     }
     ctx->prof.launches[K_MGNET] += cnt.launches;
     ctx->prof.flops[K_MGNET] += cnt.flops;
+}
+
+void mgnet_precondition_batch(mgnet* net, rte_ctx* const* ctxs, const double* const* v, float* const* z, int B) {
+    if (B == 1 || net->prec != MGNET_BF16) {
+        for (int b = 0; b < B; ++b) mgnet_precondition(net, ctxs[b], v[b], z[b]);
+        return;
+    }
+    const int I = ctxs[0]->I;
+    for (int b = 0; b < B; ++b) {
+        check_ctx(net, ctxs[b]);
+        if (ctxs[b]->I != I) throw StatusError{RTE_EINVAL, "batched preconditioning needs one grid size"};
+    }
+    for (int b0 = 0; b0 < B; b0 += nn::kTcMaxBatch) {
+        TcSamples S;
+        S.B = B - b0 < nn::kTcMaxBatch ? B - b0 : nn::kTcMaxBatch;
+        for (int b = 0; b < S.B; ++b) {
+            S.F[b] = &features(net, ctxs[b0 + b], false);
+            S.r[b] = v[b0 + b];
+            S.z[b] = z[b0 + b];
+        }
+        ProfScope ps(ctxs[b0], K_MGNET, (double)ctxs[b0]->n * 12 * S.B, 0);
+        tc_precondition(net, S, I);
+    }
 }
 
 }  // namespace rte

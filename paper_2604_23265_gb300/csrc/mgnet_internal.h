@@ -12,4 +12,9 @@ void mgnet_prepare(mgnet* net, rte_ctx* ctx);
 // z = D Net(v): the learned preconditioner applied to one Krylov vector.
 void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z);
 
+// The same for B vectors of B contexts of one grid size (a lockstep group):
+// the tensor-core layers run once for all of them (batches of up to 16), each
+// sample with its own medium; every z_b is the same bits as alone.
+void mgnet_precondition_batch(mgnet* net, rte_ctx* const* ctxs, const double* const* v, float* const* z, int B);
+
 }  // namespace rte

@@ -9,6 +9,7 @@ namespace rte {
 namespace nn {
 
 constexpr int kMaxTaps = 16;
+constexpr int kTcMaxBatch = 16;     // samples of one batched tensor-core launch
 
 // Taps of a gather convolution: input pixel (S gy + dy[t], S gx + dx[t]),
 // weight offset wi[t] inside the kernel window.
@@ -100,6 +101,14 @@ struct TcConv {
     const double* base64 = nullptr;  // FP64 [B][Co][Ho][Wo]
     void* y8 = nullptr;              // BF16 C8 output, or
     float* y32 = nullptr;            // FP32 [B][Co][Ho][Wo] output
+    // per-sample pointers (batched != 0; B <= kTcMaxBatch), used instead of
+    // the batch-strided pointers above: a batch of samples from different
+    // solves, each with its own input, output and medium
+    int batched = 0;
+    const double* x64_b[kTcMaxBatch] = {};    // [Ci][Hi][Wi] each
+    const float* gate_b[kTcMaxBatch] = {};    // [Co][Ho][Wo] each
+    const double* base64_b[kTcMaxBatch] = {}; // [Co][Ho][Wo] each
+    float* y32_b[kTcMaxBatch] = {};           // [Co][Ho][Wo] each
 };
 size_t tc_weight_bytes(int T, int Ci, int Co);
 // packs W[t][i][o] = w[(o so + i si) KK + wi_t] into dst (tc_weight_bytes)

@@ -400,7 +400,38 @@ struct GroupRunner {
             if (s->phase == kStep) live.push_back(s);
         if (live.empty()) return;
         if ((int)live.size() > cap) throw StatusError{RTE_EINVAL, "group larger than its capacity"};
-        for (Solver* s : live) s->precondition();
+        // preconditioners: solves sharing a network and a grid size run its
+        // layers once for all of them
+        std::vector<bool> taken(live.size(), false);
+        for (size_t q = 0; q < live.size(); ++q) {
+            if (taken[q]) continue;
+            Solver& s = *live[q];
+            if (!s.cycle_net) {
+                s.precondition();
+                continue;
+            }
+            std::vector<Solver*> same;
+            for (size_t r = q; r < live.size(); ++r)
+                if (!taken[r] && live[r]->cycle_net && live[r]->pc == s.pc && live[r]->ctx->I == s.ctx->I) {
+                    same.push_back(live[r]);
+                    taken[r] = true;
+                }
+            if (same.size() == 1) {
+                s.precondition();
+                continue;
+            }
+            std::vector<rte_ctx*> cs;
+            std::vector<const double*> vs;
+            std::vector<float*> zs;
+            for (Solver* t : same) {
+                cs.push_back(t->ctx);
+                vs.push_back(t->ws->V + (size_t)t->j * t->n);
+                zs.push_back(t->ws->Z + (size_t)t->j * t->n);
+                t->zj = zs.back();
+                t->z_double = false;
+            }
+            mgnet_precondition_batch(s.pc, cs.data(), vs.data(), zs.data(), (int)same.size());
+        }
         int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, kmax = 1;
         size_t smem_ba = 0;
         bool f32 = true;

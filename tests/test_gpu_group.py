@@ -53,8 +53,9 @@ def test_group_is_bit_identical_to_lone_solves(lib, count, inner):
 
 
 def test_group_with_networks_and_early_endings(lib):
-    """Two solves with a network (same M), one with max_iter reached, one with a
-    zero right-hand side, the rest block Jacobi: each equals its lone solve."""
+    """Three solves with one network and grid size (their V-cycles run as one
+    batch of tensor-core layers), one with max_iter reached, one with a zero
+    right-hand side, the rest block Jacobi: each equals its lone solve."""
     from paper_2604_23265_gb300 import rte
     media = _mixed(5, seed=7, grids=(16,), dirs=(8,))
     zero = W.mixed_instance(999, grids=(8,), dirs=(8,))
@@ -64,7 +65,7 @@ def test_group_with_networks_and_early_endings(lib):
     shape = W.NetShape(M=8, levels=2, c0=8, cmax=16, cc=4, ccmax=8)
     net = rte.MgNet(shape)
     net.set_params(W.init_params(shape, seed=1, proj_scale=0.02, vcycle_scale=0.5))
-    pcs = [net, net, None, None, None, None]
+    pcs = [net, net, net, None, None, None]
     kws = dict(tol=1e-9, restart=15, max_iter=60)
     lone = [_lone(rte, md, pc=pc, **kws) for md, pc in zip(media, pcs)]
     ctxs = [rte.Context.from_medium(md) for md in media]
