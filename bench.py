@@ -117,14 +117,34 @@ def _barrier(world):
         dist.barrier()
 
 
-def _max_over_ranks(world, value):
+def _reduce(world, value, op):
+    """value reduced over the ranks (NCCL tensors on the GPU, gloo on the host)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    return _reduce(world, value, dist.ReduceOp.MAX)
+
+
+def _weak_value(world, steps, ms_local, converged_local):
+    """Whole-job solves/s of a replicated run: the solves of all ranks over the
+    slowest rank's time, zero unless every rank converged; and that time."""
+    ms_max = _max_over_ranks(world, ms_local)
+    ok = converged_local
+    if world > 1:
+        import torch.distributed as dist
+        ok = _reduce(world, 1.0 if converged_local else 0.0, dist.ReduceOp.MIN) > 0.5
+    return ((steps * world) / (ms_max / 1e3) if ok else 0.0), ms_max
 
 
 def cpu_baseline(md, gpu_iters):
@@ -266,9 +286,8 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
-    ms_max = _max_over_ranks(world, ms)
     converged = all(i["converged"] for i in infos)
-    value = (args.steps * world if converged else 0) / (ms_max / 1e3)
+    value, ms_max = _weak_value(world, args.steps, ms, converged)
     iters = infos[-1]["iterations"]
     roof, kernels = _roofline(rte, stream, prof)
     launches = sum(v[0] for v in prof.values())
