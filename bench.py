@@ -486,6 +486,49 @@ def batched_leg(count, seed=23):
             "converged": all(i["converged"] for i in grp), "bit_identical_to_lone": bool(same)}
 
 
+def run_paper_protocol(args):
+    """The paper's own setting (Sec. 4.1-4.2): 32 x 32 cells, M = 4 directions,
+    polynomial media with eps = 0.01 (c + 0.1).  A network is trained on
+    args.pp_train media with the plain loss and another with the ATFPS-filtered
+    loss (delta = 1e-2); both precondition FGMRES(50) to 1e-8 on 10 unseen
+    media, beside block Jacobi.  Prints one JSON line of iteration counts."""
+    import torch
+    from paper_2604_23265_gb300 import rte, train
+    torch.cuda.set_device(0)
+    train_media = [W.polynomial_diffusion(s) for s in range(args.pp_train)]
+    test_media = [W.polynomial_diffusion(10000 + s) for s in range(10)]
+    out = {"mode": "paper_protocol",
+           "workload": ("32x32 cells, M=4, polynomial sigma_T, sigma_a (degree 1-4), eps=0.01(c+0.1), q=1, "
+                        "zero inflow; FGMRES(50) to rel-res 1e-8"),
+           "train_media": args.pp_train, "train_steps": args.pp_steps}
+
+    def solve_all(net):
+        its, fell = [], []
+        for md in test_media:
+            ctx = rte.Context.from_medium(md)
+            x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+            info = ctx.solve(x, pc=net, tol=1e-8, restart=50)
+            its.append(info["iterations"] if info["converged"] else None)
+            fell.append(bool(info["fell_back"]))
+            ctx.close()
+        return its, fell
+
+    bj, _ = solve_all(None)
+    out["block_jacobi_iterations"] = bj
+    for loss in ("plain", "filtered"):
+        net, ctxs, losses, secs = train.train_for(train_media, steps=args.pp_steps, batch=8, lr0=3e-3, seed=0,
+                                                  n_krylov=16, n_smooth=16, loss=loss, delta=1e-2)
+        for c in ctxs:
+            c.close()
+        its, fell = solve_all(net)
+        ratio = [b / i for b, i in zip(bj, its) if b and i]
+        out[loss] = {"iterations": its, "fell_back": fell, "train_seconds": secs,
+                     "final_loss": float(np.mean(losses[-20:])),
+                     "mean_bj_over_mgnet": float(np.mean(ratio)) if ratio else None}
+        net.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores as the reference arm (bounded samples)."""
     world, rank, _ = _dist()
@@ -528,6 +571,10 @@ def main():
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--train-seed", type=int, default=0, help="seed of the weights and input draws")
+    ap.add_argument("--paper-protocol", action="store_true",
+                    help="the paper's 32x32x4 polynomial-media experiment (plain vs filtered loss vs block Jacobi)")
+    ap.add_argument("--pp-train", type=int, default=64, help="training media of --paper-protocol")
+    ap.add_argument("--pp-steps", type=int, default=2000, help="training steps of --paper-protocol")
     ap.add_argument("--c0", type=int, default=16, help="network width at the finest level")
     ap.add_argument("--cmax", type=int, default=64, help="largest network width")
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
@@ -544,6 +591,8 @@ def main():
         run_reference(args)
     elif args.precond_only > 0:
         run_precond_only(args)
+    elif args.paper_protocol:
+        run_paper_protocol(args)
     else:
         run_ours(args)
 
