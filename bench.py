@@ -573,8 +573,8 @@ def main():
     ap.add_argument("--train-seed", type=int, default=0, help="seed of the weights and input draws")
     ap.add_argument("--paper-protocol", action="store_true",
                     help="the paper's 32x32x4 polynomial-media experiment (plain vs filtered loss vs block Jacobi)")
-    ap.add_argument("--pp-train", type=int, default=64, help="training media of --paper-protocol")
-    ap.add_argument("--pp-steps", type=int, default=2000, help="training steps of --paper-protocol")
+    ap.add_argument("--pp-train", type=int, default=256, help="training media of --paper-protocol")
+    ap.add_argument("--pp-steps", type=int, default=6000, help="training steps of --paper-protocol")
     ap.add_argument("--c0", type=int, default=16, help="network width at the finest level")
     ap.add_argument("--cmax", type=int, default=64, help="largest network width")
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
