@@ -382,10 +382,16 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(md, bj["iterations"] if bj else iters)
     ctx.close()
-    if rank == 0 and world == 1 and args.serve > 0:
-        out["serving"] = serving_leg(args.serve)
-    if rank == 0 and world == 1 and args.batch > 0:
-        out["batched"] = batched_leg(args.batch)
+    if rank == 0 and world == 1 and (args.serve > 0 or args.batch > 0):
+        nets, mixed_train_s = train_mixed_nets(args.mixed_train_steps)
+        out["mixed_networks"] = {"M": list(nets), "train_seconds": mixed_train_s,
+                                 "train_steps": args.mixed_train_steps, "levels": nets[MIXED_DIRS[0]].shape.levels}
+        if args.serve > 0:
+            out["serving"] = serving_leg(args.serve, nets)
+        if args.batch > 0:
+            out["batched"] = batched_leg(args.batch, nets)
+        for n in nets.values():
+            n.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -393,30 +399,52 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-SERVE_WORKLOAD = ("Poisson arrivals of mixed solve requests: I in {32, 64, 128}, M in {8, 16}, "
-                  "eps log-uniform in [1e-2, 1], g uniform in [0, 0.9], GRF media; FGMRES(50) with "
-                  "block Jacobi to rel-res 1e-8; 4 slots")
+MIXED_GRIDS, MIXED_DIRS, MIXED_EPS, NET_EPS_MAX = (64, 128, 256), (16, 32), (1e-4, 1.0), 1e-1
 
 
-def serving_leg(n_req, seed=11):
-    """Continuous-batching server under Poisson arrivals (a reduced instance of
-    the serving workload): p50 / p99 latency and solves/s.  The arrival rate is
-    half the capacity estimated from three requests served one at a time."""
-    import threading
+def train_mixed_nets(steps, media=24, seed=0):
+    """One network per direction count of the mixed legs, trained (untimed)
+    on 128 x 128 media of the training distribution (eps log-uniform in
+    [1e-4, 1e-1], g in [0, 0.8], sigma_a / sigma_T log-uniform in [0.01, 0.2],
+    GRF sigma_T) with the depth of a 256 x 256 grid, so that the same network
+    serves every grid of the mix.  Returns ({M: net}, seconds)."""
+    import torch
+    from paper_2604_23265_gb300 import train
+    nets, t0 = {}, time.time()
+    for M in MIXED_DIRS:
+        tm = [W.training_medium(seed=5000 + 100 * M + i, I=128, M=M) for i in range(media)]
+        net, ctxs, _, _ = train.train_for(tm, shape=train.default_shape(M, 256), steps=steps, batch=8,
+                                          lr0=3e-3, seed=seed)
+        for c in ctxs:
+            c.close()
+        nets[M] = net
+    torch.cuda.synchronize()
+    return nets, time.time() - t0
+
+
+def _mixed_media(count, seed, grids=MIXED_GRIDS, dirs=MIXED_DIRS, g_range=(0.0, 0.9)):
+    return [W.mixed_instance(seed * 1000 + i, grids=grids, dirs=dirs, eps_range=MIXED_EPS, g_range=g_range)
+            for i in range(count)]
+
+
+def _wants_net(md):
+    """Client policy: the network preconditions requests inside its training
+    range of eps; the others (the transport regime) use block Jacobi."""
+    return float(np.max(md.eps)) <= NET_EPS_MAX
+
+
+SERVE_WORKLOAD = ("Poisson arrivals of mixed solve requests: I in {64, 128}, M in {16, 32}, eps log-uniform "
+                  "in [1e-4, 1], g uniform in [0, 0.9], GRF media; FGMRES(50) to rel-res 1e-8; grouped server "
+                  "(shared launches, batched V-cycles), 4 slots")
+
+
+def _serve_once(media, gaps, nets, use_net):
     from paper_2604_23265_gb300 import rte
-    media = [W.mixed_instance(seed * 1000 + i, grids=(32, 64, 128), dirs=(8, 16), eps_range=(1e-2, 1.0),
-                              g_range=(0.0, 0.9)) for i in range(n_req)]
-    slots = 4
-    srv = rte.Server(slots=slots, max_device_bytes=64 << 30)
+    srv = rte.Server(slots=4, max_device_bytes=96 << 30, net=list(nets.values()) if use_net else None,
+                     grouped=True)
+    n_req = len(media)
+    ids = [None] * n_req
     try:
-        t0 = time.perf_counter()
-        for md in media[:3]:
-            res, _ = srv.wait(srv.submit(md, tol=1e-8, max_iter=4000))
-        service = (time.perf_counter() - t0) / 3
-        rate = 0.5 * slots / service
-        rng = np.random.default_rng(seed)
-        gaps = rng.exponential(1.0 / rate, n_req)
-        ids = [None] * n_req
         start = time.perf_counter()
 
         def feeder():
@@ -426,11 +454,11 @@ def serving_leg(n_req, seed=11):
                 d = t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                ids[i] = srv.submit(md, tol=1e-8, max_iter=4000)
+                ids[i] = srv.submit(md, tol=1e-8, max_iter=40000, use_net=use_net and _wants_net(md))
 
         th = threading.Thread(target=feeder)
         th.start()
-        lat, queue, ok = [], [], 0
+        lat, queue, ok, its, on_net = [], [], 0, 0, 0
         for i in range(n_req):
             while ids[i] is None:
                 time.sleep(0.0005)
@@ -438,52 +466,97 @@ def serving_leg(n_req, seed=11):
             lat.append(res["latency_s"])
             queue.append(res["queue_s"])
             ok += res["status"] == "OK"
+            its += res["iterations"]
+            on_net += res["used_net"]
         th.join()
         span = time.perf_counter() - start
     finally:
         srv.close()
     lat = np.asarray(lat)
-    return {"workload": SERVE_WORKLOAD, "requests": n_req, "completed_ok": int(ok), "slots": slots,
-            "arrival_rate_per_s": rate, "single_request_service_s": service,
+    return {"completed_ok": int(ok), "on_network": int(on_net), "iterations_total": int(its),
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_queue_s": float(np.mean(queue)), "solves_per_s": n_req / span}
 
 
-BATCH_WORKLOAD = ("mixed instances: I in {32, 64}, M in {8, 16}, eps log-uniform in [1e-2, 1], g uniform in "
-                  "[0, 0.8], GRF media; FGMRES(50) with block Jacobi to rel-res 1e-8")
+def serving_leg(n_req, nets, seed=11):
+    """Continuous-batching server under Poisson arrivals (a reduced instance of
+    the serving workload), once with the per-M networks (requests inside their
+    eps range) and once with block Jacobi only, on the same requests and the
+    same arrival times: p50 / p99 latency and solves/s of each.  The arrival
+    rate is half the capacity of four slots estimated from the mean
+    block-Jacobi service time of three requests served alone."""
+    from paper_2604_23265_gb300 import rte
+    media = _mixed_media(n_req, seed, grids=(64, 128))
+    srv = rte.Server(slots=1, max_device_bytes=96 << 30)
+    try:
+        t0 = time.perf_counter()
+        for md in media[:3]:
+            srv.wait(srv.submit(md, tol=1e-8, max_iter=40000))
+        service = (time.perf_counter() - t0) / 3
+    finally:
+        srv.close()
+    rate = 0.5 * 4 / service
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_req)
+    out = {"workload": SERVE_WORKLOAD, "requests": n_req, "slots": 4, "arrival_rate_per_s": rate,
+           "single_request_service_s": service,
+           "policy": f"network for the request's M when eps <= {NET_EPS_MAX:g}, else block Jacobi"}
+    out["mgnet"] = _serve_once(media, gaps, nets, True)
+    out["block_jacobi"] = _serve_once(media, gaps, nets, False)
+    # headline keys: the MgNet arm
+    for k in ("completed_ok", "p50_latency_s", "p99_latency_s", "mean_queue_s", "solves_per_s"):
+        out[k] = out["mgnet"][k]
+    return out
 
 
-def batched_leg(count, seed=23):
-    """count solves of mixed small instances: one grouped call (shared launches
-    per Arnoldi round) against the same solves one after the other; both on
-    the device, set-up excluded, results compared bit for bit."""
+BATCH_WORKLOAD = ("mixed instances: I in {64, 128}, M in {16, 32}, eps log-uniform in [1e-4, 1], g uniform in "
+                  "[0, 0.8], GRF media; FGMRES(50) to rel-res 1e-8; per-M networks for eps <= 0.1, block "
+                  "Jacobi otherwise")
+
+
+def batched_leg(count, nets, seed=23):
+    """count solves of mixed instances: one grouped call (the Arnoldi steps of
+    all of them in shared launches, the V-cycles of one network and grid
+    batched) against the same solves one after the other, results compared
+    bit for bit; and the grouped call with block Jacobi only.  All on the
+    device, set-up excluded."""
     import torch
     from paper_2604_23265_gb300 import rte
-    media = [W.mixed_instance(seed * 1000 + i, grids=(32, 64), dirs=(8, 16), eps_range=(1e-2, 1.0),
-                              g_range=(0.0, 0.8)) for i in range(count)]
+    media = _mixed_media(count, seed, grids=(64, 128), g_range=(0.0, 0.8))
+    pcs = [nets[md.M] if _wants_net(md) else None for md in media]
     ctxs = [rte.Context.from_medium(md) for md in media]
     xs1 = [torch.zeros(c.n, dtype=torch.float64, device="cuda") for c in ctxs]
     xs2 = [torch.zeros(c.n, dtype=torch.float64, device="cuda") for c in ctxs]
-    for c, x in zip(ctxs, xs1):            # warm-up (workspaces)
-        c.solve(x, tol=1e-8, max_iter=5, raise_on_error=False)
-    rte.solve_group(ctxs, xs2, tol=1e-8, max_iter=5)
+    kw = dict(tol=1e-8, max_iter=40000)
+    for c, x, pc in zip(ctxs, xs1, pcs):            # warm-up (workspaces, network features)
+        c.solve(x, pc=pc, tol=1e-8, max_iter=5, raise_on_error=False)
+    rte.solve_group(ctxs, xs2, pcs=pcs, tol=1e-8, max_iter=5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lone = [c.solve(x, tol=1e-8) for c, x in zip(ctxs, xs1)]
+    lone = [c.solve(x, pc=pc, **kw) for c, x, pc in zip(ctxs, xs1, pcs)]
     torch.cuda.synchronize()
     t_lone = time.perf_counter() - t0
     t0 = time.perf_counter()
-    grp = rte.solve_group(ctxs, xs2, tol=1e-8)
+    grp = rte.solve_group(ctxs, xs2, pcs=pcs, **kw)
     torch.cuda.synchronize()
     t_grp = time.perf_counter() - t0
     same = all(a["iterations"] == b["iterations"] and torch.equal(x1, x2)
                for a, b, x1, x2 in zip(lone, grp, xs1, xs2))
+    for x in xs2:
+        x.zero_()
+    t0 = time.perf_counter()
+    bj = rte.solve_group(ctxs, xs2, **kw)
+    torch.cuda.synchronize()
+    t_bj = time.perf_counter() - t0
     for c in ctxs:
         c.close()
-    return {"workload": BATCH_WORKLOAD, "instances": count,
+    return {"workload": BATCH_WORKLOAD, "instances": count, "on_network": int(sum(p is not None for p in pcs)),
             "grouped_solves_per_s": count / t_grp, "one_at_a_time_solves_per_s": count / t_lone,
             "speedup": t_lone / t_grp, "iterations_total": int(sum(i["iterations"] for i in grp)),
-            "converged": all(i["converged"] for i in grp), "bit_identical_to_lone": bool(same)}
+            "converged": all(i["converged"] for i in grp), "bit_identical_to_lone": bool(same),
+            "block_jacobi_grouped_solves_per_s": count / t_bj,
+            "block_jacobi_iterations_total": int(sum(i["iterations"] for i in bj)),
+            "block_jacobi_converged": all(i["converged"] for i in bj),
+            "mgnet_vs_block_jacobi": t_bj / t_grp}
 
 
 def run_paper_protocol(args):
@@ -580,10 +653,12 @@ def main():
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
                     help="training loss of the network: Eq. loss or the ATFPS-filtered Eq. loss_delta")
     ap.add_argument("--delta", type=float, default=1e-2, help="ATFPS selection threshold (filtered loss)")
-    ap.add_argument("--batch", type=int, default=32,
+    ap.add_argument("--batch", type=int, default=24,
                     help="instances of the grouped-solve leg (shared launches); 0 skips it")
-    ap.add_argument("--serve", type=int, default=24,
+    ap.add_argument("--serve", type=int, default=20,
                     help="requests of the serving leg (p50/p99 latency); 0 skips it")
+    ap.add_argument("--mixed-train-steps", type=int, default=1500,
+                    help="training steps of each per-M network of the serving and grouped legs")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")
     ap.add_argument("--dirs", type=int, default=64, help="profiling only: directions")
     args = ap.parse_args()

@@ -332,9 +332,16 @@ typedef struct mgnet_config {
     int act;          /* 0: linear smoothers, 1: ReLU */
 } mgnet_config;
 
+/* stream: the network's initial CUDA stream (NULL: the legacy default
+ * stream).  A call with a context runs on the context's stream and the
+ * network keeps that stream for its calls without one (set/get params, save,
+ * load, clone), so such a stream must outlive those calls; mgnet_destroy
+ * waits for the whole device and uses no stream. */
 RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** out);
 RTE_API void mgnet_destroy(mgnet* net);
 RTE_API int64_t mgnet_param_count(const mgnet* net);
+/* The configuration the network was created with.  EINVAL for NULL. */
+RTE_API rte_status mgnet_get_config(const mgnet* net, mgnet_config* cfg);
 
 /* Arithmetic of the V-cycle convolutions when the network preconditions
  * (mgnet_precond, mgnet_apply, rte_solve); training always uses FP32.
@@ -399,14 +406,20 @@ RTE_API rte_status mgnet_load(mgnet* net, const char* path);
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of solve requests (no counterpart in the
  * paper).  rte_server_create starts `slots` worker threads, each with its own
- * CUDA stream (and its own copy of net, if net is not NULL).  Submitted
+ * CUDA stream (and its own copy of each network).  Submitted
  * requests (host arrays, copied at submission) wait in FIFO order and are
  * admitted as soon as a slot is free and their estimated device footprint
  * fits in max_device_bytes together with the requests already running; the
  * admitted solves overlap on the GPU and each releases its slot and bytes the
- * moment it finishes.  A request runs rte_setup, rte_solve (MgNet when
- * use_net and the server has a network, else block Jacobi) and
- * rte_reconstruct; results are the same bits as a lone solve.
+ * moment it finishes.  A request runs rte_setup, rte_solve and
+ * rte_reconstruct; results are the same bits as a lone solve.  With use_net
+ * the solve is preconditioned by the server's network for the request's M
+ * whose depth fits its grid (I divisible by 2^(levels-1)); a request no
+ * network fits, or without use_net, uses block Jacobi
+ * (rte_result.used_net tells which).  rte_server_create_multi takes up to 16
+ * networks (host array of count handles, read during the call; each is
+ * copied, so the caller keeps ownership), at most one per M (EINVAL
+ * otherwise); rte_server_create is the same with one network or none (NULL).
  * Errors are per request (rte_result.status): a malformed medium gives
  * EINVAL, a cancelled one ECANCELLED; submit rejects a request that can never
  * fit (ENOMEM) or is malformed (EINVAL).  inject_alloc_failure_id makes that
@@ -447,6 +460,7 @@ typedef struct rte_result {
     double latency_s;          /* submission to completion */
     double queue_s;            /* submission to admission */
     size_t footprint;          /* estimated device bytes */
+    int used_net;              /* 1: a network preconditioned the solve, 0: block Jacobi */
 } rte_result;
 typedef struct rte_server_stats_t {
     int64_t queued, completed;
@@ -456,6 +470,8 @@ typedef struct rte_server_stats_t {
 
 RTE_API void rte_server_config_default(rte_server_config* cfg);
 RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, rte_server** out);
+RTE_API rte_status rte_server_create_multi(const rte_server_config* cfg, mgnet* const* nets, int count,
+                                           rte_server** out);
 RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* req, int64_t* id_out);
 RTE_API rte_status rte_server_wait(rte_server* s, int64_t id, double timeout_ms, rte_result* res,
                                    double* psi_host);

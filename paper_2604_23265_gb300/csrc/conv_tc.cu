@@ -217,8 +217,11 @@ struct Geo {
     uint32_t xoff;
 };
 
+// Two CTAs per SM (at most 128 registers a thread): on the finest levels the
+// grid is several times the SM count, and a second resident CTA overlaps one
+// tile's loads and MMAs with the other's epilogue (a third costs spills).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__ TcConv a, const Geo g) {
+__global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__ TcConv a, const Geo g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mma_bar[kMaxStages];
     __shared__ __align__(8) uint64_t w_bar, x_bar;

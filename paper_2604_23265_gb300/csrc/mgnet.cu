@@ -39,6 +39,7 @@ struct Param {
 
 struct Features {            // CoeffNet outputs of one medium for one weight version
     uint64_t version = ~0ull;
+    uint64_t stamp = 0;      // last use (least recently used entries are evicted)
     int I = 0;
     void* block = nullptr;
     std::vector<float*> zc, gc, mean, inv, a, ai;
@@ -72,7 +73,8 @@ struct mgnet {
     int wsB = 0, wsI = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    std::map<uint64_t, rte::Features> feats;
+    std::map<uint64_t, rte::Features> feats;   // by context uid, at most kFeatureCache entries
+    uint64_t fclock = 0;
     // helpers for the per-sample scalars
     double* d_scal = nullptr;
     double* h_scal = nullptr;
@@ -236,8 +238,21 @@ void bwd_data_s1(mgnet* n, const float* gout, int B, int Co, int H, const float*
 }
 
 // ------------------------------------------------------------------ CoeffNet
+// Features of more contexts than this are not kept: a server sets up a new
+// context per request, and the least recently used entry (never one of the
+// up to 16 samples of the current batch) makes room.
+constexpr size_t kFeatureCache = 64;
+
 Features& features(mgnet* n, rte_ctx* ctx, bool force) {
+    if (n->feats.size() >= kFeatureCache && !n->feats.count(ctx->uid)) {
+        auto old = n->feats.begin();
+        for (auto it = n->feats.begin(); it != n->feats.end(); ++it)
+            if (it->second.stamp < old->second.stamp) old = it;
+        if (old->second.block) cudaFree(old->second.block);   // waits for the kernels that read it
+        n->feats.erase(old);
+    }
     Features& F = n->feats[ctx->uid];
+    F.stamp = ++n->fclock;
     const int I = ctx->I, L = n->L;
     if (!force && F.version == n->version && F.I == I) return F;
     if (!F.block || F.I != I) {
@@ -765,6 +780,7 @@ int grid_for(int64_t n) {
     return (int)(b < 2048 ? (b > 0 ? b : 1) : 2048);
 }
 
+// The network works on the stream of the context it is called with.
 void check_ctx(mgnet* n, rte_ctx* ctx) {
     if (ctx->M != n->M) throw StatusError{RTE_EINVAL, "network and context have different M"};
     if (ctx->I % (1 << (n->L - 1)) != 0 || (ctx->I >> (n->L - 1)) < 1)
@@ -986,7 +1002,9 @@ RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out) {
 
 RTE_API void mgnet_destroy(mgnet* n) {
     if (!n) return;
-    cudaStreamSynchronize(n->stream);
+    // the network's stream is the one of the context it ran with last, which
+    // may be gone by now: wait for the whole device instead
+    cudaDeviceSynchronize();
     for (auto& kv : n->feats)
         if (kv.second.block) cudaFree(kv.second.block);
     if (n->ws) cudaFree(n->ws);
@@ -1000,6 +1018,12 @@ RTE_API void mgnet_destroy(mgnet* n) {
 }
 
 RTE_API int64_t mgnet_param_count(const mgnet* n) { return n ? (int64_t)n->np : -1; }
+
+RTE_API rte_status mgnet_get_config(const mgnet* n, mgnet_config* cfg) {
+    if (!n || !cfg) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    *cfg = mgnet_config{n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax, n->act};
+    return RTE_OK;
+}
 
 RTE_API rte_status mgnet_set_precision(mgnet* n, int precision) {
     if (!n || (precision != MGNET_FP32 && precision != MGNET_BF16)) {

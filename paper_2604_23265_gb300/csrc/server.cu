@@ -46,6 +46,7 @@ struct Job {
     double g = 0.0;
     rte_solve_opts opts{};
     int use_net = 0;
+    int net = -1;                     // index of the server's network for (I, M), -1: block Jacobi
     size_t footprint = 0;
     Clock::time_point t_submit, t_start, t_end;
     volatile int cancel = 0;
@@ -66,7 +67,8 @@ struct Job {
 struct rte_server {
     rte_server_config cfg{};
     int device = 0;
-    std::vector<mgnet*> nets;                  // one network copy per slot (or empty)
+    std::vector<mgnet_config> net_cfg;         // the networks the server holds, one per M
+    std::vector<std::vector<mgnet*>> nets;     // [slot][network]: a copy per slot (one stream each)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<rte::Job>> queue;
@@ -79,7 +81,7 @@ struct rte_server {
     int64_t completed = 0;
     // grouped mode
     cudaStream_t gst = nullptr;
-    mgnet* gnet = nullptr;
+    std::vector<mgnet*> gnets;                 // grouped mode: one copy per network on gst
     std::deque<std::shared_ptr<rte::Job>> setup_q;   // admitted, waiting for a setup thread
     std::vector<std::shared_ptr<rte::Job>> ready;    // set up, waiting to join the group
     std::condition_variable cv_setup, cv_group;
@@ -107,11 +109,20 @@ bool valid_request(const rte_request* r, std::string& why) {
     return true;
 }
 
+// The network for a request of I x I cells and M directions: the one with
+// the same M whose V-cycle depth divides I; -1 when there is none.
+int pick_net(const rte_server* s, int I, int M) {
+    for (size_t k = 0; k < s->net_cfg.size(); ++k) {
+        const mgnet_config& c = s->net_cfg[k];
+        if (c.M == M && I % (1 << (c.levels - 1)) == 0) return (int)k;
+    }
+    return -1;
+}
+
 void worker_main(rte_server* s, int slot) {
     cudaSetDevice(s->device);
     cudaStream_t st = nullptr;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    mgnet* net = slot < (int)s->nets.size() ? s->nets[slot] : nullptr;
     while (true) {
         std::shared_ptr<Job> job;
         bool admitted = false;
@@ -158,7 +169,7 @@ void worker_main(rte_server* s, int slot) {
                     job->err = cudaGetErrorString(e);
                 } else {
                     job->opts.cancel = &job->cancel;
-                    mgnet* pc = (job->use_net && net) ? net : nullptr;
+                    mgnet* pc = job->net >= 0 ? s->nets[slot][job->net] : nullptr;
                     job->status = rte_solve(ctx, pc, &job->opts, x, &job->info);
                     if (job->status == RTE_OK || job->status == RTE_ENOTCONV) {
                         rte_reconstruct(ctx, x, psi);
@@ -332,7 +343,7 @@ void group_main(rte_server* s) {
             }
             for (auto& job : joining) {
                 job->opts.cancel = &job->cancel;
-                mgnet* pc = (job->use_net && s->gnet) ? s->gnet : nullptr;
+                mgnet* pc = job->net >= 0 ? s->gnets[job->net] : nullptr;
                 try {
                     live.emplace_back(job, group_solve_new(job->ctx, pc, job->opts, job->x));
                 } catch (const StatusError& e) {
@@ -402,15 +413,37 @@ RTE_API void rte_server_config_default(rte_server_config* c) {
     c->grouped = 0;
 }
 
-RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, rte_server** out) {
-    if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64 || cfg->max_device_bytes == 0) {
-        set_error(nullptr, "bad server configuration (slots in [1, 64])");
+static void destroy_nets(rte_server* s) {
+    for (auto& v : s->nets)
+        for (mgnet* m : v) mgnet_destroy(m);
+    s->nets.clear();
+    for (mgnet* m : s->gnets) mgnet_destroy(m);
+    s->gnets.clear();
+}
+
+RTE_API rte_status rte_server_create_multi(const rte_server_config* cfg, mgnet* const* nets, int count,
+                                           rte_server** out) {
+    if (!cfg || !out || cfg->slots < 1 || cfg->slots > 64 || cfg->max_device_bytes == 0 || count < 0 ||
+        count > 16 || (count > 0 && !nets)) {
+        set_error(nullptr, "bad server configuration (slots in [1, 64], at most 16 networks)");
         return RTE_EINVAL;
     }
     *out = nullptr;
+    std::vector<mgnet_config> ncfg;
+    for (int k = 0; k < count; ++k) {
+        mgnet_config c{};
+        if (mgnet_get_config(nets[k], &c) != RTE_OK) return RTE_EINVAL;
+        for (const mgnet_config& o : ncfg)
+            if (o.M == c.M) {
+                set_error(nullptr, "two networks for the same M");
+                return RTE_EINVAL;
+            }
+        ncfg.push_back(c);
+    }
     rte_server* s = new (std::nothrow) rte_server();
     if (!s) { set_error(nullptr, "host allocation failed"); return RTE_ENOMEM; }
     s->cfg = *cfg;
+    s->net_cfg = ncfg;
     cudaGetDevice(&s->device);
     if (cfg->grouped) {
         if (cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking) != cudaSuccess) {
@@ -418,13 +451,16 @@ RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, r
             set_error(nullptr, "cudaStreamCreate failed");
             return RTE_ECUDA;
         }
-        if (net) {
-            rte_status st = mgnet_clone(net, s->gst, &s->gnet);
+        for (int k = 0; k < count; ++k) {
+            mgnet* c = nullptr;
+            rte_status st = mgnet_clone(nets[k], s->gst, &c);
             if (st != RTE_OK) {
+                destroy_nets(s);
                 cudaStreamDestroy(s->gst);
                 delete s;
                 return st;
             }
+            s->gnets.push_back(c);
         }
         s->workers.emplace_back(admit_main, s);
         s->workers.emplace_back(setup_main, s);
@@ -433,21 +469,25 @@ RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, r
         *out = s;
         return RTE_OK;
     }
-    if (net) {
-        for (int i = 0; i < cfg->slots; ++i) {
+    s->nets.resize(cfg->slots);
+    for (int i = 0; i < cfg->slots; ++i)
+        for (int k = 0; k < count; ++k) {
             mgnet* c = nullptr;
-            rte_status st = mgnet_clone(net, nullptr, &c);
+            rte_status st = mgnet_clone(nets[k], nullptr, &c);
             if (st != RTE_OK) {
-                for (mgnet* m : s->nets) mgnet_destroy(m);
+                destroy_nets(s);
                 delete s;
                 return st;
             }
-            s->nets.push_back(c);
+            s->nets[i].push_back(c);
         }
-    }
     for (int i = 0; i < cfg->slots; ++i) s->workers.emplace_back(worker_main, s, i);
     *out = s;
     return RTE_OK;
+}
+
+RTE_API rte_status rte_server_create(const rte_server_config* cfg, mgnet* net, rte_server** out) {
+    return rte_server_create_multi(cfg, net ? &net : nullptr, net ? 1 : 0, out);
 }
 
 RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* r, int64_t* id_out) {
@@ -469,7 +509,8 @@ RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* r, int64_
     job->opts.tol = r->tol > 0 ? r->tol : 1e-8;
     if (r->max_iter > 0) job->opts.max_iter = r->max_iter;
     if (r->restart > 0) job->opts.restart = r->restart;
-    job->use_net = r->use_net && (!s->nets.empty() || s->gnet);
+    job->net = r->use_net ? pick_net(s, r->I, r->M) : -1;
+    job->use_net = job->net >= 0;
     job->footprint = footprint(r->I, r->M, job->opts.restart, job->use_net);
     if (job->footprint > s->cfg.max_device_bytes) {
         set_error(nullptr, "request needs more device memory than the server budget");
@@ -495,6 +536,7 @@ static void fill_result(const Job& j, rte_result* res, double* psi_host) {
         res->latency_s = std::chrono::duration<double>(j.t_end - j.t_submit).count();
         res->queue_s = std::chrono::duration<double>(j.t_start - j.t_submit).count();
         res->footprint = j.footprint;
+        res->used_net = j.use_net;
     }
     if (psi_host && !j.psi.empty()) std::memcpy(psi_host, j.psi.data(), j.psi.size() * sizeof(double));
 }
@@ -561,7 +603,6 @@ RTE_API void rte_server_destroy(rte_server* s) {
         }
     }
     s->cv_done.notify_all();
-    for (mgnet* m : s->nets) mgnet_destroy(m);
     {
         // grouped mode: requests set up but never run
         std::lock_guard<std::mutex> lk(s->mu);
@@ -578,7 +619,7 @@ RTE_API void rte_server_destroy(rte_server* s) {
         }
     }
     s->cv_done.notify_all();
-    if (s->gnet) mgnet_destroy(s->gnet);
+    destroy_nets(s);
     if (s->gst) {
         cudaStreamSynchronize(s->gst);
         cudaStreamDestroy(s->gst);

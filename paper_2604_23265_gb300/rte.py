@@ -92,6 +92,7 @@ SIGNATURES = {
     "rte_profile": (_I, [_P, _I]),
     "rte_server_config_default": (None, [_P]),
     "rte_server_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
+    "rte_server_create_multi": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
     "rte_server_submit": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "rte_server_wait": (_I, [_P, ctypes.c_int64, _D, _P, _P]),
     "rte_server_cancel": (_I, [_P, ctypes.c_int64]),
@@ -101,6 +102,7 @@ SIGNATURES = {
     "mgnet_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "mgnet_destroy": (None, [_P]),
     "mgnet_param_count": (ctypes.c_int64, [_P]),
+    "mgnet_get_config": (_I, [_P, _P]),
     "mgnet_set_precision": (_I, [_P, _I]),
     "rte_solve_group": (_I, [_P, _P, _I, _P, _P, _P, _P]),
     "mgnet_set_loss": (_I, [_P, _I]),
@@ -204,7 +206,7 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", _I), ("info", SolveInfo), ("latency_s", _D), ("queue_s", _D),
-                ("footprint", ctypes.c_size_t)]
+                ("footprint", ctypes.c_size_t), ("used_net", _I)]
 
 
 class ServerStats(ctypes.Structure):
@@ -216,14 +218,17 @@ class Server:
     """Continuous-batching solve server (rte_server_*); thread-safe."""
 
     def __init__(self, slots=4, max_device_bytes=64 << 30, net=None, inject_alloc_failure_id=-1, grouped=False):
+        """net: None, one MgNet, or a list of MgNets with distinct M (a request
+        with use_net runs on the one for its M whose depth fits its grid)."""
         cfg = ServerConfig()
         load().rte_server_config_default(ctypes.byref(cfg))
         cfg.slots, cfg.max_device_bytes = int(slots), int(max_device_bytes)
         cfg.inject_alloc_failure_id = int(inject_alloc_failure_id)
         cfg.grouped = 1 if grouped else 0
+        nets = [] if net is None else (list(net) if isinstance(net, (list, tuple)) else [net])
+        arr = (ctypes.c_void_p * max(len(nets), 1))(*[m.ptr for m in nets])
         out = ctypes.c_void_p()
-        _check(load().rte_server_create(ctypes.byref(cfg), net.ptr if net is not None else None,
-                                        ctypes.byref(out)))
+        _check(load().rte_server_create_multi(ctypes.byref(cfg), arr, len(nets), ctypes.byref(out)))
         self.ptr = out
         self._meta = {}
 
@@ -246,7 +251,7 @@ class Server:
                                       psi.ctypes.data_as(_P)))
         del self._meta[rid]
         d = {"status": STATUS_NAMES[res.status], "latency_s": res.latency_s, "queue_s": res.queue_s,
-             "footprint": res.footprint}
+             "footprint": res.footprint, "used_net": bool(res.used_net)}
         if res.status != RTE_OK:
             msg = load().rte_last_error(None)
             d["error"] = msg.decode() if msg else ""
@@ -316,6 +321,12 @@ class MgNet:
         self.ptr = out
         self.shape = shape
         self.count = int(load().mgnet_param_count(self.ptr))
+
+    def config(self):
+        """The library's record of the configuration (mgnet_get_config)."""
+        c = MgNetConfig()
+        _check(load().mgnet_get_config(self.ptr, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in c._fields_}
 
     def close(self):
         if getattr(self, "ptr", None):

@@ -105,3 +105,46 @@ def test_cancellation(lib, grouped):
     for md, (r, psi) in zip(quick, rq):
         assert r["status"] == "OK"
         np.testing.assert_array_equal(psi, _lone(md)[1])
+
+
+def _net(M, levels, seed):
+    from paper_2604_23265_gb300 import rte
+    shape = W.NetShape(M=M, levels=levels, c0=8, cmax=16, cc=4, ccmax=8)
+    net = rte.MgNet(shape)
+    net.set_params(W.init_params(shape, seed=seed, proj_scale=0.02, vcycle_scale=0.5))
+    return net
+
+
+@pytest.mark.parametrize("grouped", [False, True])
+def test_networks_per_direction_count(lib, grouped):
+    """A server holding networks for M = 8 (3 levels) and M = 16 (2 levels):
+    each request with use_net runs on the network of its M when the depth fits
+    its grid, else (M = 4, or I = 18 not divisible by 4 for the 3-level net)
+    on block Jacobi; every result is the bits of the lone solve with the same
+    preconditioner.  Two networks with one M are rejected."""
+    from paper_2604_23265_gb300 import rte
+    n8, n16 = _net(8, 3, 1), _net(16, 2, 2)
+    assert n8.config()["M"] == 8 and n8.config()["levels"] == 3
+    meds = [W.grf_diffusive(30 + i, I=I, M=M, eps=1e-2, g=0.3)
+            for i, (I, M) in enumerate([(16, 8), (24, 16), (32, 8), (18, 8), (16, 4), (32, 16), (24, 8)])]
+    expect_net = [True, True, True, False, False, True, True]
+    srv = rte.Server(slots=3, net=[n8, n16], grouped=grouped)
+    kw = dict(tol=1e-8, max_iter=400)
+    ids = [srv.submit(md, use_net=True, **kw) for md in meds]
+    got = [srv.wait(i) for i in ids]
+    srv.close()
+    for md, want, (res, psi) in zip(meds, expect_net, got):
+        assert res["status"] in ("OK", "ENOTCONV"), res
+        assert res["used_net"] == want
+        pc = ({8: n8, 16: n16}[md.M]) if want else None
+        ctx = rte.Context.from_medium(md)
+        x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+        info = ctx.solve(x, pc=pc, raise_on_error=False, **kw)
+        ref = torch.zeros(md.M * md.I * md.I, dtype=torch.float64, device="cuda")
+        ctx.reconstruct(x, ref)
+        torch.cuda.synchronize()
+        assert res["iterations"] == info["iterations"] and res["fell_back"] == info["fell_back"]
+        np.testing.assert_array_equal(psi, ref.cpu().numpy())
+        ctx.close()
+    with pytest.raises(rte.RteError):
+        rte.Server(slots=1, net=[n8, _net(8, 2, 3)], grouped=grouped)
