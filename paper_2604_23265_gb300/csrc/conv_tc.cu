@@ -26,6 +26,11 @@
 //    shared memory, else a ring of three stages overlapping the MMAs.
 //  * FP64 (the lift from the Krylov vector [2M][I][I]): loaded and converted
 //    by the threads.
+//  * streamed (layers whose weights do not stay resident: more than
+//    kResidentWeightBytes per CTA, or more than 256 output channels): a ring
+//    of stages, stage u = (tap, block of KB channel chunks), each holding the
+//    gathered activation rows and the matching weight slice (one bulk copy);
+//    output channels beyond 256 are split into equal slices over blockIdx.z.
 // The weights of a layer are packed once per weight version into the MMA
 // layout (tc_pack) and arrive by bulk async copies of 8 KB.
 //
@@ -56,8 +61,11 @@ constexpr int kRows = 128;           // pixels per CTA = MMA M = TMEM lanes
 constexpr int kThreads = 256;
 constexpr int kMaxStages = 3;
 constexpr long long kSpinLimit = 1ll << 24;
+constexpr size_t kResidentWeightBytes = 112 * 1024;   // per CTA, else streamed
+constexpr int kStreamChunks = 8;                       // KB: channel chunks of 8 per stage
+constexpr int kMaxSlice = 256;                         // output channels per CTA (MMA N)
 
-enum Mode { kGather = 0, kF64 = 1, kHalo = 2 };
+enum Mode { kGather = 0, kF64 = 1, kHalo = 2, kStream = 3 };
 
 __device__ int g_tc_status;          // 1 once a bounded wait expired
 
@@ -205,15 +213,17 @@ struct Chain {
 };
 
 // Geometry of one launch (host computed).
-// KC: channel chunks of 8 per MMA row (even); Npad: output channels rounded
-// up to 16; NS: stages (gather modes); ncols: TMEM columns (power of two >=
-// Npad); halo mode: tile SW x R class-grid pixels, halo box BW x BH, tiles_x
-// tiles across the width, tiles_y down the height; xoff: byte offset of the
-// input staging area (1024-aligned).
+// KC: channel chunks of 8 per MMA row (even); Npad: output channels of this
+// CTA (its slice) rounded up to 16; NS: stages (gather and streamed modes);
+// ncols: TMEM columns (power of two >= Npad); halo mode: tile SW x R
+// class-grid pixels, halo box BW x BH, tiles_x tiles across the width,
+// tiles_y down the height; streamed mode: KB chunks per stage, NKB blocks
+// per tap; xoff: byte offset of the input staging area (1024-aligned).
 struct Geo {
     int KC, Npad, NS;
     uint32_t ncols;
     int SW, R, BW, BH, tiles_x, tiles_y;
+    int KB, NKB;
     uint32_t xoff;
 };
 
@@ -224,6 +234,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__ TcConv a, const Geo g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mma_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t wst_bar[kMaxStages];   // streamed mode: weight slice of a stage
     __shared__ __align__(8) uint64_t w_bar, x_bar;
     __shared__ uint32_t tslot;
     __shared__ int fail;
@@ -236,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
     const uint32_t wbase = saddr(smem), xbase = wbase + g.xoff;
     const int KCi = (a.Ci + 7) / 8;
     const int OY0 = a.oy0[cls], OX0 = a.ox0[cls];
+    const int zs = blockIdx.z, cbase = zs * Npad;       // output channels cbase .. cbase + Npad - 1
 
     // tile of this CTA: halo mode, rows y0 .. y0 + R - 1, columns x0 .. x0 + SW - 1
     // of batch entry tb; gather modes, 128 consecutive pixels from p0
@@ -278,7 +290,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
     }
     if (tid == 0) {
         fail = 0;
-        for (int s = 0; s < kMaxStages; ++s) mbar_init(&mma_bar[s], 1);
+        for (int s = 0; s < kMaxStages; ++s) {
+            mbar_init(&mma_bar[s], 1);
+            mbar_init(&wst_bar[s], 1);
+        }
         mbar_init(&w_bar, 1);
         mbar_init(&x_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -287,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    if (tid == 0) {      // this class's packed weights: bulk copies of 8 KB tracked by w_bar
+    if (MODE != kStream && tid == 0) {   // this class's packed weights: bulk copies of 8 KB tracked by w_bar
         mbar_expect(&w_bar, wbytes);
         const char* src = static_cast<const char*>(a.w) + (size_t)cls * wbytes;
         for (uint32_t off = 0; off < wbytes; off += 8192) {
@@ -328,14 +343,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
             const float* gsrc = a.batched ? a.gate_b[eb] : a.gate;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const int co = c16 * 16 + i;
+                const int co = cbase + c16 * 16 + i;
                 if (co < a.Co) gt[i] = __ldg(gsrc + (size_t)co * oplane + opix);
             }
         }
         if (a.base8) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int kc = c16 * 2 + h;
+                const int kc = (cbase >> 3) + c16 * 2 + h;
                 if (kc < KCo) {
                     float t8[8];
                     unpack8(__ldg(reinterpret_cast<const uint4*>(a.base8) + ((size_t)eb * KCo + kc) * oplane + opix),
@@ -348,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
             const double* bsrc = a.batched ? a.base64_b[eb] : a.base64 + (size_t)eb * a.Co * oplane;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const int co = c16 * 16 + i;
+                const int co = cbase + c16 * 16 + i;
                 if (co < a.Co) bb[i] = (float)__ldg(bsrc + (size_t)co * oplane + opix);
             }
         }
@@ -392,6 +407,74 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
             tc_commit(&mma_bar[0]);
         }
         if (!mbar_wait(&mma_bar[0], 0)) ok = false;
+    } else if (MODE == kStream) {
+        // stage u = (tap t, block kb of KB chunks): this thread gathers row r,
+        // chunks half, half + 2, ... of the block; thread 0 copies the weight
+        // slice [tap][slice][kb] (b_bytes) behind the rows; the gather of stage
+        // u overlaps the MMAs of stage u - 1
+        const int KB = g.KB, NKB = g.NKB, U = T * NKB;
+        const uint32_t a_bytes = (uint32_t)KB * 2048, b_bytes = (uint32_t)Npad * KB * 16;
+        const uint32_t sbytes = a_bytes + b_bytes;
+        const int r = tid & (kRows - 1), half = tid >> 7;
+        int b = 0, gy = 0, gx = 0;
+        const bool live = pixel(r, b, gy, gx);
+        const uint32_t row_off = (uint32_t)((r >> 3) * KB) * 128 + (uint32_t)(r & 7) * 16;
+        const char* wsrc = static_cast<const char*>(a.w);
+        const size_t plane = (size_t)a.Hi * a.Wi;
+        const uint4* xp = reinterpret_cast<const uint4*>(a.x8);
+        auto load = [&](int u, int s) {
+            const int t = u / NKB, kb = u - t * NKB, tt = cls * T + t;
+            const uint32_t sa = xbase + (uint32_t)s * sbytes;
+            if (tid == 0) {
+                const size_t off = (((size_t)tt * gridDim.z + zs) * NKB + kb) * b_bytes;
+                mbar_expect(&wst_bar[s], b_bytes);
+                for (uint32_t o = 0; o < b_bytes; o += 8192) {
+                    const uint32_t nb = b_bytes - o < 8192 ? b_bytes - o : 8192;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            sa + a_bytes + o),
+                        "l"(wsrc + off + o), "r"(nb), "r"(saddr(&wst_bar[s]))
+                        : "memory");
+                }
+            }
+            const int iy = a.S * gy + a.dy[tt], ix = a.S * gx + a.dx[tt];
+            const bool in = live && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+            const size_t pix = in ? (size_t)iy * a.Wi + ix : 0;
+            for (int kcl = half; kcl < KB; kcl += 2) {
+                const int kc = kb * KB + kcl;
+                const bool okc = in && kc < KCi;
+                const uint4* src = okc ? xp + ((size_t)b * KCi + kc) * plane + pix : xp;
+                cp_async16(sa + row_off + kcl * 128, src, okc ? 16u : 0u);
+            }
+            cp_async_commit();
+        };
+        Chain chain(tmem);               // used by thread 0 only
+        auto consume = [&](int u, bool last) {
+            const int s = u % NS;
+            const uint32_t sa = xbase + (uint32_t)s * sbytes;
+            if (last) cp_async_wait<0>(); else cp_async_wait<1>();
+            if (a.relu_in)
+                for (int kcl = half; kcl < KB; kcl += 2) relu16(sa + row_off + kcl * 128);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                if (!mbar_wait(&wst_bar[s], (unsigned)(u / NS) & 1u)) ok = false;
+                if (ok) {
+                    tc_fence_after();
+                    uint64_t ad = sdesc(sa, 128, KB * 128), bd = sdesc(sa + a_bytes, 128, KB * 128);
+                    for (int j = 0; j < KB / 2; ++j, ad += 16, bd += 16) chain.mma(ad, bd, idesc);
+                }
+                tc_commit(&mma_bar[s]);
+            }
+        };
+        for (int u = 0; u < U; ++u) {
+            const int s = u % NS;
+            if (u >= NS && !mbar_wait(&mma_bar[s], (unsigned)((u / NS) - 1) & 1u)) ok = false;
+            load(u, s);
+            if (u > 0) consume(u - 1, false);
+        }
+        consume(U - 1, true);
+        if (!mbar_wait(&mma_bar[(U - 1) % NS], (unsigned)((U - 1) / NS) & 1u)) ok = false;
     } else {
         // this thread gathers row r, channel chunks kc = half, half + 2, ...
         const int r = tid & (kRows - 1), half = tid >> 7;
@@ -491,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
             if (!mbar_wait(&mma_bar[(T - 1) % NS], (unsigned)((T - 1) / NS) & 1u)) ok = false;
         }
     }
-    if (tid == 0 && !mbar_wait(&w_bar, 0)) ok = false;   // the weight copy has landed in every case
+    if (MODE != kStream && tid == 0 && !mbar_wait(&w_bar, 0)) ok = false;   // the weight copy has landed
     if (MODE == kHalo && tid == 0 && !mbar_wait(&x_bar, 0)) ok = false;
     tc_fence_after();
     if (!ok) {
@@ -513,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
         if (elive) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int kc = c16 * 2 + h;
+                const int kc = (cbase >> 3) + c16 * 2 + h;
                 if (kc >= KCo) break;
                 float v[8];
 #pragma unroll
@@ -575,8 +658,55 @@ __global__ void k_tc_pack(const float* __restrict__ w, int so, int si, int KK, T
     }
 }
 
+// streamed layout: entry ((((t Z + z) NKB + kb) (Ns/8) + g) KB + kcl) 8 + rr holds
+// W[t][(kb KB + kcl) 8 .. +7][z Ns + 8 g + rr] (zero outside Ci x Co), so the
+// weight slice of stage (t, z, kb) is one contiguous block of Ns KB 16 bytes
+__global__ void k_tc_pack_stream(const float* __restrict__ w, int so, int si, int KK, Taps tp, int Ci, int Co,
+                                 int Ns, int Z, int KB, int NKB, uint4* __restrict__ out) {
+    const int groups = Ns / 8;
+    const int64_t n = (int64_t)tp.T * Z * NKB * groups * KB * 8;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = e;
+        const int rr = (int)(q % 8);
+        q /= 8;
+        const int kcl = (int)(q % KB);
+        q /= KB;
+        const int g = (int)(q % groups);
+        q /= groups;
+        const int kb = (int)(q % NKB);
+        q /= NKB;
+        const int z = (int)(q % Z), t = (int)(q / Z);
+        const int co = z * Ns + g * 8 + rr, kc = kb * KB + kcl;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ci = kc * 8 + j;
+            v[j] = (co < Co && ci < Ci) ? w[((size_t)co * so + (size_t)ci * si) * KK + tp.wi[t]] : 0.f;
+        }
+        out[e] = pack8(v);
+    }
+}
+
 int chunks_kc(int Ci) { return ((Ci + 15) / 16) * 2; }
 int pad_n(int Co) { return ((Co + 15) / 16) * 16; }
+
+// Output-channel slices of a layer: Z slices of Ns channels (a multiple of
+// 16, at most kMaxSlice) covering Co.
+void slices(int Co, int& Z, int& Ns) {
+    Z = (pad_n(Co) + kMaxSlice - 1) / kMaxSlice;
+    Ns = pad_n((Co + Z - 1) / Z);
+}
+
+// Weights of one CTA (Tc taps of its class) too large to stay resident.
+bool streamed(int Tc, int Ci, int Co) {
+    return pad_n(Co) > kMaxSlice || (size_t)Tc * pad_n(Co) * chunks_kc(Ci) * 16 > kResidentWeightBytes;
+}
+
+void stream_blocks(int Ci, int& KB, int& NKB) {
+    const int KC = chunks_kc(Ci);
+    KB = KC < kStreamChunks ? KC : kStreamChunks;
+    NKB = (KC + KB - 1) / KB;
+}
 
 struct KernelLimits {
     size_t max_dyn = 0;
@@ -636,19 +766,20 @@ EncodeTiled encoder() {
 }
 
 template <int MODE>
-void launch(const TcConv& a, Geo g, size_t stage_area, bool pdl, unsigned grid_x, cudaStream_t st) {
+void launch(const TcConv& a, Geo g, size_t stage_area, bool pdl, unsigned grid_x, cudaStream_t st,
+            unsigned slices_z = 1) {
     g.ncols = 32;
     while (g.ncols < (uint32_t)g.Npad) g.ncols <<= 1;
     int k = 0;
     while ((32u << k) < g.ncols) ++k;
     const KernelLimits& L = limits<MODE>();
-    const size_t wbytes = (size_t)a.T * g.Npad * g.KC * 16;
+    const size_t wbytes = MODE == kStream ? 0 : (size_t)a.T * g.Npad * g.KC * 16;   // resident weights
     g.xoff = (uint32_t)((wbytes + 1023) & ~(size_t)1023);
     size_t smem = g.xoff + stage_area;
     if (smem < L.floor_bytes[k]) smem = L.floor_bytes[k];
     if (smem > L.max_dyn) throw StatusError{RTE_EINVAL, "tensor-core convolution: tile exceeds shared memory"};
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid_x, (unsigned)a.classes);
+    cfg.gridDim = dim3(grid_x, (unsigned)a.classes, slices_z);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -662,9 +793,29 @@ void launch(const TcConv& a, Geo g, size_t stage_area, bool pdl, unsigned grid_x
 
 }  // namespace
 
-size_t tc_weight_bytes(int T, int Ci, int Co) { return (size_t)T * pad_n(Co) * chunks_kc(Ci) * 16; }
+size_t tc_weight_bytes(int T, int classes, int Ci, int Co) {
+    if (streamed(T / classes, Ci, Co)) {
+        int Z = 0, Ns = 0, KB = 0, NKB = 0;
+        slices(Co, Z, Ns);
+        stream_blocks(Ci, KB, NKB);
+        return (size_t)T * Z * NKB * Ns * KB * 16;
+    }
+    return (size_t)T * pad_n(Co) * chunks_kc(Ci) * 16;
+}
 
-void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int Co, void* dst, cudaStream_t st) {
+void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int classes, int Ci, int Co, void* dst,
+             cudaStream_t st) {
+    if (streamed(tp.T / classes, Ci, Co)) {
+        int Z = 0, Ns = 0, KB = 0, NKB = 0;
+        slices(Co, Z, Ns);
+        stream_blocks(Ci, KB, NKB);
+        const int64_t n = (int64_t)tp.T * Z * NKB * (Ns / 8) * KB * 8;
+        const int64_t blocks = (n + 255) / 256;
+        k_tc_pack_stream<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, st>>>(
+            w, so, si, KK, tp, Ci, Co, Ns, Z, KB, NKB, static_cast<uint4*>(dst));
+        check(cudaGetLastError(), "k_tc_pack_stream");
+        return;
+    }
     const int KC = chunks_kc(Ci), Npad = pad_n(Co);
     const int n = tp.T * (Npad / 8) * KC * 8;
     k_tc_pack<<<(n + 255) / 256, 256, 0, st>>>(w, so, si, KK, tp, Ci, Co, KC, Npad, static_cast<uint4*>(dst));
@@ -677,7 +828,7 @@ void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
         a.Ci < 1 || a.Co < 1 || !a.w || (!a.x8) == (!(a.x64 || (a.batched && a.x64_b[0]))) ||
         (!a.y8) == (!(a.y32 || (a.batched && a.y32_b[0]))) || (a.batched && a.B > kTcMaxBatch))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: bad arguments"};
-    if (pad_n(a.Co) > 256) throw StatusError{RTE_EINVAL, "tensor-core convolution: more than 256 output channels"};
+    const bool stream = streamed(a.T, a.Ci, a.Co);
     if (reinterpret_cast<uintptr_t>(a.w) % 16 || (a.x8 && reinterpret_cast<uintptr_t>(a.x8) % 16) ||
         (a.y8 && reinterpret_cast<uintptr_t>(a.y8) % 16) || (a.base8 && reinterpret_cast<uintptr_t>(a.base8) % 16))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: buffers must be 16-byte aligned"};
@@ -692,8 +843,20 @@ void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
     g.Npad = pad_n(a.Co);
     const int T = a.T;
     if (a.x64 || (a.batched && a.x64_b[0])) {
+        if (stream) throw StatusError{RTE_EINVAL, "tensor-core convolution: lift weights too large"};
         g.NS = T;
         launch<kF64>(a, g, (size_t)T * g.KC * 2048, pdl, (unsigned)((total + kRows - 1) / kRows), st);
+        return;
+    }
+    if (stream) {
+        int Z = 0;
+        slices(a.Co, Z, g.Npad);
+        stream_blocks(a.Ci, g.KB, g.NKB);
+        const int U = T * g.NKB;
+        g.NS = U < kMaxStages ? U : kMaxStages;
+        const size_t sbytes = (size_t)g.KB * 2048 + (size_t)g.Npad * g.KB * 16;
+        launch<kStream>(a, g, (size_t)g.NS * sbytes, pdl, (unsigned)((total + kRows - 1) / kRows), st,
+                        (unsigned)Z);
         return;
     }
     bool halo = a.S == 1 && a.Hg == a.Hi && a.Wg == a.Wi;

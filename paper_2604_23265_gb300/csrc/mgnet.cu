@@ -430,11 +430,11 @@ size_t tc_forward(mgnet* n, const TcSamples& S, int I, TcMode mode) {
     };
     size_t cursor = 0;
     auto run = [&](nn::TcConv c, const char* wname, int so, int si, int KK, const Taps& tp) {
-        const size_t bytes = nn::tc_weight_bytes(tp.T, c.Ci, c.Co);
+        const size_t bytes = nn::tc_weight_bytes(tp.T, c.classes, c.Ci, c.Co);
         void* dst = static_cast<char*>(n->tcw) + cursor;
         cursor += bytes;
         if (mode == TcMode::Plan) return;
-        if (mode == TcMode::Pack) nn::tc_pack(P(n, wname), so, si, KK, tp, c.Ci, c.Co, dst, n->stream);
+        if (mode == TcMode::Pack) nn::tc_pack(P(n, wname), so, si, KK, tp, c.classes, c.Ci, c.Co, dst, n->stream);
         c.w = dst;
         c.T = tp.T / c.classes;
         for (int t = 0; t < tp.T; ++t) {

@@ -86,7 +86,7 @@ struct TcConv {
     const double* x64 = nullptr;     // FP64 [B][Ci][Hi][Wi] input (converted on load)
     int B = 1, Ci = 0, Hi = 0, Wi = 0;
     int relu_in = 0;                 // ReLU applied to the gathered input
-    const void* w = nullptr;         // packed weights (tc_pack, classes x tc_weight_bytes(T, Ci, Co))
+    const void* w = nullptr;         // packed weights (tc_pack of the classes T taps: tc_weight_bytes bytes)
     int Co = 0;
     int Hg = 0, Wg = 0, S = 1;       // class grid and input stride
     int OS = 1;                      // output placement OS g + (oy0, ox0)[class]
@@ -110,9 +110,13 @@ struct TcConv {
     const double* base64_b[kTcMaxBatch] = {}; // [Co][Ho][Wo] each
     float* y32_b[kTcMaxBatch] = {};           // [Co][Ho][Wo] each
 };
-size_t tc_weight_bytes(int T, int Ci, int Co);
+// Bytes of the packed weights of T taps (classes x taps per class): the
+// resident layout, or the streamed one for layers whose per-CTA weights
+// exceed the resident limit or that have more than 256 output channels.
+size_t tc_weight_bytes(int T, int classes, int Ci, int Co);
 // packs W[t][i][o] = w[(o so + i si) KK + wi_t] into dst (tc_weight_bytes)
-void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int Ci, int Co, void* dst, cudaStream_t st);
+void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int classes, int Ci, int Co, void* dst,
+             cudaStream_t st);
 // pdl: programmatic dependent launch (the weights must not be written by the
 // previous kernel in the stream)
 void tc_conv(const TcConv& a, bool pdl, cudaStream_t st);

@@ -53,12 +53,16 @@ def test_forward_matches_oracle(lib, I, M, levels):
 # three pipeline stages, 128-pixel tiles with a ragged tail (24 x 24, 8 x 8
 # coarse grids), 64-channel levels (72 KB of weights per CTA), and a 128-wide
 # lift / projection (M = 64, 128 TMEM columns), the largest direction count
-# (M = 80: 160-wide lift input and projection, 256 TMEM columns), and ReLU
-# smoothers.
+# (M = 80: 160-wide lift input and projection, 256 TMEM columns), ReLU
+# smoothers, and layers whose weights are streamed per (tap, 64-channel block)
+# stage: widths 64-256 (one slice), 64-512 (two slices of 256 output channels)
+# and 40-320 (two slices of 160, channel blocks padded, ReLU on the gathers).
 @pytest.mark.parametrize("I,M,levels,c0,cmax,act", [(16, 8, 3, 8, 16, "linear"), (24, 4, 2, 8, 16, "linear"),
                                                     (32, 16, 4, 16, 64, "linear"), (8, 8, 1, 8, 16, "linear"),
                                                     (64, 64, 4, 16, 64, "linear"), (40, 20, 2, 24, 48, "linear"),
-                                                    (32, 8, 3, 16, 32, "relu"), (16, 80, 2, 16, 32, "linear")])
+                                                    (32, 8, 3, 16, 32, "relu"), (16, 80, 2, 16, 32, "linear"),
+                                                    (16, 8, 3, 64, 256, "linear"), (16, 8, 4, 64, 512, "linear"),
+                                                    (24, 8, 4, 40, 320, "relu")])
 def test_tensor_core_forward_matches_oracle(lib, I, M, levels, c0, cmax, act):
     rte, shape, params, md, ctx, net, p = _setup(I=I, M=M, levels=levels, c0=c0, cmax=cmax,
                                                  cc=4, ccmax=8, act=act)
