@@ -8,7 +8,8 @@ correlation length 0.1), sigma_a = 0.05 sigma_T, q = 1 on the central
 One step = one complete solve (Krylov iteration, FP64 residual refinement and
 the solution update) of the device-resident system, preconditioned by the
 learned MgNet V-cycle over block Jacobi.  The network is trained first (on
-other media of the same distribution, untimed, reported as mgnet.train_seconds);
+32 other media of the same distribution at 128 x 128 cells, untimed, reported
+as mgnet.train_seconds);
 block-Jacobi GMRES on the same medium is timed in the same run for comparison.  `e2e` times the public
 API end to end per step: rte_setup from pinned host arrays (H2D inside),
 the solve, the angular-flux reconstruction and its copy back to the host.
@@ -278,8 +279,11 @@ def run_ours(args):
     net, train_s, train_loss = None, 0.0, None
     if args.pc == "mgnet":
         # the network is trained before the timed region on other media of the
-        # same distribution (seeds 101..), never on the benchmark medium
-        media = [W.grf_diffusive(seed=101 + i, I=I, M=M) for i in range(args.train_media)]
+        # same distribution (seeds 101..), never on the benchmark medium, at
+        # the training grid size (the same fields in domain units, coarser
+        # cells) with the depth of the benchmark grid
+        It = min(args.train_size, I) if args.train_size > 0 else I
+        media = [W.grf_diffusive(seed=101 + i, I=It, M=M) for i in range(args.train_media)]
         shape = train.default_shape(M, I, c0=args.c0, cmax=args.cmax)
         net, tctx, losses, train_s = train.train_for(media, shape=shape, steps=args.train_steps, batch=8,
                                                      lr0=3e-3, seed=args.train_seed, loss=args.loss,
@@ -371,6 +375,7 @@ def run_ours(args):
         out["mgnet"] = {"loss": args.loss, "delta": args.delta if args.loss == "filtered" else None,
                         "train_seed": args.train_seed,
                         "train_seconds": train_s, "train_media": args.train_media,
+                        "train_grid": min(args.train_size, I) if args.train_size > 0 else I,
                         "train_steps": args.train_steps, "final_loss": train_loss,
                         "levels": net.shape.levels, "params": net.count}
     if bj is not None:
@@ -382,6 +387,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(md, bj["iterations"] if bj else iters)
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_atfps:
+        out["atfps"] = atfps_leg()
     if rank == 0 and world == 1 and (args.serve > 0 or args.batch > 0):
         nets, mixed_train_s = train_mixed_nets(args.mixed_train_steps)
         out["mixed_networks"] = {"M": list(nets), "train_seconds": mixed_train_s,
@@ -559,6 +566,54 @@ def batched_leg(count, nets, seed=23):
             "mgnet_vs_block_jacobi": t_bj / t_grp}
 
 
+ATFPS_WORKLOAD = ("64 x 64 cells, M = 16, eps = 1e-3, g = 0.5, GRF medium (the benchmark distribution); "
+                  "FGMRES(50) to rel-res 1e-8 on the full TFPS system (block Jacobi) and on the compressed ATFPS "
+                  "system (preconditioned by mask o D S) followed by the layer reconstruction")
+
+
+def atfps_leg(deltas=(1e-2, 1e-3), I=64, M=16, seed=5):
+    """The compressed ATFPS solve with layer reconstruction (Sec. 2.3.3-2.3.4)
+    beside the full TFPS solve of the same medium: unknowns kept, set-up
+    (filter, compressed blocks) and solve times, iterations, and the largest
+    cell-centre deviation of the angular flux from the full solution."""
+    import torch
+    from paper_2604_23265_gb300 import rte
+    md = W.grf_diffusive(seed=seed, I=I, M=M, eps=1e-3)
+    ctx = rte.Context.from_medium(md)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.solve(x, tol=1e-8)                      # warm-up (workspace)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    full = ctx.solve(x, tol=1e-8)
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    psi = torch.zeros(M * I * I, dtype=torch.float64, device="cuda")
+    ctx.reconstruct(x, psi)
+    ref = psi.clone()
+    out = {"workload": ATFPS_WORKLOAD, "n": ctx.n,
+           "full": {"iterations": full["iterations"], "seconds": t_full, "converged": bool(full["converged"])}}
+    for d in deltas:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rows = ctx.atfps_setup(d)
+        xc = torch.zeros_like(x)
+        ctx.atfps_solve(xc, tol=1e-8, max_iter=1)   # builds the compressed blocks
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        xc.zero_()
+        t0 = time.perf_counter()
+        inf = ctx.atfps_solve(xc, tol=1e-8, raise_on_error=False)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        ctx.reconstruct(xc, psi)
+        dev = float((psi - ref).abs().max() / ref.abs().max())
+        out[f"delta_{d:g}"] = {"kept": rows, "kept_fraction": rows / ctx.n, "setup_seconds": t_setup,
+                               "iterations": inf["iterations"], "solve_seconds": t_solve,
+                               "converged": bool(inf["converged"]), "max_rel_dev_psi_centres": dev}
+    ctx.close()
+    return out
+
+
 def run_paper_protocol(args):
     """The paper's own setting (Sec. 4.1-4.2): 32 x 32 cells, M = 4 directions,
     polynomial media with eps = 0.01 (c + 0.1).  A network is trained on
@@ -637,8 +692,10 @@ def main():
                          "(block-Jacobi FGMRES(50) on this workload, as measured on the GPU)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--pc", default="mgnet", choices=["mgnet", "bj"])
-    ap.add_argument("--train-steps", type=int, default=1500)
-    ap.add_argument("--train-media", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=6000)
+    ap.add_argument("--train-media", type=int, default=32)
+    ap.add_argument("--train-size", type=int, default=128,
+                    help="grid side of the training media (0: the benchmark grid)")
     ap.add_argument("--no-bj", action="store_true", help="skip the block-Jacobi comparison solve")
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
@@ -657,6 +714,7 @@ def main():
                     help="instances of the grouped-solve leg (shared launches); 0 skips it")
     ap.add_argument("--serve", type=int, default=20,
                     help="requests of the serving leg (p50/p99 latency); 0 skips it")
+    ap.add_argument("--no-atfps", action="store_true", help="skip the compressed ATFPS leg")
     ap.add_argument("--mixed-train-steps", type=int, default=1500,
                     help="training steps of each per-M network of the serving and grouped legs")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")

@@ -288,6 +288,28 @@ RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts
                              double* x_dev, rte_solve_info* info);
 
 /* ---------------------------------------------------------------------------
+ * rte_atfps_solve -- the compressed ATFPS solve with layer reconstruction
+ * (Sec. 2.3.3-2.3.4): the kept coefficients solve the compressed system of
+ * Eq. 2DAdaptiveTFPS_linear_sys, A_bar alpha_bar = b_bar (its rows the kept
+ * projections of every interface jump, Eqs. 2DAdaptiveTFPS_continuity_cond /
+ * boundary_cond, i.e. A_bar = F A restricted to the kept columns, b_bar = F b),
+ * by flexible GMRES right-preconditioned by mask o D S (FP64 throughout):
+ * S takes each compressed row back onto the rows of its interface as its kept
+ * basis column (F S = I) and D is the block-Jacobi inverse of the full system,
+ * so that with nothing dropped A_bar mask o D S = F (A D) F^{-1}, the block-
+ * Jacobi operator of the full system up to similarity; then,
+ * with layers != 0, every dropped coefficient from the dropped projection of
+ * its interface's jump of that smooth solution (Eqs. 2DAdaptive_TFPS_layer1 /
+ * layer2), else zero.  Requires rte_atfps_setup (EINVAL otherwise).
+ * x_dev: double [2M][N] (device), the full coefficient vector on return (the
+ * layout of rte_solve; rte_reconstruct gives the angular flux).  opts as for
+ * rte_solve except that inner_precision and stall_ratio are not used; the
+ * reported relres is ||b_bar - A_bar alpha_bar|| / ||b_bar|| (b_bar and the
+ * residual in slot layout).  Synchronous. */
+RTE_API rte_status rte_atfps_solve(rte_ctx* ctx, const rte_solve_opts* opts, int layers, double* x_dev,
+                                   rte_solve_info* info);
+
+/* ---------------------------------------------------------------------------
  * rte_solve_group -- count (1..1024) solves of rte_solve advancing in
  * lockstep: in every round each live solve takes one Arnoldi step, and the
  * steps of all of them run as shared launches (inner operator w = B z and its

@@ -174,3 +174,105 @@ def loss_and_grad_filtered(params, shape, problems, Ds, Fs, masks, coeff_xs, rs)
     P = ids["params"]
     return total, {k: grads[i] if grads[i] is not None else np.zeros_like(params[k])
                    for k, i in P.items()}
+
+
+# ------------------------------------------------------------------ compressed solve
+# Sec. 2.3.3 (Eq. 2DAdaptiveTFPS_linear_sys) and Sec. 2.3.4 (Eqs.
+# 2DAdaptive_TFPS_layer1 / layer2).  Pinned by P17 (delta = 0: the compressed
+# solution is the TFPS solution), P18 (closed form q / sigma_a), P19 (the
+# reconstructed layers cancel the dropped projections of every interface jump
+# up to the neglected cross-face terms; a wrong sign doubles them) and P20
+# (accuracy improves as delta decreases; layers recover the face values).
+
+
+def interface_columns(p, cells_groups, mask, rows=None):
+    """The functions behind the columns of ``interface_basis``'s E, in the
+    same order (kept, then dropped): (cell, slot, side, scale) with side 0
+    for C- (or the boundary cell) and 1 for C+, and scale the max-norm the
+    column had before E's scaling to one (the dropped columns are l^k itself,
+    restricted to the incoming rows on a boundary)."""
+    M2 = p.M // 2
+    kept, dropped = [], []
+    for side, (c, grp) in enumerate(cells_groups):
+        slots = grp * M2 + np.arange(M2)
+        order = slots[np.argsort(np.abs(p.xi[p.mat_id[c]][slots]), kind="stable")]
+        Lc = p.L[p.mat_id[c]]
+        for k in order:
+            col = Lc[:, k] if rows is None else Lc[rows, k]
+            (kept if mask[k, c] else dropped).append((c, int(k), side, float(np.abs(col).max())))
+    return kept + dropped
+
+
+def compressed_system(p, delta):
+    """Eq. 2DAdaptiveTFPS_linear_sys: the rows are the kept projections of
+    every interface jump (Eqs. 2DAdaptiveTFPS_continuity_cond / boundary_cond,
+    F of ``filter_operator``) of the solution built from the kept functions
+    only; the unknowns are the kept coefficients in [2M][N] order.  Returns
+    (A_bar, b_bar, keep, mask): A_bar = F A[:, keep], b_bar = F b."""
+    F, mask = filter_operator(p, delta)
+    keep = np.flatnonzero(mask.ravel())
+    A = p.assemble().tocsc()
+    return (F @ A[:, keep]).tocsr(), F @ p.rhs().ravel(), keep, mask
+
+
+def compressed_solve(p, delta):
+    """The smooth coefficients: the compressed system solved by dense LU,
+    scattered into [2M][N] with zeros at the dropped functions."""
+    from . import krylov
+    Ab, bb, keep, mask = compressed_system(p, delta)
+    alpha = np.zeros(2 * p.M * p.N)
+    alpha[keep] = krylov.dense_solve(Ab, bb)
+    return alpha.reshape(2 * p.M, p.N), mask
+
+
+def interface_jumps(p, alpha):
+    """Per interface (``interfaces`` order) the midpoint jump of the solution
+    built from alpha: psi_{C-} - psi_{C+} over all M directions on an interior
+    interface, psi_C - inflow over the incoming directions on a boundary,
+    read off the rows of A alpha - b (rows of C- carry +jump, of C+ -jump)."""
+    M2 = p.M // 2
+    y = p.apply(alpha) - p.rhs()
+    pos = {(f, m): j for f in range(4) for j, m in enumerate(p.dirs[f])}
+    out = []
+    for kind, cm, cp, fm, fp in interfaces(p):
+        if kind == "in":
+            J = np.empty(p.M)
+            for m in range(p.M):
+                if (fm, m) in pos:
+                    J[m] = y[fm * M2 + pos[(fm, m)], cm]
+                else:
+                    J[m] = -y[fp * M2 + pos[(fp, m)], cp]
+        else:
+            J = y[fm * M2:(fm + 1) * M2, cm].copy()
+        out.append(J)
+    return out
+
+
+def layer_reconstruction(p, alpha_smooth, mask):
+    """Eqs. 2DAdaptive_TFPS_layer1 / layer2: every dropped coefficient from
+    the dropped projection of its interface's jump of the smooth solution,
+    alpha_{C-}^k = P^k(psi_{C+} - psi_{C-}), alpha_{C+}^k = P^k(psi_{C-} -
+    psi_{C+}), on a boundary alpha_C^k = P^k(inflow - psi_C); P^k l^k = 1 is
+    read as the coordinate in the basis of unit max-norm columns divided by
+    the column's scale."""
+    alpha = np.array(alpha_smooth, dtype=np.float64, copy=True)
+    for (kind, cm, cp, fm, fp), J in zip(interfaces(p), interface_jumps(p, alpha_smooth)):
+        if kind == "in":
+            groups, rows = [(cm, fm), (cp, fp)], None
+        else:
+            groups, rows = [(cm, fm)], p.dirs[fm]
+        E, s = interface_basis(p, groups, mask, rows=rows)
+        cols = interface_columns(p, groups, mask, rows=rows)
+        if s == len(cols):
+            continue
+        beta = np.linalg.solve(E, J)[s:]
+        for b, (c, k, side, scale) in zip(beta, cols[s:]):
+            alpha[k, c] = (-b if side == 0 else b) / scale
+    return alpha
+
+
+def atfps_solution(p, delta):
+    """(alpha_delta with layers, alpha_smooth, mask): the compressed solve
+    followed by the layer reconstruction."""
+    smooth, mask = compressed_solve(p, delta)
+    return layer_reconstruction(p, smooth, mask), smooth, mask

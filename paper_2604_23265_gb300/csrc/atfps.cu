@@ -33,16 +33,27 @@ namespace rte {
 
 struct Atfps {
     double delta = 0.0;
-    int nif = 0;                    // interfaces with at least one kept function
+    int nif = 0;                    // interfaces (every face of the grid)
     int64_t rows = 0;               // kept coordinates over all interfaces
+    int64_t ndrop = 0;              // dropped functions over all interfaces
     size_t bytes = 0;
     std::vector<void*> allocs;
     unsigned char* mask = nullptr;  // [2M][N], 1 = kept
-    int* desc = nullptr;            // [nif][8]: C-, C+ (-1 on a boundary), face of C-, face of C+, s, rows of E, r0
-    long long* off = nullptr;       // [nif] offset of the interface's projections
-    double* proj = nullptr;         // projections, [m][k] per interface
+    int* desc = nullptr;            // [nif][8]: C-, C+ (-1 on a boundary), face of C-, face of C+, s, rows of E, r0, d0
+    long long* off = nullptr;       // [nif] offset of the interface's kept projections
+    double* proj = nullptr;         // kept projections, [m][k] per interface
+    double* ekeep = nullptr;        // kept columns of E (unit max-norm), [m][k] per interface
+    long long* loff = nullptr;      // [nif] offset of the interface's dropped projections
+    double* lproj = nullptr;        // dropped projections, [m][d] per interface
+    long long* kcol = nullptr;      // [rows] slot index k N + c of the function behind each kept row
+    long long* dcol = nullptr;      // [ndrop] slot index of each dropped function
+    double* dsc = nullptr;          // [ndrop] -1 / scale (C- or boundary cell) or +1 / scale (C+)
     int* singular = nullptr;        // set when an interface basis is numerically singular
     std::vector<unsigned char> mask_h;
+    // compressed solve (built by the first atfps_solve after the set-up)
+    double* bbar = nullptr;         // [2M][N] compressed right-hand side in slot layout (zero at dropped slots)
+    double* scratch = nullptr;      // [2M][N] row-space scratch
+    double* scratch2 = nullptr;     // [2M][N] row-space scratch
 };
 
 namespace {
@@ -62,13 +73,17 @@ __global__ void __launch_bounds__(kBuildThreads)
     k_atfps_build(const int* __restrict__ desc, const long long* __restrict__ off, const int* __restrict__ ord,
                   const int* __restrict__ dirs, const double* __restrict__ L64, const int* __restrict__ mat,
                   const unsigned char* __restrict__ mask, int M, int N, double pivot_tol,
-                  double* __restrict__ proj, int* __restrict__ singular) {
+                  double* __restrict__ proj, double* __restrict__ ekeep, const long long* __restrict__ loff,
+                  double* __restrict__ lproj,
+                  long long* __restrict__ kcol, long long* __restrict__ dcol, double* __restrict__ dsc,
+                  int* __restrict__ singular) {
     extern __shared__ double sm[];
     __shared__ int col_cell[2 * 64], col_slot[2 * 64];
+    __shared__ double col_scale[2 * 64];
     __shared__ double red[kBuildThreads / 32];
     __shared__ int s_piv;
     const int* d = desc + 8 * blockIdx.x;
-    const int cm = d[0], cp = d[1], fm = d[2], fp = d[3], s = d[4], Mi = d[5];
+    const int cm = d[0], cp = d[1], fm = d[2], fp = d[3], s = d[4], Mi = d[5], r0 = d[6], d0 = d[7];
     const int M2 = M / 2, n2 = 2 * M;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* E = sm;                   // column-major: E[j * Mi + r]
@@ -139,6 +154,13 @@ __global__ void __launch_bounds__(kBuildThreads)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         for (int r = lane; r < Mi; r += 32) E[j * Mi + r] = mx > 0.0 ? E[j * Mi + r] / mx : 0.0;
+        if (lane == 0) col_scale[j] = mx;
+    }
+    __syncthreads();
+    // the kept columns, [m][k], before the elimination overwrites E
+    for (int e = tid; e < s * Mi; e += blockDim.x) {
+        const int m = e / s, k = e - m * s;
+        ekeep[off[blockIdx.x] + e] = E[k * Mi + m];
     }
     // Gauss-Jordan: E X = I with partial pivoting (A = E kept in place, row-swapped)
     for (int e = tid; e < Mi * Mi; e += blockDim.x) X[e] = (e / Mi == e % Mi) ? 1.0 : 0.0;
@@ -191,11 +213,27 @@ __global__ void __launch_bounds__(kBuildThreads)
         __syncthreads();
     }
     if (tid == 0 && bad) atomicExch(singular, 1);
-    // kept rows of the inverse, stored [m][k]
+    __syncthreads();
+    // kept rows of the inverse, stored [m][k], and the functions behind them
     double* out = proj + off[blockIdx.x];
     for (int e = tid; e < s * Mi; e += blockDim.x) {
         const int m = e / s, k = e - m * s;
         out[e] = X[k * Mi + m];
+    }
+    for (int k = tid; k < s; k += blockDim.x) kcol[r0 + k] = (long long)col_slot[k] * N + col_cell[k];
+    // dropped rows [m][d]; a dropped column is its function itself scaled to
+    // max-norm one, so P^k l^k = scale
+    const int nd = Mi - s;
+    double* lout = lproj + loff[blockIdx.x];
+    for (int e = tid; e < nd * Mi; e += blockDim.x) {
+        const int m = e / nd, dd = e - m * nd;
+        lout[e] = X[(s + dd) * Mi + m];
+    }
+    for (int dd = tid; dd < nd; dd += blockDim.x) {
+        const int j = s + dd;
+        dcol[d0 + dd] = (long long)col_slot[j] * N + col_cell[j];
+        const double sc = col_scale[j] > 0.0 ? 1.0 / col_scale[j] : 0.0;
+        dsc[d0 + dd] = col_cell[j] == cm ? -sc : sc;
     }
 }
 
@@ -216,10 +254,13 @@ __device__ __forceinline__ size_t iface_row(const int* d, const int* rowinfo, in
     return (size_t)(fp * M2 + rowinfo[fp * M + m]) * N + cp;
 }
 
-// out[r0 + k] = sum_m P[m][k] sign_m y[row_m]: one warp per interface
+// out[r0 + k] = sum_m P[m][k] sign_m y[row_m]: one warp per interface.  With
+// kcol the row goes to slot kcol[r0 + k] instead (slot layout [2M][N]), as
+// bsub - value when bsub is given.
 __global__ void k_atfps_apply(const int* __restrict__ desc, const long long* __restrict__ off,
                               const int* __restrict__ rowinfo, const double* __restrict__ proj, int nif, int M,
-                              int N, const double* __restrict__ y, double* __restrict__ out) {
+                              int N, const double* __restrict__ y, double* __restrict__ out,
+                              const long long* __restrict__ kcol, const double* __restrict__ bsub) {
     __shared__ double yv[8][80];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + w;
@@ -236,7 +277,67 @@ __global__ void k_atfps_apply(const int* __restrict__ desc, const long long* __r
     for (int k = lane; k < s; k += 32) {
         double acc = 0.0;
         for (int m = 0; m < Mi; ++m) acc = fma(P[(size_t)m * s + k], yv[w][m], acc);
-        out[r0 + k] = acc;
+        if (kcol) {
+            const long long q = kcol[r0 + k];
+            out[q] = bsub ? bsub[q] - acc : acc;
+        } else {
+            out[r0 + k] = acc;
+        }
+    }
+}
+
+// Layer coefficients (Eqs. 2DAdaptive_TFPS_layer1 / layer2): w = b - A x of
+// the smooth solution x holds, on the rows of an interface, -(jump); the
+// dropped coordinate beta_d of the jump gives x[dcol] = dsc beta_d (the sign
+// by the function's side).  One warp per interface.
+__global__ void k_atfps_layers(const int* __restrict__ desc, const long long* __restrict__ loff,
+                               const int* __restrict__ rowinfo, const double* __restrict__ lproj,
+                               const long long* __restrict__ dcol, const double* __restrict__ dsc, int nif, int M,
+                               int N, const double* __restrict__ w, double* __restrict__ x) {
+    __shared__ double jv[8][80];
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + wp;
+    if (i >= nif) return;
+    const int* d = desc + 8 * i;
+    const int s = d[4], Mi = d[5], d0 = d[7], nd = Mi - s;
+    if (nd == 0) return;
+    for (int m = lane; m < Mi; m += 32) {
+        double sg;
+        const size_t row = iface_row(d, rowinfo, m, M, N, sg);
+        jv[wp][m] = -sg * w[row];
+    }
+    __syncwarp();
+    const double* P = lproj + loff[i];
+    for (int dd = lane; dd < nd; dd += 32) {
+        double acc = 0.0;
+        for (int m = 0; m < Mi; ++m) acc = fma(P[(size_t)m * nd + dd], jv[wp][m], acc);
+        x[dcol[d0 + dd]] = dsc[d0 + dd] * acc;
+    }
+}
+
+// Right inverse of F (F S = I): y[row_m] = sign_m sum_k E[m][k] r[kcol[r0 + k]]
+// -- each compressed row (in slot layout) back to the rows of its interface
+// as the kept basis column; every row of A is written once.  One warp per
+// interface.
+__global__ void k_atfps_S(const int* __restrict__ desc, const long long* __restrict__ off,
+                          const int* __restrict__ rowinfo, const double* __restrict__ ekeep,
+                          const long long* __restrict__ kcol, int nif, int M, int N, const double* __restrict__ r,
+                          double* __restrict__ y) {
+    __shared__ double rv[8][80];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + w;
+    if (i >= nif) return;
+    const int* d = desc + 8 * i;
+    const int s = d[4], Mi = d[5], r0 = d[6];
+    for (int k = lane; k < s; k += 32) rv[w][k] = r[kcol[r0 + k]];
+    __syncwarp();
+    const double* E = ekeep + off[i];
+    for (int m = lane; m < Mi; m += 32) {
+        double acc = 0.0;
+        for (int k = 0; k < s; ++k) acc = fma(E[(size_t)m * s + k], rv[w][k], acc);
+        double sg;
+        const size_t row = iface_row(d, rowinfo, m, M, N, sg);
+        y[row] = sg * acc;
     }
 }
 
@@ -328,9 +429,9 @@ void atfps_setup(rte_ctx* ctx, double delta) {
             if (rowinfo[f * M + m] >= 0) dirs[f * M2 + rowinfo[f * M + m]] = m;
     // interfaces (order as in the header comment) and their kept counts
     std::vector<int> desc;
-    std::vector<long long> off;
-    long long total = 0;
-    int64_t rows = 0;
+    std::vector<long long> off, loff;
+    long long total = 0, ltotal = 0;
+    int64_t rows = 0, ndrop = 0;
     auto kept_in = [&](int c, int grp) {
         int s = 0;
         for (int q = 0; q < M2; ++q) s += a->mask_h[(size_t)(grp * M2 + q) * N + c];
@@ -338,12 +439,14 @@ void atfps_setup(rte_ctx* ctx, double delta) {
     };
     auto add = [&](int cm, int cp, int fm, int fp) {
         const int s = kept_in(cm, fm) + (cp >= 0 ? kept_in(cp, fp) : 0);
-        if (s == 0) return;
         const int Mi = cp >= 0 ? M : M2;
-        desc.insert(desc.end(), {cm, cp, fm, fp, s, Mi, (int)rows, 0});
+        desc.insert(desc.end(), {cm, cp, fm, fp, s, Mi, (int)rows, (int)ndrop});
         off.push_back(total);
+        loff.push_back(ltotal);
         total += (long long)s * Mi;
+        ltotal += (long long)(Mi - s) * Mi;
         rows += s;
+        ndrop += Mi - s;
     };
     for (int iy = 0; iy < I; ++iy)
         for (int ix = 0; ix + 1 < I; ++ix) add(iy * I + ix, iy * I + ix + 1, 1, 0);
@@ -359,6 +462,7 @@ void atfps_setup(rte_ctx* ctx, double delta) {
     }
     a->nif = (int)off.size();
     a->rows = rows;
+    a->ndrop = ndrop;
     a->mask = atfps_alloc<unsigned char>(ctx, a, a->mask_h.size());
     check(cudaMemcpyAsync(a->mask, a->mask_h.data(), a->mask_h.size(), cudaMemcpyHostToDevice, ctx->stream), "h2d");
     a->singular = atfps_alloc<int>(ctx, a, 1);
@@ -369,6 +473,14 @@ void atfps_setup(rte_ctx* ctx, double delta) {
     a->desc = atfps_alloc<int>(ctx, a, desc.size());
     a->off = atfps_alloc<long long>(ctx, a, off.size());
     a->proj = atfps_alloc<double>(ctx, a, (size_t)total);
+    a->ekeep = atfps_alloc<double>(ctx, a, (size_t)total);
+    a->loff = atfps_alloc<long long>(ctx, a, loff.size());
+    a->lproj = atfps_alloc<double>(ctx, a, (size_t)ltotal);
+    a->kcol = atfps_alloc<long long>(ctx, a, (size_t)rows);
+    a->dcol = atfps_alloc<long long>(ctx, a, (size_t)ndrop);
+    a->dsc = atfps_alloc<double>(ctx, a, (size_t)ndrop);
+    check(cudaMemcpyAsync(a->loff, loff.data(), loff.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                          ctx->stream), "h2d");
     int* d_ord = atfps_alloc<int>(ctx, a, ord.size());
     int* d_dirs = atfps_alloc<int>(ctx, a, dirs.size());
     check(cudaMemcpyAsync(a->desc, desc.data(), desc.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "h2d");
@@ -381,7 +493,9 @@ void atfps_setup(rte_ctx* ctx, double delta) {
     raise_smem_limit((const void*)k_atfps_build, (size_t)(smem));
     // a pivot below 1e-12 of the (unit max-norm) columns: cond(E) beyond ~1e12
     k_atfps_build<<<a->nif, kBuildThreads, smem, ctx->stream>>>(a->desc, a->off, d_ord, d_dirs, ctx->L64, ctx->mat,
-                                                                a->mask, M, N, 1e-12, a->proj, a->singular);
+                                                                a->mask, M, N, 1e-12, a->proj, a->ekeep, a->loff,
+                                                                a->lproj,
+                                                                a->kcol, a->dcol, a->dsc, a->singular);
     check(cudaGetLastError(), "k_atfps_build");
     int bad = 0;
     check(cudaMemcpyAsync(&bad, a->singular, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "d2h");
@@ -397,7 +511,7 @@ void atfps_apply(rte_ctx* ctx, const double* y, double* out) {
     if (!a) throw StatusError{RTE_EINVAL, "no ATFPS filter on this context (rte_atfps_setup)"};
     if (a->nif == 0) return;
     k_atfps_apply<<<(a->nif + 7) / 8, 256, 0, ctx->stream>>>(a->desc, a->off, ctx->rowinfo, a->proj, a->nif, ctx->M,
-                                                             ctx->N, y, out);
+                                                             ctx->N, y, out, nullptr, nullptr);
     check(cudaGetLastError(), "k_atfps_apply");
 }
 
@@ -409,6 +523,62 @@ void atfps_apply_t(rte_ctx* ctx, const double* r, double* y) {
     k_atfps_apply_t<<<(a->nif + 7) / 8, 256, 0, ctx->stream>>>(a->desc, a->off, ctx->rowinfo, a->proj, a->nif,
                                                                ctx->M, ctx->N, r, y);
     check(cudaGetLastError(), "k_atfps_apply_t");
+}
+
+namespace {
+Atfps* need_filter(rte_ctx* ctx) {
+    if (!ctx->atfps) throw StatusError{RTE_EINVAL, "no ATFPS filter on this context (rte_atfps_setup)"};
+    return ctx->atfps;
+}
+
+int grid_for(rte_ctx* ctx, int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8); }
+
+// b_bar and the scratch, once per filter
+void comp_prepare(rte_ctx* ctx) {
+    Atfps* a = need_filter(ctx);
+    if (a->bbar) return;
+    const int64_t n = ctx->n;
+    a->scratch = atfps_alloc<double>(ctx, a, (size_t)n);
+    a->scratch2 = atfps_alloc<double>(ctx, a, (size_t)n);
+    a->bbar = atfps_alloc<double>(ctx, a, (size_t)n);
+    k_atfps_apply<<<(a->nif + 7) / 8, 256, 0, ctx->stream>>>(a->desc, a->off, ctx->rowinfo, a->proj, a->nif, ctx->M,
+                                                             ctx->N, ctx->b, a->bbar, a->kcol, nullptr);
+    check(cudaGetLastError(), "k_atfps_apply");
+}
+}  // namespace
+
+const double* atfps_comp_rhs(rte_ctx* ctx) {
+    comp_prepare(ctx);
+    return ctx->atfps->bbar;
+}
+
+void atfps_comp_precond(rte_ctx* ctx, const double* z, double* out) {
+    Atfps* a = need_filter(ctx);
+    comp_prepare(ctx);
+    k_atfps_S<<<(a->nif + 7) / 8, 256, 0, ctx->stream>>>(a->desc, a->off, ctx->rowinfo, a->ekeep, a->kcol, a->nif,
+                                                         ctx->M, ctx->N, z, a->scratch2);
+    check(cudaGetLastError(), "k_atfps_S");
+    launch_block_apply(ctx, false, a->scratch2, true, out, true);
+    atfps_mask_mul(ctx, out);
+}
+
+void atfps_comp_apply(rte_ctx* ctx, const double* x, double* out, bool residual) {
+    Atfps* a = need_filter(ctx);
+    launch_apply(ctx, true, x, a->scratch, true, nullptr);
+    check(cudaMemsetAsync(out, 0, (size_t)ctx->n * sizeof(double), ctx->stream), "memset");
+    k_atfps_apply<<<(a->nif + 7) / 8, 256, 0, ctx->stream>>>(a->desc, a->off, ctx->rowinfo, a->proj, a->nif, ctx->M,
+                                                             ctx->N, a->scratch, out, a->kcol,
+                                                             residual ? a->bbar : nullptr);
+    check(cudaGetLastError(), "k_atfps_apply");
+}
+
+void atfps_layers(rte_ctx* ctx, double* x) {
+    Atfps* a = need_filter(ctx);
+    comp_prepare(ctx);
+    launch_apply(ctx, true, x, a->scratch, true, ctx->b);        // b - A x
+    k_atfps_layers<<<(a->nif + 7) / 8, 256, 0, ctx->stream>>>(a->desc, a->loff, ctx->rowinfo, a->lproj, a->dcol,
+                                                              a->dsc, a->nif, ctx->M, ctx->N, a->scratch, x);
+    check(cudaGetLastError(), "k_atfps_layers");
 }
 
 void atfps_mask_mul(rte_ctx* ctx, double* x) {

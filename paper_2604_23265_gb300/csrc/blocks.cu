@@ -19,35 +19,14 @@
 namespace rte {
 namespace {
 
-__global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restrict__ mat,
-                                                      const double* __restrict__ tau,
-                                                      const double* __restrict__ xi,
-                                                      const double* __restrict__ L,
-                                                      const int* __restrict__ rowdir,
-                                                      double* __restrict__ Dt,
-                                                      int* __restrict__ singular) {
-    extern __shared__ double smd[];
-    const int n2 = 2 * M, M2 = M / 2, ld = n2 + 1;
-    double* A = smd;                     // [n2][ld]
-    double* fac = A + n2 * ld;           // [n2]
-    double* half = fac + n2;             // [n2]
-    int* perm = reinterpret_cast<int*>(half + n2);   // [n2]
+// In-place Gauss-Jordan inversion with partial pivoting of the n2 x n2 block
+// A (row stride ld) in shared memory by the whole CTA; fac, perm: n2 scratch
+// each.  Row swaps are undone as column swaps.  Returns true (thread 0) when a
+// pivot is zero or not finite.
+__device__ bool gauss_jordan_inplace(double* A, int n2, int ld, double* fac, int* perm) {
     __shared__ int s_piv;
     __shared__ double s_pivval;
-    const int c = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int mc = mat[c];
-    const double t = tau[c];
-    for (int k = tid; k < n2; k += nt) half[k] = exp(-0.5 * t * fabs(xi[(size_t)mc * n2 + k]));
-    __syncthreads();
-    const double* Lm = L + (size_t)mc * M * n2;
-    for (int e = tid; e < n2 * n2; e += nt) {
-        const int r = e / n2, k = e - r * n2;
-        const int f = r / M2, fk = k / M2;
-        const double d = (f == fk) ? 1.0 : ((f == (fk ^ 1)) ? half[k] * half[k] : half[k]);
-        A[r * ld + k] = Lm[(size_t)rowdir[r] * n2 + k] * d;
-    }
-    __syncthreads();
     bool bad = false;
     for (int k = 0; k < n2; ++k) {
         if (tid < 32) {
@@ -103,6 +82,37 @@ __global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restri
         }
         __syncthreads();
     }
+    return bad;
+}
+
+__global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restrict__ mat,
+                                                      const double* __restrict__ tau,
+                                                      const double* __restrict__ xi,
+                                                      const double* __restrict__ L,
+                                                      const int* __restrict__ rowdir,
+                                                      double* __restrict__ Dt,
+                                                      int* __restrict__ singular) {
+    extern __shared__ double smd[];
+    const int n2 = 2 * M, M2 = M / 2, ld = n2 + 1;
+    double* A = smd;                     // [n2][ld]
+    double* fac = A + n2 * ld;           // [n2]
+    double* half = fac + n2;             // [n2]
+    int* perm = reinterpret_cast<int*>(half + n2);   // [n2]
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int mc = mat[c];
+    const double t = tau[c];
+    for (int k = tid; k < n2; k += nt) half[k] = exp(-0.5 * t * fabs(xi[(size_t)mc * n2 + k]));
+    __syncthreads();
+    const double* Lm = L + (size_t)mc * M * n2;
+    for (int e = tid; e < n2 * n2; e += nt) {
+        const int r = e / n2, k = e - r * n2;
+        const int f = r / M2, fk = k / M2;
+        const double d = (f == fk) ? 1.0 : ((f == (fk ^ 1)) ? half[k] * half[k] : half[k]);
+        A[r * ld + k] = Lm[(size_t)rowdir[r] * n2 + k] * d;
+    }
+    __syncthreads();
+    const bool bad = gauss_jordan_inplace(A, n2, ld, fac, perm);
     double* out = Dt + (size_t)c * n2 * n2;
     for (int e = tid; e < n2 * n2; e += nt) {
         const int j = e / n2, i = e - j * n2;

@@ -203,6 +203,16 @@ void atfps_apply_t(rte_ctx* ctx, const double* r, double* y);
 // x [n] (TFPS coefficients, [2M][N]) *= selection mask
 void atfps_mask_mul(rte_ctx* ctx, double* x);
 int64_t atfps_rows(const rte_ctx* ctx);   // -1 without a filter
+// Compressed ATFPS system (Eq. 2DAdaptiveTFPS_linear_sys) in slot layout
+// [2M][N] (a kept row at the slot of its function, zero at dropped slots):
+// b_bar; out = A_bar x or b_bar - A_bar x (FP64); the preconditioner
+// out = mask o D S z (S the right inverse of F: each compressed row as its
+// kept interface basis column); the layer coefficients of Eqs.
+// 2DAdaptive_TFPS_layer1 / layer2 written into x's dropped slots.
+const double* atfps_comp_rhs(rte_ctx* ctx);
+void atfps_comp_apply(rte_ctx* ctx, const double* x, double* out, bool residual);
+void atfps_comp_precond(rte_ctx* ctx, const double* z, double* out);
+void atfps_layers(rte_ctx* ctx, double* x);
 
 // block kernels (blocks.cu) ------------------------------------------------
 // builds G_C for every cell, inverts it into ctx->Dt (FP64) and forms the

@@ -219,6 +219,10 @@ struct Solver {
     int64_t n = 0;
     double bnorm = 0.0, prev_res = -1.0;
     bool use_net = false, first = true, cycle_net = false;
+    // compressed ATFPS system (Eq. 2DAdaptiveTFPS_linear_sys) in slot layout:
+    // operator A_bar (mask o D S), right-hand side b_bar, FP64 throughout, no network
+    bool comp = false;
+    const double* rhs = nullptr;
     int j = 0, k = 0;                 // Arnoldi step in the cycle; columns for the cycle end
     const void* zj = nullptr;
     bool z_double = true;
@@ -237,7 +241,9 @@ struct Solver {
         n = ctx->n;
         gblk = ctx->num_sms * 4;
         if (!opts.use_x0) check(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->stream), "zero x");
-        launch_norm(ctx, ctx->b, ws->est + 2);
+        rhs = ctx->b;
+        if (comp) rhs = atfps_comp_rhs(ctx);
+        launch_norm(ctx, rhs, ws->est + 2);
         bnorm = read_scalar(ctx, ws, ws->est + 2);
         if (bnorm == 0.0) {
             check(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->stream), "zero x");
@@ -252,8 +258,10 @@ struct Solver {
     // true residual in FP64 and the decisions on it; false when the solve ends
     bool cycle_begin() {
         if (first && !opts.use_x0)
-            check(cudaMemcpyAsync(ws->w, ctx->b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+            check(cudaMemcpyAsync(ws->w, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
                   "r = b");
+        else if (comp)
+            atfps_comp_apply(ctx, x, ws->w, true);
         else
             launch_apply(ctx, true, x, ws->w, true, ctx->b);
         first = false;
@@ -305,7 +313,10 @@ struct Solver {
 
     // w = B z_j
     void inner_apply() {
-        if (opts.inner_precision == RTE_F32) {
+        if (comp) {
+            atfps_comp_precond(ctx, static_cast<const double*>(zj), ws->tmp);
+            atfps_comp_apply(ctx, ws->tmp, ws->w, false);
+        } else if (opts.inner_precision == RTE_F32) {
             launch_response_apply(ctx, zj, z_double, ws->w, true);
         } else {
             launch_block_apply(ctx, false, zj, z_double, ws->tmp, true);
@@ -355,7 +366,10 @@ struct Solver {
                     k_lincomb<double><<<gblk, 256, 0, ctx->stream>>>(ws->V, k, n, ws->y, ws->tmp);
                 check(cudaGetLastError(), "k_lincomb");
             }
-            launch_block_apply(ctx, false, ws->tmp, true, ws->w, true);   // D dy
+            if (comp)
+                atfps_comp_precond(ctx, ws->tmp, ws->w);                   // mask o D S dy
+            else
+                launch_block_apply(ctx, false, ws->tmp, true, ws->w, true);   // D dy
             ProfScope ps(ctx, K_XUPDATE, (double)n * 24);
             k_axpy<<<gblk, 256, 0, ctx->stream>>>(x, ws->w, n);
             check(cudaGetLastError(), "k_axpy");
@@ -549,6 +563,55 @@ void group_rounds_step(GroupRounds* r, GroupSolve* const* set, int count) {
 
 void group_rounds_free(GroupRounds* r) { delete r; }
 
+namespace {
+rte_status run_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, double* x_dev, rte_solve_info* info,
+                     bool comp, bool layers) {
+    if (!ctx || !x_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
+    Solver S;
+    S.ctx = ctx;
+    S.pc = pc;
+    S.x = x_dev;
+    S.comp = comp;
+    if (opts_in) S.opts = *opts_in; else rte_solve_opts_default(&S.opts);
+    if (!valid_opts(S.opts)) {
+        set_error(ctx, "bad solve options (restart in [1, 64], tol > 0)");
+        return RTE_EINVAL;
+    }
+    try {
+        if (comp && !ctx->atfps) throw StatusError{RTE_EINVAL, "no ATFPS filter on this context (rte_atfps_setup)"};
+        if (S.start()) {
+            while (S.cycle_begin()) {
+                do {
+                    S.precondition();
+                    S.inner_apply();
+                    S.orthogonalise_step();
+                    check(cudaMemcpyAsync(S.ws->est_host, S.ws->est, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                          ctx->stream), "d2h est");
+                    check(cudaStreamSynchronize(ctx->stream), "step sync");
+                    prof_resolve(ctx);
+                } while (S.after_step(S.ws->est_host[0], S.ws->est_host[1]));
+                S.cycle_end();
+            }
+        }
+        if (comp && layers && (S.status == RTE_OK || S.status == RTE_ENOTCONV)) {
+            atfps_layers(ctx, x_dev);
+            check(cudaStreamSynchronize(ctx->stream), "sync");
+        }
+    } catch (const CudaError& e) {
+        S.status = cuda_status(ctx, e.code, e.where);
+    } catch (const StatusError& e) {
+        set_error(ctx, e.msg);
+        S.status = e.code;
+    } catch (const std::bad_alloc&) {
+        set_error(ctx, "host allocation failed");
+        S.status = RTE_ENOMEM;
+    }
+    S.inf.seconds = S.elapsed_ms() * 1e-3;
+    if (info) *info = S.inf;
+    return S.status;
+}
+}  // namespace
+
 }  // namespace rte
 
 using namespace rte;
@@ -591,45 +654,15 @@ RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev) {
     return RTE_OK;
 }
 
-RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in,
-                             double* x_dev, rte_solve_info* info) {
-    if (!ctx || !x_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
-    Solver S;
-    S.ctx = ctx;
-    S.pc = pc;
-    S.x = x_dev;
-    if (opts_in) S.opts = *opts_in; else rte_solve_opts_default(&S.opts);
-    if (!valid_opts(S.opts)) {
-        set_error(ctx, "bad solve options (restart in [1, 64], tol > 0)");
-        return RTE_EINVAL;
-    }
-    try {
-        if (S.start()) {
-            while (S.cycle_begin()) {
-                do {
-                    S.precondition();
-                    S.inner_apply();
-                    S.orthogonalise_step();
-                    check(cudaMemcpyAsync(S.ws->est_host, S.ws->est, 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                                          ctx->stream), "d2h est");
-                    check(cudaStreamSynchronize(ctx->stream), "step sync");
-                    prof_resolve(ctx);
-                } while (S.after_step(S.ws->est_host[0], S.ws->est_host[1]));
-                S.cycle_end();
-            }
-        }
-    } catch (const CudaError& e) {
-        S.status = cuda_status(ctx, e.code, e.where);
-    } catch (const StatusError& e) {
-        set_error(ctx, e.msg);
-        S.status = e.code;
-    } catch (const std::bad_alloc&) {
-        set_error(ctx, "host allocation failed");
-        S.status = RTE_ENOMEM;
-    }
-    S.inf.seconds = S.elapsed_ms() * 1e-3;
-    if (info) *info = S.inf;
-    return S.status;
+
+RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, double* x_dev,
+                             rte_solve_info* info) {
+    return rte::run_solve(ctx, pc, opts_in, x_dev, info, false, false);
+}
+
+RTE_API rte_status rte_atfps_solve(rte_ctx* ctx, const rte_solve_opts* opts, int layers, double* x_dev,
+                                   rte_solve_info* info) {
+    return rte::run_solve(ctx, nullptr, opts, x_dev, info, true, layers != 0);
 }
 
 RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int count,

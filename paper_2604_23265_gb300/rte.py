@@ -86,6 +86,7 @@ SIGNATURES = {
     "rte_arnoldi_basis": (_I, [_P, _I, _P]),
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "rte_solve": (_I, [_P, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]),
+    "rte_atfps_solve": (_I, [_P, ctypes.POINTER(SolveOpts), _I, _P, ctypes.POINTER(SolveInfo)]),
     "rte_eigenbasis": (_I, [_I, _D, _D, _I, _P, _P]),
     "rte_fp64_fma_rate": (_I, [_P, ctypes.POINTER(_D)]),
     "rte_fp32_fma_rate": (_I, [_P, ctypes.POINTER(_D)]),
@@ -596,6 +597,25 @@ class Context:
         pcp = pc.ptr if pc is not None else None
         st = load().rte_solve(self.ptr, pcp, ctypes.byref(o), _dev(x, torch.float64, self.n),
                               ctypes.byref(inf))
+        d = inf.as_dict()
+        d["status"] = STATUS_NAMES[st] if 0 <= st < 10 else st
+        if raise_on_error and st not in (RTE_OK, RTE_ENOTCONV):
+            _check(st, self.ptr)
+        return d
+
+    def atfps_solve(self, x, layers=True, tol=1e-8, restart=50, max_iter=20000, use_x0=False, timeout_ms=0.0,
+                    raise_on_error=True):
+        """Compressed ATFPS solve (rte_atfps_solve) after atfps_setup(delta):
+        x (float64 [2M][N] device) receives the kept coefficients and, with
+        layers, the reconstructed dropped ones."""
+        import torch
+        o = SolveOpts()
+        load().rte_solve_opts_default(ctypes.byref(o))
+        o.tol, o.restart, o.max_iter = float(tol), int(restart), int(max_iter)
+        o.use_x0, o.timeout_ms = int(use_x0), float(timeout_ms)
+        inf = SolveInfo()
+        st = load().rte_atfps_solve(self.ptr, ctypes.byref(o), 1 if layers else 0, _dev(x, torch.float64, self.n),
+                                    ctypes.byref(inf))
         d = inf.as_dict()
         d["status"] = STATUS_NAMES[st] if 0 <= st < 10 else st
         if raise_on_error and st not in (RTE_OK, RTE_ENOTCONV):
