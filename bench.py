@@ -248,7 +248,10 @@ def run_precond_only(args):
     torch.cuda.set_device(0)
     md = W.grf_diffusive(seed=0, I=args.size, M=args.dirs)
     ctx = rte.Context.from_medium(md)
-    net = rte.MgNet(train.default_shape(md.M, md.I))
+    shape = train.default_shape(md.M, md.I, c0=args.c0, cmax=args.cmax)
+    if args.levels > 0:
+        shape.levels = args.levels
+    net = rte.MgNet(shape)
     net.set_params(W.init_params(net.shape, seed=0, proj_scale=0.01, vcycle_scale=0.5))
     v = torch.tensor(W.random_vector(ctx.n, 1), device="cuda")
     v /= v.norm()
@@ -262,7 +265,28 @@ def run_precond_only(args):
     ev1.record()
     torch.cuda.synchronize()
     print(json.dumps({"mode": "precond_only", "I": md.I, "M": md.M, "levels": net.shape.levels,
+                      "c0": net.shape.c0, "cmax": net.shape.cmax,
                       "ms_per_application": ev0.elapsed_time(ev1) / args.precond_only}), flush=True)
+
+
+def run_setup_only(args):
+    """Profiling mode: time the context set-up (rte_setup from host arrays:
+    tables, right-hand side, per-cell block inversion and response matrices)
+    args.setup_only times on the workload's medium."""
+    import torch
+    from paper_2604_23265_gb300 import rte
+    torch.cuda.set_device(0)
+    md = W.grf_diffusive(seed=0, I=args.size, M=args.dirs)
+    times = []
+    for _ in range(args.setup_only + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = rte.Context.from_medium(md)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        ctx.close()
+    print(json.dumps({"mode": "setup_only", "I": md.I, "M": md.M, "seconds_per_setup": float(np.mean(times[1:])),
+                      "first_seconds": times[0]}), flush=True)
 
 
 def run_ours(args):
@@ -337,18 +361,23 @@ def run_ours(args):
     h2d = sum(a.nbytes for a in hs)
     psi_host = torch.empty(md.M * md.I * md.I, dtype=torch.float64).pin_memory()
     d2h = psi_host.numel() * 8
-    e2e_times = []
+    e2e_times, e2e_parts = [], []
     for _ in range(0 if args.no_e2e else args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = rte.Context(md.I, md.M, hs[0], hs[1], hs[2], hs[3], md.g, hs[4], stream=stream)
         x2 = torch.zeros(c2.n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         i2 = c2.solve(x2, pc=net, **opts)
+        t2 = time.perf_counter()
         psi = torch.empty(md.M * md.I * md.I, dtype=torch.float64, device="cuda")
         c2.reconstruct(x2, psi)
         psi_host.copy_(psi, non_blocking=True)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        e2e_times.append(t3 - t0)
+        e2e_parts.append((t1 - t0, t2 - t1, t3 - t2))
         c2.close()
         converged = converged and bool(i2["converged"])
     e2e_s = _max_over_ranks(world, sum(e2e_times)) if e2e_times else float("nan")
@@ -366,7 +395,11 @@ def run_ours(args):
         "fell_back": bool(infos[-1]["fell_back"]),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "seconds_per_step": ({"setup": float(np.mean([p[0] for p in e2e_parts])),
+                                      "solve": float(np.mean([p[1] for p in e2e_parts])),
+                                      "reconstruct_and_copy": float(np.mean([p[2] for p in e2e_parts]))}
+                                     if e2e_parts else None)},
         "roofline": roof,
         "kernels": kernels,
         "clocks": clocks,
@@ -700,6 +733,10 @@ def main():
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--setup-only", type=int, default=0,
+                    help="profiling only: time the context set-up this many times and exit")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="profiling only (--precond-only): network depth (0: the grid's default)")
     ap.add_argument("--train-seed", type=int, default=0, help="seed of the weights and input draws")
     ap.add_argument("--paper-protocol", action="store_true",
                     help="the paper's 32x32x4 polynomial-media experiment (plain vs filtered loss vs block Jacobi)")
@@ -724,6 +761,8 @@ def main():
         run_reference(args)
     elif args.precond_only > 0:
         run_precond_only(args)
+    elif args.setup_only > 0:
+        run_setup_only(args)
     elif args.paper_protocol:
         run_paper_protocol(args)
     else:
