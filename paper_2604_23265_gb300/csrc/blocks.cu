@@ -27,6 +27,7 @@ __device__ bool gauss_jordan_inplace(double* A, int n2, int ld, double* fac, int
     __shared__ int s_piv;
     __shared__ double s_pivval;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int R = nt >= n2 ? nt / n2 : 1;          // row classes per column
     bool bad = false;
     for (int k = 0; k < n2; ++k) {
         if (tid < 32) {
@@ -63,11 +64,18 @@ __device__ bool gauss_jordan_inplace(double* A, int n2, int ld, double* fac, int
         }
         for (int i = tid; i < n2; i += nt) fac[i] = (i == k) ? 0.0 : A[i * ld + k];
         __syncthreads();
-        for (int e = tid; e < n2 * n2; e += nt) {
-            const int i = e / n2, j = e - i * n2;
-            if (i == k) continue;
-            const double base = (j == k) ? 0.0 : A[i * ld + j];
-            A[i * ld + j] = fma(-fac[i], A[k * ld + j], base);
+        // thread: column j, rows r0, r0 + R, ...; the pivot row's entry stays
+        // in a register, a warp covers consecutive columns of one row
+        for (int c0 = tid; c0 < R * n2; c0 += nt) {
+            const int j = c0 % n2, r0 = c0 / n2;
+            const double pk = A[k * ld + j];
+            const bool jk = (j == k);
+#pragma unroll 8
+            for (int i = r0; i < n2; i += R) {
+                if (i == k) continue;
+                const double base = jk ? 0.0 : A[i * ld + j];
+                A[i * ld + j] = fma(-fac[i], pk, base);
+            }
         }
         __syncthreads();
     }
@@ -85,7 +93,7 @@ __device__ bool gauss_jordan_inplace(double* A, int n2, int ld, double* fac, int
     return bad;
 }
 
-__global__ void __launch_bounds__(256) k_build_invert(int M, const int* __restrict__ mat,
+__global__ void __launch_bounds__(512) k_build_invert(int M, const int* __restrict__ mat,
                                                       const double* __restrict__ tau,
                                                       const double* __restrict__ xi,
                                                       const double* __restrict__ L,
@@ -368,10 +376,13 @@ void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
     const int M = ctx->M, n2 = 2 * M;
     const size_t smem = sizeof(double) * ((size_t)n2 * (n2 + 1) + 3 * n2);
     raise_smem_limit((const void*)k_build_invert, (size_t)(smem));
+    // one CTA per SM fits (the block is 2M x (2M+1) doubles): 16 warps hide
+    // the shared-memory and FP64 latencies of the elimination
+    const int threads_inv = n2 >= 128 ? 512 : (n2 >= 64 ? 256 : 128);
     const int threads = n2 >= 64 ? 256 : 128;
     {
         ProfScope ps(ctx, K_INVERT, (double)ctx->N * n2 * n2 * 8);
-        k_build_invert<<<ctx->N, threads, smem, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi,
+        k_build_invert<<<ctx->N, threads_inv, smem, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi,
                                                                ctx->L64, ctx->rowdir, ctx->Dt,
                                                                singular_dev);
         check(cudaGetLastError(), "k_build_invert");
