@@ -648,45 +648,57 @@ def atfps_leg(deltas=(1e-2, 1e-3), I=64, M=16, seed=5):
 
 
 def run_paper_protocol(args):
-    """The paper's own setting (Sec. 4.1-4.2): 32 x 32 cells, M = 4 directions,
-    polynomial media with eps = 0.01 (c + 0.1).  A network is trained on
-    args.pp_train media with the plain loss and another with the ATFPS-filtered
-    loss (delta = 1e-2); both precondition FGMRES(50) to 1e-8 on 10 unseen
-    media, beside block Jacobi.  Prints one JSON line of iteration counts."""
+    """The paper's own experiments (Sec. 4): 32 x 32 cells, M = 4 directions,
+    polynomial media, in the diffusion (eps = 0.01 (c + 0.1)), transport
+    (eps = 1) and sharp-interface (six layouts mixing the two) regimes.  Per
+    regime, args.pp_train media split 4:1 into training and validation media;
+    a network is trained with the plain loss and another with the ATFPS-
+    filtered loss (delta = 1e-2), the validation loss followed at twelve
+    checkpoints; both precondition FGMRES(50) to 1e-8 on 10 unseen media,
+    beside block Jacobi.  Prints one JSON line."""
     import torch
     from paper_2604_23265_gb300 import rte, train
     torch.cuda.set_device(0)
-    train_media = [W.polynomial_diffusion(s) for s in range(args.pp_train)]
-    test_media = [W.polynomial_diffusion(10000 + s) for s in range(10)]
+    regimes = ["diffusion", "transport", "interface"] if args.pp_regimes == "all" else args.pp_regimes.split(",")
     out = {"mode": "paper_protocol",
-           "workload": ("32x32 cells, M=4, polynomial sigma_T, sigma_a (degree 1-4), eps=0.01(c+0.1), q=1, "
-                        "zero inflow; FGMRES(50) to rel-res 1e-8"),
-           "train_media": args.pp_train, "train_steps": args.pp_steps}
+           "workload": ("32x32 cells, M=4, polynomial sigma_T, sigma_a (degree 1-4), q=1, zero inflow; eps by "
+                        "regime; FGMRES(50) to rel-res 1e-8"),
+           "media_per_regime": args.pp_train, "train_val_split": "4:1", "train_steps": args.pp_steps,
+           "interface_layouts": list(W.INTERFACE_LAYOUTS)}
+    for regime in regimes:
+        media = [W.polynomial_medium(s, regime) for s in range(args.pp_train)]
+        n_val = max(1, len(media) // 5)
+        train_media, val_media = media[n_val:], media[:n_val]
+        test_media = [W.polynomial_medium(10000 + s, regime) for s in range(10)]
 
-    def solve_all(net):
-        its, fell = [], []
-        for md in test_media:
-            ctx = rte.Context.from_medium(md)
-            x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
-            info = ctx.solve(x, pc=net, tol=1e-8, restart=50)
-            its.append(info["iterations"] if info["converged"] else None)
-            fell.append(bool(info["fell_back"]))
-            ctx.close()
-        return its, fell
+        def solve_all(net):
+            its, fell = [], []
+            for md in test_media:
+                ctx = rte.Context.from_medium(md)
+                x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+                info = ctx.solve(x, pc=net, tol=1e-8, restart=50)
+                its.append(info["iterations"] if info["converged"] else None)
+                fell.append(bool(info["fell_back"]))
+                ctx.close()
+            return its, fell
 
-    bj, _ = solve_all(None)
-    out["block_jacobi_iterations"] = bj
-    for loss in ("plain", "filtered"):
-        net, ctxs, losses, secs = train.train_for(train_media, steps=args.pp_steps, batch=8, lr0=3e-3, seed=0,
-                                                  n_krylov=16, n_smooth=16, loss=loss, delta=1e-2)
-        for c in ctxs:
-            c.close()
-        its, fell = solve_all(net)
-        ratio = [b / i for b, i in zip(bj, its) if b and i]
-        out[loss] = {"iterations": its, "fell_back": fell, "train_seconds": secs,
-                     "final_loss": float(np.mean(losses[-20:])),
-                     "mean_bj_over_mgnet": float(np.mean(ratio)) if ratio else None}
-        net.close()
+        bj, _ = solve_all(None)
+        res = {"block_jacobi_iterations": bj}
+        for loss in ("plain", "filtered"):
+            curve = []
+            net, ctxs, losses, secs = train.train_for(train_media, steps=args.pp_steps, batch=8, lr0=3e-3, seed=0,
+                                                      n_krylov=16, n_smooth=16, loss=loss, delta=1e-2,
+                                                      val_media=val_media, val_every=max(1, args.pp_steps // 12),
+                                                      curve=curve)
+            for c in ctxs:
+                c.close()
+            its, fell = solve_all(net)
+            ratio = [b / i for b, i in zip(bj, its) if b and i]
+            res[loss] = {"iterations": its, "fell_back": fell, "fallback_rate": float(np.mean(fell)),
+                         "train_seconds": secs, "final_loss": float(np.mean(losses[-20:])),
+                         "mean_bj_over_mgnet": float(np.mean(ratio)) if ratio else None, "curve": curve}
+            net.close()
+        out[regime] = res
     print(json.dumps(out), flush=True)
 
 
@@ -742,6 +754,8 @@ def main():
                     help="the paper's 32x32x4 polynomial-media experiment (plain vs filtered loss vs block Jacobi)")
     ap.add_argument("--pp-train", type=int, default=256, help="training media of --paper-protocol")
     ap.add_argument("--pp-steps", type=int, default=6000, help="training steps of --paper-protocol")
+    ap.add_argument("--pp-regimes", default="all",
+                    help="--paper-protocol regimes: all, or a comma list of diffusion, transport, interface")
     ap.add_argument("--c0", type=int, default=16, help="network width at the finest level")
     ap.add_argument("--cmax", type=int, default=64, help="largest network width")
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],

@@ -45,13 +45,16 @@ def training_inputs(ctx, md, n_krylov=32, n_smooth=32, seed=0, noise=0.1):
     return out
 
 
-def train(net, ctxs, inputs, steps=600, batch=8, lr0=3e-3, seed=0, log=None):
+def train(net, ctxs, inputs, steps=600, batch=8, lr0=3e-3, seed=0, log=None, checkpoint=None, every=0):
     """Adam + cosine annealing; each step draws one medium and `batch` of its
-    inputs.  Returns the list of batch losses."""
+    inputs.  checkpoint(step, net, losses) is called every `every` steps and
+    after the last one.  Returns the list of batch losses."""
     rng = np.random.default_rng(seed)
     losses = []
     t0 = time.time()
     for it in range(steps):
+        if checkpoint is not None and every > 0 and it % every == 0:
+            checkpoint(it, net, losses)
         lr = 0.5 * lr0 * (1.0 + math.cos(math.pi * it / steps))
         m = int(rng.integers(len(ctxs)))
         pool = inputs[m]
@@ -60,6 +63,8 @@ def train(net, ctxs, inputs, steps=600, batch=8, lr0=3e-3, seed=0, log=None):
         losses.append(loss)
         if log is not None and (it % 100 == 0 or it == steps - 1):
             log(f"step {it} loss {loss:.4f} lr {lr:.2e} {time.time() - t0:.1f}s")
+    if checkpoint is not None and every > 0:
+        checkpoint(steps, net, losses)
     return losses
 
 
@@ -70,8 +75,15 @@ def default_shape(M, I, c0=16, cmax=64):
     return workloads.NetShape(M=M, levels=levels, c0=c0, cmax=cmax, cc=8, ccmax=32, act="linear")
 
 
+def validation_loss(net, ctxs, inputs, batch=8):
+    """Mean loss of the network (no update) over held-out media, `batch`
+    inputs of each."""
+    vals = [net.loss_grad(c, inp[:batch])[0] for c, inp in zip(ctxs, inputs)]
+    return float(np.mean(vals))
+
+
 def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_smooth=32, seed=0,
-              log=None, loss="plain", delta=1e-2):
+              log=None, loss="plain", delta=1e-2, val_media=None, val_every=0, curve=None):
     """Create a network for the media's (I, M), generate inputs and train it
     with the plain loss (Eq. loss) or the ATFPS-filtered one (Eq. loss_delta,
     selection threshold delta).  Returns (net, contexts, losses, seconds)."""
@@ -89,5 +101,23 @@ def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_sm
         raise ValueError("loss is 'plain' or 'filtered'")
     inputs = [training_inputs(c, md, n_krylov, n_smooth, seed + 17 * i)
               for i, (c, md) in enumerate(zip(ctxs, media))]
-    losses = train(net, ctxs, inputs, steps, batch, lr0, seed, log)
+    check = None
+    vctx = []
+    if val_media:
+        # held-out media (the paper's validation split): the same loss, no update
+        vctx = [rte.Context.from_medium(md) for md in val_media]
+        if loss == "filtered":
+            for c in vctx:
+                c.atfps_setup(delta)
+        vin = [training_inputs(c, md, n_krylov, n_smooth, seed + 7919 + 17 * i)
+               for i, (c, md) in enumerate(zip(vctx, val_media))]
+
+        def check(it, n, so_far):
+            recent = so_far[-val_every:]
+            if curve is not None:
+                curve.append({"step": it, "train_loss": float(np.mean(recent)) if recent else None,
+                              "val_loss": validation_loss(n, vctx, vin, batch)})
+    losses = train(net, ctxs, inputs, steps, batch, lr0, seed, log, checkpoint=check, every=val_every)
+    for c in vctx:
+        c.close()
     return net, ctxs, losses, time.time() - t0

@@ -159,10 +159,18 @@ def mixed_instance(seed: int, grids=(64, 128, 256), dirs=(16, 32),
                   zero_inflow(I, M))
 
 
-def polynomial_diffusion(seed: int, I: int = 32, M: int = 4) -> Medium:
-    """Paper-shaped instance (Sec. 4.1-4.2): polynomial sigma_T and sigma_a of
-    degree n ~ {1..4}, sigma_T shifted so sigma_T - sigma_a >= 0.2,
-    eps = 0.01 (c + 0.1) with c ~ U[0, 1], q = 1, zero inflow."""
+INTERFACE_LAYOUTS = ("diffusion left, transport right", "transport left, diffusion right",
+                     "diffusion bottom, transport top", "transport bottom, diffusion top",
+                     "diffusion in [0.25, 0.75]^2, transport outside", "transport in [0.25, 0.75]^2, diffusion outside")
+
+
+def polynomial_medium(seed: int, regime: str = "diffusion", I: int = 32, M: int = 4, layout=None) -> Medium:
+    """Paper-shaped instance (Sec. 4.1): polynomial sigma_T and sigma_a of
+    degree n ~ {1..4}, sigma_T shifted so sigma_T - sigma_a >= 0.2, q = 1,
+    zero inflow, and eps by regime: diffusion eps = 0.01 (c + 0.1), c ~ U[0, 1];
+    transport eps = 1; interface: the diffusion eps on one part of the square
+    and 1 on the rest, in one of the six layouts of INTERFACE_LAYOUTS (by cell
+    centre; layout = seed mod 6 unless given)."""
     rng = np.random.default_rng(20260 + seed)
     n = int(rng.integers(1, 5))
     sT = polynomial_coefficient(I, rng, n)
@@ -170,9 +178,27 @@ def polynomial_diffusion(seed: int, I: int = 32, M: int = 4) -> Medium:
     gap = np.min(sT - sa)
     if gap < 0.2:
         sT = sT + (0.2 - gap)
-    eps = 0.01 * (rng.uniform(0.0, 1.0) + 0.1)
+    eps_d = 0.01 * (rng.uniform(0.0, 1.0) + 0.1)
     N = I * I
-    return Medium(I, M, sT, sa, np.ones(N), np.full(N, eps), 0.0, zero_inflow(I, M))
+    if regime == "diffusion":
+        eps = np.full(N, eps_d)
+    elif regime == "transport":
+        eps = np.ones(N)
+    elif regime == "interface":
+        lay = seed % 6 if layout is None else int(layout)
+        xc = (np.arange(I) + 0.5) / I
+        X, Y = np.meshgrid(xc, xc)                  # X[iy, ix], cell iy * I + ix
+        box = (np.abs(X - 0.5) < 0.25) & (np.abs(Y - 0.5) < 0.25)
+        diff = [X < 0.5, X >= 0.5, Y < 0.5, Y >= 0.5, box, ~box][lay]
+        eps = np.where(diff.ravel(), eps_d, 1.0)
+    else:
+        raise ValueError("regime is diffusion, transport or interface")
+    return Medium(I, M, sT, sa, np.ones(N), eps, 0.0, zero_inflow(I, M))
+
+
+def polynomial_diffusion(seed: int, I: int = 32, M: int = 4) -> Medium:
+    """The diffusion-regime paper-shaped instance (polynomial_medium)."""
+    return polynomial_medium(seed, "diffusion", I, M)
 
 
 def random_vector(n: int, seed: int) -> np.ndarray:

@@ -269,3 +269,26 @@ def test_full_size_diffusive_apply_matches_oracle(lib):
     b = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
     ctx.rhs(b)
     np.testing.assert_allclose(b.cpu().numpy(), p.rhs().ravel(), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("layout,M", [(0, 4), (3, 8), (4, 4), (5, 8)])
+def test_sharp_interface_media_match_oracle(lib, layout, M):
+    """Per-cell eps (the paper's sharp-interface media: eps = 1 on one part of
+    the square, 0.01 (c + 0.1) on the rest, every cell its own material): the
+    FP64 apply to 1e-12 and the solution to the oracle's dense LU."""
+    md = W.polynomial_medium(40 + layout, "interface", I=16, M=M, layout=layout)
+    md.inflow = W.random_inflow(md.I, M, layout + 3)
+    assert 0 < (md.eps < 1).mean() < 1
+    p, ctx = _oracle(md), _gpu(md)
+    x = W.random_vector(ctx.n, 11)
+    y = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.apply(_t(x), y)
+    ref = p.apply(x.reshape(2 * M, -1)).ravel()
+    assert _rel(y.cpu().numpy(), ref) <= 1e-12 + 2.0 ** -52 / p.omg.min()
+    xs = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(xs, tol=1e-11, restart=40)
+    assert info["converged"], info
+    xl = krylov.dense_solve(p.assemble(), p.rhs().ravel())
+    psi = torch.zeros(M * md.I * md.I, dtype=torch.float64, device="cuda")
+    ctx.reconstruct(xs, psi)
+    assert _rel(psi.cpu().numpy(), p.reconstruct(xl.reshape(2 * M, -1)).ravel()) <= 1e-8
