@@ -422,6 +422,8 @@ def run_ours(args):
     ctx.close()
     if rank == 0 and world == 1 and not args.no_atfps:
         out["atfps"] = atfps_leg()
+    if rank == 0 and world == 1 and not args.no_pcg:
+        out["per_cell_gamma"] = per_cell_gamma_leg(net)
     if rank == 0 and world == 1 and (args.serve > 0 or args.batch > 0):
         nets, mixed_train_s = train_mixed_nets(args.mixed_train_steps)
         out["mixed_networks"] = {"M": list(nets), "train_seconds": mixed_train_s,
@@ -647,6 +649,43 @@ def atfps_leg(deltas=(1e-2, 1e-3), I=64, M=16, seed=5):
     return out
 
 
+PCG_WORKLOAD = ("256 x 256 cells, M = 64, eps = 1e-3, g = 0.5, sigma_T = exp(GRF, ell = 0.1), sigma_a / sigma_T = "
+                "0.05 exp(0.5 GRF') (a second field: every cell its own 1 - gamma, 65,536 materials), q = 1 on the "
+                "central square; FGMRES(50) to rel-res 1e-8")
+
+
+def per_cell_gamma_leg(net=None):
+    """A medium whose scattering ratio varies from cell to cell (the paper's
+    independent sigma_T and sigma_a fields) at the benchmark size: set-up time
+    with the batched device eigenbases, block-Jacobi solve, and the benchmark
+    network (trained on uniform-ratio media) as an out-of-distribution check."""
+    import torch
+    from paper_2604_23265_gb300 import rte
+    I, M = 256, 64
+    base = W.grf_diffusive(seed=0, I=I, M=M)
+    rho = 0.05 * np.exp(0.5 * W.gaussian_field(I, 0.1, 977))
+    md = W.Medium(I, M, base.sigma_T, rho * base.sigma_T, base.q, base.eps, base.g, base.inflow)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = rte.Context.from_medium(md)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    out = {"workload": PCG_WORKLOAD, "materials": ctx.info()["nmat"], "setup_seconds": t_setup}
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    for name, pc in (("block_jacobi", None), ("benchmark_network", net)):
+        if name == "benchmark_network" and net is None:
+            continue
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inf = ctx.solve(x, pc=pc, tol=1e-8, raise_on_error=False)
+        torch.cuda.synchronize()
+        out[name] = {"iterations": inf["iterations"], "seconds": time.perf_counter() - t0,
+                     "converged": bool(inf["converged"]), "fell_back": bool(inf["fell_back"])}
+    ctx.close()
+    return out
+
+
 def run_paper_protocol(args):
     """The paper's own experiments (Sec. 4): 32 x 32 cells, M = 4 directions,
     polynomial media, in the diffusion (eps = 0.01 (c + 0.1)), transport
@@ -766,6 +805,7 @@ def main():
     ap.add_argument("--serve", type=int, default=20,
                     help="requests of the serving leg (p50/p99 latency); 0 skips it")
     ap.add_argument("--no-atfps", action="store_true", help="skip the compressed ATFPS leg")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the per-cell scattering-ratio leg")
     ap.add_argument("--mixed-train-steps", type=int, default=1500,
                     help="training steps of each per-M network of the serving and grouped legs")
     ap.add_argument("--size", type=int, default=256, help="profiling only: grid side")

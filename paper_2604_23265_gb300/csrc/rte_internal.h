@@ -14,6 +14,7 @@ namespace rte {
 constexpr int kMaxKrylov = 64;      // largest restart (vectors orthogonalised against)
 constexpr int kRedThreads = 256;    // block size of the reduction kernels
 constexpr int kScal = 256;          // small device scalars per context
+constexpr int kHostEigenMaterials = 16;   // more materials: eigenbases on the device
 
 struct Workspace;                   // Krylov buffers of rte_solve (solve.cu)
 struct Atfps;                       // ATFPS loss filter of a context (atfps.cu)
@@ -203,6 +204,13 @@ void atfps_apply_t(rte_ctx* ctx, const double* r, double* y);
 // x [n] (TFPS coefficients, [2M][N]) *= selection mask
 void atfps_mask_mul(rte_ctx* ctx, double* x);
 int64_t atfps_rows(const rte_ctx* ctx);   // -1 without a filter
+// Eigenbases of many materials on the device (eigen.cu): xi [nmat][2M], L64
+// [nmat][M][2M] and its copies Lt64 [nmat][2M][M], Lt32, L32, from the
+// materials' 1 - gamma, the HG matrix K [M][M] and the direction cosines.
+void device_eigenbases(rte_ctx* ctx, const std::vector<double>& omg, const std::vector<double>& K,
+                       const std::vector<double>& cdir, const std::vector<double>& sdir, double* xi_dev,
+                       double* L64_dev, double* Lt64_dev, float* Lt32_dev, float* L32_dev);
+
 // Compressed ATFPS system (Eq. 2DAdaptiveTFPS_linear_sys) in slot layout
 // [2M][N] (a kept row at the slot of its function, zero at dropped slots):
 // b_bar; out = A_bar x or b_bar - A_bar x (FP64); the preconditioner

@@ -387,9 +387,13 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     ctx->mat_h.resize(N);
     for (int c = 0; c < N; ++c) ctx->mat_h[c] = mats[omg[c]];
     const int n2 = 2 * M;
+    // many materials (1 - gamma varying from cell to cell): the eigenbases are
+    // computed on the device, batched; a few: on the host
+    const bool dev_eig = ctx->nmat > kHostEigenMaterials;
     ctx->xi_h.assign((size_t)ctx->nmat * n2, 0.0);
-    ctx->L_h.assign((size_t)ctx->nmat * M * n2, 0.0);
+    if (!dev_eig) ctx->L_h.assign((size_t)ctx->nmat * M * n2, 0.0);
     for (auto& kv : mats) {
+        if (dev_eig) break;
         std::vector<double> xx, Lx, xy, Ly;
         eigenbasis(M, std::min(kv.first, 1.0), K, cdir, 0, xx, Lx);
         eigenbasis(M, std::min(kv.first, 1.0), K, sdir, 1, xy, Ly);
@@ -424,26 +428,47 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
             rowdir[f * M2 + j] = dirs[f][j];
         }
     }
-    std::vector<double> Lt64((size_t)ctx->nmat * n2 * M);
-    std::vector<float> Lt32(Lt64.size()), L32(ctx->L_h.size());
-    for (int j = 0; j < ctx->nmat; ++j)
-        for (int m = 0; m < M; ++m)
-            for (int k = 0; k < n2; ++k) {
-                const double v = ctx->L_h[((size_t)j * M + m) * n2 + k];
-                Lt64[((size_t)j * n2 + k) * M + m] = v;
-                Lt32[((size_t)j * n2 + k) * M + m] = (float)v;
-                L32[((size_t)j * M + m) * n2 + k] = (float)v;
-            }
     std::vector<double> infl((size_t)4 * I * M, 0.0);
     if (inflow) std::memcpy(infl.data(), inflow, infl.size() * sizeof(double));
     ctx->mat = upload(ctx, ctx->mat_h);
     ctx->tau = upload(ctx, tau);
     ctx->chis = upload(ctx, chis);
-    ctx->xi = upload(ctx, ctx->xi_h);
-    ctx->L64 = upload(ctx, ctx->L_h);
-    ctx->L32 = upload(ctx, L32);
-    ctx->Lt64 = upload(ctx, Lt64);
-    ctx->Lt32 = upload(ctx, Lt32);
+    if (dev_eig) {
+        const size_t nb = (size_t)ctx->nmat * M * n2;
+        ctx->xi = static_cast<double*>(dev_alloc(ctx, ctx->xi_h.size() * sizeof(double)));
+        ctx->L64 = static_cast<double*>(dev_alloc(ctx, nb * sizeof(double)));
+        ctx->Lt64 = static_cast<double*>(dev_alloc(ctx, nb * sizeof(double)));
+        ctx->Lt32 = static_cast<float*>(dev_alloc(ctx, nb * sizeof(float)));
+        ctx->L32 = static_cast<float*>(dev_alloc(ctx, nb * sizeof(float)));
+        std::vector<double> omv(ctx->nmat);
+        for (auto& kv : mats) omv[kv.second] = std::min(kv.first, 1.0);
+        device_eigenbases(ctx, omv, K, cdir, sdir, ctx->xi, ctx->L64, ctx->Lt64, ctx->Lt32, ctx->L32);
+        check(cudaMemcpyAsync(ctx->xi_h.data(), ctx->xi, ctx->xi_h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                              ctx->stream), "d2h xi");
+        check(cudaStreamSynchronize(ctx->stream), "sync");
+        for (int j = 0; j < ctx->nmat; ++j)
+            for (int k = 0; k < M2; ++k) {
+                const double* x = &ctx->xi_h[(size_t)j * n2];
+                if (!(x[k] < 0 && x[M2 + k] > 0 && x[M + k] < 0 && x[M + M2 + k] > 0))
+                    throw StatusError{RTE_ESINGULAR, "eigenvalue inertia is not M/2 negative, M/2 positive"};
+            }
+    } else {
+        std::vector<double> Lt64((size_t)ctx->nmat * n2 * M);
+        std::vector<float> Lt32(Lt64.size()), L32(ctx->L_h.size());
+        for (int j = 0; j < ctx->nmat; ++j)
+            for (int m = 0; m < M; ++m)
+                for (int k = 0; k < n2; ++k) {
+                    const double v = ctx->L_h[((size_t)j * M + m) * n2 + k];
+                    Lt64[((size_t)j * n2 + k) * M + m] = v;
+                    Lt32[((size_t)j * n2 + k) * M + m] = (float)v;
+                    L32[((size_t)j * M + m) * n2 + k] = (float)v;
+                }
+        ctx->xi = upload(ctx, ctx->xi_h);
+        ctx->L64 = upload(ctx, ctx->L_h);
+        ctx->L32 = upload(ctx, L32);
+        ctx->Lt64 = upload(ctx, Lt64);
+        ctx->Lt32 = upload(ctx, Lt32);
+    }
     ctx->rowinfo = upload(ctx, rowinfo);
     ctx->rowdir = upload(ctx, rowdir);
     ctx->inflow = upload(ctx, infl);
@@ -601,7 +626,15 @@ RTE_API rte_status rte_reconstruct(rte_ctx* ctx, const double* x_dev, double* ps
 RTE_API rte_status rte_export_basis(const rte_ctx* ctx, double* xi, double* L, int* mat_id) {
     if (!ctx) { set_error(nullptr, "NULL ctx"); return RTE_EINVAL; }
     if (xi) std::memcpy(xi, ctx->xi_h.data(), ctx->xi_h.size() * sizeof(double));
-    if (L) std::memcpy(L, ctx->L_h.data(), ctx->L_h.size() * sizeof(double));
+    if (L && !ctx->L_h.empty()) {
+        std::memcpy(L, ctx->L_h.data(), ctx->L_h.size() * sizeof(double));
+    } else if (L) {                      // bases computed on the device
+        const size_t nb = (size_t)ctx->nmat * ctx->M * 2 * ctx->M;
+        if (cudaMemcpy(L, ctx->L64, nb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error(nullptr, "cudaMemcpy (bases)");
+            return RTE_ECUDA;
+        }
+    }
     if (mat_id) std::memcpy(mat_id, ctx->mat_h.data(), ctx->mat_h.size() * sizeof(int));
     return RTE_OK;
 }
