@@ -531,8 +531,6 @@ Atfps* need_filter(rte_ctx* ctx) {
     return ctx->atfps;
 }
 
-int grid_for(rte_ctx* ctx, int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8); }
-
 // b_bar and the scratch, once per filter
 void comp_prepare(rte_ctx* ctx) {
     Atfps* a = need_filter(ctx);

@@ -19,7 +19,6 @@ namespace rte {
 namespace nn {
 namespace {
 
-constexpr int kTileCo = 64;      // output channels per CTA
 constexpr int kTileG = 8;        // 8 x 8 class-grid pixels per CTA
 constexpr int kChunk = 8;        // input channels staged per pass
 constexpr int kMaxPatch = 20;    // staged patch side of the weight-gradient tile

@@ -154,12 +154,6 @@ __global__ void k_backsub(int k, int m, const double* __restrict__ H, const doub
     }
 }
 
-__global__ void k_f2d(const float* __restrict__ x, int64_t n, double* __restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (double)x[i];
-}
-
 // out = sum_k Z[k] y[k]   (Z float or double)
 template <typename TZ>
 __global__ void k_lincomb(const TZ* __restrict__ Z, int K, int64_t n, const double* __restrict__ y,
@@ -179,12 +173,6 @@ __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         x[i] += d[i];
-}
-
-__global__ void k_isfinite_f(const float* __restrict__ x, int64_t n, int* flag) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (!isfinite(x[i])) { *flag = 1; return; }
 }
 
 double read_scalar(rte_ctx* ctx, Workspace* ws, const double* dev) {
