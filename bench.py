@@ -776,7 +776,7 @@ def main():
                          "(block-Jacobi FGMRES(50) on this workload, as measured on the GPU)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--pc", default="mgnet", choices=["mgnet", "bj"])
-    ap.add_argument("--train-steps", type=int, default=6000)
+    ap.add_argument("--train-steps", type=int, default=9000)
     ap.add_argument("--train-media", type=int, default=32)
     ap.add_argument("--train-size", type=int, default=128,
                     help="grid side of the training media (0: the benchmark grid)")
