@@ -5,7 +5,7 @@ block-Jacobi or an MgNet preconditioner but not its variant, restart or
 orthogonalisation; the reading used here is right-preconditioned flexible
 GMRES(m) (the preconditioner may change between iterations), x0 = 0 unless
 given, Arnoldi by modified Gram-Schmidt with one full reorthogonalisation, and
-convergence judged by the recomputed residual ||b - A x|| / ||b||.
+convergence decided by the recomputed residual ||b - A x|| / ||b||.
 
 Pins: dense LU solve (P7), Arnoldi orthonormality and finite termination (P15).
 """
