@@ -281,6 +281,9 @@ typedef struct rte_solve_info {
     int fell_back;         /* 1 if MgNet was replaced by block Jacobi */
     double relres;         /* final true relative residual (FP64) */
     double seconds;        /* wall time of the call */
+    int history_len;       /* entries of history */
+    double history[32];    /* true relative residual at the start of each restart cycle
+                              (the first 32; the last entry is the final one) */
 } rte_solve_info;
 
 RTE_API void rte_solve_opts_default(rte_solve_opts* opts);
@@ -364,6 +367,14 @@ RTE_API void mgnet_destroy(mgnet* net);
 RTE_API int64_t mgnet_param_count(const mgnet* net);
 /* The configuration the network was created with.  EINVAL for NULL. */
 RTE_API rte_status mgnet_get_config(const mgnet* net, mgnet_config* cfg);
+
+/* Host-side fault injection (no counterpart in the paper): with
+ * MGNET_FAULT_NAN every output of the preconditioner (mgnet_precond and the
+ * solves using the network) is overwritten with NaN, as a failing network
+ * would produce; the solver detects the non-finite step and falls back to
+ * block Jacobi.  No device fault is raised.  EINVAL for another kind. */
+typedef enum mgnet_fault { MGNET_FAULT_NONE = 0, MGNET_FAULT_NAN = 1 } mgnet_fault;
+RTE_API rte_status mgnet_inject_fault(mgnet* net, int kind);
 
 /* Arithmetic of the V-cycle convolutions when the network preconditions
  * (mgnet_precond, mgnet_apply, rte_solve); training always uses FP32.

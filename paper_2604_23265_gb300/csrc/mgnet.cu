@@ -53,6 +53,7 @@ struct mgnet {
     int act = 0;                     // smoother activation: 0 identity, 1 ReLU
     int prec = 1;                    // inference convolutions: 0 FP32 CUDA cores, 1 BF16 tensor cores
     int loss = 0;                    // training loss: 0 plain (Eq. loss), 1 ATFPS-filtered (Eq. loss_delta)
+    int fault = 0;                   // host-side fault injection: 1 = every preconditioner output is NaN
     void* lscr = nullptr;            // scratch of the filtered loss
     size_t lscr_bytes = 0;
     // tensor-core inference path: BF16 C8 activations, packed weights
@@ -883,6 +884,7 @@ void mgnet_prepare(mgnet* net, rte_ctx* ctx) {
 }
 
 void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
+    NvtxRange range("MgNet V-cycle");
     check_ctx(net, ctx);
     Features& F = features(net, ctx, false);
     // count the forward's convolutions (launches, FP32 flops) for the profile
@@ -908,6 +910,8 @@ void mgnet_precondition(mgnet* net, rte_ctx* ctx, const double* v, float* z) {
         check(cudaGetLastError(), "k_scale_out");
         cnt.launches += 4;                                // norm, sqrt, normalise, scale
     }
+    if (net->fault == MGNET_FAULT_NAN)
+        check(cudaMemsetAsync(z, 0xFF, (size_t)ctx->n * sizeof(float), net->stream), "fault injection");
     ctx->prof.launches[K_MGNET] += cnt.launches;
     ctx->prof.flops[K_MGNET] += cnt.flops;
 }
@@ -932,6 +936,10 @@ void mgnet_precondition_batch(mgnet* net, rte_ctx* const* ctxs, const double* co
         }
         ProfScope ps(ctxs[b0], K_MGNET, (double)ctxs[b0]->n * 12 * S.B, 0);
         tc_precondition(net, S, I);
+        if (net->fault == MGNET_FAULT_NAN)
+            for (int b = 0; b < S.B; ++b)
+                check(cudaMemsetAsync(S.z[b], 0xFF, (size_t)ctxs[b0 + b]->n * sizeof(float), net->stream),
+                      "fault injection");
     }
 }
 
@@ -994,6 +1002,7 @@ RTE_API rte_status mgnet_clone(const mgnet* src, void* stream, mgnet** out) {
     check(cudaMemcpyAsync(n->p, src->p, n->np * 4, cudaMemcpyDeviceToDevice, n->stream), "d2d");
     n->prec = src->prec;
     n->loss = src->loss;
+    n->fault = src->fault;
     check(cudaStreamSynchronize(n->stream), "sync");
     ++n->version;
     return RTE_OK;
@@ -1018,6 +1027,15 @@ RTE_API void mgnet_destroy(mgnet* n) {
 }
 
 RTE_API int64_t mgnet_param_count(const mgnet* n) { return n ? (int64_t)n->np : -1; }
+
+RTE_API rte_status mgnet_inject_fault(mgnet* n, int kind) {
+    if (!n || (kind != MGNET_FAULT_NONE && kind != MGNET_FAULT_NAN)) {
+        set_error(nullptr, "bad argument (MGNET_FAULT_NONE or MGNET_FAULT_NAN)");
+        return RTE_EINVAL;
+    }
+    n->fault = kind;
+    return RTE_OK;
+}
 
 RTE_API rte_status mgnet_get_config(const mgnet* n, mgnet_config* cfg) {
     if (!n || !cfg) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }

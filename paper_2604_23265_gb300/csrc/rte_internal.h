@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -112,6 +113,14 @@ inline void check(cudaError_t e, const char* where) {
 // lowering it: concurrent callers (server threads, contexts of different M)
 // cannot shrink the limit under another thread's pending launch.
 void raise_smem_limit(const void* kern, size_t bytes);
+
+// NVTX range for the phases of a call (visible to profilers; no cost without one)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // profiling (setup.cu): wrap every launch of the library.
 // Counts the launch and its algorithmic bytes; with profiling on, brackets the

@@ -352,6 +352,7 @@ T* upload(rte_ctx* ctx, const std::vector<T>& h) {
 
 void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const double* q,
            const double* eps, int eps_is_scalar, const double* inflow) {
+    NvtxRange range("rte_setup");
     const int I = ctx->I, M = ctx->M, N = ctx->N, M2 = M / 2;
     const double h = 1.0 / I;
     int dev = 0;

@@ -245,6 +245,7 @@ struct Solver {
 
     // true residual in FP64 and the decisions on it; false when the solve ends
     bool cycle_begin() {
+        NvtxRange range("restart cycle: true residual");
         if (first && !opts.use_x0)
             check(cudaMemcpyAsync(ws->w, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
                   "r = b");
@@ -256,6 +257,7 @@ struct Solver {
         launch_norm(ctx, ws->w, ws->est + 3);
         const double beta = read_scalar(ctx, ws, ws->est + 3);
         inf.relres = beta / bnorm;
+        if (inf.history_len < 32) inf.history[inf.history_len++] = inf.relres;
         if (!std::isfinite(beta)) {
             set_error(ctx, "non-finite residual");
             status = RTE_ESTALL;
@@ -314,6 +316,7 @@ struct Solver {
 
     // CGS2, v_{j+1}, Givens
     void orthogonalise_step() {
+        NvtxRange range("Gram-Schmidt and Givens");
         const int K = j + 1;
         orthogonalise(ctx, ws, ws->V, K);
         launch_scale(ctx, ws->w, ws->hcol + K, ws->V + (size_t)(j + 1) * n);
@@ -555,6 +558,7 @@ namespace {
 rte_status run_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, double* x_dev, rte_solve_info* info,
                      bool comp, bool layers) {
     if (!ctx || !x_dev) { set_error(ctx, "NULL argument"); return RTE_EINVAL; }
+    NvtxRange range(comp ? "rte_atfps_solve" : "rte_solve");
     Solver S;
     S.ctx = ctx;
     S.pc = pc;

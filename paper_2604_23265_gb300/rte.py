@@ -51,10 +51,13 @@ class SolveOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
-                ("fell_back", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("fell_back", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("history_len", ctypes.c_int), ("history", ctypes.c_double * 32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("history", "history_len")}
+        d["history"] = [self.history[i] for i in range(min(self.history_len, 32))]
+        return d
 
 
 class KernelStat(ctypes.Structure):
@@ -104,6 +107,7 @@ SIGNATURES = {
     "mgnet_destroy": (None, [_P]),
     "mgnet_param_count": (ctypes.c_int64, [_P]),
     "mgnet_get_config": (_I, [_P, _P]),
+    "mgnet_inject_fault": (_I, [_P, _I]),
     "mgnet_set_precision": (_I, [_P, _I]),
     "rte_solve_group": (_I, [_P, _P, _I, _P, _P, _P, _P]),
     "mgnet_set_loss": (_I, [_P, _I]),
@@ -322,6 +326,13 @@ class MgNet:
         self.ptr = out
         self.shape = shape
         self.count = int(load().mgnet_param_count(self.ptr))
+
+    FAULT_NONE, FAULT_NAN = 0, 1
+
+    def inject_fault(self, kind):
+        """Host-side fault injection (mgnet_inject_fault): FAULT_NAN makes every
+        preconditioner output NaN; FAULT_NONE restores normal operation."""
+        _check(load().mgnet_inject_fault(self.ptr, int(kind)))
 
     def config(self):
         """The library's record of the configuration (mgnet_get_config)."""

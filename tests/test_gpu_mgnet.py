@@ -212,3 +212,31 @@ def test_save_load_roundtrip(lib, tmp_path):
     (tmp_path / "bad.bin").write_bytes(bytes(raw))
     with pytest.raises(rte.RteError):
         net2.load(tmp_path / "bad.bin")
+
+
+def test_injected_nan_network_falls_back_alone_and_grouped(lib):
+    """Host-side fault injection: a network whose every output is NaN makes the
+    first Arnoldi step non-finite; the solver drops it, switches to block
+    Jacobi and converges, alone and in a lockstep group, with no device
+    fault.  Clearing the fault restores the network's own solve."""
+    rte, shape, params, md, ctx, net, p = _setup(I=16, M=8, levels=3, proj=0.05)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    good = ctx.solve(x, pc=net, tol=1e-10, restart=30)
+    net.inject_fault(rte.MgNet.FAULT_NAN)
+    x.zero_()
+    bad = ctx.solve(x, pc=net, tol=1e-10, restart=30)
+    assert bad["converged"] and bad["fell_back"], bad
+    assert torch.isfinite(x).all()
+    r = p.rhs().ravel() - p.apply(x.cpu().numpy().reshape(2 * md.M, -1)).ravel()
+    assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 1e-10
+    ctx2 = rte.Context.from_medium(md)
+    xs = [torch.zeros(ctx2.n, dtype=torch.float64, device="cuda")]
+    grp = rte.solve_group([ctx2], xs, pcs=[net], tol=1e-10, restart=30)
+    assert grp[0]["iterations"] == bad["iterations"] and torch.equal(xs[0], x)
+    net.inject_fault(rte.MgNet.FAULT_NONE)
+    x.zero_()
+    again = ctx.solve(x, pc=net, tol=1e-10, restart=30)
+    assert again["iterations"] == good["iterations"] and again["fell_back"] == good["fell_back"]
+    with pytest.raises(rte.RteError):
+        net.inject_fault(7)
+    ctx2.close()

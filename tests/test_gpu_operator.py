@@ -292,3 +292,16 @@ def test_sharp_interface_media_match_oracle(lib, layout, M):
     psi = torch.zeros(M * md.I * md.I, dtype=torch.float64, device="cuda")
     ctx.reconstruct(xs, psi)
     assert _rel(psi.cpu().numpy(), p.reconstruct(xl.reshape(2 * M, -1)).ravel()) <= 1e-8
+
+
+def test_solve_reports_residual_history(lib):
+    """The solve info carries the true relative residual at the start of every
+    restart cycle: 1 for x0 = 0, decreasing, the last entry the final one."""
+    md = _generic(12, 8, 7, eps=0.05)
+    ctx = _gpu(md)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, tol=1e-10, restart=10)
+    h = info["history"]
+    assert info["converged"] and len(h) == min(info["cycles"] + 1, 32)
+    assert h[0] == 1.0 and h[-1] == info["relres"]
+    assert all(b < a for a, b in zip(h, h[1:]))
