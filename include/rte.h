@@ -427,9 +427,13 @@ RTE_API rte_status mgnet_train_step(mgnet* net, rte_ctx* ctx, const double* cons
 RTE_API rte_status mgnet_loss_grad(mgnet* net, rte_ctx* ctx, const double* const* r_dev, int batch,
                                    double* loss_out, float* grad_host);
 
-/* Weights to / from a file: "MGNET002", seven int32 (M, levels, c0, cmax, cc,
- * ccmax, act), int64 count, count float32, uint32 word checksum.  Load checks the
- * configuration and checksum (EINVAL on mismatch). */
+/* Checkpoint to / from a file: "MGNET003", seven int32 (M, levels, c0, cmax,
+ * cc, ccmax, act), int64 count, int64 Adam step, then count float32 weights,
+ * count float32 Adam first moments, count float32 second moments, and a uint32
+ * checksum (the step plus every 32-bit word, modulo 2^32).  Load checks the
+ * configuration and checksum (EINVAL on mismatch) and restores weights, moments
+ * and step, so training resumes where it stopped; it also reads the older
+ * weights-only "MGNET002" layout (no step, no moments; the Adam state is reset). */
 RTE_API rte_status mgnet_save(mgnet* net, const char* path);
 /* A new network with the same configuration and weights (its own caches and
  * workspace, so copies can serve different streams at once). */

@@ -1163,18 +1163,20 @@ RTE_API rte_status mgnet_train_step(mgnet* n, rte_ctx* ctx, const double* const*
 RTE_API rte_status mgnet_save(mgnet* n, const char* path) {
     if (!n || !path) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
     MG_GUARD_BEGIN
-    std::vector<float> h(n->np);
+    // weights, then the Adam moments m and v (p, g, m, v are consecutive)
+    std::vector<float> h(3 * n->np);
     check(cudaMemcpyAsync(h.data(), n->p, n->np * 4, cudaMemcpyDeviceToHost, n->stream), "d2h");
+    check(cudaMemcpyAsync(h.data() + n->np, n->m, 2 * n->np * 4, cudaMemcpyDeviceToHost, n->stream), "d2h");
     check(cudaStreamSynchronize(n->stream), "sync");
     FILE* f = std::fopen(path, "wb");
     if (!f) throw StatusError{RTE_EINVAL, "cannot open file for writing"};
     const int32_t hdr[7] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax, n->act};
-    const int64_t cnt = (int64_t)n->np;
-    uint32_t sum = 0;
-    for (size_t i = 0; i < n->np; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
-    bool ok = std::fwrite("MGNET002", 1, 8, f) == 8 && std::fwrite(hdr, 4, 7, f) == 7 &&
-              std::fwrite(&cnt, 8, 1, f) == 1 && std::fwrite(h.data(), 4, n->np, f) == n->np &&
-              std::fwrite(&sum, 4, 1, f) == 1;
+    const int64_t cnt = (int64_t)n->np, step = n->step;
+    uint32_t sum = (uint32_t)step;
+    for (size_t i = 0; i < h.size(); ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
+    bool ok = std::fwrite("MGNET003", 1, 8, f) == 8 && std::fwrite(hdr, 4, 7, f) == 7 &&
+              std::fwrite(&cnt, 8, 1, f) == 1 && std::fwrite(&step, 8, 1, f) == 1 &&
+              std::fwrite(h.data(), 4, h.size(), f) == h.size() && std::fwrite(&sum, 4, 1, f) == 1;
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) throw StatusError{RTE_EINVAL, "write failed"};
     return RTE_OK;
@@ -1188,19 +1190,27 @@ RTE_API rte_status mgnet_load(mgnet* n, const char* path) {
     if (!f) throw StatusError{RTE_EINVAL, "cannot open file"};
     char magic[8];
     int32_t hdr[7];
-    int64_t cnt = 0;
-    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MGNET002", 8) == 0 &&
-              std::fread(hdr, 4, 7, f) == 7 && std::fread(&cnt, 8, 1, f) == 1;
+    int64_t cnt = 0, step = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8;
+    const bool v3 = ok && std::memcmp(magic, "MGNET003", 8) == 0;
+    ok = ok && (v3 || std::memcmp(magic, "MGNET002", 8) == 0) && std::fread(hdr, 4, 7, f) == 7 &&
+         std::fread(&cnt, 8, 1, f) == 1 && (!v3 || std::fread(&step, 8, 1, f) == 1);
     const int32_t want[7] = {n->M, n->L, n->c0, n->cmax, n->cc, n->ccmax, n->act};
-    ok = ok && std::memcmp(hdr, want, sizeof(want)) == 0 && cnt == (int64_t)n->np;
-    std::vector<float> h(ok ? n->np : 0);
-    uint32_t sum = 0, stored = 0;
-    ok = ok && std::fread(h.data(), 4, n->np, f) == n->np && std::fread(&stored, 4, 1, f) == 1;
+    ok = ok && std::memcmp(hdr, want, sizeof(want)) == 0 && cnt == (int64_t)n->np && step >= 0;
+    const size_t floats = ok ? (v3 ? 3 : 1) * n->np : 0;
+    std::vector<float> h(floats);
+    uint32_t sum = (uint32_t)step, stored = 0;
+    ok = ok && std::fread(h.data(), 4, floats, f) == floats && std::fread(&stored, 4, 1, f) == 1;
     std::fclose(f);
     if (ok)
-        for (size_t i = 0; i < n->np; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
-    if (!ok || sum != stored) throw StatusError{RTE_EINVAL, "not a matching MGNET002 file or bad checksum"};
-    return mgnet_set_params(n, h.data(), cnt);
+        for (size_t i = 0; i < floats; ++i) { uint32_t w; std::memcpy(&w, &h[i], 4); sum += w; }
+    if (!ok || sum != stored) throw StatusError{RTE_EINVAL, "not a matching MGNET002/003 file or bad checksum"};
+    const rte_status st = mgnet_set_params(n, h.data(), cnt);      // also resets the Adam state
+    if (st != RTE_OK || !v3) return st;
+    check(cudaMemcpyAsync(n->m, h.data() + n->np, 2 * n->np * 4, cudaMemcpyHostToDevice, n->stream), "h2d");
+    check(cudaStreamSynchronize(n->stream), "sync");
+    n->step = (int)step;
+    return RTE_OK;
     MG_GUARD_END(n)
 }
 

@@ -45,14 +45,21 @@ def training_inputs(ctx, md, n_krylov=32, n_smooth=32, seed=0, noise=0.1):
     return out
 
 
-def train(net, ctxs, inputs, steps=600, batch=8, lr0=3e-3, seed=0, log=None, checkpoint=None, every=0):
+def train(net, ctxs, inputs, steps=600, batch=8, lr0=3e-3, seed=0, log=None, checkpoint=None, every=0,
+          start_step=0):
     """Adam + cosine annealing; each step draws one medium and `batch` of its
     inputs.  checkpoint(step, net, losses) is called every `every` steps and
-    after the last one.  Returns the list of batch losses."""
+    after the last one.  start_step resumes a run of `steps` steps (from a
+    network saved with its Adam state, MgNet.save / load): the draws of the
+    earlier steps are replayed and the schedule continues at start_step.
+    Returns the list of batch losses of the steps run."""
     rng = np.random.default_rng(seed)
+    for _ in range(start_step):
+        m = int(rng.integers(len(ctxs)))
+        rng.choice(len(inputs[m]), size=min(batch, len(inputs[m])), replace=False)
     losses = []
     t0 = time.time()
-    for it in range(steps):
+    for it in range(start_step, steps):
         if checkpoint is not None and every > 0 and it % every == 0:
             checkpoint(it, net, losses)
         lr = 0.5 * lr0 * (1.0 + math.cos(math.pi * it / steps))

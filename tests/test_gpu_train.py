@@ -29,3 +29,40 @@ def test_trained_mgnet_beats_block_jacobi(lib):
     b = p.rhs().ravel()
     r = b - p.apply(x.cpu().numpy().reshape(2 * test.M, -1)).ravel()
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-8
+
+
+
+def test_checkpoint_resumes_training(lib, tmp_path):
+    """A 40-step run saved with its Adam state after 20 steps and resumed from
+    the file at step 20 ends where the uninterrupted run ends (up to the
+    rounding of the atomic weight-gradient sums); resuming from the weights
+    alone (the Adam state reset) does not."""
+    from paper_2604_23265_gb300 import rte, train
+    media = [W.grf_diffusive(s, I=16, M=8, eps=1e-2) for s in range(1, 3)]
+    shape = W.NetShape(M=8, levels=3, c0=8, cmax=16, cc=4, ccmax=8)
+    ctxs = [rte.Context.from_medium(md) for md in media]
+    inputs = [train.training_inputs(c, md, 8, 8, 5 + i) for i, (c, md) in enumerate(zip(ctxs, media))]
+    kw = dict(steps=40, batch=4, lr0=3e-3, seed=9)
+
+    def fresh():
+        n = rte.MgNet(shape)
+        n.set_params(W.init_params(shape, seed=4, proj_scale=0.0, vcycle_scale=0.5))
+        return n
+
+    a = fresh()
+    train.train(a, ctxs, inputs, **kw)
+    c = fresh()
+    train.train(c, ctxs, inputs, checkpoint=lambda it, n, ls: n.save(tmp_path / "ck.bin") if it == 20 else None,
+                every=20, **kw)
+    d = fresh()
+    d.load(tmp_path / "ck.bin")
+    train.train(d, ctxs, inputs, start_step=20, **kw)
+    p0, pa, pd = fresh().get_params(), a.get_params(), d.get_params()
+    assert np.linalg.norm(pd - pa) <= 1e-3 * np.linalg.norm(pa - p0)
+    e = fresh()
+    e.load(tmp_path / "ck.bin")
+    e.set_params(e.get_params())                  # same weights, Adam state reset
+    train.train(e, ctxs, inputs, start_step=20, **kw)
+    assert np.linalg.norm(e.get_params() - pa) > 10 * np.linalg.norm(pd - pa)
+    for ctx in ctxs:
+        ctx.close()
