@@ -70,3 +70,51 @@ def test_setup_rejects_bad_arguments_without_gpu(libpath):
     opts = rte.SolveOpts()
     lib.rte_solve_opts_default(ctypes.byref(opts))
     assert opts.tol == 1e-8 and opts.restart == 50 and opts.inner_precision == rte.RTE_F32
+
+
+# the ctypes mirrors of the public structs and the C declarations agree on
+# size and on every field offset (compiled with the host C compiler)
+STRUCTS = {
+    "rte_ctx_info": ("CtxInfo", ["I", "M", "N", "nmat", "n", "device_bytes"]),
+    "rte_solve_opts": ("SolveOpts", ["tol", "restart", "max_iter", "inner_precision", "use_x0", "stall_ratio",
+                                     "timeout_ms", "cancel"]),
+    "rte_solve_info": ("SolveInfo", ["iterations", "cycles", "converged", "fell_back", "relres", "seconds",
+                                     "history_len", "history"]),
+    "mgnet_config": ("MgNetConfig", ["M", "levels", "c0", "cmax", "cc", "ccmax", "act"]),
+    "rte_server_config": ("ServerConfig", ["max_device_bytes", "slots", "inject_alloc_failure_id", "grouped"]),
+    "rte_request": ("Request", ["I", "M", "sigma_T", "sigma_a", "q", "eps", "eps_is_scalar", "g", "inflow", "tol",
+                                "max_iter", "restart", "use_net"]),
+    "rte_result": ("Result", ["status", "info", "latency_s", "queue_s", "footprint", "used_net"]),
+    "rte_server_stats_t": ("ServerStats", ["queued", "completed", "active", "bytes_in_use"]),
+    "rte_kernel_stat": ("KernelStat", ["name", "launches", "ms", "bytes", "flops"]),
+}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    import shutil
+    import subprocess
+    from paper_2604_23265_gb300 import rte
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ['#include <stdio.h>', '#include "rte.h"', "int main(void) {"]
+    for cname, (_, fields) in STRUCTS.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            name, field, value = line.split()
+            got[(name, field)] = int(value)
+    for cname, (pyname, fields) in STRUCTS.items():
+        cls = getattr(rte, pyname)
+        assert ctypes.sizeof(cls) == got[(cname, "size")], cname
+        for f in fields:
+            assert getattr(cls, f).offset == got[(cname, f)], (cname, f)
