@@ -296,12 +296,16 @@ void device_eigenbases(rte_ctx* ctx, const std::vector<double>& omg, const std::
                          al(refl.size() * 4) + al(pencils * h * 8) + al(pencils * h * M * 8) + al(4);
     char* buf = nullptr;
     check(cudaMallocAsync(&buf, bytes, ctx->stream), "cudaMallocAsync (eigenbases)");
+    struct Scratch {                    // released on every path out of here
+        char* p;
+        cudaStream_t st;
+        ~Scratch() { cudaFreeAsync(p, st); }
+    } scratch{buf, ctx->stream};
     auto take = [&](size_t b) {
         char* p = buf;
         buf += al(b);
         return p;
     };
-    char* base = buf;
     double* d_omg = reinterpret_cast<double*>(take(omg.size() * 8));
     double* d_K = reinterpret_cast<double*>(take(K.size() * 8));
     double* d_kw = reinterpret_cast<double*>(take(M * 8));
@@ -312,7 +316,6 @@ void device_eigenbases(rte_ctx* ctx, const std::vector<double>& omg, const std::
     double* d_xp = reinterpret_cast<double*>(take(pencils * h * 8));
     double* d_lp = reinterpret_cast<double*>(take(pencils * h * M * 8));
     int* d_bad = reinterpret_cast<int*>(take(4));
-    (void)base;
     auto up = [&](void* dst, const void* src, size_t b) {
         check(cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, ctx->stream), "h2d (eigenbases)");
     };
@@ -339,7 +342,6 @@ void device_eigenbases(rte_ctx* ctx, const std::vector<double>& omg, const std::
     int bad = 0;
     check(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream), "d2h");
     check(cudaStreamSynchronize(ctx->stream), "sync (eigenbases)");
-    cudaFreeAsync(base, ctx->stream);
     if (bad) throw StatusError{RTE_ESINGULAR, "scattering operator not positive definite"};
 }
 

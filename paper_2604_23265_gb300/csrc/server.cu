@@ -91,15 +91,29 @@ namespace rte {
 namespace {
 
 // Device bytes a solve holds: D (FP64) and R (FP32) blocks, per-cell tables,
-// b and the operator scratch, the Krylov basis (FP64) and MgNet outputs (FP32).
-size_t footprint(int I, int M, int restart, bool net) {
+// the eigenbases of its materials (FP64 and FP32, plain and transposed), b and
+// the operator scratch, the Krylov basis (FP64) and MgNet outputs (FP32).
+size_t footprint(int I, int M, int restart, bool net, size_t nmat) {
     const size_t N = (size_t)I * I, n2 = 2 * (size_t)M, n = n2 * N;
     size_t b = N * n2 * n2 * (8 + 4);
     b += n * 8 * 6;                                    // b, trace scratch (2n), w, tmp, x
     b += (size_t)(restart + 1) * n * 8 + (size_t)restart * n * 4;
-    b += N * 64 + (size_t)M * n2 * 48;                 // per-cell and basis tables
+    b += N * 64 + nmat * (size_t)M * n2 * (8 + 8 + 4 + 4) + nmat * n2 * 8;   // per-cell and basis tables
     if (net) b += n * 4 * 16;                          // network activations (upper bound)
     return b + (64u << 20);
+}
+
+// materials of a request: distinct 1 - gamma = eps^2 sigma_a / sigma_T, as rte_setup counts them
+size_t count_materials(const Job& j) {
+    std::vector<double> w;
+    w.reserve(j.sT.size());
+    for (size_t c = 0; c < j.sT.size(); ++c) {
+        const double e = j.eps_is_scalar ? j.eps[0] : j.eps[c];
+        const double v = e * e * j.sa[c] / j.sT[c];
+        if (std::isfinite(v)) w.push_back(v);   // a malformed medium fails at set-up
+    }
+    std::sort(w.begin(), w.end());
+    return (size_t)(std::unique(w.begin(), w.end()) - w.begin());
 }
 
 bool valid_request(const rte_request* r, std::string& why) {
@@ -511,7 +525,7 @@ RTE_API rte_status rte_server_submit(rte_server* s, const rte_request* r, int64_
     if (r->restart > 0) job->opts.restart = r->restart;
     job->net = r->use_net ? pick_net(s, r->I, r->M) : -1;
     job->use_net = job->net >= 0;
-    job->footprint = footprint(r->I, r->M, job->opts.restart, job->use_net);
+    job->footprint = footprint(r->I, r->M, job->opts.restart, job->use_net, count_materials(*job));
     if (job->footprint > s->cfg.max_device_bytes) {
         set_error(nullptr, "request needs more device memory than the server budget");
         return RTE_ENOMEM;
