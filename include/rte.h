@@ -8,6 +8,14 @@
  * 2DTFPS_boundary_cond, 2DTFPS_linear_sys) with flexible GMRES preconditioned
  * by block Jacobi or by a learned MgNet V-cycle (Sec. 3, Sec. 4).
  *
+ * Contents: context set-up and the operator (rte_setup, rte_apply,
+ * rte_apply_adjoint, rte_block_apply, rte_reconstruct, ...); the solve
+ * (rte_solve) and grouped solves in shared launches (rte_solve_group); the
+ * ATFPS filter and the compressed solve with layer reconstruction (rte_atfps_*,
+ * Sec. 2.3); the learned preconditioner (mgnet_*: forward, training on either
+ * loss, checkpoints, fault injection); the continuous-batching server
+ * (rte_server_*); per-kernel accounting (rte_profile*).
+ *
  * Conventions shared by every call
  * --------------------------------
  * Grid: unit square, I x I cells, h = 1/I; cell index c = iy*I + ix covers
