@@ -18,7 +18,9 @@ tfps    -- DOM quadrature and HG kernel (Sec. 2.1, Eq. hg, Eq. DORTE_2d),
 krylov  -- right-preconditioned flexible GMRES with modified Gram-Schmidt plus
            one reorthogonalisation, dense LU reference solve.
 atfps   -- ATFPS selection, interface bases, projections and the filtered
-           loss (Sec. 2.3, Eq. def_V_delta, Eq. loss_delta).
+           loss (Sec. 2.3, Eq. def_V_delta, Eq. loss_delta); the compressed
+           system, its solve and the layer reconstruction (Sec. 2.3.3-2.3.4,
+           Eqs. 2DAdaptiveTFPS_linear_sys, 2DAdaptive_TFPS_layer1 / layer2).
 mgnet   -- CoeffNet + MgNet V-cycle forward/backward and Adam (Sec. 3).
 
 Parity status of each function is stated in its docstring; functions with no
