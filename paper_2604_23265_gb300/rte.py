@@ -55,6 +55,7 @@ class SolveInfo(ctypes.Structure):
                 ("history_len", ctypes.c_int), ("history", ctypes.c_double * 32)]
 
     def as_dict(self):
+        """The fields as a dict, the residual history trimmed to its entries."""
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("history", "history_len")}
         d["history"] = [self.history[i] for i in range(min(self.history_len, 32))]
         return d
@@ -238,6 +239,8 @@ class Server:
         self._meta = {}
 
     def submit(self, md, tol=1e-8, use_net=False, max_iter=0, restart=0):
+        """Queue a solve of the medium md (rte_server_submit); returns the request id. use_net:
+        precondition with the server's network for md.M when one fits the grid."""
         arrs = [np.ascontiguousarray(a, np.float64) for a in
                 (md.sigma_T, md.sigma_a, md.q, np.asarray(md.eps).reshape(-1), md.inflow)]
         eps_scalar = int(arrs[3].size == 1)
@@ -249,6 +252,8 @@ class Server:
         return rid.value
 
     def wait(self, rid, timeout_ms=0.0):
+        """Block until request rid is done (rte_server_wait); returns (result dict, psi as a host array
+        [M * N])."""
         M, I = self._meta[rid]
         res = Result()
         psi = np.zeros(M * I * I)
@@ -264,14 +269,17 @@ class Server:
         return d, psi
 
     def cancel(self, rid):
+        """Cancel request rid (rte_server_cancel)."""
         _check(load().rte_server_cancel(self.ptr, int(rid)))
 
     def stats(self):
+        """Queue, occupancy and byte counters (rte_server_stats)."""
         st = ServerStats()
         _check(load().rte_server_stats(self.ptr, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in st._fields_}
 
     def close(self):
+        """Stop the server (rte_server_destroy); requests still waiting are cancelled."""
         if getattr(self, "ptr", None):
             load().rte_server_destroy(self.ptr)
             self.ptr = None
@@ -341,6 +349,7 @@ class MgNet:
         return {k: getattr(c, k) for k, _ in c._fields_}
 
     def close(self):
+        """Free the network (mgnet_destroy)."""
         if getattr(self, "ptr", None):
             load().mgnet_destroy(self.ptr)
             self.ptr = None
@@ -353,12 +362,14 @@ class MgNet:
 
     @staticmethod
     def flatten(params, shape):
+        """Parameter dict -> float32 vector in the library's order (workloads.param_shapes)."""
         from . import workloads
         return np.concatenate([np.asarray(params[name], np.float64).ravel()
                                for name, _ in workloads.param_shapes(shape)]).astype(np.float32)
 
     @staticmethod
     def unflatten(flat, shape):
+        """float32 vector -> parameter dict of float64 arrays."""
         from . import workloads
         out, o = {}, 0
         for name, shp in workloads.param_shapes(shape):
@@ -368,6 +379,7 @@ class MgNet:
         return out
 
     def set_params(self, params):
+        """Set the weights from a dict or a flat vector (mgnet_set_params; resets the Adam state)."""
         flat = params if isinstance(params, np.ndarray) else self.flatten(params, self.shape)
         flat = np.ascontiguousarray(flat, np.float32)
         _check(load().mgnet_set_params(self.ptr, flat.ctypes.data_as(_P), flat.size))
@@ -382,6 +394,7 @@ class MgNet:
 
     @precision.setter
     def precision(self, value):
+        """Set the convolution arithmetic (mgnet_set_precision; RteError for another value)."""
         _check(load().mgnet_set_precision(self.ptr, int(value)))
 
     PLAIN, FILTERED = 0, 1
@@ -394,6 +407,7 @@ class MgNet:
 
     @loss.setter
     def loss(self, value):
+        """Set the training loss (mgnet_set_loss; RteError for another value)."""
         _check(load().mgnet_set_loss(self.ptr, int(value)))
 
     @staticmethod
@@ -402,17 +416,20 @@ class MgNet:
         return int(load().mgnet_kernel_status(1 if reset else 0))
 
     def get_params(self):
+        """The weights as a float32 vector (mgnet_get_params)."""
         flat = np.zeros(self.count, np.float32)
         _check(load().mgnet_get_params(self.ptr, flat.ctypes.data_as(_P), flat.size))
         return flat
 
     def precond(self, ctx, r, z):
+        """z = Net(r) in face-flux space (mgnet_precond): r float64 [n], z float32 [n], device tensors."""
         import torch
         _check(load().mgnet_precond(self.ptr, ctx.ptr, _dev(r, torch.float64, ctx.n),
                                     _dev(z, torch.float32, ctx.n)))
         return z
 
     def apply(self, ctx, r, z):
+        """z = D Net(r) (mgnet_apply): r, z float64 [n], device tensors."""
         import torch
         _check(load().mgnet_apply(self.ptr, ctx.ptr, _dev(r, torch.float64, ctx.n),
                                   _dev(z, torch.float64, ctx.n)))
@@ -424,6 +441,8 @@ class MgNet:
         return arr
 
     def train_step(self, ctx, rs, lr):
+        """One Adam step on a batch of right-hand sides of ctx (mgnet_train_step); returns the batch
+        loss before the step."""
         loss = ctypes.c_double()
         arr = self._ptrs(ctx, rs)
         _check(load().mgnet_train_step(self.ptr, ctx.ptr, ctypes.cast(arr, _P), len(rs), float(lr),
@@ -431,6 +450,7 @@ class MgNet:
         return loss.value
 
     def loss_grad(self, ctx, rs):
+        """(loss, gradient as a float32 vector) without updating the weights (mgnet_loss_grad)."""
         loss = ctypes.c_double()
         g = np.zeros(self.count, np.float32)
         arr = self._ptrs(ctx, rs)
@@ -439,9 +459,11 @@ class MgNet:
         return loss.value, g
 
     def save(self, path):
+        """Checkpoint the weights and the Adam state to path (mgnet_save)."""
         _check(load().mgnet_save(self.ptr, str(path).encode()))
 
     def load(self, path):
+        """Restore a checkpoint from path (mgnet_load)."""
         _check(load().mgnet_load(self.ptr, str(path).encode()))
 
 
@@ -472,9 +494,11 @@ class Context:
 
     @classmethod
     def from_medium(cls, md, stream=None):
+        """The context of a workloads.Medium (rte_setup)."""
         return cls(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow, stream)
 
     def close(self):
+        """Free the context (rte_destroy)."""
         if getattr(self, "ptr", None):
             load().rte_destroy(self.ptr)
             self.ptr = None
@@ -486,22 +510,26 @@ class Context:
             pass
 
     def info(self):
+        """Sizes, materials and device bytes (rte_ctx_info)."""
         i = CtxInfo()
         _check(load().rte_info(self.ptr, ctypes.byref(i)), self.ptr)
         return {k: getattr(i, k) for k, _ in i._fields_}
 
     def rhs(self, b):
+        """Write b of Eq. 2DTFPS_linear_sys into the float64 device vector b."""
         import torch
         _check(load().rte_rhs(self.ptr, _dev(b, torch.float64, self.n)), self.ptr)
         return b
 
     def apply(self, x, y, precision=RTE_F64):
+        """y = A x (rte_apply), FP64 or FP32 by precision."""
         import torch
         dt = torch.float64 if precision == RTE_F64 else torch.float32
         _check(load().rte_apply(self.ptr, precision, _dev(x, dt, self.n), _dev(y, dt, self.n)), self.ptr)
         return y
 
     def apply_adjoint(self, y, x, precision=RTE_F64):
+        """x = A^T y (rte_apply_adjoint)."""
         import torch
         dt = torch.float64 if precision == RTE_F64 else torch.float32
         _check(load().rte_apply_adjoint(self.ptr, precision, _dev(y, dt, self.n), _dev(x, dt, self.n)),
@@ -509,18 +537,21 @@ class Context:
         return x
 
     def block_apply(self, r, z, transpose=False):
+        """z = D r, or D^T r with transpose, with the per-cell inverse blocks (rte_block_apply)."""
         import torch
         _check(load().rte_block_apply(self.ptr, int(transpose), _dev(r, torch.float32, self.n),
                                       _dev(z, torch.float32, self.n)), self.ptr)
         return z
 
     def reconstruct(self, x, psi):
+        """Angular flux at the cell centres, psi float64 [M][N] (rte_reconstruct)."""
         import torch
         _check(load().rte_reconstruct(self.ptr, _dev(x, torch.float64, self.n),
                                       _dev(psi, torch.float64, self.M * self.N)), self.ptr)
         return psi
 
     def export_basis(self):
+        """(xi [nmat][2M], L [nmat][M][2M], material of every cell) (rte_export_basis)."""
         info = self.info()
         nmat, M, N = info["nmat"], self.M, self.N
         xi = np.zeros((nmat, 2 * M))
@@ -546,6 +577,8 @@ class Context:
         return w
 
     def cgs2(self, V, k, w, h):
+        """One classical Gram-Schmidt step with reorthogonalisation of w against k vectors of V
+        (rte_cgs2)."""
         import torch
         _check(load().rte_cgs2(self.ptr, _dev(V, torch.float64, k * self.n), int(k),
                                _dev(w, torch.float64, self.n), _dev(h, torch.float64, k + 1)),
@@ -579,12 +612,14 @@ class Context:
         return m.reshape(2 * self.M, self.I * self.I)
 
     def atfps_apply(self, y, out):
+        """out = F y, the kept interface projections (rte_atfps_apply)."""
         import torch
         _check(load().rte_atfps_apply(self.ptr, _dev(y, torch.float64, self.n),
                                       _dev(out, torch.float64, self.atfps_rows)), self.ptr)
         return out
 
     def atfps_apply_t(self, r, y):
+        """y = F^T r (rte_atfps_apply_t)."""
         import torch
         _check(load().rte_atfps_apply_t(self.ptr, _dev(r, torch.float64, self.atfps_rows),
                                         _dev(y, torch.float64, self.n)), self.ptr)
@@ -598,6 +633,7 @@ class Context:
 
     def solve(self, x, pc=None, tol=1e-8, restart=50, max_iter=20000, inner_precision=RTE_F32,
               use_x0=False, stall_ratio=0.9, timeout_ms=0.0, raise_on_error=True):
+        """FGMRES(restart) solve of A x = b (rte_solve); pc None is block Jacobi. Returns the info dict."""
         import torch
         o = SolveOpts()
         load().rte_solve_opts_default(ctypes.byref(o))
