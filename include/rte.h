@@ -187,7 +187,7 @@ RTE_API rte_status rte_response_apply(rte_ctx* ctx, const double* v_dev, double*
  * at V_dev + j*n) by classical Gram-Schmidt with one reorthogonalisation,
  * w <- w - V (V^T w) twice; h_dev[0..k-1] receives the summed projections and
  * h_dev[k] = ||w|| after orthogonalisation; w is then scaled to unit norm
- * unless that norm is zero.  1 <= k <= 128.  Asynchronous.
+ * unless that norm is zero.  1 <= k <= 64 (EINVAL otherwise).  Asynchronous.
  * ------------------------------------------------------------------------- */
 RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_dev, double* h_dev);
 
@@ -210,9 +210,10 @@ RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_
  * 640 blocks x 64 projections, the two projection vectors, a ticket counter),
  * present on every GPU that loads the library until the process exits.
  * Limits: 1 <= k <= 64 (EINVAL otherwise), n >= 1, device ordinal < 64.
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call on a device shares the array and the ticket is cleared
+ * The first successful call on a device looks up the array's device address
+ * (with that device current) and caches it; make that first call before any
+ * stream capture.  A look-up that fails is not cached: the next call tries
+ * again.  Every call on a device shares the array and the ticket is cleared
  * at the start of each call, so calls that overlap on the GPU (other streams
  * or threads) race: serialise them.  Calls nothing that allocates.
  * ------------------------------------------------------------------------- */

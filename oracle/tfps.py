@@ -191,6 +191,21 @@ class Problem:
         # decay factor of each slot at each face: d[k, f, cell] (Eq. 2D_eigenfunc)
         self.dec = self._decays()
 
+    def use_basis(self, xi, L):
+        """Replace the eigenbases by given ones (same materials, same slot order).
+
+        xi (nmat, 2M), L (nmat, M, 2M).  The operator of Eq. 2DTFPS_linear_sys
+        is then assembled on exactly those eigenpairs, so an implementation that
+        exports its own basis can be compared on A alone, apart from how its
+        eigen-solver rounds the slowly decaying modes (whose conditioning is
+        1/(1 - gamma)).  Returns self."""
+        xi = np.asarray(xi, np.float64).reshape(self.nmat, 2 * self.M)
+        L = np.asarray(L, np.float64).reshape(self.nmat, self.M, 2 * self.M)
+        self.xi = xi.copy()
+        self.L = L.copy()
+        self.dec = self._decays()
+        return self
+
     # slot k -> the face its basis function is centred at (0..3)
     def slot_face(self, k):
         return k // (self.M // 2)

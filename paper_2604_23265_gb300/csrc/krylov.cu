@@ -482,12 +482,35 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 // looked up once per device with that device current and cached here.
 constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocDevice {
-    std::once_flag once;
+    std::mutex mu;
+    bool ready = false;          // set only once every set-up step succeeded
     double* ptr = nullptr;
     int num_sms = 0;
-    cudaError_t err = cudaSuccess;
 };
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+// Looks up the scratch array's device address and the launch limits of this
+// device once; a failure (e.g. during a stream capture, or with a pending
+// error) is returned and not cached, so a later call retries.
+cudaError_t noalloc_setup(NoAllocDevice& d, int dev) {
+    std::lock_guard<std::mutex> lock(d.mu);
+    if (d.ready) return cudaSuccess;
+    double* ptr = nullptr;
+    int sms = 0;
+    cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mdot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kMaxKrylov * kT * sizeof(double)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kMaxKrylov * kT * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    d.ptr = ptr;
+    d.num_sms = sms;
+    d.ready = true;
+    return cudaSuccess;
+}
 
 int noalloc_grid(int64_t n, int num_sms, int per_sm) {
     per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
@@ -520,18 +543,8 @@ extern "C" RTE_API rte_status rte_cgs2_noalloc(const double* V_dev, int k, int64
         return RTE_EINVAL;
     }
     NoAllocDevice& d = g_noalloc_dev[dev];
-    std::call_once(d.once, [&d, dev]() {
-        d.err = cudaGetSymbolAddress((void**)&d.ptr, g_noalloc_scratch);
-        if (d.err == cudaSuccess)
-            d.err = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (d.err == cudaSuccess)
-            d.err = cudaFuncSetAttribute(k_mdot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxKrylov * kT * sizeof(double)));
-        if (d.err == cudaSuccess)
-            d.err = cudaFuncSetAttribute(k_update_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxKrylov * kT * sizeof(double)));
-    });
-    if (d.err != cudaSuccess) return cuda_status(nullptr, d.err, "rte_cgs2_noalloc set-up");
+    e = noalloc_setup(d, dev);
+    if (e != cudaSuccess) return cuda_status(nullptr, e, "rte_cgs2_noalloc set-up");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* partials = d.ptr;
     double* h1 = partials + (size_t)kNoAllocBlocks * kMaxKrylov;

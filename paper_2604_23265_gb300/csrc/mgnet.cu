@@ -79,6 +79,7 @@ struct mgnet {
     // helpers for the per-sample scalars
     double* d_scal = nullptr;
     double* h_scal = nullptr;
+    double* d_part = nullptr;        // [2 x 2048] block partial sums (inside d_scal's allocation)
 
     int C(int l) const { int c = c0 << l; return c < cmax ? c : cmax; }
     int Cc(int l) const { int c = cc << l; return c < ccmax ? c : ccmax; }
@@ -144,9 +145,15 @@ struct Acts {
     std::vector<float*> gf, gu, t1, t2b, t3;
     float *gpsi, *gtmp;
     float *wloss, *rloss, *scr;
+    float* wpart;                  // partial sums of the deterministic weight gradients
+    size_t wpart_floats;
 };
 
 size_t level_elems(mgnet* n, int B, int I, int l) { return (size_t)B * n->C(l) * (I >> l) * (I >> l); }
+
+// floats of the weight-gradient partial sums: at least every parameter once
+// (one partial block of the largest layer) and 4 Mi (16 MB)
+size_t wpart_floats(mgnet* n) { return n->np > ((size_t)1 << 22) ? n->np : ((size_t)1 << 22); }
 
 Acts carve(mgnet* n, Arena& ar, int B, int I) {
     Acts a{};
@@ -158,6 +165,8 @@ Acts carve(mgnet* n, Arena& ar, int B, int I) {
     a.wloss = ar.f(nin);
     a.rloss = ar.f(nin);
     a.scr = ar.f(nin);
+    a.wpart_floats = wpart_floats(n);
+    a.wpart = ar.f(a.wpart_floats);
     const int L = n->L;
     for (int l = 0; l < L; ++l) {
         const size_t e = level_elems(n, B, I, l);
@@ -188,7 +197,7 @@ Acts carve(mgnet* n, Arena& ar, int B, int I) {
 }
 
 size_t arena_bytes(mgnet* n, int B, int I) {
-    size_t total = 7 * ((size_t)B * 2 * n->M * I * I * 4 + 256);
+    size_t total = 7 * ((size_t)B * 2 * n->M * I * I * 4 + 256) + wpart_floats(n) * 4 + 256;
     for (int l = 0; l < n->L; ++l) total += 15 * (level_elems(n, B, I, l) * 4 + 256);
     total += 6 * (level_elems(n, B, I, n->L - 1) * 4 + 256);
     return total + 4096;
@@ -548,6 +557,11 @@ void tc_precondition(mgnet* n, const TcSamples& S, int I) {
 // ------------------------------------------------------------------ backward
 // Given a.gpsi (dLoss/dpsi), accumulate every parameter gradient into n->g.
 void backward(mgnet* n, Features& F, Acts& a, rte_ctx* ctx, int B, int I) {
+    nn::WgradScratch wscr{a.wpart, a.wpart_floats, ctx->num_sms};
+    struct ResetScratch {
+        ~ResetScratch() { nn::tl_wgrad_scratch = nullptr; }
+    } reset_scratch;
+    nn::tl_wgrad_scratch = &wscr;
     const int L = n->L, M2 = 2 * n->M;
     const Taps t3 = nn::taps_conv(3, 1), t1 = nn::taps_conv(1, 0), t4 = nn::taps_conv(4, 1);
     cudaStream_t st = n->stream;
@@ -693,9 +707,12 @@ __global__ void k_scale_out(const float* __restrict__ psi, int64_t n, const doub
         z[i] = psi[i] * s;
 }
 
-// out[0] += sum a^2, out[1] += sum b^2 (float inputs, double sums)
+// Block partial sums of the loss norms, added in a fixed order by k_finish_pairs
+// (no atomics: the loss and its gradient are the same bits on every run).
+// part[2 blockIdx.x + {0, 1}] = the block's sums of a^2 and b^2 (float inputs,
+// double sums)
 __global__ void k_norms2(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
-                         double* __restrict__ out) {
+                         double* __restrict__ part) {
     __shared__ double ra[32], rb[32];
     double sa = 0.0, sb = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -711,8 +728,26 @@ __global__ void k_norms2(const float* __restrict__ a, const float* __restrict__ 
     if (threadIdx.x == 0) {
         double ta = 0.0, tb = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += ra[w]; tb += rb[w]; }
-        atomicAdd(out, ta);
-        atomicAdd(out + 1, tb);
+        part[2 * blockIdx.x] = ta;
+        part[2 * blockIdx.x + 1] = tb;
+    }
+}
+
+// out[k] += sum over blocks b < nb of part[width b + k], k < width (one block
+// of 256 threads; fixed summation order)
+__global__ void k_finish_pairs(const double* __restrict__ part, int nb, int width, double* __restrict__ out) {
+    __shared__ double red[256];
+    for (int k = 0; k < width; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)width * b + k];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] += red[0];
+        __syncthreads();
     }
 }
 
@@ -728,9 +763,9 @@ __global__ void k_sub_from_d(double* __restrict__ y, const float* __restrict__ x
         y[i] -= (double)x[i];
 }
 
-// out[0] += ||a||^2 (double), out[1] += ||b||^2 (float)
+// part[2 blockIdx.x + {0, 1}] = the block's ||a||^2 (double) and ||b||^2 (float)
 __global__ void k_sumsq_df(const double* __restrict__ a, int64_t na, const float* __restrict__ b, int64_t nb,
-                           double* __restrict__ out) {
+                           double* __restrict__ part) {
     __shared__ double ra[32], rb[32];
     double sa = 0.0, sb = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -746,8 +781,8 @@ __global__ void k_sumsq_df(const double* __restrict__ a, int64_t na, const float
     if (threadIdx.x == 0) {
         double ta = 0.0, tb = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += ra[w]; tb += rb[w]; }
-        atomicAdd(out, ta);
-        atomicAdd(out + 1, tb);
+        part[2 * blockIdx.x] = ta;
+        part[2 * blockIdx.x + 1] = tb;
     }
 }
 
@@ -757,7 +792,8 @@ __global__ void k_sub_f(const float* __restrict__ a, const float* __restrict__ b
         out[i] = a[i] - b[i];
 }
 
-__global__ void k_double_norm(const double* __restrict__ r, int64_t n, double* __restrict__ out) {
+// part[blockIdx.x] = the block's sum of r^2
+__global__ void k_double_norm(const double* __restrict__ r, int64_t n, double* __restrict__ part) {
     __shared__ double red[32];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -768,7 +804,7 @@ __global__ void k_double_norm(const double* __restrict__ r, int64_t n, double* _
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(out, t);
+        part[blockIdx.x] = t;
     }
 }
 
@@ -794,7 +830,8 @@ void load_inputs(mgnet* n, rte_ctx* ctx, const double* const* r, int B, Acts& a)
     const int64_t len = ctx->n;
     check(cudaMemsetAsync(n->d_scal, 0, 64 * sizeof(double), n->stream), "memset");
     for (int b = 0; b < B; ++b) {
-        k_double_norm<<<grid_for(len), 256, 0, n->stream>>>(r[b], len, n->d_scal + b);
+        k_double_norm<<<grid_for(len), 256, 0, n->stream>>>(r[b], len, n->d_part);
+        k_finish_pairs<<<1, 256, 0, n->stream>>>(n->d_part, grid_for(len), 1, n->d_scal + b);
     }
     k_sqrt_inplace<<<1, 64, 0, n->stream>>>(n->d_scal, B);
     for (int b = 0; b < B; ++b)
@@ -829,7 +866,8 @@ double loss_and_seed_filtered(mgnet* n, rte_ctx* ctx, Acts& a, int B) {
         launch_apply(ctx, true, alpha, y, true, nullptr);                   // A alpha
         k_sub_from_d<<<grid_for(len), 256, 0, n->stream>>>(y, x, len);
         atfps_apply(ctx, y, res + (size_t)b * R);
-        k_sumsq_df<<<grid_for(len), 256, 0, n->stream>>>(res + (size_t)b * R, R, x, len, sums + 2 * b);
+        k_sumsq_df<<<grid_for(len), 256, 0, n->stream>>>(res + (size_t)b * R, R, x, len, n->d_part);
+        k_finish_pairs<<<1, 256, 0, n->stream>>>(n->d_part, grid_for(len), 2, sums + 2 * b);
     }
     check(cudaGetLastError(), "filtered loss");
     check(cudaMemcpyAsync(n->h_scal, sums, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, n->stream), "d2h");
@@ -860,7 +898,8 @@ double loss_and_seed(mgnet* n, rte_ctx* ctx, Acts& a, int B) {
         const float* x = a.x + (size_t)b * len;
         launch_response_apply(ctx, psi, false, a.wloss, false);            // B psi
         k_sub_f<<<grid_for(len), 256, 0, n->stream>>>(x, a.wloss, len, a.rloss + 0);
-        k_norms2<<<grid_for(len), 256, 0, n->stream>>>(a.rloss, x, len, sums + 2 * b);
+        k_norms2<<<grid_for(len), 256, 0, n->stream>>>(a.rloss, x, len, n->d_part);
+        k_finish_pairs<<<1, 256, 0, n->stream>>>(n->d_part, grid_for(len), 2, sums + 2 * b);
         launch_response_apply_t(ctx, a.rloss, a.gpsi + (size_t)b * len, a.scr);   // B^T res
     }
     check(cudaMemcpyAsync(n->h_scal, sums, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, n->stream), "d2h");
@@ -978,7 +1017,8 @@ RTE_API rte_status mgnet_create(const mgnet_config* cfg, void* stream, mgnet** o
     n->m = n->g + n->np;
     n->v = n->m + n->np;
     check(cudaMemsetAsync(n->p, 0, n->np * 16, n->stream), "memset");
-    check(cudaMalloc(&n->d_scal, 128 * sizeof(double)), "cudaMalloc");
+    check(cudaMalloc(&n->d_scal, (128 + 2 * 2048) * sizeof(double)), "cudaMalloc");
+    n->d_part = n->d_scal + 128;
     check(cudaMallocHost(&n->h_scal, 128 * sizeof(double)), "cudaMallocHost");
     check(cudaStreamSynchronize(n->stream), "sync");
     *out = n;

@@ -73,6 +73,15 @@ struct Counters {
 };
 extern thread_local Counters* tl_counters;
 
+// Partial-sum scratch of the deterministic weight gradient (wgrad): cap floats
+// on the device; set by the network around its backward pass.
+struct WgradScratch {
+    float* part = nullptr;
+    size_t cap = 0;
+    int num_sms = 1;
+};
+extern thread_local WgradScratch* tl_wgrad_scratch;
+
 void conv(const ConvArgs& a, cudaStream_t st);
 // Tensor-core (tcgen05) gather convolution of the inference forward pass
 // (conv_tc.cu): BF16 operands, FP32 accumulation.  Activations are BF16 in the
@@ -122,6 +131,8 @@ void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int classes
 void tc_conv(const TcConv& a, bool pdl, cudaStream_t st);
 // 1 once a bounded wait of the tensor-core kernel expired (reset on request).
 int conv_tc_status(bool reset);
+// dw += the weight gradient of one convolution; deterministic (per-CTA
+// partial sums in tl_wgrad_scratch, added in a fixed order, no atomics)
 void wgrad(const WgradArgs& a, cudaStream_t st);
 void bn_stats(const float* x, int B, int C, int HW, float* mean, float* invstd, cudaStream_t st);
 void bn_relu(const float* x, int B, int C, int HW, const float* mean, const float* invstd,

@@ -13,6 +13,8 @@
 //   v = acc (+ bias[o]) (+ cst); raw = v; v *= gate; v *= mask > 0;
 //   v = sign v (+ base) (+ y);  y = v.
 // Weight gradients use the same tap tables (k_wgrad).
+#include <cmath>
+
 #include "nn_internal.h"
 
 namespace rte {
@@ -155,47 +157,87 @@ __global__ void __launch_bounds__(256) k_conv_small(ConvArgs a) {
 
 // dW[(o so + i si) KK + wi_t] += sum_{b, gy, gx} G[b][o][OS gy + OY0][OS gx + OX0]
 //                                      * X[b][i][S gy + dy_t][S gx + dx_t]
-// CTA: 16 o x 16 i over an 8 x 8 class-grid tile of one batch entry.
-__global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
+// Deterministic in two launches.  k_wgrad: CTA (x, y) owns 16 o x 16 i
+// (y) and the work items q = x, x + P, x + 2P, ... of the (batch entry,
+// 8 x 8 class-grid tile) list; it accumulates them in that order in
+// registers (one sum per tap) and writes its partial sums to
+// part[x][o][i][t].  k_wgrad_reduce adds the P partials of every weight in
+// order x = 0..P-1 onto dW.  No atomics: a training step gives the same bits
+// on every run.
+__global__ void __launch_bounds__(256) k_wgrad(WgradArgs a, int P, float* __restrict__ part) {
     __shared__ float gs[16][kTileG * kTileG];
     __shared__ float xs[16][kMaxPatch][kMaxPatch + 1];
     const int tid = threadIdx.x;
     const int tilesx = (a.Wg + kTileG - 1) / kTileG;
-    const int gy0 = (blockIdx.x / tilesx) * kTileG, gx0 = (blockIdx.x % tilesx) * kTileG;
+    const int tiles = tilesx * ((a.Hg + kTileG - 1) / kTileG);
+    const int items = tiles * a.B;
     const int otiles = (a.Co + 15) / 16;
     const int o0 = (blockIdx.y % otiles) * 16, i0 = (blockIdx.y / otiles) * 16;
-    const int b = blockIdx.z;
     const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
     const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
-    for (int e = tid; e < 16 * kTileG * kTileG; e += 256) {
-        const int o = e / (kTileG * kTileG), p = e - o * kTileG * kTileG;
-        const int gy = gy0 + p / kTileG, gx = gx0 + p % kTileG;
-        float v = 0.f;
-        if (o0 + o < a.Co && gy < a.Hg && gx < a.Wg)
-            v = a.g[(((size_t)b * a.Co + o0 + o) * a.Hgo + a.OS * gy + a.OY0) * a.Wgo + a.OS * gx + a.OX0];
-        gs[o][p] = v;
-    }
-    for (int e = tid; e < 16 * PY * PX; e += 256) {
-        const int i = e / (PY * PX), rem = e - i * PY * PX;
-        const int yy = rem / PX, xx = rem - yy * PX;
-        const int iy = a.S * gy0 + a.tp.dymin + yy, ix = a.S * gx0 + a.tp.dxmin + xx;
-        float v = 0.f;
-        if (i0 + i < a.Ci && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi) {
-            v = a.x[(((size_t)b * a.Ci + i0 + i) * a.Hi + iy) * a.Wi + ix];
-            if (a.relu_in) v = fmaxf(v, 0.f);
-        }
-        xs[i][yy][xx] = v;
-    }
-    __syncthreads();
     const int o = tid >> 4, i = tid & 15;
-    if (o0 + o >= a.Co || i0 + i >= a.Ci) return;
-    for (int t = 0; t < a.tp.T; ++t) {
-        float acc = 0.f;
-        for (int p = 0; p < kTileG * kTileG; ++p) {
-            const int py = p / kTileG, px = p - py * kTileG;
-            acc = fmaf(gs[o][p], xs[i][a.S * py + a.tp.dy[t] - a.tp.dymin][a.S * px + a.tp.dx[t] - a.tp.dxmin], acc);
+    const bool own = (o0 + o < a.Co) && (i0 + i < a.Ci);
+    float acc[kMaxTaps];
+#pragma unroll
+    for (int t = 0; t < kMaxTaps; ++t) acc[t] = 0.f;
+    for (int q = blockIdx.x; q < items; q += P) {
+        const int b = q / tiles, tile = q - b * tiles;
+        const int gy0 = (tile / tilesx) * kTileG, gx0 = (tile % tilesx) * kTileG;
+        __syncthreads();                 // the previous item's reads are done
+        for (int e = tid; e < 16 * kTileG * kTileG; e += 256) {
+            const int oo = e / (kTileG * kTileG), p = e - oo * kTileG * kTileG;
+            const int gy = gy0 + p / kTileG, gx = gx0 + p % kTileG;
+            float v = 0.f;
+            if (o0 + oo < a.Co && gy < a.Hg && gx < a.Wg)
+                v = a.g[(((size_t)b * a.Co + o0 + oo) * a.Hgo + a.OS * gy + a.OY0) * a.Wgo + a.OS * gx + a.OX0];
+            gs[oo][p] = v;
         }
-        atomicAdd(&a.dw[((size_t)(o0 + o) * a.so + (size_t)(i0 + i) * a.si) * a.KK + a.tp.wi[t]], acc);
+        for (int e = tid; e < 16 * PY * PX; e += 256) {
+            const int ii = e / (PY * PX), rem = e - ii * PY * PX;
+            const int yy = rem / PX, xx = rem - yy * PX;
+            const int iy = a.S * gy0 + a.tp.dymin + yy, ix = a.S * gx0 + a.tp.dxmin + xx;
+            float v = 0.f;
+            if (i0 + ii < a.Ci && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi) {
+                v = a.x[(((size_t)b * a.Ci + i0 + ii) * a.Hi + iy) * a.Wi + ix];
+                if (a.relu_in) v = fmaxf(v, 0.f);
+            }
+            xs[ii][yy][xx] = v;
+        }
+        __syncthreads();
+        if (own) {
+#pragma unroll
+            for (int t = 0; t < kMaxTaps; ++t) {
+                if (t < a.tp.T) {
+                    const int ty = a.tp.dy[t] - a.tp.dymin, tx = a.tp.dx[t] - a.tp.dxmin;
+                    float s = 0.f;          // the tile's sum, then added (two-level summation)
+                    for (int p = 0; p < kTileG * kTileG; ++p) {
+                        const int py = p / kTileG, px = p - py * kTileG;
+                        s = fmaf(gs[o][p], xs[i][a.S * py + ty][a.S * px + tx], s);
+                    }
+                    acc[t] += s;
+                }
+            }
+        }
+    }
+    if (!own) return;
+    float* dst = part + (((size_t)blockIdx.x * a.Co + o0 + o) * a.Ci + i0 + i) * a.tp.T;
+#pragma unroll
+    for (int t = 0; t < kMaxTaps; ++t)
+        if (t < a.tp.T) dst[t] = acc[t];
+}
+
+// dW[(o so + i si) KK + wi_t] += sum_{x < P} part[x][o][i][t], x ascending.
+// The taps of one launch address distinct weights (checked on the host), so
+// every weight has one writer.
+__global__ void k_wgrad_reduce(WgradArgs a, int P, const float* __restrict__ part) {
+    const size_t per = (size_t)a.Co * a.Ci * a.tp.T;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per; e += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int x = 0; x < P; ++x) s += part[(size_t)x * per + e];
+        const int t = (int)(e % a.tp.T);
+        const size_t oi = e / a.tp.T;
+        const int i = (int)(oi % a.Ci), o = (int)(oi / a.Ci);
+        a.dw[((size_t)o * a.so + (size_t)i * a.si) * a.KK + a.tp.wi[t]] += s;
     }
 }
 
@@ -343,13 +385,17 @@ __global__ void k_channel_sum(const float* __restrict__ g, int B, int C, int HW,
     }
 }
 
+// Adam (Kingma & Ba): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+// p -= lr (m / c1) / (sqrt(v / c2) + eps), c_i = 1 - b_i^t.  The constants
+// 1 - b_i and c_i come from the host, computed in FP64 and rounded once (in
+// FP32, 1 - 0.999f is 1.3e-5 away from 1e-3).
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       float* __restrict__ v, size_t n, float lr, float b1, float b2, float omb1,
+                       float omb2, float eps, float c1, float c2) {
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[e];
-        const float mi = b1 * m[e] + (1.f - b1) * gi;
-        const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+        const float mi = b1 * m[e] + omb1 * gi;
+        const float vi = b2 * v[e] + omb2 * gi * gi;
         m[e] = mi;
         v[e] = vi;
         p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -390,14 +436,34 @@ void conv(const ConvArgs& a, cudaStream_t st) {
     check(cudaGetLastError(), "k_conv");
 }
 
+thread_local WgradScratch* tl_wgrad_scratch = nullptr;
+
 void wgrad(const WgradArgs& a, cudaStream_t st) {
     const int PY = (kTileG - 1) * a.S + (a.tp.dymax - a.tp.dymin) + 1;
     const int PX = (kTileG - 1) * a.S + (a.tp.dxmax - a.tp.dxmin) + 1;
-    if (PY > kMaxPatch || PX > kMaxPatch || a.tp.T > kMaxTaps)
+    if (PY > kMaxPatch || PX > kMaxPatch || a.tp.T > kMaxTaps || a.tp.T < 1)
         throw StatusError{RTE_EINVAL, "wgrad tile too large"};
+    for (int t = 0; t < a.tp.T; ++t)
+        for (int u = 0; u < t; ++u)
+            if (a.tp.wi[t] == a.tp.wi[u]) throw StatusError{RTE_EINVAL, "wgrad: repeated weight tap"};
+    const WgradScratch* ws = tl_wgrad_scratch;
+    if (!ws || !ws->part) throw StatusError{RTE_EINVAL, "wgrad: no partial-sum scratch"};
     const int tiles = ((a.Hg + kTileG - 1) / kTileG) * ((a.Wg + kTileG - 1) / kTileG);
-    dim3 grid(tiles, ((a.Co + 15) / 16) * ((a.Ci + 15) / 16), a.B);
-    k_wgrad<<<grid, 256, 0, st>>>(a);
+    const int items = tiles * a.B;
+    const int oi = ((a.Co + 15) / 16) * ((a.Ci + 15) / 16);
+    const size_t per = (size_t)a.Co * a.Ci * a.tp.T;
+    // about four CTAs per SM in all, at most one partial block per work item,
+    // and the partials within the scratch
+    int P = (4 * ws->num_sms + oi - 1) / oi;
+    if (P > items) P = items;
+    const size_t fit = ws->cap / per;
+    if (fit < 1) throw StatusError{RTE_EINVAL, "wgrad: layer larger than the partial-sum scratch"};
+    if ((size_t)P > fit) P = (int)fit;
+    if (P < 1) P = 1;
+    dim3 grid(P, oi);
+    k_wgrad<<<grid, 256, 0, st>>>(a, P, ws->part);
+    const size_t rb = (per + 255) / 256;
+    k_wgrad_reduce<<<(unsigned)(rb < 4096 ? rb : 4096), 256, 0, st>>>(a, P, ws->part);
     check(cudaGetLastError(), "k_wgrad");
 }
 
@@ -443,8 +509,12 @@ void channel_sum(const float* g, int B, int C, int HW, float* out, cudaStream_t 
 
 void adam(float* p, const float* g, float* m, float* v, size_t n, float lr, int step, cudaStream_t st) {
     const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-    k_adam<<<ew_blocks(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
+    // bias corrections 1 - beta^t in FP64, then rounded once: in FP32,
+    // 1 - 0.999f^t loses about five digits to cancellation at small t
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)step));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)step));
+    k_adam<<<ew_blocks(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, (float)(1.0 - 0.9), (float)(1.0 - 0.999),
+                                         1e-8f, c1, c2);
     check(cudaGetLastError(), "k_adam");
 }
 

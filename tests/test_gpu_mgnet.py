@@ -1,8 +1,9 @@
 """GPU parity of the MgNet preconditioner against the FP64 oracle (same seeded
 weights and inputs): forward, loss, every parameter's gradient, training and
 the MgNet-preconditioned solve.  FP32 network arithmetic: relative L2 bars of
-1e-4 (outputs) and 2e-3 (gradients, sums over up to 65k products); the
-tensor-core forward (BF16 operands): 2e-2."""
+1e-4 (outputs) and 1e-3 (gradients: the bar the oracle's own gradients meet
+against finite differences; FP32 sums over up to 65k products stay two orders
+below it); the tensor-core forward (BF16 operands): 2e-2."""
 import numpy as np
 import pytest
 
@@ -145,7 +146,8 @@ def test_loss_and_gradients_match_oracle(lib, levels, batch):
     G = rte.MgNet.unflatten(g, shape)
     for k in gref:
         scale = max(np.linalg.norm(gref[k]), 1e-3 * max(np.linalg.norm(v) for v in gref.values()))
-        assert np.linalg.norm(G[k] - gref[k]) <= 2e-3 * scale, k
+        err = np.linalg.norm(G[k] - gref[k]) / scale
+        assert err <= 1e-3, (k, err)
 
 
 def test_training_reduces_loss(lib):

@@ -104,6 +104,44 @@ def test_adam_first_step_moves_by_lr_sign():
     np.testing.assert_allclose(p["w"], [0.99, -1.99, 2.99], atol=1e-7)
 
 
+def test_adam_constant_gradient_moves_by_lr_every_step():
+    """With a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every step t (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so each of
+    five steps moves a parameter by lr g / (|g| + eps).  A wrong power of
+    either beta in the bias corrections breaks this from step 2 on."""
+    g0 = np.array([0.5, -4.0, 2e-3, 7.0])
+    p = {"w": np.zeros(4)}
+    st = {}
+    lr, eps = 0.01, 1e-8
+    for t in range(1, 6):
+        mgnet.adam_step(p, {"w": g0.copy()}, st, lr=lr)
+        np.testing.assert_allclose(p["w"], -t * lr * g0 / (np.abs(g0) + eps), rtol=1e-12, atol=0)
+        np.testing.assert_allclose(st["m"]["w"], (1 - 0.9 ** t) * g0, rtol=1e-13)
+        np.testing.assert_allclose(st["v"]["w"], (1 - 0.999 ** t) * g0 ** 2, rtol=1e-13)
+
+
+def test_adam_alternating_gradient_closed_form():
+    """Gradient (-1)^(t+1) g: the geometric sums give
+    m_t = (1 - b1) g (-1)^(t+1) (1 - (-b1)^t) / (1 + b1) and v_t = (1 - b2^t) g^2,
+    so the step at t is lr (-1)^(t+1) g c_t / (|g| + eps) with
+    c_t = (1 - b1)(1 - (-b1)^t) / ((1 + b1)(1 - b1^t)): c_1 = 1, c_2 = 1/19.
+    Pins the relative weighting of old and new gradients in m (a swapped b1
+    and 1 - b1 gives c_2 = 0.81/0.19 instead) and the bias correction of v."""
+    b1 = 0.9
+    g0 = np.array([3.0, -0.25])
+    p = {"w": np.zeros(2)}
+    st = {}
+    lr = 0.1
+    expect = np.zeros(2)
+    for t in range(1, 6):
+        sgn = (-1.0) ** (t + 1)
+        mgnet.adam_step(p, {"w": sgn * g0}, st, lr=lr)
+        c = (1 - b1) * (1 - (-b1) ** t) / ((1 + b1) * (1 - b1 ** t))
+        expect = expect - lr * sgn * g0 * c / (np.abs(g0) + 1e-8)
+        np.testing.assert_allclose(p["w"], expect, rtol=1e-12, atol=1e-16)
+    assert abs((1 - b1) * (1 - b1 ** 2) / ((1 + b1) * (1 - b1 ** 2)) - 1 / 19) < 1e-15
+
+
 def test_cosine_schedule_endpoints():
     assert mgnet.cosine_lr(1e-3, 0, 100) == 1e-3
     assert abs(mgnet.cosine_lr(1e-3, 100, 100)) < 1e-18

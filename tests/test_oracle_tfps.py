@@ -220,6 +220,26 @@ def test_P9_AD_invariant_to_eigenvector_signs():
     np.testing.assert_allclose(y1, y2, atol=1e-12)
 
 
+def test_use_basis_takes_the_given_eigenpairs():
+    """Problem.use_basis (how a device's exported basis enters the oracle):
+    its own basis changes nothing; a basis with flipped column signs gives the
+    same traces for the coefficients with the same signs flipped (so the given
+    L is used); eigenvalues scaled by 2 give the decays of a cell twice as
+    thick (so the given xi is used)."""
+    I, M = 5, 8
+    md = W.polynomial_diffusion(3, I=I, M=M)
+    p = _problem(md)
+    x = W.random_vector(2 * M * p.N, 4).reshape(2 * M, -1)
+    y0 = p.apply(x)
+    q = _problem(md).use_basis(p.xi, p.L)
+    np.testing.assert_array_equal(q.apply(x), y0)
+    flip = np.where(np.random.default_rng(3).uniform(size=2 * M) < 0.5, -1.0, 1.0)
+    q = _problem(md).use_basis(p.xi, p.L * flip[None, None, :])
+    np.testing.assert_allclose(q.apply(x * flip[:, None]), y0, rtol=0, atol=1e-14 * np.abs(y0).max())
+    q = _problem(md).use_basis(2 * p.xi, p.L)
+    np.testing.assert_allclose(q.dec, _problem(md).dec ** 2, rtol=1e-13, atol=0)
+
+
 def test_P10_adjoint_dot():
     I, M = 7, 16
     md = W.checkerboard_transport(1, I=I, M=M)
