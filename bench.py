@@ -194,49 +194,63 @@ def cpu_baseline(md, gpu_iters):
                        f"iterations (the GPU solve's count), n={n}")}
 
 
-# DRAM traffic per launch over the algorithmic bytes, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel at 128 x 128
-# cells, M = 32, 26 basis vectors; the bench scales it by the algorithmic
-# bytes of its own average launch.  The fused second Gram-Schmidt pass
-# re-reads part of V from DRAM (its chunk of 26 vectors does not stay in L1/L2
-# between the update and the dots); the pass is FP64-bound, so the re-read
-# costs no time.
-TRAFFIC_RATIO = {"update_dot": 1.756, "mdot": 1.014, "update_norm": 0.986, "response_apply": 0.995}
+# DRAM traffic per launch over the algorithmic bytes, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum); the bench scales it by the
+# algorithmic bytes of its own average launch.  The df64 Gram-Schmidt passes
+# read each basis row once (the second pass re-reads it from shared memory).
+TRAFFIC_RATIO = {"response_apply": 0.995}
+TRAFFIC_SOURCE = {"response_apply": "ncu DRAM bytes per launch at 128x128, M=32"}
+
+# Nominal FP64 rate of a GB300 (152 SMs x 2.07 GHz x 2 FP64 FMA per clock x 2
+# flops): the roof of the FP64 operator apply, the one FP64-bound kernel left.
+FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
+
+# kernel classes whose time is bound by the FP64 pipe (everything else of the
+# solve streams memory, or is latency: the network is on the tensor cores)
+FP64_BOUND = {"traces", "build_invert", "response_build"}
 
 
 def _roofline(rte, stream, prof):
-    """Roofline of the dominant kernel class (largest summed event time)."""
+    """Roofline of the dominant kernel class (largest summed event time), and
+    every class's fraction of its own roof."""
     kname, (kl, kms, kbytes, kflops) = max(prof.items(), key=lambda kv: kv[1][1])
     hbm_peak, peak_src = _peaks()
     total_ms = max(sum(v[1] for v in prof.values()), 1e-9)
+    probe = rte.fp64_fma_rate(stream) / 1e3
+    hbm_src = ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s")
     if kname == "mgnet":
         peak, psrc = _bf16_peak()
         roof = {"bound": "tensor", "kernel": "mgnet convolutions (tcgen05, BF16)",
                 "achieved": kflops / (kms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": psrc}
-    elif kflops > 0:
-        # Gram-Schmidt passes: ~1 FP64 FMA per 8 bytes, below the memory ridge here
-        peak = rte.fp64_fma_rate(stream) / 1e3
+    elif kname in FP64_BOUND:
         roof = {"bound": "alu", "kernel": kname, "achieved": kflops / (kms / 1e3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "measured FP64 FMA throughput (rte_fp64_fma_rate, same run)"}
+                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 4 flops/clk); measured DFMA probe "
+                               "%.3f TFLOP/s in the same run" % probe}
     else:
         roof = {"bound": "hbm", "kernel": kname, "achieved": kbytes / (kms / 1e3) / 1e9,
-                "peak": hbm_peak, "unit": "GB/s",
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                else "fallback 6.8 TB/s"}
+                "peak": hbm_peak, "unit": "GB/s", "peak_source": hbm_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     ratio = TRAFFIC_RATIO.get(kname)
     roof["traffic"] = ratio * kbytes / kl if (ratio and kl) else None
     if ratio:
-        roof["traffic_source"] = ("ncu DRAM bytes per launch at 128x128, M=32, scaled by algorithmic "
-                                  "bytes per launch (ratio %.3f)" % ratio)
+        roof["traffic_source"] = "%s, scaled by algorithmic bytes per launch (ratio %.3f)" % (
+            TRAFFIC_SOURCE[kname], ratio)
     roof["launches"] = kl
     roof["share"] = kms / total_ms
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_ms, 4),
-                   "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None,
-                   "TFLOPs": round(v[3] / (v[1] / 1e3) / 1e12, 3) if v[1] > 0 and v[3] else None}
-               for k, v in prof.items() if v[0]}
+    kernels = {}
+    for k, v in prof.items():
+        if not v[0]:
+            continue
+        e = {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_ms, 4),
+             "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None,
+             "TFLOPs": round(v[3] / (v[1] / 1e3) / 1e12, 3) if v[1] > 0 and v[3] else None}
+        if v[1] > 0 and e["GBps"] is not None:
+            e["hbm_frac"] = round(e["GBps"] / hbm_peak, 3)
+        if k in FP64_BOUND and e["TFLOPs"]:
+            e["fp64_frac"] = round(e["TFLOPs"] / FP64_NOMINAL_TFLOPS, 3)
+        kernels[k] = e
     return roof, kernels
 
 

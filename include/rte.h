@@ -192,6 +192,28 @@ RTE_API rte_status rte_response_apply(rte_ctx* ctx, const double* v_dev, double*
 RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_dev, double* h_dev);
 
 /* ---------------------------------------------------------------------------
+ * rte_cgs2_df64 -- the Gram-Schmidt step of rte_cgs2 on df64 vectors, the
+ * arithmetic rte_solve uses for its Arnoldi process (Sec. 4, GMRES).  A df64
+ * vector of n elements is two float planes, hi [n] then lo [n], holding the
+ * value hi + lo with |lo| <= ulp(hi) (48 significant bits; a double x is
+ * stored as hi = (float)x, lo = (float)(x - hi)).  V_dev: k df64 vectors,
+ * vector j at V_dev + 2 j n (orthonormal); w_dev: one df64 vector,
+ * orthogonalised in place by two classical Gram-Schmidt passes with df64
+ * products and sums on the FP32 pipe, then scaled to unit norm unless that
+ * norm is zero; h_dev (double [k + 1]): the summed projections and the norm.
+ * 1 <= k <= 64 (EINVAL otherwise); n = the context's unknowns; all pointers
+ * 16-byte aligned.  ETIMEOUT if a bounded wait inside a pass ran out (the
+ * outputs are then NaN).  Asynchronous except for that check, which
+ * synchronises with the device.
+ * ------------------------------------------------------------------------- */
+RTE_API rte_status rte_cgs2_df64(rte_ctx* ctx, const float* V_dev, int k, float* w_dev, double* h_dev);
+
+/* rte_arnoldi_basis_df64 -- rte_arnoldi_basis with the df64 arithmetic of
+ * rte_solve: k (1..64) Arnoldi vectors of A D started from b / ||b||, written
+ * as df64 vectors (vector j at V_dev + 2 j n, float [k][2][n]).  Synchronous. */
+RTE_API rte_status rte_arnoldi_basis_df64(rte_ctx* ctx, int k, float* V_dev);
+
+/* ---------------------------------------------------------------------------
  * rte_cgs2_noalloc -- the Gram-Schmidt step of rte_cgs2 without a context and
  * without any device allocation.  No counterpart in the paper: it exists for
  * callers that cannot let a library allocate device memory -- an application
@@ -259,8 +281,9 @@ RTE_API rte_status rte_atfps_apply_t(rte_ctx* ctx, const double* r_dev, double* 
 
 /* ---------------------------------------------------------------------------
  * rte_solve -- solve A x = b for this context's b by right-preconditioned
- * flexible GMRES(restart): Arnoldi in FP64 with classical Gram-Schmidt plus
- * reorthogonalisation, Givens/Hessenberg least squares in FP64 on the device,
+ * flexible GMRES(restart): Arnoldi on df64 vectors (48 significant bits, see
+ * rte_cgs2_df64) with classical Gram-Schmidt plus reorthogonalisation,
+ * Givens/Hessenberg least squares in FP64 on the device,
  * inner operator applies in opts->inner_precision, and the true residual
  * ||b - A x|| / ||b|| recomputed in FP64 at the end of every cycle decides
  * convergence.  pc: NULL = block Jacobi (Sec. 4); else the MgNet

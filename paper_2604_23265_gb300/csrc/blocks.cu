@@ -14,6 +14,7 @@
 //
 // Storage: Dt[c][j][i] = D_C[i][j] (column-major per cell) so that the apply
 // z_i = sum_j D_ij r_j streams each block once with 16-byte loads.
+#include "df64.h"
 #include "rte_internal.h"
 
 namespace rte {
@@ -264,6 +265,38 @@ __global__ void k_gather(int I, int M, const TV* __restrict__ v, const TO* __res
     gather_run<TV, TO, TW>(I, M, v, o, w, blockIdx.x, gridDim.x);
 }
 
+// The same into a df64 w (planar hi / lo, df64.h): v is the FP32 vector vh
+// (vl null) or the df64 vector (vh, vl); o is FP32.  v - o is formed exactly
+// by TwoSum, so w carries v to 48 bits and the FP32 neighbour term exactly.
+__device__ void gather_df_run(int I, int M, const float* __restrict__ vh, const float* __restrict__ vl,
+                              const float* __restrict__ o, float* __restrict__ w, int bid, int nb) {
+    const int N = I * I, M2 = M / 2;
+    const int64_t n = (int64_t)2 * M * N;
+    for (int64_t e = (int64_t)bid * blockDim.x + threadIdx.x; e < n; e += (int64_t)nb * blockDim.x) {
+        const int row = (int)(e / N);
+        const int c = (int)(e - (int64_t)row * N);
+        const int f = row / M2, j = row - f * M2;
+        const int iy = c / I, ix = c - iy * I;
+        int nbr = -1;
+        if (f == 0 && ix > 0) nbr = c - 1;
+        if (f == 1 && ix < I - 1) nbr = c + 1;
+        if (f == 2 && iy > 0) nbr = c - I;
+        if (f == 3 && iy < I - 1) nbr = c + I;
+        const float ov = nbr >= 0 ? o[(int64_t)((f ^ 1) * M2 + j) * N + nbr] : 0.f;
+        float s, t, h, l;
+        df::two_sum(vh[e], -ov, s, t);
+        if (vl) t = __fadd_rn(t, vl[e]);
+        df::two_sum(s, t, h, l);
+        w[e] = h;
+        w[n + e] = l;
+    }
+}
+
+__global__ void k_gather_df(int I, int M, const float* __restrict__ vh, const float* __restrict__ vl,
+                            const float* __restrict__ o, float* __restrict__ w) {
+    gather_df_run(I, M, vh, vl, o, w, blockIdx.x, gridDim.x);
+}
+
 // q = P u: every row (f, j) of cell C takes the neighbour's row (opp f, j)
 // across f (zero on the boundary).  P is its own transpose.
 __global__ void k_permute(int I, int M, const float* __restrict__ u, float* __restrict__ q) {
@@ -482,19 +515,13 @@ __global__ void __launch_bounds__(256) k_block_apply_group(const GroupItem* __re
     extern __shared__ __align__(16) unsigned char smb[];
     const GroupItem& it = items[group_item_ba<&GroupItem::b_ba>(items, count)];
     const int bid = blockIdx.x - it.b_ba;
-    if (it.z_double)
-        block_apply_run<float, double, float>(it.M, it.N, it.Rt, static_cast<const double*>(it.z), it.o, bid, smb);
-    else
-        block_apply_run<float, float, float>(it.M, it.N, it.Rt, static_cast<const float*>(it.z), it.o, bid, smb);
+    block_apply_run<float, float, float>(it.M, it.N, it.Rt, it.z, it.o, bid, smb);
 }
 
 __global__ void k_gather_group(const GroupItem* __restrict__ items, int count) {
     const GroupItem& it = items[group_item_ba<&GroupItem::b_ga>(items, count)];
     const int bid = blockIdx.x - it.b_ga;
-    if (it.z_double)
-        gather_run<double, float, double>(it.I, it.M, static_cast<const double*>(it.z), it.o, it.w, bid, it.n_ga);
-    else
-        gather_run<float, float, double>(it.I, it.M, static_cast<const float*>(it.z), it.o, it.w, bid, it.n_ga);
+    gather_df_run(it.I, it.M, it.z, it.z_lo, it.o, it.w, bid, it.n_ga);
 }
 }  // namespace
 
@@ -547,6 +574,18 @@ void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* 
         k_gather<double, float, float><<<g, 256, 0, ctx->stream>>>(ctx->I, M, (const double*)v, o,
                                                                    (float*)w);
     check(cudaGetLastError(), "k_gather");
+}
+
+void launch_response_apply_df(rte_ctx* ctx, const float* z_hi, const float* z_lo, float* w) {
+    const int M = ctx->M, n2 = 2 * M;
+    float* o = reinterpret_cast<float*>(ctx->trace_out);
+    const double bytes = (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * 8;
+    block_apply_t<float, float, float>(ctx, ctx->Rt, z_hi, o, K_RESPONSE_APPLY, bytes);
+    int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
+    const int g = (int)(want < cap ? want : cap);
+    ProfScope ps(ctx, K_GATHER, (double)ctx->n * ((z_lo ? 8 : 4) + 4 + 8));
+    k_gather_df<<<g, 256, 0, ctx->stream>>>(ctx->I, M, z_hi, z_lo, o, w);
+    check(cudaGetLastError(), "k_gather_df");
 }
 
 }  // namespace rte

@@ -366,6 +366,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
                 const int co = cbase + c16 * 16 + i;
                 if (co < a.Co) bb[i] = (float)__ldg(bsrc + (size_t)co * oplane + opix);
             }
+        } else if (a.batched && a.base32_b[0]) {
+            const float* bsrc = a.base32_b[eb];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int co = cbase + c16 * 16 + i;
+                if (co < a.Co) bb[i] = __ldg(bsrc + (size_t)co * oplane + opix);
+            }
         }
     };
     float eg[16], eb8[16];
@@ -488,15 +495,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
             const uint32_t dst = xbase + (uint32_t)s * stage_bytes + row_off;
             const size_t plane = (size_t)a.Hi * a.Wi;
             if (MODE == kF64) {
-                const double* xp = (a.batched ? a.x64_b[b] : a.x64 + (size_t)b * a.Ci * plane) +
-                                   (in ? (size_t)iy * a.Wi + ix : 0);
+                // FP64 or FP32 input vector (x64 / x64_b, or x32_b), rounded on load
+                const bool f32 = a.batched && a.x32_b[0];
+                const size_t pix = in ? (size_t)iy * a.Wi + ix : 0;
+                const double* xp = f32 ? nullptr : (a.batched ? a.x64_b[b] : a.x64 + (size_t)b * a.Ci * plane) + pix;
+                const float* xq = f32 ? a.x32_b[b] + pix : nullptr;
 #pragma unroll 4
                 for (int kc = half; kc < KC; kc += 2) {
                     float v[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int ci = kc * 8 + j;
-                        const float x = (in && ci < a.Ci) ? (float)__ldg(xp + (size_t)ci * plane) : 0.f;
+                        float x = 0.f;
+                        if (in && ci < a.Ci)
+                            x = f32 ? __ldg(xq + (size_t)ci * plane) : (float)__ldg(xp + (size_t)ci * plane);
                         v[j] = a.relu_in ? fmaxf(x, 0.f) : x;
                     }
                     const uint4 pk = pack8(v);
@@ -825,7 +837,8 @@ void tc_pack(const float* w, int so, int si, int KK, const Taps& tp, int classes
 void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
     TcConv a = in;
     if (a.T < 1 || a.classes < 1 || a.classes > 4 || a.T * a.classes > kMaxTaps || a.S < 1 || a.S > 2 ||
-        a.Ci < 1 || a.Co < 1 || !a.w || (!a.x8) == (!(a.x64 || (a.batched && a.x64_b[0]))) ||
+        a.Ci < 1 || a.Co < 1 || !a.w ||
+        (!a.x8) == (!(a.x64 || (a.batched && (a.x64_b[0] || a.x32_b[0])))) ||
         (!a.y8) == (!(a.y32 || (a.batched && a.y32_b[0]))) || (a.batched && a.B > kTcMaxBatch))
         throw StatusError{RTE_EINVAL, "tensor-core convolution: bad arguments"};
     const bool stream = streamed(a.T, a.Ci, a.Co);
@@ -842,7 +855,7 @@ void tc_conv(const TcConv& in, bool pdl, cudaStream_t st) {
     g.KC = chunks_kc(a.Ci);
     g.Npad = pad_n(a.Co);
     const int T = a.T;
-    if (a.x64 || (a.batched && a.x64_b[0])) {
+    if (a.x64 || (a.batched && (a.x64_b[0] || a.x32_b[0]))) {
         if (stream) throw StatusError{RTE_EINVAL, "tensor-core convolution: lift weights too large"};
         g.NS = T;
         launch<kF64>(a, g, (size_t)T * g.KC * 2048, pdl, (unsigned)((total + kRows - 1) / kRows), st);

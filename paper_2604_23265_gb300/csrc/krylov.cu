@@ -1,6 +1,8 @@
-// Krylov kernels of flexible GMRES: multi-dot, fused Gram-Schmidt passes,
-// norms, scaling, solution update, Givens/Hessenberg update and the
-// triangular solve -- all FP64 on the device.
+// FP64 Krylov kernels: multi-dot, fused Gram-Schmidt passes, norms, scaling
+// and the solution update, on double vectors.  They serve the FP64 entry
+// points (rte_cgs2, rte_cgs2_noalloc, rte_arnoldi_basis) and the norms of
+// FP64 residuals; the solver's own Arnoldi step runs on df64 vectors
+// (krylov_df.cu), which stream at the memory bound instead of the FP64 pipe's.
 //
 // Classical Gram-Schmidt with one reorthogonalisation is done in three passes
 // over the basis V (k vectors of n doubles, vector j at V + j*n):
@@ -346,66 +348,7 @@ int red_blocks(rte_ctx* ctx, int64_t n) {
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-// the item whose block range [start, start + count) holds this block
-template <int GroupItem::*START>
-__device__ int group_item(const GroupItem* items, int count) {
-    __shared__ int s_item;
-    if (threadIdx.x == 0) {
-        int i = 0;
-        while (i + 1 < count && items[i + 1].*START <= (int)blockIdx.x) ++i;
-        s_item = i;
-    }
-    __syncthreads();
-    return s_item;
-}
-
-__global__ void __launch_bounds__(kT) k_mdot_group(const GroupItem* __restrict__ items, int count) {
-    extern __shared__ double s_part[];
-    const GroupItem& it = items[group_item<&GroupItem::b_md>(items, count)];
-    mdot_run(it.V, it.K, it.n, it.w, it.partials, it.counter, it.h1, blockIdx.x - it.b_md, it.n_md, s_part);
-}
-
-__global__ void __launch_bounds__(kT) k_update_dot_group(const GroupItem* __restrict__ items, int count) {
-    extern __shared__ double s_part[];
-    const GroupItem& it = items[group_item<&GroupItem::b_ud>(items, count)];
-    update_dot_run(it.V, it.K, it.n, it.w, it.h1, it.partials, it.counter, it.h2, blockIdx.x - it.b_ud, it.n_ud,
-                   s_part);
-}
-
-__global__ void __launch_bounds__(kT) k_update_norm_group(const GroupItem* __restrict__ items, int count) {
-    const GroupItem& it = items[group_item<&GroupItem::b_rd>(items, count)];
-    update_norm_run(it.V, it.K, it.n, it.w, it.h1, it.h2, it.partials, it.counter, it.hcol, blockIdx.x - it.b_rd,
-                    it.n_rd);
-}
-
-__global__ void __launch_bounds__(kT) k_scale_group(const GroupItem* __restrict__ items, int count) {
-    const GroupItem& it = items[group_item<&GroupItem::b_rd>(items, count)];
-    scale_run(it.w, it.hcol + it.K, it.n, it.Vnext, blockIdx.x - it.b_rd, it.n_rd);
-}
-
 }  // namespace
-
-void group_ortho_geometry(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd) {
-    *n_md = dot_blocks(ctx, ctx->n, K, (const void*)k_mdot);
-    *n_ud = dot_blocks(ctx, ctx->n, K, (const void*)k_update_dot);
-    *n_rd = red_blocks(ctx, ctx->n);
-}
-
-void launch_group_orthogonalise(const GroupItem* items_dev, int count, int blocks_md, int blocks_ud,
-                                int blocks_rd, int kmax, cudaStream_t st) {
-    static std::once_flag once;
-    std::call_once(once, [] {
-        const int smax = (int)(kMaxKrylov * kT * sizeof(double));
-        raise_smem_limit((const void*)k_mdot_group, (size_t)(smax));
-        raise_smem_limit((const void*)k_update_dot_group, (size_t)(smax));
-    });
-    const size_t smem = (size_t)kmax * kT * sizeof(double);
-    k_mdot_group<<<blocks_md, kT, smem, st>>>(items_dev, count);
-    k_update_dot_group<<<blocks_ud, kT, smem, st>>>(items_dev, count);
-    k_update_norm_group<<<blocks_rd, kT, 0, st>>>(items_dev, count);
-    k_scale_group<<<blocks_rd, kT, 0, st>>>(items_dev, count);
-    check(cudaGetLastError(), "grouped Gram-Schmidt");
-}
 
 void launch_mdot(rte_ctx* ctx, const double* V, int k, const double* w, double* h) {
     const int g = dot_blocks(ctx, ctx->n, k, (const void*)k_mdot);

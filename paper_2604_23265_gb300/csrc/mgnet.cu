@@ -80,6 +80,8 @@ struct mgnet {
     double* d_scal = nullptr;
     double* h_scal = nullptr;
     double* d_part = nullptr;        // [2 x 2048] block partial sums (inside d_scal's allocation)
+    double* fin64 = nullptr;         // FP64 copy of an FP32 input (CUDA-core forward)
+    size_t fin64_n = 0;
 
     int C(int l) const { int c = c0 << l; return c < cmax ? c : cmax; }
     int Cc(int l) const { int c = cc << l; return c < ccmax ? c : ccmax; }
@@ -424,6 +426,7 @@ struct TcSamples {
     int B = 1;
     const Features* F[nn::kTcMaxBatch] = {};
     const double* r[nn::kTcMaxBatch] = {};
+    const float* r32[nn::kTcMaxBatch] = {};    // FP32 inputs instead of r (all samples or none)
     float* z[nn::kTcMaxBatch] = {};
 };
 
@@ -463,7 +466,12 @@ size_t tc_forward(mgnet* n, const TcSamples& S, int I, TcMode mode) {
     };
     {   // lift: FP64 Krylov vectors -> f_0
         nn::TcConv c = conv(nullptr, M2, I, n->C(0), I, 1, A.f.empty() ? nullptr : A.f[0], I);
-        for (int b = 0; b < B; ++b) c.x64_b[b] = S.r[b];
+        for (int b = 0; b < B; ++b) {
+            if (S.r32[0])
+                c.x32_b[b] = S.r32[b];
+            else
+                c.x64_b[b] = S.r[b];
+        }
         run(c, "lift.w", M2, 1, 1, t1);
     }
     auto smooth_first = [&](int l, void* u) {            // u = (B * act(f)) o ainv
@@ -531,7 +539,10 @@ size_t tc_forward(mgnet* n, const TcSamples& S, int I, TcMode mode) {
         nn::TcConv c = conv(uup, n->C(0), I, M2, I, 1, nullptr, I);
         for (int b = 0; b < B; ++b) {
             c.y32_b[b] = S.z[b];
-            c.base64_b[b] = S.r[b];
+            if (S.r32[0])
+                c.base32_b[b] = S.r32[b];
+            else
+                c.base64_b[b] = S.r[b];
         }
         run(c, "proj.w", n->C(0), 1, 1, t1);
     }
@@ -982,6 +993,75 @@ void mgnet_precondition_batch(mgnet* net, rte_ctx* const* ctxs, const double* co
     }
 }
 
+__global__ void k_f32_to_f64(const float* __restrict__ x, int64_t n, double* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+
+void mgnet_precondition_f(mgnet* net, rte_ctx* ctx, const float* v, float* z) {
+    if (net->prec != MGNET_BF16) {
+        // the CUDA-core forward normalises an FP64 input: widen v first
+        if (net->fin64_n < (size_t)ctx->n) {
+            if (net->fin64) cudaFree(net->fin64);
+            net->fin64 = nullptr;
+            net->fin64_n = 0;
+            check(cudaMalloc(&net->fin64, (size_t)ctx->n * sizeof(double)), "cudaMalloc (network input)");
+            net->fin64_n = (size_t)ctx->n;
+        }
+        k_f32_to_f64<<<grid_for(ctx->n), 256, 0, ctx->stream>>>(v, ctx->n, net->fin64);
+        check(cudaGetLastError(), "k_f32_to_f64");
+        mgnet_precondition(net, ctx, net->fin64, z);
+        return;
+    }
+    NvtxRange range("MgNet V-cycle");
+    check_ctx(net, ctx);
+    Features& F = features(net, ctx, false);
+    nn::Counters cnt;
+    struct Reset {
+        ~Reset() { nn::tl_counters = nullptr; }
+    } reset;
+    nn::tl_counters = &cnt;
+    {
+        ProfScope ps(ctx, K_MGNET, (double)ctx->n * 8, 0);
+        TcSamples S;
+        S.F[0] = &F;
+        S.r32[0] = v;
+        S.z[0] = z;
+        tc_precondition(net, S, ctx->I);
+    }
+    if (net->fault == MGNET_FAULT_NAN)
+        check(cudaMemsetAsync(z, 0xFF, (size_t)ctx->n * sizeof(float), net->stream), "fault injection");
+    ctx->prof.launches[K_MGNET] += cnt.launches;
+    ctx->prof.flops[K_MGNET] += cnt.flops;
+}
+
+void mgnet_precondition_batch_f(mgnet* net, rte_ctx* const* ctxs, const float* const* v, float* const* z, int B) {
+    if (B == 1 || net->prec != MGNET_BF16) {
+        for (int b = 0; b < B; ++b) mgnet_precondition_f(net, ctxs[b], v[b], z[b]);
+        return;
+    }
+    const int I = ctxs[0]->I;
+    for (int b = 0; b < B; ++b) {
+        check_ctx(net, ctxs[b]);
+        if (ctxs[b]->I != I) throw StatusError{RTE_EINVAL, "batched preconditioning needs one grid size"};
+    }
+    for (int b0 = 0; b0 < B; b0 += nn::kTcMaxBatch) {
+        TcSamples S;
+        S.B = B - b0 < nn::kTcMaxBatch ? B - b0 : nn::kTcMaxBatch;
+        for (int b = 0; b < S.B; ++b) {
+            S.F[b] = &features(net, ctxs[b0 + b], false);
+            S.r32[b] = v[b0 + b];
+            S.z[b] = z[b0 + b];
+        }
+        ProfScope ps(ctxs[b0], K_MGNET, (double)ctxs[b0]->n * 8 * S.B, 0);
+        tc_precondition(net, S, I);
+        if (net->fault == MGNET_FAULT_NAN)
+            for (int b = 0; b < S.B; ++b)
+                check(cudaMemsetAsync(S.z[b], 0xFF, (size_t)ctxs[b0 + b]->n * sizeof(float), net->stream),
+                      "fault injection");
+    }
+}
+
 }  // namespace rte
 
 using namespace rte;
@@ -1061,6 +1141,7 @@ RTE_API void mgnet_destroy(mgnet* n) {
     if (n->tcw) cudaFree(n->tcw);
     if (n->lscr) cudaFree(n->lscr);
     if (n->p) cudaFree(n->p);
+    if (n->fin64) cudaFree(n->fin64);
     if (n->d_scal) cudaFree(n->d_scal);
     if (n->h_scal) cudaFreeHost(n->h_scal);
     delete n;

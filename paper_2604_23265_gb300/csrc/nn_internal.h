@@ -118,6 +118,9 @@ struct TcConv {
     const float* gate_b[kTcMaxBatch] = {};    // [Co][Ho][Wo] each
     const double* base64_b[kTcMaxBatch] = {}; // [Co][Ho][Wo] each
     float* y32_b[kTcMaxBatch] = {};           // [Co][Ho][Wo] each
+    // FP32 input / base per sample (batched only), in place of x64_b / base64_b
+    const float* x32_b[kTcMaxBatch] = {};     // [Ci][Hi][Wi] each
+    const float* base32_b[kTcMaxBatch] = {};  // [Co][Ho][Wo] each
 };
 // Bytes of the packed weights of T taps (classes x taps per class): the
 // resident layout, or the streamed one for layers whose per-CTA weights

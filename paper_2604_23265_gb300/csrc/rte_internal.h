@@ -150,20 +150,21 @@ void launch_coef_inputs(rte_ctx* ctx, const double* sT, const double* sa, const 
 // launch -- the same block count as its own launch would use, so the
 // instance's arithmetic (reduction order included) is that of a lone solve.
 struct GroupItem {
-    // inner operator w = z - P R z (z double or float), o = R z scratch
+    // inner operator w = z - P R z, o = R z scratch; z is the FP32 network
+    // output, or the df64 Krylov vector v_j (block Jacobi: hi plane z, lo plane z_lo)
     const float* Rt;
-    const void* z;
-    int z_double;
+    const float* z;
+    const float* z_lo;
     float* o;
     int I, M, N;
     int64_t n;
-    // Gram-Schmidt against V[0..K), new vector to Vnext
-    const double* V;
-    double* w;
+    // Gram-Schmidt of the df64 w against the df64 V[0..K), new vector to Vnext
+    const float* V;
+    float* w;
     double* h1;
     double* h2;
     double* hcol;
-    double* Vnext;
+    float* Vnext;
     double* partials;
     unsigned* counter;
     int K;
@@ -176,18 +177,22 @@ struct GroupItem {
     double* est;             // the instance's own status (est, ||w||)
     double* est_out;         // and a copy in the group's array
     // block ranges: [b_x, b_x + n_x) of the grouped launch of kernel x
-    int b_ba, n_ba, b_ga, n_ga, b_md, n_md, b_ud, n_ud, b_rd, n_rd;
+    int b_ba, n_ba, b_ga, n_ga, b_md, n_md, b_ud, n_ud, b_rd, n_rd, b_sc, n_sc;
 };
 // w = z - P R z for every item (two grouped launches)
 void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba, int blocks_ga,
                            size_t smem_ba, cudaStream_t st);
 // block counts and shared memory of one item's response apply / gather
 void group_response_geometry(rte_ctx* ctx, int* n_ba, int* n_ga, size_t* smem_ba);
-// CGS2 (three passes) and the scaling to Vnext for every item
-void launch_group_orthogonalise(const GroupItem* items_dev, int count, int blocks_md, int blocks_ud,
-                                int blocks_rd, int kmax, cudaStream_t st);
-// block counts of one item's Gram-Schmidt passes
-void group_ortho_geometry(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd);
+// CGS2 (three df64 passes) and the scaling to Vnext for every item; maps_dev
+// holds the items' tensor maps (encode_group_gs_maps of the same items,
+// group_gs_maps_bytes each, 64-byte aligned, copied to the device before)
+void launch_group_orthogonalise_df(const GroupItem* items_dev, const void* maps_dev, int count, int blocks_md,
+                                   int blocks_ud, int blocks_rd, int blocks_sc, int kmax, cudaStream_t st);
+size_t group_gs_maps_bytes();
+void encode_group_gs_maps(const GroupItem* items_host, int count, void* maps_host);
+// block counts of one item's Gram-Schmidt passes and scaling
+void group_ortho_geometry_df(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd, int* n_sc);
 
 // lockstep groups of solves (solve.cu), for the grouped server: a solve
 // (started on creation: workspace, initial guess, ||b||) and rounds over a set
@@ -256,6 +261,26 @@ void launch_update_norm(rte_ctx* ctx, const double* V, int k, double* w, const d
                         const double* h2, double* out);
 // out[0] = ||x||
 void launch_norm(rte_ctx* ctx, const double* x, double* out);
+
+// df64 Krylov vectors (df64.h; krylov_df.cu): planar hi [n] then lo [n]
+// floats, vector k of a basis at V + 2 k n.
+// CGS2 of w against V[0..K) in three HBM-bound passes: h1, h2 and
+// hcol = [h1 + h2, ||w||], w left orthogonalised (not normalised)
+void launch_orthogonalise_df(rte_ctx* ctx, const float* V, int K, float* w, double* h1, double* h2,
+                             double* hcol);
+// v = w / s[0] (v = w if s[0] == 0)
+void launch_scale_df(rte_ctx* ctx, const float* w, const double* s, float* v);
+// out = x / s[0] (s may be null), double -> df64
+void launch_split_df(rte_ctx* ctx, const double* x, const double* s, float* out);
+// df64 -> double
+void launch_compose_df(rte_ctx* ctx, const float* x, double* out);
+// out = sum_k V_k y_k, df64 basis, double out
+void launch_lincomb_df(rte_ctx* ctx, const float* V, int K, const double* y, double* out);
+// w (df64) = z - P R z for z the FP32 vector z_hi (z_lo null) or the df64
+// vector (z_hi, z_lo); R z in FP32 from z_hi
+void launch_response_apply_df(rte_ctx* ctx, const float* z_hi, const float* z_lo, float* w);
+// 1 if a bounded wait of a df64 Gram-Schmidt pass ran out (reset clears), -1 on error
+int krylov_timeout_flag(bool reset);
 // y = x * (1 / s[0]) unless s[0] == 0 (then y = x)
 void launch_scale(rte_ctx* ctx, const double* x, const double* s, double* y);
 // x += sum_k Z[k] y[k]  (Z float, k vectors)

@@ -690,6 +690,21 @@ RTE_API rte_status rte_cgs2(rte_ctx* ctx, const double* V_dev, int k, double* w_
     RTE_GUARD_END(ctx)
 }
 
+RTE_API rte_status rte_cgs2_df64(rte_ctx* ctx, const float* V_dev, int k, float* w_dev, double* h_dev) {
+    if (!ctx || !V_dev || !w_dev || !h_dev || k < 1 || k > kMaxKrylov) {
+        set_error(ctx, "bad argument (need 1 <= k <= 64)");
+        return RTE_EINVAL;
+    }
+    RTE_GUARD_BEGIN
+    double* h1 = ctx->scal;                 // [64] first projection
+    double* h2 = ctx->scal + kMaxKrylov;    // [64] second projection
+    launch_orthogonalise_df(ctx, V_dev, k, w_dev, h1, h2, h_dev);
+    launch_scale_df(ctx, w_dev, h_dev + k, w_dev);
+    if (krylov_timeout_flag(true) == 1) throw StatusError{RTE_ETIMEOUT, "a bounded wait of a Gram-Schmidt pass ran out"};
+    return RTE_OK;
+    RTE_GUARD_END(ctx)
+}
+
 RTE_API rte_status rte_eigenbasis(int M, double g, double one_minus_gamma, int axis, double* xi,
                                   double* L) {
     if (M < 4 || M % 4 != 0 || M > 112 || !(std::fabs(g) < 1.0) || !(one_minus_gamma > 0.0) ||

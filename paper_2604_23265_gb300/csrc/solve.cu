@@ -7,9 +7,12 @@
 // keeps B accurate, whereas alpha = D y itself cancels heavily in the
 // diffusive limit and needs FP64.  Per Arnoldi step j:
 //   z_j = Net(v_j)  (MgNet, in face-flux space)  or  z_j = v_j
-//   w   = B z_j                                   FP32 products, FP64 vectors
-//   CGS2: h = V^T w twice, w /= ||w|| -> v_{j+1}  (FP64)
+//   w   = B z_j                                   FP32 products, df64 w
+//   CGS2: h = V^T w twice, w /= ||w|| -> v_{j+1}  (df64 vectors, FP64 h)
 //   Givens update of the Hessenberg column         (FP64, one thread)
+// The Krylov vectors V and w are df64 (df64.h: a float pair, 48 significant
+// bits): the Gram-Schmidt passes then stream at the memory bound on the FP32
+// pipe, where FP64 vectors would be bound by this GPU's narrow FP64 pipe.
 // The host reads only the residual estimate after each step.  At the end of a
 // cycle y = H^{-1} g, dy = Z y, alpha += D dy (FP64), and the true residual
 // r = b - A alpha is recomputed in FP64: it alone decides convergence
@@ -26,10 +29,12 @@ namespace rte {
 
 struct Workspace {
     int m = 0;
-    double* V = nullptr;      // [(m+1)][n]
-    float* Z = nullptr;       // [m][n]
-    double* w = nullptr;      // [n]
-    double* tmp = nullptr;    // [n] FP64 copy of z for FP64 inner applies
+    float* V = nullptr;       // [(m+1)][2][n] df64 Krylov basis (hi plane, lo plane)
+    float* Z = nullptr;       // [m][n] network outputs (flexible GMRES)
+    float* w = nullptr;       // [2][n] df64 vector being orthogonalised
+    double* w64 = nullptr;    // [n] FP64 residual / FP64 operator output
+    double* tmp = nullptr;    // [n] FP64 scratch (D z, Z y)
+    double* tmp2 = nullptr;   // [n] FP64 copy of a df64 Krylov vector
     double* H = nullptr;      // [(m+1) * m] column-major, ld = m+1
     double* cs = nullptr;     // [m]
     double* sn = nullptr;     // [m]
@@ -75,10 +80,12 @@ Workspace* get_workspace(rte_ctx* ctx, int m) {
     ctx->ws = ws;
     ws->m = m;
     const size_t n = (size_t)ctx->n;
-    ws->V = ws_alloc<double>(ctx, ws, (size_t)(m + 1) * n);
+    ws->V = ws_alloc<float>(ctx, ws, (size_t)(m + 1) * 2 * n);
     ws->Z = ws_alloc<float>(ctx, ws, (size_t)m * n);    // MgNet outputs (flexible GMRES)
-    ws->w = ws_alloc<double>(ctx, ws, n);
+    ws->w = ws_alloc<float>(ctx, ws, 2 * n);
+    ws->w64 = ws_alloc<double>(ctx, ws, n);
     ws->tmp = ws_alloc<double>(ctx, ws, n);
+    ws->tmp2 = ws_alloc<double>(ctx, ws, n);
     ws->H = ws_alloc<double>(ctx, ws, (size_t)(m + 1) * m);
     ws->cs = ws_alloc<double>(ctx, ws, m);
     ws->sn = ws_alloc<double>(ctx, ws, m);
@@ -92,16 +99,14 @@ Workspace* get_workspace(rte_ctx* ctx, int m) {
     return ws;
 }
 
-// Orthogonalises w against V[0..K) (orthonormal) by classical Gram-Schmidt
-// with one reorthogonalisation in three passes over V, leaving
-// ws->hcol = [h1 + h2, ||w||] and the projected (unnormalised) vector in w.
-// On the diffusive workloads the second projection is needed at almost every
-// step (the first removes more than half of w's squared length at 98% of the
-// steps), so it is always done.
-void orthogonalise(rte_ctx* ctx, Workspace* ws, const double* V, int K) {
-    launch_mdot(ctx, V, K, ws->w, ws->h1);
-    launch_update_dot(ctx, V, K, ws->w, ws->h1, ws->h2);
-    launch_update_norm(ctx, V, K, ws->w, ws->h1, ws->h2, ws->hcol);
+// FP64 Arnoldi orthogonalisation of the double vector w against V[0..K)
+// (rte_arnoldi_basis): classical Gram-Schmidt with one reorthogonalisation in
+// three passes, leaving ws->hcol = [h1 + h2, ||w||] and the projected
+// (unnormalised) vector in w.
+void orthogonalise64(rte_ctx* ctx, Workspace* ws, const double* V, int K, double* w) {
+    launch_mdot(ctx, V, K, w, ws->h1);
+    launch_update_dot(ctx, V, K, w, ws->h1, ws->h2);
+    launch_update_norm(ctx, V, K, w, ws->h1, ws->h2, ws->hcol);
 }
 
 // Start of a cycle: g = (beta, 0, ...), H = 0.
@@ -212,8 +217,8 @@ struct Solver {
     bool comp = false;
     const double* rhs = nullptr;
     int j = 0, k = 0;                 // Arnoldi step in the cycle; columns for the cycle end
-    const void* zj = nullptr;
-    bool z_double = true;
+    const float* zj = nullptr;        // z_j: the network output, or the hi plane of v_j
+    const float* zj_lo = nullptr;     // lo plane of v_j when z_j = v_j (block Jacobi)
     int phase = 0;                    // grouped runs: 0 cycle start next, 1 stepping, 2 done
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
@@ -243,18 +248,20 @@ struct Solver {
         return true;
     }
 
+    float* vec(int k) const { return ws->V + (size_t)2 * k * n; }
+
     // true residual in FP64 and the decisions on it; false when the solve ends
     bool cycle_begin() {
         NvtxRange range("restart cycle: true residual");
         if (first && !opts.use_x0)
-            check(cudaMemcpyAsync(ws->w, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+            check(cudaMemcpyAsync(ws->w64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
                   "r = b");
         else if (comp)
-            atfps_comp_apply(ctx, x, ws->w, true);
+            atfps_comp_apply(ctx, x, ws->w64, true);
         else
-            launch_apply(ctx, true, x, ws->w, true, ctx->b);
+            launch_apply(ctx, true, x, ws->w64, true, ctx->b);
         first = false;
-        launch_norm(ctx, ws->w, ws->est + 3);
+        launch_norm(ctx, ws->w64, ws->est + 3);
         const double beta = read_scalar(ctx, ws, ws->est + 3);
         inf.relres = beta / bnorm;
         if (inf.history_len < 32) inf.history[inf.history_len++] = inf.relres;
@@ -276,7 +283,7 @@ struct Solver {
             status = RTE_ECANCELLED;
             return false;
         }
-        launch_scale(ctx, ws->w, ws->est + 3, ws->V);
+        launch_split_df(ctx, ws->w64, ws->est + 3, vec(0));        // v_0 = r / beta
         {
             ProfScope ps(ctx, K_CYCLE, 0.0);
             k_cycle_start<<<1, 256, 0, ctx->stream>>>(m, ws->est + 3, ws->H, ws->g);
@@ -290,27 +297,40 @@ struct Solver {
 
     // z_j: the network's output, or v_j itself (block Jacobi is inside B)
     void precondition() {
-        const double* vj = ws->V + (size_t)j * n;
-        zj = vj;
-        z_double = true;
+        zj = vec(j);
+        zj_lo = vec(j) + n;
         if (cycle_net) {
             float* zf = ws->Z + (size_t)j * n;
-            mgnet_precondition(pc, ctx, vj, zf);
+            mgnet_precondition_f(pc, ctx, vec(j), zf);
             zj = zf;
-            z_double = false;
+            zj_lo = nullptr;
         }
+    }
+
+    // z_j as a double vector in ws->tmp2 (FP64 inner operators)
+    const double* zj_double() {
+        if (zj_lo) {
+            launch_compose_df(ctx, zj, ws->tmp2);
+            return ws->tmp2;
+        }
+        return nullptr;
     }
 
     // w = B z_j
     void inner_apply() {
         if (comp) {
-            atfps_comp_precond(ctx, static_cast<const double*>(zj), ws->tmp);
-            atfps_comp_apply(ctx, ws->tmp, ws->w, false);
+            atfps_comp_precond(ctx, zj_double(), ws->tmp);
+            atfps_comp_apply(ctx, ws->tmp, ws->w64, false);
+            launch_split_df(ctx, ws->w64, nullptr, ws->w);
         } else if (opts.inner_precision == RTE_F32) {
-            launch_response_apply(ctx, zj, z_double, ws->w, true);
+            launch_response_apply_df(ctx, zj, zj_lo, ws->w);
         } else {
-            launch_block_apply(ctx, false, zj, z_double, ws->tmp, true);
-            launch_apply(ctx, true, ws->tmp, ws->w, true, nullptr);
+            if (zj_lo)
+                launch_block_apply(ctx, false, zj_double(), true, ws->tmp, true);
+            else
+                launch_block_apply(ctx, false, zj, false, ws->tmp, true);
+            launch_apply(ctx, true, ws->tmp, ws->w64, true, nullptr);
+            launch_split_df(ctx, ws->w64, nullptr, ws->w);
         }
     }
 
@@ -318,8 +338,8 @@ struct Solver {
     void orthogonalise_step() {
         NvtxRange range("Gram-Schmidt and Givens");
         const int K = j + 1;
-        orthogonalise(ctx, ws, ws->V, K);
-        launch_scale(ctx, ws->w, ws->hcol + K, ws->V + (size_t)(j + 1) * n);
+        launch_orthogonalise_df(ctx, ws->V, K, ws->w, ws->h1, ws->h2, ws->hcol);
+        launch_scale_df(ctx, ws->w, ws->hcol + K, vec(j + 1));
         ProfScope ps(ctx, K_GIVENS, 0.0);
         k_givens<<<1, 32, 0, ctx->stream>>>(j, m, ws->hcol, ws->H, ws->cs, ws->sn, ws->g, ws->est);
         check(cudaGetLastError(), "k_givens");
@@ -349,20 +369,19 @@ struct Solver {
                 k_backsub<<<1, 32, 0, ctx->stream>>>(k, m, ws->H, ws->g, ws->y);
                 check(cudaGetLastError(), "k_backsub");
             }
-            {
-                ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + (cycle_net ? 4 : 8) * k));
-                if (cycle_net)
-                    k_lincomb<float><<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
-                else
-                    k_lincomb<double><<<gblk, 256, 0, ctx->stream>>>(ws->V, k, n, ws->y, ws->tmp);
+            if (cycle_net) {
+                ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + 4 * k));
+                k_lincomb<float><<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
                 check(cudaGetLastError(), "k_lincomb");
+            } else {
+                launch_lincomb_df(ctx, ws->V, k, ws->y, ws->tmp);
             }
             if (comp)
-                atfps_comp_precond(ctx, ws->tmp, ws->w);                   // mask o D S dy
+                atfps_comp_precond(ctx, ws->tmp, ws->w64);                   // mask o D S dy
             else
-                launch_block_apply(ctx, false, ws->tmp, true, ws->w, true);   // D dy
+                launch_block_apply(ctx, false, ws->tmp, true, ws->w64, true);   // D dy
             ProfScope ps(ctx, K_XUPDATE, (double)n * 24);
-            k_axpy<<<gblk, 256, 0, ctx->stream>>>(x, ws->w, n);
+            k_axpy<<<gblk, 256, 0, ctx->stream>>>(x, ws->w64, n);
             check(cudaGetLastError(), "k_axpy");
         }
         ++inf.cycles;
@@ -379,20 +398,26 @@ struct GroupRunner {
     int cap = 0;
     GroupItem* items_h = nullptr;
     GroupItem* items_d = nullptr;
+    void* maps_h = nullptr;        // tensor maps of the items' Gram-Schmidt passes
+    void* maps_d = nullptr;
     double* est_h = nullptr;
     double* est_d = nullptr;
 
     GroupRunner(cudaStream_t s, int capacity) : st(s), cap(capacity) {
         check(cudaMallocHost(&items_h, cap * sizeof(GroupItem)), "cudaMallocHost");
+        check(cudaMallocHost(&maps_h, cap * group_gs_maps_bytes()), "cudaMallocHost");
         check(cudaMallocHost(&est_h, 2 * cap * sizeof(double)), "cudaMallocHost");
         check(cudaMallocAsync(&items_d, cap * sizeof(GroupItem), st), "cudaMallocAsync");
+        check(cudaMallocAsync(&maps_d, cap * group_gs_maps_bytes(), st), "cudaMallocAsync");
         check(cudaMallocAsync(&est_d, 2 * cap * sizeof(double), st), "cudaMallocAsync");
     }
     ~GroupRunner() {
         if (items_d) cudaFreeAsync(items_d, st);
+        if (maps_d) cudaFreeAsync(maps_d, st);
         if (est_d) cudaFreeAsync(est_d, st);
         cudaStreamSynchronize(st);
         if (items_h) cudaFreeHost(items_h);
+        if (maps_h) cudaFreeHost(maps_h);
         if (est_h) cudaFreeHost(est_h);
     }
 
@@ -426,18 +451,18 @@ struct GroupRunner {
                 continue;
             }
             std::vector<rte_ctx*> cs;
-            std::vector<const double*> vs;
+            std::vector<const float*> vs;
             std::vector<float*> zs;
             for (Solver* t : same) {
                 cs.push_back(t->ctx);
-                vs.push_back(t->ws->V + (size_t)t->j * t->n);
+                vs.push_back(t->vec(t->j));
                 zs.push_back(t->ws->Z + (size_t)t->j * t->n);
                 t->zj = zs.back();
-                t->z_double = false;
+                t->zj_lo = nullptr;
             }
-            mgnet_precondition_batch(s.pc, cs.data(), vs.data(), zs.data(), (int)same.size());
+            mgnet_precondition_batch_f(s.pc, cs.data(), vs.data(), zs.data(), (int)same.size());
         }
-        int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, kmax = 1;
+        int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, sc = 0, kmax = 1;
         size_t smem_ba = 0;
         bool f32 = true;
         for (size_t q = 0; q < live.size(); ++q) {
@@ -445,14 +470,14 @@ struct GroupRunner {
             GroupItem& it = items_h[q];
             rte_ctx* c = s.ctx;
             const int K = s.j + 1;
-            int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0;
+            int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0, nsc = 0;
             size_t sm = 0;
             group_response_geometry(c, &nba, &nga, &sm);
-            group_ortho_geometry(c, K, &nmd, &nud, &nrd);
+            group_ortho_geometry_df(c, K, &nmd, &nud, &nrd, &nsc);
             f32 = f32 && s.opts.inner_precision == RTE_F32;
             it.Rt = c->Rt;
             it.z = s.zj;
-            it.z_double = s.z_double ? 1 : 0;
+            it.z_lo = s.zj_lo;
             it.o = reinterpret_cast<float*>(c->trace_out);
             it.I = c->I;
             it.M = c->M;
@@ -463,7 +488,7 @@ struct GroupRunner {
             it.h1 = s.ws->h1;
             it.h2 = s.ws->h2;
             it.hcol = s.ws->hcol;
-            it.Vnext = s.ws->V + (size_t)(s.j + 1) * s.n;
+            it.Vnext = s.vec(s.j + 1);
             it.partials = c->partials;
             it.counter = c->counter;
             it.K = K;
@@ -480,17 +505,20 @@ struct GroupRunner {
             it.b_md = md; it.n_md = nmd; md += nmd;
             it.b_ud = ud; it.n_ud = nud; ud += nud;
             it.b_rd = rd; it.n_rd = nrd; rd += nrd;
+            it.b_sc = sc; it.n_sc = nsc; sc += nsc;
             kmax = K > kmax ? K : kmax;
             smem_ba = sm > smem_ba ? sm : smem_ba;
         }
         const int nl = (int)live.size();
         check(cudaMemcpyAsync(items_d, items_h, nl * sizeof(GroupItem), cudaMemcpyHostToDevice, st), "h2d items");
+        encode_group_gs_maps(items_h, nl, maps_h);
+        check(cudaMemcpyAsync(maps_d, maps_h, nl * group_gs_maps_bytes(), cudaMemcpyHostToDevice, st), "h2d maps");
         if (f32) {
             launch_group_response(items_d, nl, ba, ga, smem_ba, st);
         } else {
             for (Solver* s : live) s->inner_apply();
         }
-        launch_group_orthogonalise(items_d, nl, md, ud, rd, kmax, st);
+        launch_group_orthogonalise_df(items_d, maps_d, nl, md, ud, rd, sc, kmax, st);
         k_givens_group<<<nl, 32, 0, st>>>(items_d);
         check(cudaGetLastError(), "k_givens_group");
         check(cudaMemcpyAsync(est_h, est_d, 2 * nl * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h est");
@@ -585,6 +613,10 @@ rte_status run_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, dou
                 S.cycle_end();
             }
         }
+        if (krylov_timeout_flag(true) == 1) {
+            set_error(ctx, "a bounded wait of a Gram-Schmidt pass ran out");
+            S.status = RTE_ETIMEOUT;
+        }
         if (comp && layers && (S.status == RTE_OK || S.status == RTE_ENOTCONV)) {
             atfps_layers(ctx, x_dev);
             check(cudaStreamSynchronize(ctx->stream), "sync");
@@ -631,10 +663,10 @@ RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev) {
         launch_norm(ctx, ctx->b, ws->est + 3);
         launch_scale(ctx, ctx->b, ws->est + 3, V_dev);
         for (int j = 0; j + 1 < k; ++j) {
-            launch_response_apply(ctx, V_dev + (size_t)j * n, true, ws->w, true);
+            launch_response_apply(ctx, V_dev + (size_t)j * n, true, ws->w64, true);
             const int K = j + 1;
-            orthogonalise(ctx, ws, V_dev, K);
-            launch_scale(ctx, ws->w, ws->hcol + K, V_dev + (size_t)(j + 1) * n);
+            orthogonalise64(ctx, ws, V_dev, K, ws->w64);
+            launch_scale(ctx, ws->w64, ws->hcol + K, V_dev + (size_t)(j + 1) * n);
         }
         check(cudaStreamSynchronize(ctx->stream), "sync");
     } catch (const CudaError& e) {
@@ -646,6 +678,31 @@ RTE_API rte_status rte_arnoldi_basis(rte_ctx* ctx, int k, double* V_dev) {
     return RTE_OK;
 }
 
+
+RTE_API rte_status rte_arnoldi_basis_df64(rte_ctx* ctx, int k, float* V_dev) {
+    if (!ctx || !V_dev || k < 1 || k > kMaxKrylov) { set_error(ctx, "bad argument (1 <= k <= 64)"); return RTE_EINVAL; }
+    try {
+        Workspace* ws = get_workspace(ctx, ctx->ws ? ctx->ws->m : kMaxKrylov);
+        if (ws->m < k) ws = get_workspace(ctx, kMaxKrylov);
+        const int64_t n = ctx->n;
+        launch_norm(ctx, ctx->b, ws->est + 3);
+        launch_split_df(ctx, ctx->b, ws->est + 3, V_dev);
+        for (int j = 0; j + 1 < k; ++j) {
+            float* vj = V_dev + (size_t)2 * j * n;
+            launch_response_apply_df(ctx, vj, vj + n, ws->w);
+            launch_orthogonalise_df(ctx, V_dev, j + 1, ws->w, ws->h1, ws->h2, ws->hcol);
+            launch_scale_df(ctx, ws->w, ws->hcol + j + 1, V_dev + (size_t)2 * (j + 1) * n);
+        }
+        check(cudaStreamSynchronize(ctx->stream), "sync");
+        if (krylov_timeout_flag(true) == 1) throw StatusError{RTE_ETIMEOUT, "a bounded wait of a Gram-Schmidt pass ran out"};
+    } catch (const CudaError& e) {
+        return cuda_status(ctx, e.code, e.where);
+    } catch (const StatusError& e) {
+        set_error(ctx, e.msg);
+        return e.code;
+    }
+    return RTE_OK;
+}
 
 RTE_API rte_status rte_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, double* x_dev,
                              rte_solve_info* info) {
@@ -699,6 +756,10 @@ RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int 
             for (Solver* s : set) any = any || s->phase != GroupRunner::kDone;
             if (!any) break;
             runner.round(set);
+        }
+        if (krylov_timeout_flag(true) == 1) {
+            fatal = RTE_ETIMEOUT;
+            fatal_msg = "a bounded wait of a Gram-Schmidt pass ran out";
         }
     } catch (const CudaError& e) {
         fatal = cuda_status(nullptr, e.code, e.where);

@@ -86,6 +86,8 @@ SIGNATURES = {
     "rte_export_blocks": (_I, [_P, _P, _P]),
     "rte_response_apply": (_I, [_P, _P, _P]),
     "rte_cgs2": (_I, [_P, _P, _I, _P, _P]),
+    "rte_cgs2_df64": (_I, [_P, _P, _I, _P, _P]),
+    "rte_arnoldi_basis_df64": (_I, [_P, _I, _P]),
     "rte_cgs2_noalloc": (_I, [_P, _I, ctypes.c_int64, _P, _P, _P]),
     "rte_arnoldi_basis": (_I, [_P, _I, _P]),
     "rte_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
@@ -584,6 +586,21 @@ class Context:
                                _dev(w, torch.float64, self.n), _dev(h, torch.float64, k + 1)),
                self.ptr)
         return h
+
+    def cgs2_df64(self, V, k, w, h):
+        """rte_cgs2 on df64 vectors (float32 tensors: V [k][2][n], w [2][n], hi plane then lo plane;
+        h float64 [k + 1]) with the arithmetic of the solver's Arnoldi step (rte_cgs2_df64)."""
+        import torch
+        _check(load().rte_cgs2_df64(self.ptr, _dev(V, torch.float32, 2 * k * self.n), int(k),
+                                    _dev(w, torch.float32, 2 * self.n), _dev(h, torch.float64, k + 1)),
+               self.ptr)
+        return h
+
+    def arnoldi_basis_df64(self, k, V):
+        """k Arnoldi vectors of A D as df64 (float32 tensor [k][2][n]; rte_arnoldi_basis_df64)."""
+        import torch
+        _check(load().rte_arnoldi_basis_df64(self.ptr, int(k), _dev(V, torch.float32, 2 * k * self.n)), self.ptr)
+        return V
 
     def profile(self, enable=True):
         """Clear the per-kernel counters; enable=True also times every launch."""
