@@ -108,6 +108,40 @@ RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
                              const double* eps, int eps_is_scalar, double g,
                              const double* inflow, void* stream, rte_ctx** out);
 
+/* ---------------------------------------------------------------------------
+ * rte_setup_ex -- rte_setup with a choice of how the per-cell blocks are built
+ * (no counterpart in the paper: an implementation choice).  The diagonal
+ * block G_C of a cell depends on the cell only through its material (1 -
+ * gamma) and its optical thickness tau_C.  block_mode:
+ *   RTE_BLOCKS_EXACT: every D_C = G_C^{-1} by FP64 Gauss-Jordan and
+ *     R_C = T_out,C D_C, cell by cell (the set-up cost grows with N (2M)^3);
+ *   RTE_BLOCKS_TABULATED: D and R of every material at nodes tau =
+ *     exp(0.04 i) covering its cells' range of ln tau (FP64), and each cell's
+ *     blocks as the 8-point Lagrange interpolation in ln tau of the nodes
+ *     around it (FP64; R rounded to FP32 once).  The interpolation error is
+ *     about 1e-11 of the blocks' size on well-conditioned media and below the
+ *     FP64 inversion's own rounding (cond(G_C) u) once cond(G_C) exceeds about
+ *     1e5.  The solver's true FP64 residual uses the exact per-cell traces
+ *     either way, so the solution meets the same tolerance;
+ *   RTE_BLOCKS_AUTO (rte_setup): tabulated when the medium has at least 4096
+ *     cells and at least 16 cells per node over all materials, else exact.
+ * EINVAL for another value; otherwise as rte_setup.
+ * ------------------------------------------------------------------------- */
+typedef enum rte_block_mode {
+    RTE_BLOCKS_AUTO = 0,
+    RTE_BLOCKS_EXACT = 1,
+    RTE_BLOCKS_TABULATED = 2
+} rte_block_mode;
+
+RTE_API rte_status rte_setup_ex(const rte_grid* grid, const rte_quadrature* quad,
+                                const double* sigma_T, const double* sigma_a, const double* q,
+                                const double* eps, int eps_is_scalar, double g,
+                                const double* inflow, void* stream, int block_mode, rte_ctx** out);
+
+/* Number of interpolation nodes the context's blocks were built from (0 when
+ * every block was inverted cell by cell). */
+RTE_API rte_status rte_block_setup_info(const rte_ctx* ctx, int* tabulated_nodes);
+
 RTE_API void rte_destroy(rte_ctx* ctx);
 
 /* Message of the last error of ctx (or of the calling thread if ctx is NULL). */

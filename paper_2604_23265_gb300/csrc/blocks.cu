@@ -137,13 +137,14 @@ __global__ void __launch_bounds__(512) k_build_invert(int M, const int* __restri
 // Rt[c][i][row] = R_C[row][i].  Its entries are bounded transfer
 // coefficients (row sums of |R| near one), so FP32 keeps them accurate where
 // D_C itself (entries up to ~1e5 in the diffusive limit) would not.
+template <typename TR>
 __global__ void __launch_bounds__(256) k_response(int M, const int* __restrict__ mat,
                                                   const double* __restrict__ tau,
                                                   const double* __restrict__ xi,
                                                   const double* __restrict__ L,
                                                   const int* __restrict__ rowdir,
                                                   const double* __restrict__ Dt,
-                                                  float* __restrict__ Rt) {
+                                                  TR* __restrict__ Rt) {
     extern __shared__ double smd[];
     const int n2 = 2 * M, M2 = M / 2, ld = n2 + 1;
     double* T = smd;                     // [n2][ld] outgoing traces
@@ -164,13 +165,61 @@ __global__ void __launch_bounds__(256) k_response(int M, const int* __restrict__
     }
     __syncthreads();
     const double* D = Dt + (size_t)c * n2 * n2;      // D[k][i] = Dt[i][k]
-    float* out = Rt + (size_t)c * n2 * n2;
+    TR* out = Rt + (size_t)c * n2 * n2;
     for (int e = tid; e < n2 * n2; e += nt) {
         const int i = e / n2, r = e - i * n2;
         const double* di = D + (size_t)i * n2;
         double acc = 0.0;
         for (int k = 0; k < n2; ++k) acc = fma(T[r * ld + k], __ldg(di + k), acc);
-        out[e] = (float)acc;
+        out[e] = (TR)acc;
+    }
+}
+
+// Blocks of a cell from tabulated nodes (set-up by interpolation in ln tau):
+// for the cells of bin b (all interpolating between the nodes node0 ..
+// node0 + 7), D_C = sum_p w_Cp D_p and R_C = sum_p w_Cp R_p elementwise (FP64,
+// R rounded to FP32 once).  Block (b, y) holds the node values of elements
+// 1024 y .. 1024 y + 1023 in registers and writes them for every cell of the
+// bin.  bins[b] = (node0, first, end) positions in the cell list.
+__global__ void __launch_bounds__(256) k_interp_blocks(int E, const int4* __restrict__ bins,
+                                                       const int* __restrict__ cells,
+                                                       const double* __restrict__ wts,
+                                                       const double* __restrict__ Dn,
+                                                       const double* __restrict__ Rn,
+                                                       double* __restrict__ Dt, float* __restrict__ Rt) {
+    const int4 bn = bins[blockIdx.x];
+    const int e0 = (blockIdx.y * 256 + threadIdx.x) * 4;
+    if (e0 >= E) return;                       // E = (2M)^2, a multiple of 4
+    double dn[8][4], rn[8][4];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const double2* dp = reinterpret_cast<const double2*>(Dn + (size_t)(bn.x + p) * E + e0);
+        const double2* rp = reinterpret_cast<const double2*>(Rn + (size_t)(bn.x + p) * E + e0);
+        const double2 d0 = __ldg(dp), d1 = __ldg(dp + 1), r0 = __ldg(rp), r1 = __ldg(rp + 1);
+        dn[p][0] = d0.x; dn[p][1] = d0.y; dn[p][2] = d1.x; dn[p][3] = d1.y;
+        rn[p][0] = r0.x; rn[p][1] = r0.y; rn[p][2] = r1.x; rn[p][3] = r1.y;
+    }
+    for (int pos = bn.y; pos < bn.z; ++pos) {
+        const int c = __ldg(cells + pos);
+        double w[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) w[p] = __ldg(wts + (size_t)pos * 8 + p);
+        double d[4], r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            d[q] = w[0] * dn[0][q];
+            r[q] = w[0] * rn[0][q];
+#pragma unroll
+            for (int p = 1; p < 8; ++p) {
+                d[q] = fma(w[p], dn[p][q], d[q]);
+                r[q] = fma(w[p], rn[p][q], r[q]);
+            }
+        }
+        double2* dd = reinterpret_cast<double2*>(Dt + (size_t)c * E + e0);
+        dd[0] = make_double2(d[0], d[1]);
+        dd[1] = make_double2(d[2], d[3]);
+        *reinterpret_cast<float4*>(Rt + (size_t)c * E + e0) =
+            make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
     }
 }
 
@@ -421,11 +470,70 @@ void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
         check(cudaGetLastError(), "k_build_invert");
     }
     const size_t smem2 = sizeof(double) * ((size_t)n2 * (n2 + 1) + n2);
-    raise_smem_limit((const void*)k_response, (size_t)(smem2));
+    raise_smem_limit((const void*)k_response<float>, (size_t)(smem2));
     ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * n2 * n2 * 12);
-    k_response<<<ctx->N, threads, smem2, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi, ctx->L64,
-                                                        ctx->rowdir, ctx->Dt, ctx->Rt);
+    k_response<float><<<ctx->N, threads, smem2, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi, ctx->L64,
+                                                               ctx->rowdir, ctx->Dt, ctx->Rt);
     check(cudaGetLastError(), "k_response");
+}
+
+void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_dev) {
+    const int M = ctx->M, n2 = 2 * M, E = n2 * n2;
+    const int J = (int)plan.node_tau.size();
+    const cudaStream_t st = ctx->stream;
+    // temporary tables: node materials and tau, the nodes' D and R (FP64), the
+    // cell list, weights and bins
+    std::vector<void*> tmp;
+    auto alloc = [&](size_t bytes) {
+        void* p = nullptr;
+        check(cudaMallocAsync(&p, bytes, st), "cudaMallocAsync (tabulated blocks)");
+        tmp.push_back(p);
+        return p;
+    };
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "h2d (tabulated blocks)");
+    };
+    try {
+        int* nmat = static_cast<int*>(alloc(J * sizeof(int)));
+        double* ntau = static_cast<double*>(alloc(J * sizeof(double)));
+        double* Dn = static_cast<double*>(alloc((size_t)J * E * sizeof(double)));
+        double* Rn = static_cast<double*>(alloc((size_t)J * E * sizeof(double)));
+        int* cells = static_cast<int*>(alloc(plan.cells.size() * sizeof(int)));
+        double* wts = static_cast<double*>(alloc(plan.weights.size() * sizeof(double)));
+        int4* bins = static_cast<int4*>(alloc(plan.bins.size() * sizeof(int4)));
+        up(nmat, plan.node_mat.data(), J * sizeof(int));
+        up(ntau, plan.node_tau.data(), J * sizeof(double));
+        up(cells, plan.cells.data(), plan.cells.size() * sizeof(int));
+        up(wts, plan.weights.data(), plan.weights.size() * sizeof(double));
+        up(bins, plan.bins.data(), plan.bins.size() * sizeof(int4));
+        const size_t smem = sizeof(double) * ((size_t)n2 * (n2 + 1) + 3 * n2);
+        raise_smem_limit((const void*)k_build_invert, smem);
+        const int threads_inv = n2 >= 128 ? 512 : (n2 >= 64 ? 256 : 128);
+        const int threads = n2 >= 64 ? 256 : 128;
+        {
+            ProfScope ps(ctx, K_INVERT, (double)J * E * 8);
+            k_build_invert<<<J, threads_inv, smem, st>>>(M, nmat, ntau, ctx->xi, ctx->L64, ctx->rowdir, Dn,
+                                                         singular_dev);
+            check(cudaGetLastError(), "k_build_invert (nodes)");
+        }
+        {
+            const size_t smem2 = sizeof(double) * ((size_t)n2 * (n2 + 1) + n2);
+            raise_smem_limit((const void*)k_response<double>, smem2);
+            ProfScope ps(ctx, K_RESPONSE, (double)J * E * 16);
+            k_response<double><<<J, threads, smem2, st>>>(M, nmat, ntau, ctx->xi, ctx->L64, ctx->rowdir, Dn, Rn);
+            check(cudaGetLastError(), "k_response (nodes)");
+        }
+        {
+            ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * E * 12);
+            const dim3 grid((unsigned)plan.bins.size(), (unsigned)((E / 4 + 255) / 256));
+            k_interp_blocks<<<grid, 256, 0, st>>>(E, bins, cells, wts, Dn, Rn, ctx->Dt, ctx->Rt);
+            check(cudaGetLastError(), "k_interp_blocks");
+        }
+    } catch (...) {
+        for (void* p : tmp) cudaFreeAsync(p, st);
+        throw;
+    }
+    for (void* p : tmp) cudaFreeAsync(p, st);
 }
 
 namespace {

@@ -83,6 +83,8 @@ struct rte_ctx {
     int max_red_blocks = 0;
 
     size_t device_bytes = 0;
+    int block_mode = 0;              // RTE_BLOCKS_AUTO / EXACT / TABULATED requested at set-up
+    int tab_nodes = 0;               // nodes of the tabulated set-up (0: per-cell inversion)
     rte::Workspace* ws = nullptr;
     rte::Atfps* atfps = nullptr;
     rte::Profiler prof;
@@ -240,6 +242,20 @@ void atfps_layers(rte_ctx* ctx, double* x);
 // builds G_C for every cell, inverts it into ctx->Dt (FP64) and forms the
 // response matrices ctx->Rt (FP32); *singular_dev set to 1 on a zero pivot.
 void launch_build_invert(rte_ctx* ctx, int* singular_dev);
+// Set-up by interpolation in ln tau (few materials, many cells): nodes of
+// each material at tau = exp(s ds) on a uniform grid of s covering the
+// cells' range; every cell's D_C and R_C are the 8-point Lagrange
+// combination of the nodes around its ln tau.  Cells are binned by their
+// first node so that one bin shares its node values.
+struct TabPlan {
+    std::vector<int> node_mat;       // [J] material of each node
+    std::vector<double> node_tau;    // [J] its tau
+    std::vector<int> cells;          // [N] cells ordered by bin
+    std::vector<double> weights;     // [N][8] Lagrange weights, in the order of cells
+    std::vector<int4> bins;          // (first node, first position, end position) in cells
+};
+void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_dev);
+
 // z = D r (or D^T r), FP64 accumulation; float or double in and out
 void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double, void* z,
                         bool z_is_double);

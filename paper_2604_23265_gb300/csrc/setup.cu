@@ -350,6 +350,79 @@ T* upload(rte_ctx* ctx, const std::vector<T>& h) {
     return d;
 }
 
+// Spacing of the interpolation nodes in ln tau and the smallest material
+// (cells) the automatic mode tabulates.  At ds = 0.04 the 8-point Lagrange
+// interpolation of D(tau) and R(tau) is exact to about 1e-11 of the blocks'
+// size on well-conditioned media, below the rounding of an FP64 inversion
+// once cond(G_C) exceeds about 1e5 and of the FP32 response matrices always.
+constexpr double kTabStep = 0.04;
+constexpr int kTabMinCells = 4096;
+
+// Decides the set-up of the per-cell blocks and, when it tabulates, plans
+// it: per material the nodes s = (base + i) ds over the range of its cells'
+// ln tau (three nodes beyond each end), per cell the first node of its
+// stencil and the Lagrange weights at t = ln(tau) / ds, cells binned by the
+// stencil's first node.  Automatic mode: at least kTabMinCells cells and 16
+// cells per node over all materials (a material of a few cells, e.g. one
+// whose 1 - gamma rounds differently, costs only its eight nodes).
+bool plan_tabulation(rte_ctx* ctx, const std::vector<double>& tau, TabPlan& plan) {
+    const int N = ctx->N, nmat = ctx->nmat;
+    if (ctx->block_mode == RTE_BLOCKS_EXACT) return false;
+    std::vector<double> smin(nmat, 1e300), smax(nmat, -1e300);
+    for (int c = 0; c < N; ++c) {
+        const int j = ctx->mat_h[c];
+        const double sv = std::log(tau[c]);
+        smin[j] = std::min(smin[j], sv);
+        smax[j] = std::max(smax[j], sv);
+    }
+    std::vector<long long> base(nmat), off(nmat + 1, 0);
+    for (int j = 0; j < nmat; ++j) {
+        base[j] = (long long)std::floor(smin[j] / kTabStep) - 3;
+        const long long J = (long long)std::floor(smax[j] / kTabStep) - base[j] + 5;
+        off[j + 1] = off[j] + J;
+    }
+    if (off[nmat] > 1 << 20) return false;
+    if (ctx->block_mode == RTE_BLOCKS_AUTO && (N < kTabMinCells || off[nmat] * 16 > N)) return false;
+    const int J = (int)off[nmat];
+    plan.node_mat.resize(J);
+    plan.node_tau.resize(J);
+    for (int j = 0; j < nmat; ++j)
+        for (long long i = off[j]; i < off[j + 1]; ++i) {
+            plan.node_mat[i] = j;
+            plan.node_tau[i] = std::exp((double)(base[j] + (i - off[j])) * kTabStep);
+        }
+    // stencil of every cell: nodes fl - 3 .. fl + 4 around t = ln(tau) / ds
+    std::vector<int> first(N);
+    std::vector<double> w((size_t)N * 8);
+    for (int c = 0; c < N; ++c) {
+        const int j = ctx->mat_h[c];
+        const double t = std::log(tau[c]) / kTabStep;
+        const long long fl = (long long)std::floor(t);
+        first[c] = (int)(off[j] + (fl - 3 - base[j]));
+        for (int m = 0; m < 8; ++m) {
+            double v = 1.0;
+            for (int q = 0; q < 8; ++q)
+                if (q != m) v *= (t - (double)(fl - 3 + q)) / (double)(m - q);
+            w[(size_t)c * 8 + m] = v;
+        }
+    }
+    // bins by first node (counting sort, cells in ascending order per bin)
+    std::vector<int> nb(J + 1, 0);
+    for (int c = 0; c < N; ++c) ++nb[first[c] + 1];
+    for (int i = 0; i < J; ++i) nb[i + 1] += nb[i];
+    plan.cells.assign(N, 0);
+    plan.weights.assign((size_t)N * 8, 0.0);
+    std::vector<int> fillp(nb.begin(), nb.end() - 1);
+    for (int c = 0; c < N; ++c) {
+        const int pos = fillp[first[c]]++;
+        plan.cells[pos] = c;
+        for (int m = 0; m < 8; ++m) plan.weights[(size_t)pos * 8 + m] = w[(size_t)c * 8 + m];
+    }
+    for (int i = 0; i < J; ++i)
+        if (nb[i + 1] > nb[i]) plan.bins.push_back(make_int4(i, nb[i], nb[i + 1], 0));
+    return true;
+}
+
 void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const double* q,
            const double* eps, int eps_is_scalar, const double* inflow) {
     NvtxRange range("rte_setup");
@@ -495,7 +568,13 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         launch_coef_inputs(ctx, dsT, dsa, de);
     }
     int* sing = reinterpret_cast<int*>(ctx->scal + kScal - 1);
-    launch_build_invert(ctx, sing);
+    TabPlan plan;
+    if (plan_tabulation(ctx, tau, plan)) {
+        ctx->tab_nodes = (int)plan.node_tau.size();
+        launch_tabulated_blocks(ctx, plan, sing);
+    } else {
+        launch_build_invert(ctx, sing);
+    }
     int sing_h = 0;
     check(cudaMemcpyAsync(&sing_h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "d2h");
     check(cudaStreamSynchronize(ctx->stream), "setup sync");
@@ -526,7 +605,19 @@ RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
                              const double* sigma_T, const double* sigma_a, const double* q,
                              const double* eps, int eps_is_scalar, double g,
                              const double* inflow, void* stream, rte_ctx** out) {
+    return rte_setup_ex(grid, quad, sigma_T, sigma_a, q, eps, eps_is_scalar, g, inflow, stream, RTE_BLOCKS_AUTO,
+                        out);
+}
+
+RTE_API rte_status rte_setup_ex(const rte_grid* grid, const rte_quadrature* quad,
+                                const double* sigma_T, const double* sigma_a, const double* q,
+                                const double* eps, int eps_is_scalar, double g,
+                                const double* inflow, void* stream, int block_mode, rte_ctx** out) {
     if (!out) { set_error(nullptr, "out is NULL"); return RTE_EINVAL; }
+    if (block_mode != RTE_BLOCKS_AUTO && block_mode != RTE_BLOCKS_EXACT && block_mode != RTE_BLOCKS_TABULATED) {
+        set_error(nullptr, "unknown block_mode");
+        return RTE_EINVAL;
+    }
     *out = nullptr;
     if (!grid || !quad || !sigma_T || !sigma_a || !q || !eps) {
         set_error(nullptr, "NULL argument");
@@ -544,6 +635,7 @@ RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
     ctx->N = grid->I * grid->I;
     ctx->n = (int64_t)2 * ctx->M * ctx->N;
     ctx->g = g;
+    ctx->block_mode = block_mode;
     ctx->stream = static_cast<cudaStream_t>(stream);
     static std::atomic<uint64_t> next_uid{1};
     ctx->uid = next_uid.fetch_add(1);
@@ -564,6 +656,12 @@ RTE_API rte_status rte_setup(const rte_grid* grid, const rte_quadrature* quad,
         return st;
     }
     *out = ctx;
+    return RTE_OK;
+}
+
+RTE_API rte_status rte_block_setup_info(const rte_ctx* ctx, int* tabulated_nodes) {
+    if (!ctx || !tabulated_nodes) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
+    *tabulated_nodes = ctx->tab_nodes;
     return RTE_OK;
 }
 

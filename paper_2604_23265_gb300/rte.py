@@ -74,6 +74,9 @@ _D = ctypes.c_double
 SIGNATURES = {
     "rte_setup": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(Quadrature), _P, _P, _P, _P, _I, _D, _P,
                        _P, ctypes.POINTER(_P)]),
+    "rte_setup_ex": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(Quadrature), _P, _P, _P, _P, _I, _D, _P,
+                          _P, _I, ctypes.POINTER(_P)]),
+    "rte_block_setup_info": (_I, [_P, ctypes.POINTER(_I)]),
     "rte_destroy": (None, [_P]),
     "rte_last_error": (ctypes.c_char_p, [_P]),
     "rte_info": (_I, [_P, ctypes.POINTER(CtxInfo)]),
@@ -472,7 +475,9 @@ class MgNet:
 class Context:
     """One RTE system (rte_setup); see include/rte.h for the layouts."""
 
-    def __init__(self, I, M, sigma_T, sigma_a, q, eps, g, inflow=None, stream=None):
+    BLOCKS_AUTO, BLOCKS_EXACT, BLOCKS_TABULATED = 0, 1, 2
+
+    def __init__(self, I, M, sigma_T, sigma_a, q, eps, g, inflow=None, stream=None, block_mode=0):
         lib = load()
         N = I * I
         self._keep = []
@@ -487,17 +492,23 @@ class Context:
         else:
             fl, pf = None, None
         out = ctypes.c_void_p()
-        st = lib.rte_setup(ctypes.byref(Grid(I)), ctypes.byref(Quadrature(M)), psT, psa, pq, pe,
-                           scalar, float(g), pf, _stream_ptr(stream), ctypes.byref(out))
+        st = lib.rte_setup_ex(ctypes.byref(Grid(I)), ctypes.byref(Quadrature(M)), psT, psa, pq, pe,
+                              scalar, float(g), pf, _stream_ptr(stream), int(block_mode), ctypes.byref(out))
         _check(st, None)
         self.ptr = out
         self.I, self.M, self.N = I, M, N
         self.n = 2 * M * N
 
     @classmethod
-    def from_medium(cls, md, stream=None):
-        """The context of a workloads.Medium (rte_setup)."""
-        return cls(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow, stream)
+    def from_medium(cls, md, stream=None, block_mode=0):
+        """The context of a workloads.Medium (rte_setup_ex; block_mode: Context.BLOCKS_*)."""
+        return cls(md.I, md.M, md.sigma_T, md.sigma_a, md.q, md.eps, md.g, md.inflow, stream, block_mode)
+
+    def tabulated_nodes(self):
+        """Interpolation nodes of the per-cell blocks (0: inverted cell by cell)."""
+        v = ctypes.c_int()
+        _check(load().rte_block_setup_info(self.ptr, ctypes.byref(v)), self.ptr)
+        return v.value
 
     def close(self):
         """Free the context (rte_destroy)."""
