@@ -303,6 +303,59 @@ def run_setup_only(args):
                       "first_seconds": times[0]}), flush=True)
 
 
+def run_gs_only(args):
+    """Profiling mode: args.gs_steps Gram-Schmidt steps (the three df64 passes
+    and the scaling, rte_cgs2_df64) of w against args.gs_only basis vectors on
+    the workload's context; prints the mean time of each pass class and its
+    algorithmic GB/s (CUDA events on the context's stream)."""
+    import torch
+    from paper_2604_23265_gb300 import rte
+    torch.cuda.set_device(0)
+    md = W.grf_diffusive(seed=0, I=args.size, M=args.dirs)
+    ctx = rte.Context.from_medium(md)
+    K, n = args.gs_only, ctx.n
+    g = torch.Generator(device="cuda").manual_seed(0)
+    V64 = torch.randn(K, n, dtype=torch.float64, device="cuda", generator=g) / np.sqrt(n)
+    hi = V64.float()
+    Vf = torch.stack([hi, (V64 - hi.double()).float()], 1).contiguous().view(-1)
+    w0 = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    w = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    h = torch.zeros(K + 1, dtype=torch.float64, device="cuda")
+    for r in range(args.gs_steps + 1):
+        if r == 1:
+            ctx.profile(True)
+        w[:n] = w0.float()
+        w[n:] = (w0 - w0.float().double()).float()
+        ctx.cgs2_df64(Vf, K, w, h)
+    prof = ctx.profile_read()
+    out = {"mode": "gs_only", "I": md.I, "M": md.M, "n": n, "K": K, "steps": args.gs_steps}
+    step_bytes = ((3 * K + 5) * 8 + 16) * n
+    tot = 0.0
+    for k in ("mdot", "update_dot", "update_norm", "scale"):
+        l, ms, byts, _ = prof[k]
+        out[k] = {"ms_per_launch": ms / max(l, 1), "GBps": byts / (ms / 1e3) / 1e9 if ms > 0 else None}
+        tot += ms / max(l, 1)
+    out["df64_step"] = {"ms": tot, "GBps": step_bytes / (tot / 1e3) / 1e9}
+    # the same step on FP64 vectors (rte_cgs2), for comparison
+    Vd = (Vf.view(K, 2, n)[:, 0, :].double() + Vf.view(K, 2, n)[:, 1, :].double()).contiguous().view(-1)
+    wd = torch.empty(n, dtype=torch.float64, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(False)
+    times = []
+    for r in range(args.gs_steps + 1):
+        wd.copy_(w0)
+        ev0.record()
+        ctx.cgs2(Vd, K, wd, h)
+        ev1.record()
+        torch.cuda.synchronize()
+        if r:
+            times.append(ev0.elapsed_time(ev1))
+    t64 = float(np.mean(times))
+    out["fp64_step"] = {"ms": t64, "GBps": step_bytes / (t64 / 1e3) / 1e9}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     from paper_2604_23265_gb300 import rte, train
@@ -438,14 +491,20 @@ def run_ours(args):
         out["atfps"] = atfps_leg()
     if rank == 0 and world == 1 and not args.no_pcg:
         out["per_cell_gamma"] = per_cell_gamma_leg(net)
+    if rank == 0 and world == 1 and args.config3_steps > 0:
+        out["config3"] = config3_leg(steps=args.config3_steps)
     if rank == 0 and world == 1 and (args.serve > 0 or args.batch > 0):
         nets, mixed_train_s = train_mixed_nets(args.mixed_train_steps)
         out["mixed_networks"] = {"M": list(nets), "train_seconds": mixed_train_s,
                                  "train_steps": args.mixed_train_steps, "levels": nets[MIXED_DIRS[0]].shape.levels}
-        if args.serve > 0:
-            out["serving"] = serving_leg(args.serve, nets)
         if args.batch > 0:
             out["batched"] = batched_leg(args.batch, nets)
+        if args.serve > 0:
+            # M = 64 requests use the benchmark network (depth of a 256 x 256 grid)
+            snets = dict(nets)
+            if net is not None and net.shape.M == 64:
+                snets[64] = net
+            out["serving"] = serving_leg(args.serve, snets)
         for n in nets.values():
             n.close()
     if rank == 0:
@@ -489,14 +548,17 @@ def _wants_net(md):
     return float(np.max(md.eps)) <= NET_EPS_MAX
 
 
-SERVE_WORKLOAD = ("Poisson arrivals of mixed solve requests: I in {64, 128}, M in {16, 32}, eps log-uniform "
-                  "in [1e-4, 1], g uniform in [0, 0.9], GRF media; FGMRES(50) to rel-res 1e-8; grouped server "
-                  "(shared launches, batched V-cycles), 4 slots")
+SERVE_GRIDS, SERVE_DIRS = (64, 128, 256, 512), (16, 32, 64)
+SERVE_WORKLOAD = ("Poisson arrivals of mixed solve requests: I in {64, 128, 256, 512}, M in {16, 32, 64}, eps "
+                  "log-uniform in [1e-4, 1], g uniform in [0, 0.9], GRF media; FGMRES(50) to rel-res 1e-8 (at most "
+                  "5000 iterations); grouped server (shared launches, batched V-cycles), 4 slots, admission by "
+                  "device footprint; arrival rates 0.5, 0.8 and 0.95 of the capacity measured with all requests "
+                  "queued at once")
 
 
-def _serve_once(media, gaps, nets, use_net):
+def _serve_once(media, gaps, nets, use_net, max_iter=40000):
     from paper_2604_23265_gb300 import rte
-    srv = rte.Server(slots=4, max_device_bytes=96 << 30, net=list(nets.values()) if use_net else None,
+    srv = rte.Server(slots=4, max_device_bytes=160 << 30, net=list(nets.values()) if use_net else None,
                      grouped=True)
     n_req = len(media)
     ids = [None] * n_req
@@ -510,7 +572,7 @@ def _serve_once(media, gaps, nets, use_net):
                 d = t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                ids[i] = srv.submit(md, tol=1e-8, max_iter=40000, use_net=use_net and _wants_net(md))
+                ids[i] = srv.submit(md, tol=1e-8, max_iter=max_iter, use_net=use_net and _wants_net(md))
 
         th = threading.Thread(target=feeder)
         th.start()
@@ -535,38 +597,37 @@ def _serve_once(media, gaps, nets, use_net):
 
 
 def serving_leg(n_req, nets, seed=11):
-    """Continuous-batching server under Poisson arrivals (a reduced instance of
-    the serving workload), once with the per-M networks (requests inside their
-    eps range) and once with block Jacobi only, on the same requests and the
-    same arrival times: p50 / p99 latency and solves/s of each.  The arrival
-    rate is half the capacity of four slots estimated from the mean
-    block-Jacobi service time of three requests served alone."""
-    from paper_2604_23265_gb300 import rte
-    media = _mixed_media(n_req, seed, grids=(64, 128))
-    srv = rte.Server(slots=1, max_device_bytes=96 << 30)
-    try:
-        t0 = time.perf_counter()
-        for md in media[:3]:
-            srv.wait(srv.submit(md, tol=1e-8, max_iter=40000))
-        service = (time.perf_counter() - t0) / 3
-    finally:
-        srv.close()
-    rate = 0.5 * 4 / service
-    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_req)
-    out = {"workload": SERVE_WORKLOAD, "requests": n_req, "slots": 4, "arrival_rate_per_s": rate,
-           "single_request_service_s": service,
-           "policy": f"network for the request's M when eps <= {NET_EPS_MAX:g}, else block Jacobi"}
-    out["mgnet"] = _serve_once(media, gaps, nets, True)
-    out["block_jacobi"] = _serve_once(media, gaps, nets, False)
-    # headline keys: the MgNet arm
+    """The serving workload: mixed requests up to 512 x 512 cells and M = 64
+    through the continuous-batching server (per-M networks inside their eps
+    range, block Jacobi otherwise).  Capacity is measured first with all
+    n_req requests queued at once (completed requests per second); then
+    n_req further requests arrive as a Poisson stream at 0.5, 0.8 and 0.95 of
+    that capacity, with p50 / p99 latency and solves/s at each rate."""
+    t_all = time.time()
+    rng = np.random.default_rng(seed)
+    sat = _serve_once(_mixed_media(n_req, seed, grids=SERVE_GRIDS, dirs=SERVE_DIRS), np.zeros(n_req), nets, True,
+                      max_iter=5000)
+    capacity = sat["solves_per_s"]
+    out = {"workload": SERVE_WORKLOAD, "requests_per_rate": n_req, "slots": 4,
+           "policy": f"network for the request's M when eps <= {NET_EPS_MAX:g}, else block Jacobi",
+           "capacity_solves_per_s": capacity, "saturation": sat, "rates": {}}
+    for k, frac in enumerate((0.5, 0.8, 0.95)):
+        media = _mixed_media(n_req, seed + 1 + k, grids=SERVE_GRIDS, dirs=SERVE_DIRS)
+        rate = frac * capacity
+        gaps = rng.exponential(1.0 / rate, n_req)
+        r = _serve_once(media, gaps, nets, True, max_iter=5000)
+        r["arrival_rate_per_s"] = rate
+        out["rates"][str(frac)] = r
+    # headline keys: the 0.8 rate
     for k in ("completed_ok", "p50_latency_s", "p99_latency_s", "mean_queue_s", "solves_per_s"):
-        out[k] = out["mgnet"][k]
+        out[k] = out["rates"]["0.8"][k]
+    out["leg_seconds"] = time.time() - t_all
     return out
 
 
-BATCH_WORKLOAD = ("mixed instances: I in {64, 128}, M in {16, 32}, eps log-uniform in [1e-4, 1], g uniform in "
-                  "[0, 0.8], GRF media; FGMRES(50) to rel-res 1e-8; per-M networks for eps <= 0.1, block "
-                  "Jacobi otherwise")
+BATCH_WORKLOAD = ("mixed instances: I in {64, 128, 256}, M in {16, 32}, eps log-uniform in [1e-4, 1], g uniform "
+                  "in [0, 0.8], GRF media; FGMRES(50) to rel-res 1e-8; per-M networks for eps <= 0.1, block "
+                  "Jacobi otherwise; the classical arm (block Jacobi for every instance) within 2000 iterations")
 
 
 def batched_leg(count, nets, seed=23):
@@ -577,7 +638,8 @@ def batched_leg(count, nets, seed=23):
     device, set-up excluded."""
     import torch
     from paper_2604_23265_gb300 import rte
-    media = _mixed_media(count, seed, grids=(64, 128), g_range=(0.0, 0.8))
+    t_all = time.time()
+    media = _mixed_media(count, seed, grids=MIXED_GRIDS, g_range=(0.0, 0.8))
     pcs = [nets[md.M] if _wants_net(md) else None for md in media]
     ctxs = [rte.Context.from_medium(md) for md in media]
     xs1 = [torch.zeros(c.n, dtype=torch.float64, device="cuda") for c in ctxs]
@@ -600,7 +662,7 @@ def batched_leg(count, nets, seed=23):
     for x in xs2:
         x.zero_()
     t0 = time.perf_counter()
-    bj = rte.solve_group(ctxs, xs2, **kw)
+    bj = rte.solve_group(ctxs, xs2, tol=1e-8, max_iter=2000)
     torch.cuda.synchronize()
     t_bj = time.perf_counter() - t0
     for c in ctxs:
@@ -609,10 +671,66 @@ def batched_leg(count, nets, seed=23):
             "grouped_solves_per_s": count / t_grp, "one_at_a_time_solves_per_s": count / t_lone,
             "speedup": t_lone / t_grp, "iterations_total": int(sum(i["iterations"] for i in grp)),
             "converged": all(i["converged"] for i in grp), "bit_identical_to_lone": bool(same),
-            "block_jacobi_grouped_solves_per_s": count / t_bj,
+            "block_jacobi_seconds_2000_iterations": t_bj,
+            "block_jacobi_converged_within_2000": int(sum(bool(i["converged"]) for i in bj)),
+            "block_jacobi_converged_solves_per_s": sum(bool(i["converged"]) for i in bj) / t_bj,
             "block_jacobi_iterations_total": int(sum(i["iterations"] for i in bj)),
-            "block_jacobi_converged": all(i["converged"] for i in bj),
-            "mgnet_vs_block_jacobi": t_bj / t_grp}
+            "leg_seconds": time.time() - t_all}
+
+
+CONFIG3_WORKLOAD = ("MgNet train + apply: 128 x 128 cells, M = 32, 4 levels, 64 hidden channels doubling per "
+                    "level (64-512), 2 smoothing convolutions per level; 2000 training pairs (40 media of the "
+                    "training distribution: GRF sigma_T with ell in [0.05, 0.2], eps log-uniform in [1e-4, 1e-1], "
+                    "g in [0, 0.8]; 50 random right-hand sides each, the paper's recipe); batch 8, Adam with "
+                    "cosine annealing from 1e-3 (Sec. 4.1)")
+
+
+def config3_leg(steps=400, n_media=40, seed=300, n_test=2):
+    """The network of the train + apply configuration trained on the GPU:
+    training steps per second (FP32 forward, backward and Adam on CUDA cores),
+    and FGMRES(50) iterations to 1e-8 on unseen media of the distribution with
+    the trained network, the untrained one (zero projection: block Jacobi
+    exactly) and block Jacobi."""
+    import torch
+    from paper_2604_23265_gb300 import rte, train
+    t_all = time.time()
+    media = [W.training_medium(seed=seed + i, I=128, M=32) for i in range(n_media)]
+    shape = W.NetShape(M=32, levels=4, c0=64, cmax=512, cc=8, ccmax=32)
+    net = rte.MgNet(shape)
+    net.set_params(W.init_params(shape, seed=0, proj_scale=0.0, vcycle_scale=0.5))
+    ctxs = [rte.Context.from_medium(md) for md in media]
+    inputs = [train.random_inputs(c, 50, seed + 17 * i) for i, c in enumerate(ctxs)]
+    pairs = sum(len(x) for x in inputs)
+    net.train_step(ctxs[0], inputs[0][:8], 0.0)             # warm-up (workspace)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train.train(net, ctxs, inputs, steps=steps, batch=8, lr0=1e-3, seed=seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    untrained = rte.MgNet(shape)
+    untrained.set_params(W.init_params(shape, seed=0, proj_scale=0.0, vcycle_scale=0.5))
+    tests = []
+    for k in range(n_test):
+        md = W.training_medium(seed=seed + 1000 + k, I=128, M=32)
+        ctx = rte.Context.from_medium(md)
+        row = {"eps": float(md.eps[0]), "g": float(md.g)}
+        for name, pc in (("trained", net), ("untrained", untrained), ("block_jacobi", None)):
+            x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+            info = ctx.solve(x, pc=pc, tol=1e-8, restart=50, max_iter=20000, raise_on_error=False)
+            row[name] = {"iterations": info["iterations"], "converged": bool(info["converged"]),
+                         "fell_back": bool(info["fell_back"])}
+        ctx.close()
+        tests.append(row)
+    untrained.close()
+    out = {"workload": CONFIG3_WORKLOAD, "pairs": pairs, "params": net.count, "train_steps": steps, "batch": 8,
+           "train_seconds": t_train, "train_steps_per_s": steps / t_train, "samples_per_s": 8 * steps / t_train,
+           "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:])),
+           "training_arithmetic": "FP32 forward, backward and Adam on CUDA cores (tensor pipe not used in training)",
+           "test_media": tests, "leg_seconds": time.time() - t_all}
+    net.close()
+    return out
 
 
 ATFPS_WORKLOAD = ("64 x 64 cells, M = 16, eps = 1e-3, g = 0.5, GRF medium (the benchmark distribution); "
@@ -751,8 +869,71 @@ def run_paper_protocol(args):
                          "train_seconds": secs, "final_loss": float(np.mean(losses[-20:])),
                          "mean_bj_over_mgnet": float(np.mean(ratio)) if ratio else None, "curve": curve}
             net.close()
+        if regime == "diffusion" and args.pp_e3:
+            res["e3"] = _paper_e3(args, test_media, solve_all, bj)
         out[regime] = res
     print(json.dumps(out), flush=True)
+
+
+def _paper_e3(args, test_media, solve_all, bj):
+    """E3 (Sec. 4.1-4.2): training-set size, 10,000 against 20,000 samples, in
+    the diffusion regime, with the ATFPS-filtered loss.  Two recipes:
+    * "paper": random right-hand sides (unit white-noise vectors in face-flux
+      space) paired with random media, ten per medium (1,000 or 2,000 media);
+    * "arnoldi_smooth": this library's inputs (16 Arnoldi vectors and 16
+      smooth-error residuals per medium; 313 or 625 media).
+    Samples are split 4:1 into training and validation by medium.  Every
+    network trains args.pp_steps steps and preconditions the same 10 test
+    media."""
+    import torch
+    from paper_2604_23265_gb300 import rte, train
+    res = {"loss": "filtered", "delta": 1e-2}
+    for recipe in ("paper", "arnoldi_smooth"):
+        for samples in (10000, 20000):
+            per = 10 if recipe == "paper" else 32
+            n_media = -(-samples // per)
+            media = [W.polynomial_medium(50000 + s, "diffusion") for s in range(n_media)]
+            n_val = n_media // 5
+            tr_media, va_media = media[n_val:], media[:n_val]
+            t0 = time.time()
+            if recipe == "paper":
+                shape = train.default_shape(tr_media[0].M, tr_media[0].I)
+                net = rte.MgNet(shape)
+                net.set_params(W.init_params(shape, seed=0, proj_scale=0.0, vcycle_scale=0.5))
+                net.loss = rte.MgNet.FILTERED
+
+                def rhs(ctx, seed):
+                    g = np.random.default_rng(seed)
+                    return [torch.tensor(g.standard_normal(ctx.n) / np.sqrt(ctx.n), device="cuda")
+                            for _ in range(per)]
+
+                ctxs = [rte.Context.from_medium(md) for md in tr_media]
+                vctx = [rte.Context.from_medium(md) for md in va_media]
+                for c in ctxs + vctx:
+                    c.atfps_setup(1e-2)
+                inputs = [rhs(c, 7 * i) for i, c in enumerate(ctxs)]
+                vin = [rhs(c, 100003 + 7 * i) for i, c in enumerate(vctx)]
+                losses = train.train(net, ctxs, inputs, steps=args.pp_steps, batch=8, lr0=3e-3, seed=0)
+                val = train.validation_loss(net, vctx, vin)
+                for c in ctxs + vctx:
+                    c.close()
+            else:
+                curve = []
+                net, ctxs, losses, _ = train.train_for(tr_media, steps=args.pp_steps, batch=8, lr0=3e-3, seed=0,
+                                                       n_krylov=16, n_smooth=16, loss="filtered", delta=1e-2,
+                                                       val_media=va_media, val_every=args.pp_steps, curve=curve)
+                val = curve[-1]["val_loss"] if curve else None
+                for c in ctxs:
+                    c.close()
+            secs = time.time() - t0
+            its, fell = solve_all(net)
+            ratio = [b / i for b, i in zip(bj, its) if b and i]
+            res[f"{recipe}_{samples}"] = {"media": n_media, "samples": n_media * per, "iterations": its,
+                                          "fell_back": fell, "mean_bj_over_mgnet": float(np.mean(ratio)) if ratio else None,
+                                          "final_train_loss": float(np.mean(losses[-20:])), "val_loss": val,
+                                          "seconds": secs}
+            net.close()
+    return res
 
 
 def run_reference(args):
@@ -798,6 +979,9 @@ def main():
     ap.add_argument("--precond-only", type=int, default=0,
                     help="profiling only: apply an untrained network this many times and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gs-only", type=int, default=0,
+                    help="profiling only: Gram-Schmidt steps against this many basis vectors")
+    ap.add_argument("--gs-steps", type=int, default=5, help="profiling only: steps of --gs-only")
     ap.add_argument("--setup-only", type=int, default=0,
                     help="profiling only: time the context set-up this many times and exit")
     ap.add_argument("--levels", type=int, default=0,
@@ -807,6 +991,7 @@ def main():
                     help="the paper's 32x32x4 polynomial-media experiment (plain vs filtered loss vs block Jacobi)")
     ap.add_argument("--pp-train", type=int, default=256, help="training media of --paper-protocol")
     ap.add_argument("--pp-steps", type=int, default=6000, help="training steps of --paper-protocol")
+    ap.add_argument("--pp-e3", type=int, default=1, help="E3 (10k vs 20k samples) in the diffusion regime")
     ap.add_argument("--pp-regimes", default="all",
                     help="--paper-protocol regimes: all, or a comma list of diffusion, transport, interface")
     ap.add_argument("--c0", type=int, default=16, help="network width at the finest level")
@@ -814,10 +999,12 @@ def main():
     ap.add_argument("--loss", default="plain", choices=["plain", "filtered"],
                     help="training loss of the network: Eq. loss or the ATFPS-filtered Eq. loss_delta")
     ap.add_argument("--delta", type=float, default=1e-2, help="ATFPS selection threshold (filtered loss)")
-    ap.add_argument("--batch", type=int, default=24,
+    ap.add_argument("--batch", type=int, default=64,
                     help="instances of the grouped-solve leg (shared launches); 0 skips it")
-    ap.add_argument("--serve", type=int, default=20,
-                    help="requests of the serving leg (p50/p99 latency); 0 skips it")
+    ap.add_argument("--serve", type=int, default=8,
+                    help="requests per arrival rate of the serving leg (p50/p99 latency); 0 skips it")
+    ap.add_argument("--config3-steps", type=int, default=400,
+                    help="training steps of the train + apply leg (128^2, M=32, widths 64-512); 0 skips it")
     ap.add_argument("--no-atfps", action="store_true", help="skip the compressed ATFPS leg")
     ap.add_argument("--no-pcg", action="store_true", help="skip the per-cell scattering-ratio leg")
     ap.add_argument("--mixed-train-steps", type=int, default=1500,
@@ -829,6 +1016,8 @@ def main():
         run_reference(args)
     elif args.precond_only > 0:
         run_precond_only(args)
+    elif args.gs_only > 0:
+        run_gs_only(args)
     elif args.setup_only > 0:
         run_setup_only(args)
     elif args.paper_protocol:

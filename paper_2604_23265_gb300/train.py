@@ -13,7 +13,9 @@ training medium:
 * residuals x = B e of smooth errors e (a smooth random field, the same in
   every face-flux slot of a cell, plus 10% white noise).  These carry the
   low-frequency error components block Jacobi cannot remove; a residual loss
-  over Arnoldi vectors alone hardly sees them, since B is small exactly there.
+  over Arnoldi vectors alone hardly sees them, since B is small exactly there;
+* or the paper's recipe (Sec. 4.1): random right-hand sides, unit white-noise
+  vectors in face-flux space (random_inputs).
 """
 from __future__ import annotations
 
@@ -25,10 +27,20 @@ import numpy as np
 from . import rte, workloads
 
 
-def training_inputs(ctx, md, n_krylov=32, n_smooth=32, seed=0, noise=0.1):
-    """List of device vectors (float64, length n) for one medium."""
+def random_inputs(ctx, count, seed=0):
+    """The paper's recipe (Sec. 4.1): random right-hand sides, here unit
+    white-noise vectors in face-flux space (float64 device vectors)."""
     import torch
-    out = []
+    g = np.random.default_rng(seed)
+    return [torch.tensor(g.standard_normal(ctx.n) / math.sqrt(ctx.n), device="cuda") for _ in range(count)]
+
+
+def training_inputs(ctx, md, n_krylov=32, n_smooth=32, seed=0, noise=0.1, n_random=0):
+    """List of device vectors (float64, length n) for one medium: n_krylov
+    Arnoldi vectors, n_smooth residuals of smooth errors and n_random random
+    right-hand sides."""
+    import torch
+    out = random_inputs(ctx, n_random, seed + 104729) if n_random > 0 else []
     if n_krylov > 0:
         V = torch.empty(n_krylov * ctx.n, dtype=torch.float64, device="cuda")
         ctx.arnoldi_basis(n_krylov, V)
@@ -90,7 +102,7 @@ def validation_loss(net, ctxs, inputs, batch=8):
 
 
 def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_smooth=32, seed=0,
-              log=None, loss="plain", delta=1e-2, val_media=None, val_every=0, curve=None):
+              log=None, loss="plain", delta=1e-2, val_media=None, val_every=0, curve=None, n_random=0):
     """Create a network for the media's (I, M), generate inputs and train it
     with the plain loss (Eq. loss) or the ATFPS-filtered one (Eq. loss_delta,
     selection threshold delta).  Returns (net, contexts, losses, seconds)."""
@@ -106,7 +118,7 @@ def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_sm
         net.loss = rte.MgNet.FILTERED
     elif loss != "plain":
         raise ValueError("loss is 'plain' or 'filtered'")
-    inputs = [training_inputs(c, md, n_krylov, n_smooth, seed + 17 * i)
+    inputs = [training_inputs(c, md, n_krylov, n_smooth, seed + 17 * i, n_random=n_random)
               for i, (c, md) in enumerate(zip(ctxs, media))]
     check = None
     vctx = []
@@ -116,7 +128,7 @@ def train_for(media, shape=None, steps=600, batch=8, lr0=3e-3, n_krylov=32, n_sm
         if loss == "filtered":
             for c in vctx:
                 c.atfps_setup(delta)
-        vin = [training_inputs(c, md, n_krylov, n_smooth, seed + 7919 + 17 * i)
+        vin = [training_inputs(c, md, n_krylov, n_smooth, seed + 7919 + 17 * i, n_random=n_random)
                for i, (c, md) in enumerate(zip(vctx, val_media))]
 
         def check(it, n, so_far):
