@@ -200,8 +200,8 @@ def cpu_baseline(md, gpu_iters):
 # (dram__bytes_read.sum + dram__bytes_write.sum); the bench scales it by the
 # algorithmic bytes of its own average launch.  The df64 Gram-Schmidt passes
 # read each basis row once (the second pass re-reads it from shared memory).
-TRAFFIC_RATIO = {"response_apply": 0.995}
-TRAFFIC_SOURCE = {"response_apply": "ncu DRAM bytes per launch at 128x128, M=32"}
+TRAFFIC_RATIO = {"response_apply": 0.9995}
+TRAFFIC_SOURCE = {"response_apply": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)"}
 
 # Nominal FP64 rate of a GB300 (152 SMs x 2.07 GHz x 2 FP64 FMA per clock x 2
 # flops): the roof of the FP64 operator apply, the one FP64-bound kernel left.
@@ -237,7 +237,7 @@ def _roofline(rte, stream, prof):
     ratio = TRAFFIC_RATIO.get(kname)
     roof["traffic"] = ratio * kbytes / kl if (ratio and kl) else None
     if ratio:
-        roof["traffic_source"] = "%s, scaled by algorithmic bytes per launch (ratio %.3f)" % (
+        roof["traffic_source"] = "%s, scaled by algorithmic bytes per launch (ratio %.4f)" % (
             TRAFFIC_SOURCE[kname], ratio)
     roof["launches"] = kl
     roof["share"] = kms / total_ms
@@ -459,7 +459,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded GRF medium per rank)",
         "config": dict(WORKLOAD, parallelism=f"replicas{world}", preconditioner=pc_name,
-                       inner="FP32 response matrices, FP64 Krylov + residual"),
+                       inner="FP32 response matrices, df64 Krylov basis, FP64 residual"),
         "iterations": iters, "relres": infos[-1]["relres"], "converged": converged,
         "fell_back": bool(infos[-1]["fell_back"]),
         "gpu_launches": launches,
