@@ -171,12 +171,7 @@ def cpu_baseline(md, gpu_iters):
     t_prob = time.perf_counter() - t0
     sub = min(p.N, 4096)
     t0 = time.perf_counter()
-    Gs = np.zeros((sub, 2 * p.M, 2 * p.M))
-    M2 = p.M // 2
-    for f in range(4):
-        for c in range(sub):
-            Gs[c, f * M2:(f + 1) * M2, :] = p.L[p.mat_id[c]][p.dirs[f], :] * p.dec[:, f, c][None, :]
-    Ds = np.linalg.inv(Gs)
+    Ds = np.linalg.inv(p.blocks_at(np.arange(sub)))
     t_inv = (time.perf_counter() - t0) * p.N / sub
     D = np.broadcast_to(Ds[:1], (p.N, 2 * p.M, 2 * p.M))
     b = p.rhs().ravel()
@@ -225,6 +220,12 @@ def _roofline(rte, stream, prof):
         roof = {"bound": "tensor", "kernel": "mgnet convolutions (tcgen05, BF16)",
                 "achieved": kflops / (kms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": psrc}
+    elif kname == "response_tc":
+        peak, psrc = _bf16_peak()
+        roof = {"bound": "tensor", "kernel": "response_tc (R z from the node tables, tcgen05 BF16 x 6 products)",
+                "achieved": kflops / (kms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": psrc,
+                "flops_note": "issued MMA flops: 6 BF16 products x 2 x 128 cells x (2M)^2 per tile and node"}
     elif kname in FP64_BOUND:
         roof = {"bound": "alu", "kernel": kname, "achieved": kflops / (kms / 1e3) / 1e12,
                 "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -358,6 +359,39 @@ def run_gs_only(args):
     ctx.close()
 
 
+def run_resp_only(args):
+    """Profiling mode: args.resp_only response applies w = v - P R v
+    (rte_response_apply) on the workload's context, on the tensor-core node path
+    and on the per-cell FP32 path; prints each one's mean time per R z launch
+    (CUDA events on the context's stream) and its rate."""
+    import torch
+    from paper_2604_23265_gb300 import rte
+    torch.cuda.set_device(0)
+    md = W.grf_diffusive(seed=0, I=args.size, M=args.dirs)
+    ctx = rte.Context.from_medium(md)
+    v = torch.tensor(W.random_vector(ctx.n, 1), device="cuda")
+    w = torch.empty(ctx.n, dtype=torch.float64, device="cuda")
+    out = {"mode": "resp_only", "I": md.I, "M": md.M, "n": ctx.n, "applies": args.resp_only,
+           "tabulated_nodes": ctx.tabulated_nodes()}
+    for path, name in ((rte.Context.RESPONSE_AUTO, "auto"), (rte.Context.RESPONSE_PER_CELL, "per_cell")):
+        ctx.set_response_path(path)
+        out[name + "_on_tensor_cores"] = ctx.response_on_tensor_cores()
+        ctx.response_apply(v, w)                         # warm-up
+        ctx.profile(True)
+        for _ in range(args.resp_only):
+            ctx.response_apply(v, w)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        k = "response_tc" if out[name + "_on_tensor_cores"] else "response_apply"
+        l, ms, byts, flops = prof[k]
+        out[name] = {"kernel": k, "ms_per_launch": ms / max(l, 1),
+                     "GBps": byts / (ms / 1e3) / 1e9 if ms > 0 else None,
+                     "TFLOPs": flops / (ms / 1e3) / 1e12 if ms > 0 and flops else None,
+                     "gather_ms_per_launch": prof["gather"][1] / max(prof["gather"][0], 1)}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     from paper_2604_23265_gb300 import rte, train
@@ -459,7 +493,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded GRF medium per rank)",
         "config": dict(WORKLOAD, parallelism=f"replicas{world}", preconditioner=pc_name,
-                       inner="FP32 response matrices, df64 Krylov basis, FP64 residual"),
+                       inner=("R z from tabulated nodes on tcgen05 (BF16 x 6 products, FP32 accuracy), df64 Krylov basis, "
+                              "FP64 residual")),
         "iterations": iters, "relres": infos[-1]["relres"], "converged": converged,
         "fell_back": bool(infos[-1]["fell_back"]),
         "gpu_launches": launches,
@@ -984,6 +1019,8 @@ def main():
     ap.add_argument("--gs-only", type=int, default=0,
                     help="profiling only: Gram-Schmidt steps against this many basis vectors")
     ap.add_argument("--gs-steps", type=int, default=5, help="profiling only: steps of --gs-only")
+    ap.add_argument("--resp-only", type=int, default=0,
+                    help="profiling only: time this many response applies (tensor-core and per-cell paths)")
     ap.add_argument("--setup-only", type=int, default=0,
                     help="profiling only: time the context set-up this many times and exit")
     ap.add_argument("--levels", type=int, default=0,
@@ -1018,6 +1055,8 @@ def main():
         run_reference(args)
     elif args.precond_only > 0:
         run_precond_only(args)
+    elif args.resp_only > 0:
+        run_resp_only(args)
     elif args.gs_only > 0:
         run_gs_only(args)
     elif args.setup_only > 0:

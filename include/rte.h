@@ -142,6 +142,31 @@ RTE_API rte_status rte_setup_ex(const rte_grid* grid, const rte_quadrature* quad
  * every block was inverted cell by cell). */
 RTE_API rte_status rte_block_setup_info(const rte_ctx* ctx, int* tabulated_nodes);
 
+/* ---------------------------------------------------------------------------
+ * rte_set_response_path -- how the inner operator B = A D = I - P R (Sec. 4,
+ * block-Jacobi right preconditioning in face-flux space) applies the response
+ * matrices R_C (no counterpart in the paper: an implementation choice):
+ *   RTE_RESPONSE_AUTO (default): on the tensor cores from the node tables when
+ *     the blocks are tabulated and 2M is 32, 64 or 128.  With R_C =
+ *     sum_p w_Cp R_p over the cell's eight stencil nodes, o_C = sum_q w_Cq
+ *     (R_q z_C) is a dense contraction per tile of cells sharing nodes; the
+ *     operands are split into three BF16 parts each (six products, FP32
+ *     accumulation), so the result keeps FP32 accuracy.  Otherwise per cell;
+ *   RTE_RESPONSE_PER_CELL: every o_C = R_C z_C from the per-cell FP32 R_C
+ *     (streamed from device memory, FP32 arithmetic).
+ * Applies to rte_response_apply, rte_solve, rte_solve_group and the
+ * network's training loss.  EINVAL for another value.
+ * rte_response_on_tensor_cores returns 1 when the context's response apply
+ * runs on the tensor cores, 0 when per cell, -1 for a NULL context.
+ * ------------------------------------------------------------------------- */
+typedef enum rte_response_path {
+    RTE_RESPONSE_AUTO = 0,
+    RTE_RESPONSE_PER_CELL = 1
+} rte_response_path;
+
+RTE_API rte_status rte_set_response_path(rte_ctx* ctx, int path);
+RTE_API int rte_response_on_tensor_cores(const rte_ctx* ctx);
+
 RTE_API void rte_destroy(rte_ctx* ctx);
 
 /* Message of the last error of ctx (or of the calling thread if ctx is NULL). */
@@ -209,7 +234,8 @@ RTE_API rte_status rte_export_blocks(rte_ctx* ctx, double* D_host, float* R_host
  * rte_response_apply -- w = A D v for v in the row space (face-flux space):
  * every cell's own rows give v back (G_C D_C = I) and each row loses the
  * neighbour's outgoing value, w = v - P R v, with R the FP32 response
- * matrices (products in FP32, v and w double [n]).  This is the operator the
+ * matrices (FP32 accuracy: per cell, or on the tensor cores from the node
+ * tables, rte_set_response_path; v and w double [n]).  This is the operator the
  * Krylov iteration of rte_solve works on (block-Jacobi right
  * preconditioning, Sec. 4).  v and w must not overlap.  Asynchronous.
  * ------------------------------------------------------------------------- */

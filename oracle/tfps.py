@@ -353,6 +353,47 @@ class Problem:
         """D_C = G_C^{-1} for every cell (block Jacobi, Sec. 4; D of Eq. loss)."""
         return np.linalg.inv(self.blocks())
 
+    def blocks_at(self, cells):
+        """G_C of the given cells only, (len(cells), 2M, 2M): ``blocks`` restricted,
+        for media too large to hold every block."""
+        M, M2 = self.M, self.M // 2
+        cells = np.asarray(cells, dtype=np.int64)
+        G = np.zeros((len(cells), 2 * M, 2 * M))
+        for f in range(4):
+            dirs = self.dirs[f]
+            for i, c in enumerate(cells):
+                Lc = self.L[self.mat_id[c]]
+                G[i, f * M2:(f + 1) * M2, :] = Lc[dirs, :] * self.dec[:, f, c][None, :]
+        return G
+
+    def block_jacobi_rows(self, v, cells):
+        """Rows of the given cells of A D v (Sec. 4: block-Jacobi right
+        preconditioning; Eq. 2DTFPS_continuity_cond / boundary_cond rows), with
+        D_C = G_C^{-1} formed only for those cells and their neighbours.
+        v : (2M, N).  Returns (2M, len(cells))."""
+        M2 = self.M // 2
+        cells = np.asarray(cells, dtype=np.int64)
+        nbs = [self.neighbour(f)[cells] for f in range(4)]
+        need = np.unique(np.concatenate([cells] + [nb[nb >= 0] for nb in nbs]))
+        G = self.blocks_at(need)
+        alpha = np.linalg.solve(G, v[:, need].T[:, :, None])[:, :, 0].T      # (2M, |need|)
+        where = {int(c): i for i, c in enumerate(need)}
+
+        def trace(f, c):
+            a = alpha[:, where[int(c)]] * self.dec[:, f, c]
+            return self.L[self.mat_id[c]] @ a
+
+        y = np.zeros((2 * self.M, len(cells)))
+        for f in range(4):
+            dirs = self.dirs[f]
+            for i, c in enumerate(cells):
+                row = trace(f, c)[dirs]
+                nb = nbs[f][i]
+                if nb >= 0:
+                    row = row - trace(OPP[f], nb)[dirs]
+                y[f * M2:(f + 1) * M2, i] = row
+        return y
+
     def reconstruct(self, alpha):
         """Angular flux at cell centres, psi[m, c] (Eq. 2DTFPS_sol at the cell centre)."""
         a = np.abs(self.xi[self.mat_id])            # (N, 2M)

@@ -523,6 +523,7 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
             k_response<double><<<J, threads, smem2, st>>>(M, nmat, ntau, ctx->xi, ctx->L64, ctx->rowdir, Dn, Rn);
             check(cudaGetLastError(), "k_response (nodes)");
         }
+        build_response_tc(ctx, plan, Rn);
         {
             ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * E * 12);
             const dim3 grid((unsigned)plan.bins.size(), (unsigned)((E / 4 + 255) / 256));
@@ -607,27 +608,16 @@ void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scra
 }
 
 namespace {
-template <int GroupItem::*START>
-__device__ int group_item_ba(const GroupItem* items, int count) {
-    __shared__ int s_item;
-    if (threadIdx.x == 0) {
-        int i = 0;
-        while (i + 1 < count && items[i + 1].*START <= (int)blockIdx.x) ++i;
-        s_item = i;
-    }
-    __syncthreads();
-    return s_item;
-}
 
 __global__ void __launch_bounds__(256) k_block_apply_group(const GroupItem* __restrict__ items, int count) {
     extern __shared__ __align__(16) unsigned char smb[];
-    const GroupItem& it = items[group_item_ba<&GroupItem::b_ba>(items, count)];
+    const GroupItem& it = items[group_item_of<&GroupItem::b_ba>(items, count)];
     const int bid = blockIdx.x - it.b_ba;
     block_apply_run<float, float, float>(it.M, it.N, it.Rt, it.z, it.o, bid, smb);
 }
 
 __global__ void k_gather_group(const GroupItem* __restrict__ items, int count) {
-    const GroupItem& it = items[group_item_ba<&GroupItem::b_ga>(items, count)];
+    const GroupItem& it = items[group_item_of<&GroupItem::b_ga>(items, count)];
     const int bid = blockIdx.x - it.b_ga;
     gather_df_run(it.I, it.M, it.z, it.z_lo, it.o, it.w, bid, it.n_ga);
 }
@@ -651,9 +641,11 @@ void group_response_geometry(rte_ctx* ctx, int* n_ba, int* n_ga, size_t* smem_ba
 
 void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba, int blocks_ga, size_t smem_ba,
                            cudaStream_t st) {
-    raise_smem_limit((const void*)k_block_apply_group, (size_t)(smem_ba));
-    k_block_apply_group<<<blocks_ba, 256, smem_ba, st>>>(items_dev, count);
-    k_gather_group<<<blocks_ga, 256, 0, st>>>(items_dev, count);
+    if (blocks_ba > 0) {
+        raise_smem_limit((const void*)k_block_apply_group, (size_t)(smem_ba));
+        k_block_apply_group<<<blocks_ba, 256, smem_ba, st>>>(items_dev, count);
+    }
+    if (blocks_ga > 0) k_gather_group<<<blocks_ga, 256, 0, st>>>(items_dev, count);
     check(cudaGetLastError(), "grouped response apply");
 }
 
@@ -662,6 +654,11 @@ void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* 
     const int M = ctx->M, n2 = 2 * M;
     float* o = reinterpret_cast<float*>(ctx->trace_out);
     const double bytes = (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * ((v_is_double ? 8 : 4) + 4);
+    if (response_tc_active(ctx)) {
+        launch_response_tc(ctx, v, v_is_double);
+        launch_gather_tiles(ctx, v, v_is_double, w, w_is_double);
+        return;
+    }
     if (v_is_double)
         block_apply_t<float, double, float>(ctx, ctx->Rt, v, o, K_RESPONSE_APPLY, bytes);
     else
@@ -688,6 +685,11 @@ void launch_response_apply_df(rte_ctx* ctx, const float* z_hi, const float* z_lo
     const int M = ctx->M, n2 = 2 * M;
     float* o = reinterpret_cast<float*>(ctx->trace_out);
     const double bytes = (double)ctx->N * n2 * n2 * 4 + (double)ctx->n * 8;
+    if (response_tc_active(ctx)) {
+        launch_response_tc(ctx, z_hi, false);
+        launch_gather_tiles_df(ctx, z_hi, z_lo, w);
+        return;
+    }
     block_apply_t<float, float, float>(ctx, ctx->Rt, z_hi, o, K_RESPONSE_APPLY, bytes);
     int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
     const int g = (int)(want < cap ? want : cap);

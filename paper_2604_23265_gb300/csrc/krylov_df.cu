@@ -38,6 +38,7 @@
 
 #include <mutex>
 
+#include "async_ptx.h"
 #include "df64.h"
 #include "rte_internal.h"
 
@@ -55,49 +56,10 @@ constexpr int kOwnB = kMaxKrylov / kCons;     // rows a consumer warp owns in ph
 constexpr int kMaxStages = 8;
 constexpr int kRowBytes = kE * 8;             // one staged row: hi then lo, 128 floats each
 constexpr int kStageBudget = 102 * 1024;      // shared memory the stages of a block aim at
-constexpr long long kSpin = 1LL << 24;
 
 enum Mode { kDot = 0, kUpdateDot = 1, kUpdateNorm = 2 };
 
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (long long i = 0; i < kSpin; ++i) {
-        unsigned done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(saddr(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// TMA tiled load of a 2-D box (x = element, y = row) into shared memory
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(saddr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_n(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
-}
+using namespace ::rte::ptx;
 
 // barrier 1 among the consumer warps only
 __device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsThr) : "memory"); }
@@ -173,8 +135,8 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init_n(&full[s], 1);
-            mbar_init_n(&empty[s], kCons);
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCons);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_consumed = 0;

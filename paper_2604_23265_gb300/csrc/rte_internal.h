@@ -24,7 +24,7 @@ struct Atfps;                       // ATFPS loss filter of a context (atfps.cu)
 enum KernelId {
     K_TRACES, K_COMBINE, K_ADJOINT, K_RECONSTRUCT, K_RHS, K_INVERT, K_BLOCK, K_BLOCK_T,
     K_MDOT, K_UPDATE_DOT, K_UPDATE_NORM, K_NORM, K_SCALE, K_XUPDATE, K_GIVENS, K_BACKSUB,
-    K_CYCLE, K_F2D, K_MGNET, K_RESPONSE, K_RESPONSE_APPLY, K_GATHER, K_COUNT
+    K_CYCLE, K_F2D, K_MGNET, K_RESPONSE, K_RESPONSE_APPLY, K_GATHER, K_RESPONSE_TC, K_TILE_ORDER, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -38,7 +38,8 @@ struct Profiler {
     std::vector<Pending> pending;
     double ms[K_COUNT] = {};
     double bytes[K_COUNT] = {};
-    double flops[K_COUNT] = {};          // FP64 flops of the kernels bound by FP64 arithmetic
+    double flops[K_COUNT] = {};          // FP64 flops of the FP64-bound kernels; FP32 for the network;
+                                         // issued BF16 tensor flops for response_tc
     long long launches[K_COUNT] = {};
 };
 
@@ -85,6 +86,16 @@ struct rte_ctx {
     size_t device_bytes = 0;
     int block_mode = 0;              // RTE_BLOCKS_AUTO / EXACT / TABULATED requested at set-up
     int tab_nodes = 0;               // nodes of the tabulated set-up (0: per-cell inversion)
+    // response apply on the tensor cores from the node tables (response_tc.cu)
+    uint16_t* tc_nodes = nullptr;    // BF16 parts of the nodes' R, staged layout
+    int4* tc_tiles = nullptr;        // (first position, cells, first node, nodes)
+    int* tc_pos_of = nullptr;        // [N] position of each cell in the list ordered by stencil
+    int* tc_first = nullptr;         // [N] first stencil node per position
+    float* tc_w16 = nullptr;         // [N][16] Lagrange weights per position, 8 hi then 8 lo floats
+    int tc_ntiles = 0;               // 0: no node tables
+    double tc_mma_flops = 0.0;       // issued tensor flops per apply
+    double tc_bytes = 0.0;           // algorithmic bytes per apply
+    int response_path = 0;           // RTE_RESPONSE_AUTO / RTE_RESPONSE_PER_CELL
     rte::Workspace* ws = nullptr;
     rte::Atfps* atfps = nullptr;
     rte::Profiler prof;
@@ -178,9 +189,27 @@ struct GroupItem {
     double* g;
     double* est;             // the instance's own status (est, ||w||)
     double* est_out;         // and a copy in the group's array
+    // tensor-core response (o in tile order, null: per cell)
+    const int* pos_of;
     // block ranges: [b_x, b_x + n_x) of the grouped launch of kernel x
-    int b_ba, n_ba, b_ga, n_ga, b_md, n_md, b_ud, n_ud, b_rd, n_rd, b_sc, n_sc;
+    int b_ba, n_ba, b_ga, n_ga, b_gt, n_gt, b_md, n_md, b_ud, n_ud, b_rd, n_rd, b_sc, n_sc;
 };
+
+// the item of a grouped launch that block blockIdx.x belongs to: the last
+// item whose first block (field START) is at most blockIdx.x
+template <int GroupItem::*START>
+__device__ inline int group_item_of(const GroupItem* items, int count) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int i = 0;
+        while (i + 1 < count && items[i + 1].*START <= (int)blockIdx.x) ++i;
+        s_item = i;
+    }
+    __syncthreads();
+    return s_item;
+}
+// the tile-ordered gathers of the items on the tensor-core path (one launch)
+void launch_group_gather_tiles(const GroupItem* items_dev, int count, int blocks, cudaStream_t st);
 // w = z - P R z for every item (two grouped launches)
 void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba, int blocks_ga,
                            size_t smem_ba, cudaStream_t st);
@@ -256,6 +285,25 @@ struct TabPlan {
 };
 void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_dev);
 
+// response apply from the node tables on the tensor cores (response_tc.cu)
+bool response_tc_supported(int M);                     // 2M in {32, 64, 128}
+// node tables (BF16 parts of the nodes' R, FP64 Rn[J][j][i]), tiles, weights
+void build_response_tc(rte_ctx* ctx, const TabPlan& plan, const double* Rn);
+bool response_tc_active(const rte_ctx* ctx);
+// o = R z (z float or double, direction-major) into response_tc_output(ctx):
+// FP32 rows in the order of the cell list, [N][2M]; on ctx's stream
+void launch_response_tc(rte_ctx* ctx, const void* z, bool z_is_double);
+// the same on stream st, not profiled (grouped solves)
+void launch_response_tc_on(rte_ctx* ctx, const void* z, bool z_is_double, cudaStream_t st);
+float* response_tc_output(rte_ctx* ctx);
+// w = v - P o with o = response_tc_output(ctx): df64 w as launch_response_apply_df,
+// or float/double w as launch_response_apply
+void launch_gather_tiles_df(rte_ctx* ctx, const float* vh, const float* vl, float* w);
+void launch_gather_tiles(rte_ctx* ctx, const void* v, bool v_is_double, void* w, bool w_is_double);
+int tile_gather_blocks(const rte_ctx* ctx);            // blocks of one tile-ordered gather
+// 1 if a bounded wait of the tensor-core response apply ran out (reset clears), -1 on error
+int response_tc_timeout_flag(bool reset);
+
 // z = D r (or D^T r), FP64 accumulation; float or double in and out
 void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_double, void* z,
                         bool z_is_double);
@@ -297,6 +345,14 @@ void launch_lincomb_df(rte_ctx* ctx, const float* V, int K, const double* y, dou
 void launch_response_apply_df(rte_ctx* ctx, const float* z_hi, const float* z_lo, float* w);
 // 1 if a bounded wait of a df64 Gram-Schmidt pass ran out (reset clears), -1 on error
 int krylov_timeout_flag(bool reset);
+// reads and clears the device flags of the bounded waits (Gram-Schmidt passes,
+// tensor-core response apply): the message of the first that ran out, or null
+inline const char* device_wait_expired() {
+    const int a = krylov_timeout_flag(true), b = response_tc_timeout_flag(true);
+    if (a == 1) return "a bounded wait of a Gram-Schmidt pass ran out";
+    if (b == 1) return "a bounded wait of the tensor-core response apply ran out";
+    return nullptr;
+}
 // y = x * (1 / s[0]) unless s[0] == 0 (then y = x)
 void launch_scale(rte_ctx* ctx, const double* x, const double* s, double* y);
 // x += sum_k Z[k] y[k]  (Z float, k vectors)

@@ -59,7 +59,7 @@ const char* const kKernelNames[K_COUNT] = {
     "traces", "combine", "adjoint", "reconstruct", "rhs", "build_invert", "block_apply",
     "block_apply_t", "mdot", "update_dot", "update_norm", "norm", "scale", "x_update",
     "givens", "backsub", "cycle_start", "f2d", "mgnet", "response_build", "response_apply",
-    "gather"};
+    "gather", "response_tc", "tile_order"};
 
 static cudaEvent_t prof_event(rte_ctx* ctx) {
     if (!ctx->prof.pool.empty()) {
@@ -665,6 +665,21 @@ RTE_API rte_status rte_block_setup_info(const rte_ctx* ctx, int* tabulated_nodes
     return RTE_OK;
 }
 
+RTE_API rte_status rte_set_response_path(rte_ctx* ctx, int path) {
+    if (!ctx) { set_error(nullptr, "NULL context"); return RTE_EINVAL; }
+    if (path != RTE_RESPONSE_AUTO && path != RTE_RESPONSE_PER_CELL) {
+        set_error(ctx, "unknown response path");
+        return RTE_EINVAL;
+    }
+    ctx->response_path = path;
+    return RTE_OK;
+}
+
+RTE_API int rte_response_on_tensor_cores(const rte_ctx* ctx) {
+    if (!ctx) return -1;
+    return response_tc_active(ctx) ? 1 : 0;
+}
+
 RTE_API rte_status rte_info(const rte_ctx* ctx, rte_ctx_info* info) {
     if (!ctx || !info) { set_error(nullptr, "NULL argument"); return RTE_EINVAL; }
     info->I = ctx->I;
@@ -798,7 +813,7 @@ RTE_API rte_status rte_cgs2_df64(rte_ctx* ctx, const float* V_dev, int k, float*
     double* h2 = ctx->scal + kMaxKrylov;    // [64] second projection
     launch_orthogonalise_df(ctx, V_dev, k, w_dev, h1, h2, h_dev);
     launch_scale_df(ctx, w_dev, h_dev + k, w_dev);
-    if (krylov_timeout_flag(true) == 1) throw StatusError{RTE_ETIMEOUT, "a bounded wait of a Gram-Schmidt pass ran out"};
+    if (const char* why = device_wait_expired()) throw StatusError{RTE_ETIMEOUT, why};
     return RTE_OK;
     RTE_GUARD_END(ctx)
 }

@@ -462,7 +462,7 @@ struct GroupRunner {
             }
             mgnet_precondition_batch_f(s.pc, cs.data(), vs.data(), zs.data(), (int)same.size());
         }
-        int ba = 0, ga = 0, md = 0, ud = 0, rd = 0, sc = 0, kmax = 1;
+        int ba = 0, ga = 0, gt = 0, md = 0, ud = 0, rd = 0, sc = 0, kmax = 1;
         size_t smem_ba = 0;
         bool f32 = true;
         for (size_t q = 0; q < live.size(); ++q) {
@@ -472,13 +472,20 @@ struct GroupRunner {
             const int K = s.j + 1;
             int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0, nsc = 0;
             size_t sm = 0;
+            int ngt = 0;
             group_response_geometry(c, &nba, &nga, &sm);
+            const bool tc = response_tc_active(c);
+            if (tc) {                      // R z on the tensor cores (launched per item), tile-ordered gather
+                nba = nga = 0;
+                ngt = tile_gather_blocks(c);
+            }
             group_ortho_geometry_df(c, K, &nmd, &nud, &nrd, &nsc);
             f32 = f32 && s.opts.inner_precision == RTE_F32;
             it.Rt = c->Rt;
             it.z = s.zj;
             it.z_lo = s.zj_lo;
             it.o = reinterpret_cast<float*>(c->trace_out);
+            it.pos_of = tc ? c->tc_pos_of : nullptr;
             it.I = c->I;
             it.M = c->M;
             it.N = c->N;
@@ -502,6 +509,7 @@ struct GroupRunner {
             it.est_out = est_d + 2 * q;
             it.b_ba = ba; it.n_ba = nba; ba += nba;
             it.b_ga = ga; it.n_ga = nga; ga += nga;
+            it.b_gt = gt; it.n_gt = ngt; gt += ngt;
             it.b_md = md; it.n_md = nmd; md += nmd;
             it.b_ud = ud; it.n_ud = nud; ud += nud;
             it.b_rd = rd; it.n_rd = nrd; rd += nrd;
@@ -514,7 +522,10 @@ struct GroupRunner {
         encode_group_gs_maps(items_h, nl, maps_h);
         check(cudaMemcpyAsync(maps_d, maps_h, nl * group_gs_maps_bytes(), cudaMemcpyHostToDevice, st), "h2d maps");
         if (f32) {
+            for (int q = 0; q < nl; ++q)
+                if (items_h[q].pos_of) launch_response_tc_on(live[q]->ctx, items_h[q].z, false, st);
             launch_group_response(items_d, nl, ba, ga, smem_ba, st);
+            launch_group_gather_tiles(items_d, nl, gt, st);
         } else {
             for (Solver* s : live) s->inner_apply();
         }
@@ -613,8 +624,8 @@ rte_status run_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, dou
                 S.cycle_end();
             }
         }
-        if (krylov_timeout_flag(true) == 1) {
-            set_error(ctx, "a bounded wait of a Gram-Schmidt pass ran out");
+        if (const char* why = device_wait_expired()) {
+            set_error(ctx, why);
             S.status = RTE_ETIMEOUT;
         }
         if (comp && layers && (S.status == RTE_OK || S.status == RTE_ENOTCONV)) {
@@ -694,7 +705,7 @@ RTE_API rte_status rte_arnoldi_basis_df64(rte_ctx* ctx, int k, float* V_dev) {
             launch_scale_df(ctx, ws->w, ws->hcol + j + 1, V_dev + (size_t)2 * (j + 1) * n);
         }
         check(cudaStreamSynchronize(ctx->stream), "sync");
-        if (krylov_timeout_flag(true) == 1) throw StatusError{RTE_ETIMEOUT, "a bounded wait of a Gram-Schmidt pass ran out"};
+        if (const char* why = device_wait_expired()) throw StatusError{RTE_ETIMEOUT, why};
     } catch (const CudaError& e) {
         return cuda_status(ctx, e.code, e.where);
     } catch (const StatusError& e) {
@@ -757,9 +768,9 @@ RTE_API rte_status rte_solve_group(rte_ctx* const* ctxs, mgnet* const* pcs, int 
             if (!any) break;
             runner.round(set);
         }
-        if (krylov_timeout_flag(true) == 1) {
+        if (const char* why = device_wait_expired()) {
             fatal = RTE_ETIMEOUT;
-            fatal_msg = "a bounded wait of a Gram-Schmidt pass ran out";
+            fatal_msg = why;
         }
     } catch (const CudaError& e) {
         fatal = cuda_status(nullptr, e.code, e.where);

@@ -77,6 +77,8 @@ SIGNATURES = {
     "rte_setup_ex": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(Quadrature), _P, _P, _P, _P, _I, _D, _P,
                           _P, _I, ctypes.POINTER(_P)]),
     "rte_block_setup_info": (_I, [_P, ctypes.POINTER(_I)]),
+    "rte_set_response_path": (_I, [_P, _I]),
+    "rte_response_on_tensor_cores": (_I, [_P]),
     "rte_destroy": (None, [_P]),
     "rte_last_error": (ctypes.c_char_p, [_P]),
     "rte_info": (_I, [_P, ctypes.POINTER(CtxInfo)]),
@@ -476,6 +478,7 @@ class Context:
     """One RTE system (rte_setup); see include/rte.h for the layouts."""
 
     BLOCKS_AUTO, BLOCKS_EXACT, BLOCKS_TABULATED = 0, 1, 2
+    RESPONSE_AUTO, RESPONSE_PER_CELL = 0, 1
 
     def __init__(self, I, M, sigma_T, sigma_a, q, eps, g, inflow=None, stream=None, block_mode=0):
         lib = load()
@@ -509,6 +512,17 @@ class Context:
         v = ctypes.c_int()
         _check(load().rte_block_setup_info(self.ptr, ctypes.byref(v)), self.ptr)
         return v.value
+
+    def set_response_path(self, path):
+        """How the inner operator applies R (rte_set_response_path; Context.RESPONSE_*)."""
+        _check(load().rte_set_response_path(self.ptr, int(path)), self.ptr)
+
+    def response_on_tensor_cores(self):
+        """True when R z runs on the tensor cores from the node tables."""
+        v = load().rte_response_on_tensor_cores(self.ptr)
+        if v < 0:
+            raise RuntimeError("rte_response_on_tensor_cores: bad context")
+        return bool(v)
 
     def close(self):
         """Free the context (rte_destroy)."""

@@ -207,6 +207,29 @@ def test_P8_blocks_are_diagonal_blocks():
         np.testing.assert_array_equal(A[np.ix_(idx, idx)], G[c])
 
 
+def test_block_jacobi_rows_match_assembled_operator():
+    """The restricted A D v of ``block_jacobi_rows`` (blocks of the sampled
+    cells and their neighbours only) equals A D v from the assembled sparse A,
+    with D the inverses of A's own diagonal blocks, at every sampled cell
+    (interior, edge and corner cells; three materials)."""
+    I, M = 7, 8
+    rng = np.random.default_rng(3)
+    sT = rng.uniform(0.5, 4, I * I)
+    sa = np.choose(rng.integers(0, 3, I * I), [0.1 * sT, 0.3 * sT, 0.05 * sT])
+    p = tfps.Problem(I, M, sT, sa, np.ones(I * I), 0.3, 0.5)
+    A = p.assemble().toarray()
+    N, n2 = p.N, 2 * M
+    v = W.random_vector(n2 * N, 21).reshape(n2, N)
+    alpha = np.zeros_like(v)
+    for c in range(N):
+        idx = np.arange(n2) * N + c
+        alpha[:, c] = np.linalg.solve(A[np.ix_(idx, idx)], v[:, c])
+    ref = (A @ alpha.ravel()).reshape(n2, N)
+    cells = np.array([0, 3, I - 1, I, 24, N - I, N - 1, 17])
+    np.testing.assert_allclose(p.block_jacobi_rows(v, cells), ref[:, cells], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(p.blocks_at(cells), p.blocks()[cells])
+
+
 def test_P9_AD_invariant_to_eigenvector_signs():
     """P9: A D does not depend on the sign of any basis vector."""
     I, M = 6, 8
