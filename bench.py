@@ -195,8 +195,13 @@ def cpu_baseline(md, gpu_iters):
 # (dram__bytes_read.sum + dram__bytes_write.sum); the bench scales it by the
 # algorithmic bytes of its own average launch.  The df64 Gram-Schmidt passes
 # read each basis row once (the second pass re-reads it from shared memory).
-TRAFFIC_RATIO = {"response_apply": 0.9995}
-TRAFFIC_SOURCE = {"response_apply": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)"}
+TRAFFIC_RATIO = {"response_apply": 0.9995, "mdot": 1.001, "update_dot": 1.000, "update_norm": 0.999,
+                 "response_tc": 0.793}
+TRAFFIC_SOURCE = {"response_apply": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)",
+                  "mdot": "ncu DRAM bytes per launch at 256x256, M=64, K=50 basis vectors",
+                  "update_dot": "ncu DRAM bytes per launch at 256x256, M=64, K=50 basis vectors",
+                  "update_norm": "ncu DRAM bytes per launch at 256x256, M=64, K=50 basis vectors",
+                  "response_tc": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)"}
 
 # Nominal FP64 rate of a GB300 (152 SMs x 2.07 GHz x 2 FP64 FMA per clock x 2
 # flops): the roof of the FP64 operator apply, the one FP64-bound kernel left.
@@ -253,6 +258,8 @@ def _roofline(rte, stream, prof):
             e["hbm_frac"] = round(e["GBps"] / hbm_peak, 3)
         if k in FP64_BOUND and e["TFLOPs"]:
             e["fp64_frac"] = round(e["TFLOPs"] / FP64_NOMINAL_TFLOPS, 3)
+        if k in ("response_tc", "mgnet") and e["TFLOPs"]:
+            e["tensor_frac"] = round(e["TFLOPs"] / _bf16_peak()[0], 3)
         kernels[k] = e
     return roof, kernels
 
