@@ -12,25 +12,28 @@
 // producer loads a chunk's rows into a shared-memory stage with two TMA
 // tensor copies (one box of the 2K basis rows, hi and lo planes, one of w),
 // completing on the stage's "full" mbarrier, up to NS stages ahead, and
-// reuses a stage once all consumer warps arrived on its "empty" mbarrier.
-// A box past n is zero-filled by the copy.  On a staged chunk:
-//   phase A (passes 2, 3): warp (q, h) sums h_k V_k over its rows k = q,
-//     q + 4, ... for the element pair 64 h + 2 lane; the four row classes'
-//     sums are added per element by the first four warps (consumer barrier)
-//     and w_t <- w_t - sum_k h_k V_kt (df64); the new w goes to HBM and back
-//     into the stage (consumer barrier);
-//   phase B (passes 1, 2): warp q owns the rows k = q, q + 8, ...; lane l
-//     accumulates V_ke w_e over its elements e = 2l, 2l + 1, 2l + 64, 2l + 65
-//     into one df64 sum per owned row, kept in registers for the whole pass.
+// reuses a stage once the warps that consumed it arrived on its "empty"
+// mbarrier.  A box past n is zero-filled by the copy.  The consumers form two
+// groups of four warps that take alternate chunks, so a group's barriers
+// never wait for the other group and two chunks are in work at once.  On a
+// staged chunk, in group g:
+//   phase A (passes 2, 3): warp w owns the element pairs 16 w .. 16 w + 15;
+//     its two half warps sum h_k V_k over the even and the odd rows (two
+//     chains each), a shuffle adds the halves, and w_t <- w_t - sum_k h_k V_kt
+//     (df64) goes to HBM and back into the stage (pass 2: group barrier);
+//   phase B (passes 1, 2): half warp h of warp w owns the rows k = w + 4 h,
+//     w + 4 h + 8, ...; lane l accumulates V_ke w_e over its elements
+//     e = 2 l + 32 t, 2 l + 32 t + 1 (t < 4) into one df64 sum per owned row,
+//     kept in registers for the whole pass.
 // Lanes work on element pairs with the packed .f32x2 instructions and rows
 // past K read a zero row.  So the re-read of V that the update and the
 // projection of pass 2 need comes from shared memory, not from HBM.  Each
-// block reduces its sums in FP64 in a fixed order and the last block (atomic
-// ticket) adds the block partials in block order: the result depends only on
-// (K, n), never on scheduling.
+// block adds its two groups' sums in FP64 in a fixed order and the last block
+// (atomic ticket) adds the block partials in block order: the result depends
+// only on (K, n), never on scheduling.
 //
 // Waits are bounded: a wait that does not complete in 2^24 polls ends the
-// block's loop (the consumers agree on it through a barrier reduction), sets
+// group's loop (its warps agree on it through a barrier reduction), sets
 // g_krylov_timeout, waits (bounded) for the copies still in flight, and
 // writes NaN partial sums, so the step's Hessenberg column is NaN and the
 // solver treats the step as failed.
@@ -50,9 +53,12 @@ namespace {
 
 constexpr int kE = 128;                       // elements per chunk
 constexpr int kCons = 8;                      // consumer warps
-constexpr int kConsThr = kCons * 32;          // consumer threads (named barrier 1)
+constexpr int kConsThr = kCons * 32;          // consumer threads
 constexpr int kThr = kConsThr + 32;           // plus one producer warp
-constexpr int kOwnB = kMaxKrylov / kCons;     // rows a consumer warp owns in phase B (k = q mod 8)
+constexpr int kGroups = 2;                    // consumer groups: group g takes the chunks i = g mod 2
+constexpr int kGW = kCons / kGroups;          // warps of a group
+constexpr int kGroupThr = kGW * 32;
+constexpr int kOwnB = kMaxKrylov / (2 * kGW); // phase B rows of a half warp (k = w + 4 half mod 8)
 constexpr int kMaxStages = 8;
 constexpr int kRowBytes = kE * 8;             // one staged row: hi then lo, 128 floats each
 constexpr int kStageBudget = 102 * 1024;      // shared memory the stages of a block aim at
@@ -61,20 +67,36 @@ enum Mode { kDot = 0, kUpdateDot = 1, kUpdateNorm = 2 };
 
 using namespace ::rte::ptx;
 
-// barrier 1 among the consumer warps only
-__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsThr) : "memory"); }
+// named barrier 2 + g among the warps of consumer group g (immediate ids,
+// so the block reserves only the barriers it uses)
+__device__ __forceinline__ void group_sync(int g) {
+    if (g == 0)
+        asm volatile("bar.sync 2, %0;" ::"n"(kGroupThr) : "memory");
+    else
+        asm volatile("bar.sync 3, %0;" ::"n"(kGroupThr) : "memory");
+}
 
-// barrier 1 among the consumer warps, returning the AND of v over them
-__device__ __forceinline__ bool cons_all(bool v) {
+// the same barrier, returning the AND of v over the group
+__device__ __forceinline__ bool group_all(int g, bool v) {
     unsigned r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((unsigned)v), "n"(kConsThr)
-        : "memory");
+    if (g == 0)
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\t"
+            "setp.ne.u32 q, %1, 0;\n\t"
+            "bar.red.and.pred p, 2, %2, q;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(r)
+            : "r"((unsigned)v), "n"(kGroupThr)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\t"
+            "setp.ne.u32 q, %1, 0;\n\t"
+            "bar.red.and.pred p, 3, %2, q;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(r)
+            : "r"((unsigned)v), "n"(kGroupThr)
+            : "memory");
     return r != 0;
 }
 
@@ -84,11 +106,23 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// sum over the 16 lanes of each half warp (lane 0 and lane 16 hold the sums)
+__device__ __forceinline__ double half_warp_sum(double v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, 16);
+    return v;
+}
+
 // Pipeline depth of a block for K basis rows: as many stages as fit the
-// budget, 2..8.  Shared memory of the block: NS stages of (K + 1) rows.
+// budget, an even number in 2..8, so that every stage serves one consumer
+// group (chunk i: stage i mod NS, group i mod 2).  With an odd count a stage
+// would alternate between the groups, and a group could wait on a stage's
+// "full" barrier two phases ahead of the other group's use of it, which the
+// parity wait cannot tell from a completed phase.  Shared memory of the
+// block: NS stages of (K + 1) rows.
 __host__ __device__ __forceinline__ int gs_stages(int K) {
     const int stage = (K + 1) * kRowBytes;
-    int ns = kStageBudget / stage;
+    int ns = (kStageBudget / stage) & ~1;
     return ns < 2 ? 2 : (ns > kMaxStages ? kMaxStages : ns);
 }
 __host__ __device__ __forceinline__ size_t gs_smem(int K) {
@@ -121,8 +155,7 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
     using df::f2;
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     __shared__ float hh[kMaxKrylov + 8], hl[kMaxKrylov + 8];      // rows past K: h = 0
-    __shared__ __align__(16) float red_u[4][2][kE];               // phase A: partial sums per row class
-    __shared__ int s_consumed;
+    __shared__ int s_issued;
     __shared__ bool s_last;
     const int K = a.K, tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
     const bool producer = wq == kCons;
@@ -136,10 +169,10 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kCons);
+            mbar_init(&empty[s], kGW);
         }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_consumed = 0;
+        mbar_init_fence();
+        s_issued = 0;
     }
     for (int e = tid; e < 2 * kE; e += kThr) zero_row[e] = 0.f;
     for (int k = tid; k < kMaxKrylov + 8; k += kThr) {
@@ -151,20 +184,23 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
     __syncthreads();
 
     bool ok = true;
+    const int g = (wq / kGW) & 1, gw = wq % kGW;                  // consumer group, warp in the group
+    const int half = lane >> 4, l16 = lane & 15;
     f2 S2[kOwnB], C2[kOwnB];
 #pragma unroll
     for (int r = 0; r < kOwnB; ++r) S2[r] = C2[r] = 0ull;
     float nS = 0.f, nC = 0.f;
 
     if (producer) {
-        // chunk i into stage i % NS once the consumers released it: one TMA
-        // box for the basis rows and one for w
+        // chunk i into stage i % NS once its group released the stage: one
+        // TMA box for the basis rows and one for w
         if (lane == 0) {
             if (global_maps) {
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mv) : "memory");
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mw) : "memory");
             }
-            for (int i = 0; i < mine; ++i) {
+            int i = 0;
+            for (; i < mine; ++i) {
                 const int s = i % NS;
                 if (i >= NS && !mbar_wait(&empty[s], (unsigned)((i / NS) + 1) & 1u)) {
                     ok = false;
@@ -173,116 +209,106 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                 const int x = (int)((int64_t)(bid + (int64_t)i * nb) * kE);
                 unsigned char* st = smem + (size_t)s * stage_bytes;
                 mbar_expect(&full[s], (uint32_t)stage_bytes);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_proxy_async();
                 tma_load_2d(st, mv, x, 0, &full[s]);
                 tma_load_2d(st + K * kRowBytes, mw, x, 0, &full[s]);
             }
+            s_issued = i;
         }
         __syncwarp();
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     } else {
-        const int qa = wq & 3, ha = wq >> 2;                       // phase A: row class, element half
-        const int RA = (K + 3) / 4;                                // phase A rows per warp (padded)
-        const int RB = (K + kCons - 1) / kCons;                    // phase B rows per warp
-        int consumed = 0;
-        for (int i = 0; i < mine; ++i) {
+        const int RA = (K + 1) / 2;                                // phase A rows of a half warp (k = half mod 2)
+        const int RB = (K + 2 * kGW - 1) / (2 * kGW);              // phase B rows of a half warp
+        for (int i = g; i < mine; i += kGroups) {
             const int s = i % NS;
             const bool got = mbar_wait(&full[s], (unsigned)(i / NS) & 1u);
-            if (!cons_all(got)) {
+            if (!group_all(g, got)) {
                 ok = false;
                 break;
             }
-            consumed = i + 1;
             const int64_t base = (int64_t)(bid + (int64_t)i * nb) * kE;
             const int rem = (int)(n - base < kE ? n - base : kE);
             float* st = reinterpret_cast<float*>(smem + (size_t)s * stage_bytes);
             float* wrow = st + K * (kRowBytes / 4);
             auto row_of = [&](int k) -> const float* { return k < K ? st + k * 2 * kE : zero_row; };
             if (MODE != kDot) {
-                // phase A: warp (qa, ha) sums h_k V_k over the rows k = qa + 4 r
-                // for the pair e0 = 64 ha + 2 lane (two row parities: two chains)
-                const int e0 = 64 * ha + 2 * lane;
+                // phase A: warp gw owns the element pairs 16 gw + l16; half warp
+                // `half` sums h_k V_k over the rows k = half + 2 j in two chains,
+                // and the halves are added by a shuffle: no cross-warp sum
+                const int e0 = 32 * gw + 2 * l16;
                 f2 uS[2] = {0ull, 0ull}, uC[2] = {0ull, 0ull};
-                for (int r = 0; r < RA; r += 2) {
+                for (int j = 0; j < RA; j += 2) {
 #pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        const int k = qa + 4 * (r + p);
+                    for (int c = 0; c < 2; ++c) {
+                        const int k = half + 2 * (j + c);
                         const float* row = row_of(k);
                         const f2 bh = df::pk(hh[k], hh[k]);
                         const f2 nbh = df::pk(-hh[k], -hh[k]), nbl = df::pk(-hl[k], -hl[k]);
                         const f2 vh = *reinterpret_cast<const f2*>(row + e0);
                         const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
-                        df::mac2(uS[p], uC[p], vh, vl, nbh, nbl, bh);
+                        df::mac2(uS[c], uC[c], vh, vl, nbh, nbl, bh);
                     }
                 }
-                float s0x, s0y, c0x, c0y, s1x, s1y, c1x, c1y;
-                df::upk(uS[0], s0x, s0y);
-                df::upk(uC[0], c0x, c0y);
-                df::upk(uS[1], s1x, s1y);
-                df::upk(uC[1], c1x, c1y);
-                float sx, tx, sy, ty;
-                df::two_sum(s0x, s1x, sx, tx);
-                df::two_sum(s0y, s1y, sy, ty);
-                red_u[qa][0][e0] = sx;
-                red_u[qa][0][e0 + 1] = sy;
-                red_u[qa][1][e0] = __fadd_rn(tx, __fadd_rn(c0x, c1x));
-                red_u[qa][1][e0 + 1] = __fadd_rn(ty, __fadd_rn(c0y, c1y));
-                cons_sync();
-                // element tid: u = the four row classes' sums, w <- w - u
-                if (tid < kE) {
-                    float uh = red_u[0][0][tid], ul = red_u[0][1][tid];
+                f2 us, ut;
+                df::two_sum2(uS[0], uS[1], us, ut);
+                f2 uc = df::add2(ut, df::add2(uC[0], uC[1]));
+                const f2 os = __shfl_xor_sync(0xffffffffu, us, 16), oc = __shfl_xor_sync(0xffffffffu, uc, 16);
+                f2 u2, ut2;
+                df::two_sum2(us, os, u2, ut2);
+                uc = df::add2(ut2, df::add2(uc, oc));
+                df::renorm2(u2, uc);
+                if (half == 0) {
+                    // w <- w - u for the pair, into the stage and HBM
+                    float uh[2], ul[2], wh[2], wl[2];
+                    df::upk(u2, uh[0], uh[1]);
+                    df::upk(uc, ul[0], ul[1]);
 #pragma unroll
-                    for (int q = 1; q < 4; ++q) {
-                        float sh, t;
-                        df::two_sum(uh, red_u[q][0][tid], sh, t);
-                        ul = __fadd_rn(ul, __fadd_rn(t, red_u[q][1][tid]));
-                        uh = sh;
+                    for (int q = 0; q < 2; ++q) {
+                        df::sub(wrow[e0 + q], wrow[kE + e0 + q], uh[q], ul[q], wh[q], wl[q]);
+                        wrow[e0 + q] = wh[q];
+                        wrow[kE + e0 + q] = wl[q];
                     }
-                    df::renorm(uh, ul);
-                    float wh, wl;
-                    df::sub(wrow[tid], wrow[kE + tid], uh, ul, wh, wl);
-                    if (tid < rem) {
-                        wrow[tid] = wh;
-                        wrow[kE + tid] = wl;
-                        a.w[base + tid] = wh;
-                        a.w[n + base + tid] = wl;
+                    if (e0 < rem) {                          // rem is a multiple of 4
+                        *reinterpret_cast<float2*>(a.w + base + e0) = make_float2(wh[0], wh[1]);
+                        *reinterpret_cast<float2*>(a.w + n + base + e0) = make_float2(wl[0], wl[1]);
                         if (MODE == kUpdateNorm) {
-                            float p, e;
-                            df::mul(wh, wl, wh, wl, p, e);
-                            df::acc(nS, nC, p, e);
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                float p, e;
+                                df::mul(wh[q], wl[q], wh[q], wl[q], p, e);
+                                df::acc(nS, nC, p, e);
+                            }
                             df::renorm(nS, nC);
                         }
                     }
                 }
-                if (MODE == kUpdateDot) cons_sync();
+                if (MODE == kUpdateDot) group_sync(g);
             }
             if (MODE != kUpdateNorm) {
-                // phase B: warp wq owns the rows k = wq + 8 r, pairs e0 = 2 lane + 64 q
-                f2 wh2[2], wl2[2], nwh2[2], nwl2[2];
+                // phase B: half warp `half` of warp gw owns the rows
+                // k = gw + 4 half + 8 r; lane l16 the pairs l16 + 16 t
+                f2 wh2[4], wl2[4], nwh2[4], nwl2[4];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e0 = 2 * lane + 64 * q;
-                    wh2[q] = *reinterpret_cast<const f2*>(wrow + e0);
-                    wl2[q] = *reinterpret_cast<const f2*>(wrow + kE + e0);
-                    nwh2[q] = df::sub2(0ull, wh2[q]);
-                    nwl2[q] = df::sub2(0ull, wl2[q]);
+                for (int t = 0; t < 4; ++t) {
+                    const int e0 = 2 * (l16 + 16 * t);
+                    wh2[t] = *reinterpret_cast<const f2*>(wrow + e0);
+                    wl2[t] = *reinterpret_cast<const f2*>(wrow + kE + e0);
+                    nwh2[t] = df::sub2(0ull, wh2[t]);
+                    nwl2[t] = df::sub2(0ull, wl2[t]);
                 }
 #pragma unroll
-                for (int rg = 0; rg < kOwnB / 4; ++rg) {
-                    if (4 * rg < RB) {
+                for (int r = 0; r < kOwnB; ++r) {
+                    if (r < RB) {
+                        const float* row = row_of(gw + kGW * half + 2 * kGW * r);
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const int e0 = 2 * lane + 64 * q;
-#pragma unroll
-                            for (int rr = 0; rr < 4; ++rr) {
-                                const float* row = row_of(wq + kCons * (4 * rg + rr));
-                                const f2 vh = *reinterpret_cast<const f2*>(row + e0);
-                                const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
-                                df::mac2(S2[4 * rg + rr], C2[4 * rg + rr], vh, vl, nwh2[q], nwl2[q], wh2[q]);
-                            }
+                        for (int t = 0; t < 4; ++t) {
+                            const int e0 = 2 * (l16 + 16 * t);
+                            const f2 vh = *reinterpret_cast<const f2*>(row + e0);
+                            const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
+                            df::mac2(S2[r], C2[r], vh, vl, nwh2[t], nwl2[t], wh2[t]);
                         }
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr) df::renorm2(S2[4 * rg + rr], C2[4 * rg + rr]);
+                        df::renorm2(S2[r], C2[r]);
                     }
                 }
             }
@@ -290,15 +316,17 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
-        if (tid == 0) s_consumed = consumed;
     }
     __syncthreads();
     if (!__syncthreads_and(ok)) {
-        // copies still in flight: chunks consumed .. min(consumed + NS, mine) - 1
+        // wait (bounded) for the last copy issued into every stage
         if (tid == 0) {
             atomicExch(&g_krylov_timeout, 1);
-            const int c0 = s_consumed, last = c0 + NS < mine ? c0 + NS : mine;
-            for (int i = c0; i < last; ++i) mbar_wait(&full[i % NS], (unsigned)(i / NS) & 1u);
+            const int iss = s_issued;
+            for (int s = 0; s < NS && s < iss; ++s) {
+                const int last = s + ((iss - 1 - s) / NS) * NS;
+                mbar_wait(&full[s], (unsigned)(last / NS) & 1u);
+            }
         }
         ok = false;
     }
@@ -306,25 +334,23 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
 
     // block sums (FP64, fixed order) into the first stage, then the last
     // block adds the blocks
-    double* red = reinterpret_cast<double*>(smem);                 // [kCons][kMaxKrylov]
+    double* red = reinterpret_cast<double*>(smem);                 // [kGroups][kMaxKrylov]
     const double bad = ok ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
     if (MODE != kUpdateNorm) {
         if (!producer) {
 #pragma unroll
             for (int r = 0; r < kOwnB; ++r) {
-                const int k = wq + kCons * r;
-                if (k < K) {
-                    float sx, sy, cx, cy;
-                    df::upk(S2[r], sx, sy);
-                    df::upk(C2[r], cx, cy);
-                    const double v = warp_sum(df::to_double(sx, cx) + df::to_double(sy, cy));
-                    if (lane == 0) red[wq * kMaxKrylov + k] = v;
-                }
+                const int k = gw + kGW * half + 2 * kGW * r;
+                float sx, sy, cx, cy;
+                df::upk(S2[r], sx, sy);
+                df::upk(C2[r], cx, cy);
+                const double v = half_warp_sum(df::to_double(sx, cx) + df::to_double(sy, cy));
+                if (l16 == 0 && k < K) red[g * kMaxKrylov + k] = v;
             }
         }
         __syncthreads();
         for (int k = tid; k < K; k += kThr)
-            a.partials[(size_t)bid * kMaxKrylov + k] = red[(k % kCons) * kMaxKrylov + k] + bad;
+            a.partials[(size_t)bid * kMaxKrylov + k] = red[k] + red[kMaxKrylov + k] + bad;
     } else {
         const double v = producer ? 0.0 : warp_sum(df::to_double(nS, nC));
         if (lane == 0) red[wq] = v;
@@ -426,19 +452,6 @@ __global__ void k_lincomb_df(const float* __restrict__ V, int K, int64_t n, cons
     }
 }
 
-// the item whose block range [start, start + count) holds this block
-template <int GroupItem::*START>
-__device__ int group_item_df(const GroupItem* items, int count) {
-    __shared__ int s_item;
-    if (threadIdx.x == 0) {
-        int i = 0;
-        while (i + 1 < count && items[i + 1].*START <= (int)blockIdx.x) ++i;
-        s_item = i;
-    }
-    __syncthreads();
-    return s_item;
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(kThr, 2) k_gs_group(const GroupItem* __restrict__ items, int count,
                                                        const GsMaps* __restrict__ maps) {
@@ -446,11 +459,11 @@ __global__ void __launch_bounds__(kThr, 2) k_gs_group(const GroupItem* __restric
     unsigned char* smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
     int q;
     if (MODE == kDot)
-        q = group_item_df<&GroupItem::b_md>(items, count);
+        q = group_item_of<&GroupItem::b_md>(items, count);
     else if (MODE == kUpdateDot)
-        q = group_item_df<&GroupItem::b_ud>(items, count);
+        q = group_item_of<&GroupItem::b_ud>(items, count);
     else
-        q = group_item_df<&GroupItem::b_rd>(items, count);
+        q = group_item_of<&GroupItem::b_rd>(items, count);
     const GroupItem& it = items[q];
     GsArgs a;
     a.V = it.V;
@@ -478,7 +491,7 @@ __global__ void __launch_bounds__(kThr, 2) k_gs_group(const GroupItem* __restric
 }
 
 __global__ void __launch_bounds__(256) k_scale_df_group(const GroupItem* __restrict__ items, int count) {
-    const GroupItem& it = items[group_item_df<&GroupItem::b_sc>(items, count)];
+    const GroupItem& it = items[group_item_of<&GroupItem::b_sc>(items, count)];
     scale_df_run(it.w, it.hcol + it.K, it.n, it.Vnext, blockIdx.x - it.b_sc, it.n_sc);
 }
 
