@@ -67,6 +67,8 @@ constexpr int kMaxSlice = 256;                         // output channels per CT
 
 enum Mode { kGather = 0, kF64 = 1, kHalo = 2, kStream = 3 };
 
+constexpr int kLiftGroup = 4;        // channel chunks a thread loads at once in the lift
+
 using namespace ::rte::ptx;
 
 __device__ int g_tc_status;          // 1 once a bounded wait expired
@@ -415,21 +417,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
                 const size_t pix = in ? (size_t)iy * a.Wi + ix : 0;
                 const double* xp = f32 ? nullptr : (a.batched ? a.x64_b[b] : a.x64 + (size_t)b * a.Ci * plane) + pix;
                 const float* xq = f32 ? a.x32_b[b] + pix : nullptr;
-#pragma unroll 4
-                for (int kc = half; kc < KC; kc += 2) {
-                    float v[8];
+                // groups of kLiftGroup chunks: every load of a group is issued
+                // before its shared-memory stores (which the compiler keeps in
+                // order with the loads), so a thread has 8 kLiftGroup loads in flight
+                for (int kc0 = half; kc0 < KC; kc0 += 2 * kLiftGroup) {
+                    float v[kLiftGroup][8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int ci = kc * 8 + j;
-                        float x = 0.f;
-                        if (in && ci < a.Ci)
-                            x = f32 ? __ldg(xq + (size_t)ci * plane) : (float)__ldg(xp + (size_t)ci * plane);
-                        v[j] = a.relu_in ? fmaxf(x, 0.f) : x;
+                    for (int q = 0; q < kLiftGroup; ++q) {
+                        const int kc = kc0 + 2 * q;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int ci = kc * 8 + j;
+                            float x = 0.f;
+                            if (in && kc < KC && ci < a.Ci)
+                                x = f32 ? __ldg(xq + (size_t)ci * plane) : (float)__ldg(xp + (size_t)ci * plane);
+                            v[q][j] = a.relu_in ? fmaxf(x, 0.f) : x;
+                        }
                     }
-                    const uint4 pk = pack8(v);
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + kc * 128), "r"(pk.x),
-                                 "r"(pk.y), "r"(pk.z), "r"(pk.w)
-                                 : "memory");
+#pragma unroll
+                    for (int q = 0; q < kLiftGroup; ++q) {
+                        const int kc = kc0 + 2 * q;
+                        if (kc < KC) {
+                            const uint4 pk = pack8(v[q]);
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + kc * 128),
+                                         "r"(pk.x), "r"(pk.y), "r"(pk.z), "r"(pk.w)
+                                         : "memory");
+                        }
+                    }
                 }
             } else {
                 const uint4* xp = reinterpret_cast<const uint4*>(a.x8);

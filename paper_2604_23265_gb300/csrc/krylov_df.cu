@@ -63,7 +63,13 @@ constexpr int kMaxStages = 8;
 constexpr int kRowBytes = kE * 8;             // one staged row: hi then lo, 128 floats each
 constexpr int kStageBudget = 102 * 1024;      // shared memory the stages of a block aim at
 
-enum Mode { kDot = 0, kUpdateDot = 1, kUpdateNorm = 2 };
+// kDot, kUpdateDot, kUpdateNorm: the three passes of CGS2 (below).  The
+// solver's deferred form uses two passes a step (launch_cgs2_deferred_df):
+//   kFixDot        v_j = (u_j - V c) / beta on the staged row j (the previous
+//                  step's second projection, deferred), then h1 = V^T w
+//   kUpdateDotNorm w' = w - V h1 into the slot of u_{j+1}, then h2 = V^T w'
+//                  and ||w'||^2
+enum Mode { kDot = 0, kUpdateDot = 1, kUpdateNorm = 2, kFixDot = 3, kUpdateDotNorm = 4 };
 
 using namespace ::rte::ptx;
 
@@ -137,9 +143,11 @@ struct GsArgs {
     float* w;                 // df64 [n]
     const double* hin;        // passes 2, 3: the projection subtracted
     const double* h1;         // pass 3: out[k] = h1[k] + hin[k]
-    double* partials;         // [nb][kMaxKrylov]
+    double* partials;         // [nb][kMaxKrylov], then [nb] (pass 1: ||w||^2)
     unsigned* counter;
     double* out;              // pass 1, 2: [K]; pass 3: [K + 1]
+    float* wout;              // phase A result (df64): kFixDot the fixed row j, else w' (null: w)
+    const double* beta;       // kFixDot: v_j = (u_j - V c) / beta[0]
 };
 
 // Tensor maps of one pass: the K basis vectors as 2K rows of n floats (row
@@ -154,9 +162,15 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                        int nb, unsigned char* smem) {
     using df::f2;
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
-    __shared__ float hh[kMaxKrylov + 8], hl[kMaxKrylov + 8];      // rows past K: h = 0
+    // the coefficients of phase A as packed pairs, per row: (h, h), (-h, -h)
+    // for the hi part and (-l, -l) for the lo part; rows past K: h = 0
+    __shared__ __align__(16) df::f2 hc[kMaxKrylov + 8][4];
     __shared__ int s_issued;
     __shared__ bool s_last;
+    __shared__ float s_bh, s_bl;                                   // kFixDot: 1 / beta
+    constexpr bool kUpdate = MODE != kDot;                          // has phase A
+    constexpr bool kDots = MODE != kUpdateNorm;                     // has phase B
+    constexpr bool kNorm = MODE == kUpdateNorm || MODE == kUpdateDotNorm;
     const int K = a.K, tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
     const bool producer = wq == kCons;
     const int64_t n = a.n;
@@ -175,11 +189,16 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
         s_issued = 0;
     }
     for (int e = tid; e < 2 * kE; e += kThr) zero_row[e] = 0.f;
+    // phase A coefficients: kFixDot c over the rows before the fixed one
+    const int KA = MODE == kFixDot ? K - 1 : K;
+    if (MODE == kFixDot && tid == 0) df::from_double(1.0 / a.beta[0], s_bh, s_bl);
     for (int k = tid; k < kMaxKrylov + 8; k += kThr) {
         float x = 0.f, y = 0.f;
-        if (MODE != kDot && k < K) df::from_double(a.hin[k], x, y);
-        hh[k] = x;
-        hl[k] = y;
+        if (kUpdate && k < KA) df::from_double(a.hin[k], x, y);
+        hc[k][0] = df::pk(x, x);
+        hc[k][1] = df::pk(-x, -x);
+        hc[k][2] = df::pk(-y, -y);
+        hc[k][3] = 0ull;
     }
     __syncthreads();
 
@@ -232,7 +251,7 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
             float* st = reinterpret_cast<float*>(smem + (size_t)s * stage_bytes);
             float* wrow = st + K * (kRowBytes / 4);
             auto row_of = [&](int k) -> const float* { return k < K ? st + k * 2 * kE : zero_row; };
-            if (MODE != kDot) {
+            if (kUpdate) {
                 // phase A: warp gw owns the element pairs 16 gw + l16; half warp
                 // `half` sums h_k V_k over the rows k = half + 2 j in two chains,
                 // and the halves are added by a shuffle: no cross-warp sum
@@ -243,8 +262,7 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                     for (int c = 0; c < 2; ++c) {
                         const int k = half + 2 * (j + c);
                         const float* row = row_of(k);
-                        const f2 bh = df::pk(hh[k], hh[k]);
-                        const f2 nbh = df::pk(-hh[k], -hh[k]), nbl = df::pk(-hl[k], -hl[k]);
+                        const f2 bh = hc[k][0], nbh = hc[k][1], nbl = hc[k][2];
                         const f2 vh = *reinterpret_cast<const f2*>(row + e0);
                         const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
                         df::mac2(uS[c], uC[c], vh, vl, nbh, nbl, bh);
@@ -259,20 +277,28 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                 uc = df::add2(ut2, df::add2(uc, oc));
                 df::renorm2(u2, uc);
                 if (half == 0) {
-                    // w <- w - u for the pair, into the stage and HBM
+                    // t <- t - u for the pair (kFixDot: times 1 / beta), into
+                    // the stage and HBM; t is w, or the row being fixed
+                    float* trow = MODE == kFixDot ? st + (K - 1) * 2 * kE : wrow;
+                    float* gout = a.wout ? a.wout : a.w;
                     float uh[2], ul[2], wh[2], wl[2];
                     df::upk(u2, uh[0], uh[1]);
                     df::upk(uc, ul[0], ul[1]);
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        df::sub(wrow[e0 + q], wrow[kE + e0 + q], uh[q], ul[q], wh[q], wl[q]);
-                        wrow[e0 + q] = wh[q];
-                        wrow[kE + e0 + q] = wl[q];
+                        df::sub(trow[e0 + q], trow[kE + e0 + q], uh[q], ul[q], wh[q], wl[q]);
+                        if (MODE == kFixDot) {
+                            float p, e;
+                            df::mul(wh[q], wl[q], s_bh, s_bl, p, e);
+                            df::two_sum(p, e, wh[q], wl[q]);
+                        }
+                        trow[e0 + q] = wh[q];
+                        trow[kE + e0 + q] = wl[q];
                     }
                     if (e0 < rem) {                          // rem is a multiple of 4
-                        *reinterpret_cast<float2*>(a.w + base + e0) = make_float2(wh[0], wh[1]);
-                        *reinterpret_cast<float2*>(a.w + n + base + e0) = make_float2(wl[0], wl[1]);
-                        if (MODE == kUpdateNorm) {
+                        *reinterpret_cast<float2*>(gout + base + e0) = make_float2(wh[0], wh[1]);
+                        *reinterpret_cast<float2*>(gout + n + base + e0) = make_float2(wl[0], wl[1]);
+                        if (kNorm) {
 #pragma unroll
                             for (int q = 0; q < 2; ++q) {
                                 float p, e;
@@ -283,9 +309,9 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                         }
                     }
                 }
-                if (MODE == kUpdateDot) group_sync(g);
+                if (kDots) group_sync(g);
             }
-            if (MODE != kUpdateNorm) {
+            if (kDots) {
                 // phase B: half warp `half` of warp gw owns the rows
                 // k = gw + 4 half + 8 r; lane l16 the pairs l16 + 16 t
                 f2 wh2[4], wl2[4], nwh2[4], nwl2[4];
@@ -336,7 +362,7 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
     // block adds the blocks
     double* red = reinterpret_cast<double*>(smem);                 // [kGroups][kMaxKrylov]
     const double bad = ok ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
-    if (MODE != kUpdateNorm) {
+    if (kDots) {
         if (!producer) {
 #pragma unroll
             for (int r = 0; r < kOwnB; ++r) {
@@ -347,10 +373,19 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                 const double v = half_warp_sum(df::to_double(sx, cx) + df::to_double(sy, cy));
                 if (l16 == 0 && k < K) red[g * kMaxKrylov + k] = v;
             }
+            if (kNorm) {
+                const double v = warp_sum(df::to_double(nS, nC));
+                if (lane == 0) red[2 * kMaxKrylov + wq] = v;
+            }
         }
         __syncthreads();
         for (int k = tid; k < K; k += kThr)
             a.partials[(size_t)bid * kMaxKrylov + k] = red[k] + red[kMaxKrylov + k] + bad;
+        if (kNorm && tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kCons; ++q) t += red[2 * kMaxKrylov + q];
+            a.partials[(size_t)nb * kMaxKrylov + bid] = t + bad;
+        }
     } else {
         const double v = producer ? 0.0 : warp_sum(df::to_double(nS, nC));
         if (lane == 0) red[wq] = v;
@@ -369,9 +404,18 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
     __threadfence();
     const int R = MODE == kUpdateNorm ? 1 : K;
     for (int k = wq; k < R; k += kThr / 32) {
-        double t = 0.0;
-        for (int b = lane; b < nb; b += 32) t += __ldcg(a.partials + (size_t)b * kMaxKrylov + k);
-        t = warp_sum(t);
+        // four independent chains, so the loads of a lane are in flight together
+        const double* pk = a.partials + k;
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        int b = lane;
+        for (; b + 96 < nb; b += 128) {
+            t0 += __ldcg(pk + (size_t)b * kMaxKrylov);
+            t1 += __ldcg(pk + (size_t)(b + 32) * kMaxKrylov);
+            t2 += __ldcg(pk + (size_t)(b + 64) * kMaxKrylov);
+            t3 += __ldcg(pk + (size_t)(b + 96) * kMaxKrylov);
+        }
+        for (; b < nb; b += 32) t0 += __ldcg(pk + (size_t)b * kMaxKrylov);
+        double t = warp_sum((t0 + t1) + (t2 + t3));
         if (lane == 0) {
             if (MODE == kUpdateNorm)
                 a.out[K] = sqrt(t);
@@ -381,6 +425,13 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
     }
     if (MODE == kUpdateNorm)
         for (int k = tid; k < K; k += kThr) a.out[k] = a.h1[k] + a.hin[k];
+    if (MODE == kUpdateDotNorm && wq == 0) {
+        // ||w'||^2 over the blocks into out[K]
+        double t = 0.0;
+        for (int b = lane; b < nb; b += 32) t += __ldcg(a.partials + (size_t)nb * kMaxKrylov + b);
+        t = warp_sum(t);
+        if (lane == 0) a.out[K] = t;
+    }
     if (tid == 0) *a.counter = 0u;
 }
 
@@ -452,18 +503,15 @@ __global__ void k_lincomb_df(const float* __restrict__ V, int K, int64_t n, cons
     }
 }
 
+// grouped solves: the two passes of the deferred step for every item
 template <int MODE>
 __global__ void __launch_bounds__(kThr, 2) k_gs_group(const GroupItem* __restrict__ items, int count,
                                                        const GsMaps* __restrict__ maps) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
-    int q;
-    if (MODE == kDot)
-        q = group_item_of<&GroupItem::b_md>(items, count);
-    else if (MODE == kUpdateDot)
-        q = group_item_of<&GroupItem::b_ud>(items, count);
-    else
-        q = group_item_of<&GroupItem::b_rd>(items, count);
+    static_assert(MODE == kFixDot || MODE == kUpdateDotNorm, "grouped passes: the deferred step");
+    const int q = MODE == kFixDot ? group_item_of<&GroupItem::b_md>(items, count)
+                                  : group_item_of<&GroupItem::b_ud>(items, count);
     const GroupItem& it = items[q];
     GsArgs a;
     a.V = it.V;
@@ -472,35 +520,32 @@ __global__ void __launch_bounds__(kThr, 2) k_gs_group(const GroupItem* __restric
     a.w = it.w;
     a.partials = it.partials;
     a.counter = it.counter;
-    if (MODE == kDot) {
-        a.hin = nullptr;
-        a.h1 = nullptr;
+    a.h1 = nullptr;
+    float* V = const_cast<float*>(it.V);
+    if (MODE == kFixDot) {
+        a.hin = it.cfix;
         a.out = it.h1;
+        a.wout = V + (size_t)2 * (it.K - 1) * it.n;
+        a.beta = it.betas + (it.K - 1);
         gs_run<MODE>(a, &maps[q].v, &maps[q].w, true, blockIdx.x - it.b_md, it.n_md, smem);
-    } else if (MODE == kUpdateDot) {
-        a.hin = it.h1;
-        a.h1 = nullptr;
-        a.out = it.h2;
-        gs_run<MODE>(a, &maps[q].v, &maps[q].w, true, blockIdx.x - it.b_ud, it.n_ud, smem);
     } else {
-        a.hin = it.h2;
-        a.h1 = it.h1;
-        a.out = it.hcol;
-        gs_run<MODE>(a, &maps[q].v, &maps[q].w, true, blockIdx.x - it.b_rd, it.n_rd, smem);
+        a.hin = it.h1;
+        a.out = it.h2;
+        a.wout = V + (size_t)2 * it.K * it.n;
+        a.beta = nullptr;
+        gs_run<MODE>(a, &maps[q].v, &maps[q].w, true, blockIdx.x - it.b_ud, it.n_ud, smem);
     }
 }
 
-__global__ void __launch_bounds__(256) k_scale_df_group(const GroupItem* __restrict__ items, int count) {
-    const GroupItem& it = items[group_item_of<&GroupItem::b_sc>(items, count)];
-    scale_df_run(it.w, it.hcol + it.K, it.n, it.Vnext, blockIdx.x - it.b_sc, it.n_sc);
+size_t gs_smem_max() {
+    size_t m = 0;
+    for (int K = 1; K <= kMaxKrylov; ++K) m = gs_smem(K) > m ? gs_smem(K) : m;
+    return m;
 }
 
 template <int MODE>
 void set_smem_limit() {
-    size_t m = 0;
-    for (int K = 1; K <= kMaxKrylov; ++K) m = gs_smem(K) > m ? gs_smem(K) : m;
-    raise_smem_limit((const void*)k_gs<MODE>, m);
-    raise_smem_limit((const void*)k_gs_group<MODE>, m);
+    raise_smem_limit((const void*)k_gs<MODE>, gs_smem_max());
 }
 
 void set_all_smem_limits() {
@@ -509,6 +554,10 @@ void set_all_smem_limits() {
         set_smem_limit<kDot>();
         set_smem_limit<kUpdateDot>();
         set_smem_limit<kUpdateNorm>();
+        set_smem_limit<kFixDot>();
+        set_smem_limit<kUpdateDotNorm>();
+        raise_smem_limit((const void*)k_gs_group<kFixDot>, gs_smem_max());
+        raise_smem_limit((const void*)k_gs_group<kUpdateDotNorm>, gs_smem_max());
     });
 }
 
@@ -579,6 +628,8 @@ void launch_orthogonalise_df(rte_ctx* ctx, const float* V, int K, float* w, doub
     a.w = w;
     a.partials = ctx->partials;
     a.counter = ctx->counter;
+    a.wout = nullptr;
+    a.beta = nullptr;
     const size_t smem = gs_smem(K);
     GsMaps maps;
     encode_maps(&maps, V, K, w, n);
@@ -610,6 +661,44 @@ void launch_orthogonalise_df(rte_ctx* ctx, const float* V, int K, float* w, doub
     }
 }
 
+void launch_cgs2_deferred_df(rte_ctx* ctx, float* V, int j, const float* w, const double* c,
+                             const double* beta_j, double* h1, double* h2nu) {
+    const int K = j + 1;
+    if (K < 1 || K > kMaxKrylov) throw StatusError{RTE_EINVAL, "Gram-Schmidt: K out of range"};
+    const int64_t n = ctx->n;
+    GsArgs a;
+    a.V = V;
+    a.K = K;
+    a.n = n;
+    a.w = const_cast<float*>(w);
+    a.partials = ctx->partials;
+    a.counter = ctx->counter;
+    a.h1 = nullptr;
+    const size_t smem = gs_smem(K);
+    GsMaps maps;
+    encode_maps(&maps, V, K, w, n);
+    {
+        const int g = gs_blocks<kFixDot>(ctx, K, n);
+        ProfScope ps(ctx, K_FIX_DOT, (double)(K + 2) * n * 8, 1, (4.0 * K - 2.0) * n);
+        a.hin = c;
+        a.out = h1;
+        a.wout = V + (size_t)2 * j * n;
+        a.beta = beta_j;
+        k_gs<kFixDot><<<g, kThr, smem, ctx->stream>>>(a, maps);
+        check(cudaGetLastError(), "k_gs (fix v_j, V^T w)");
+    }
+    {
+        const int g = gs_blocks<kUpdateDotNorm>(ctx, K, n);
+        ProfScope ps(ctx, K_UPDATE_DOT_NORM, (double)(K + 2) * n * 8, 1, (4.0 * K + 2.0) * n);
+        a.hin = h1;
+        a.out = h2nu;
+        a.wout = V + (size_t)2 * (j + 1) * n;
+        a.beta = nullptr;
+        k_gs<kUpdateDotNorm><<<g, kThr, smem, ctx->stream>>>(a, maps);
+        check(cudaGetLastError(), "k_gs (update, V^T w', ||w'||)");
+    }
+}
+
 void launch_scale_df(rte_ctx* ctx, const float* w, const double* s, float* v) {
     ProfScope ps(ctx, K_SCALE, (double)ctx->n * 16);
     k_scale_df<<<ew_grid(ctx, ctx->n), 256, 0, ctx->stream>>>(w, s, ctx->n, v);
@@ -634,11 +723,9 @@ void launch_lincomb_df(rte_ctx* ctx, const float* V, int K, const double* y, dou
     check(cudaGetLastError(), "k_lincomb_df");
 }
 
-void group_ortho_geometry_df(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd, int* n_sc) {
-    *n_md = gs_blocks<kDot>(ctx, K, ctx->n);
-    *n_ud = gs_blocks<kUpdateDot>(ctx, K, ctx->n);
-    *n_rd = gs_blocks<kUpdateNorm>(ctx, K, ctx->n);
-    *n_sc = ew_grid(ctx, ctx->n);
+void group_ortho_geometry_df(rte_ctx* ctx, int K, int* n_md, int* n_ud) {
+    *n_md = gs_blocks<kFixDot>(ctx, K, ctx->n);
+    *n_ud = gs_blocks<kUpdateDotNorm>(ctx, K, ctx->n);
 }
 
 size_t group_gs_maps_bytes() { return sizeof(GsMaps); }
@@ -649,16 +736,14 @@ void encode_group_gs_maps(const GroupItem* items_host, int count, void* maps_hos
 }
 
 void launch_group_orthogonalise_df(const GroupItem* items_dev, const void* maps_dev, int count, int blocks_md,
-                                   int blocks_ud, int blocks_rd, int blocks_sc, int kmax, cudaStream_t st) {
+                                   int blocks_ud, int kmax, cudaStream_t st) {
     const GsMaps* maps = static_cast<const GsMaps*>(maps_dev);
     set_all_smem_limits();
     // every item's stages within the shared memory of the launch
     size_t smem = 0;
     for (int K = 1; K <= kmax; ++K) smem = gs_smem(K) > smem ? gs_smem(K) : smem;
-    k_gs_group<kDot><<<blocks_md, kThr, smem, st>>>(items_dev, count, maps);
-    k_gs_group<kUpdateDot><<<blocks_ud, kThr, smem, st>>>(items_dev, count, maps);
-    k_gs_group<kUpdateNorm><<<blocks_rd, kThr, smem, st>>>(items_dev, count, maps);
-    k_scale_df_group<<<blocks_sc, 256, 0, st>>>(items_dev, count);
+    k_gs_group<kFixDot><<<blocks_md, kThr, smem, st>>>(items_dev, count, maps);
+    k_gs_group<kUpdateDotNorm><<<blocks_ud, kThr, smem, st>>>(items_dev, count, maps);
     check(cudaGetLastError(), "grouped Gram-Schmidt (df64)");
 }
 

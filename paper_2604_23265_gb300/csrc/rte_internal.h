@@ -24,7 +24,8 @@ struct Atfps;                       // ATFPS loss filter of a context (atfps.cu)
 enum KernelId {
     K_TRACES, K_COMBINE, K_ADJOINT, K_RECONSTRUCT, K_RHS, K_INVERT, K_BLOCK, K_BLOCK_T,
     K_MDOT, K_UPDATE_DOT, K_UPDATE_NORM, K_NORM, K_SCALE, K_XUPDATE, K_GIVENS, K_BACKSUB,
-    K_CYCLE, K_F2D, K_MGNET, K_RESPONSE, K_RESPONSE_APPLY, K_GATHER, K_RESPONSE_TC, K_TILE_ORDER, K_COUNT
+    K_CYCLE, K_F2D, K_MGNET, K_RESPONSE, K_RESPONSE_APPLY, K_GATHER, K_RESPONSE_TC, K_TILE_ORDER,
+    K_FIX_DOT, K_UPDATE_DOT_NORM, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -171,13 +172,17 @@ struct GroupItem {
     float* o;
     int I, M, N;
     int64_t n;
-    // Gram-Schmidt of the df64 w against the df64 V[0..K), new vector to Vnext
+    // deferred CGS2 step (launch_cgs2_deferred_df): row K - 1 of V fixed with
+    // the coefficients cfix and betas[K - 1], h1 = V^T w, w' = w - V h1 into
+    // row K, h2 = V^T w' and ||w'||^2 (h2[K])
     const float* V;
     float* w;
     double* h1;
     double* h2;
     double* hcol;
-    float* Vnext;
+    const double* cfix;
+    double* betas;
+    double* U;
     double* partials;
     unsigned* counter;
     int K;
@@ -192,7 +197,7 @@ struct GroupItem {
     // tensor-core response (o in tile order, null: per cell)
     const int* pos_of;
     // block ranges: [b_x, b_x + n_x) of the grouped launch of kernel x
-    int b_ba, n_ba, b_ga, n_ga, b_gt, n_gt, b_md, n_md, b_ud, n_ud, b_rd, n_rd, b_sc, n_sc;
+    int b_ba, n_ba, b_ga, n_ga, b_gt, n_gt, b_md, n_md, b_ud, n_ud;
 };
 
 // the item of a grouped launch that block blockIdx.x belongs to: the last
@@ -215,15 +220,15 @@ void launch_group_response(const GroupItem* items_dev, int count, int blocks_ba,
                            size_t smem_ba, cudaStream_t st);
 // block counts and shared memory of one item's response apply / gather
 void group_response_geometry(rte_ctx* ctx, int* n_ba, int* n_ga, size_t* smem_ba);
-// CGS2 (three df64 passes) and the scaling to Vnext for every item; maps_dev
-// holds the items' tensor maps (encode_group_gs_maps of the same items,
+// the deferred CGS2 step (two df64 passes) for every item; maps_dev holds
+// the items' tensor maps (encode_group_gs_maps of the same items,
 // group_gs_maps_bytes each, 64-byte aligned, copied to the device before)
 void launch_group_orthogonalise_df(const GroupItem* items_dev, const void* maps_dev, int count, int blocks_md,
-                                   int blocks_ud, int blocks_rd, int blocks_sc, int kmax, cudaStream_t st);
+                                   int blocks_ud, int kmax, cudaStream_t st);
 size_t group_gs_maps_bytes();
 void encode_group_gs_maps(const GroupItem* items_host, int count, void* maps_host);
-// block counts of one item's Gram-Schmidt passes and scaling
-void group_ortho_geometry_df(rte_ctx* ctx, int K, int* n_md, int* n_ud, int* n_rd, int* n_sc);
+// block counts of one item's two Gram-Schmidt passes (as launch_cgs2_deferred_df)
+void group_ortho_geometry_df(rte_ctx* ctx, int K, int* n_md, int* n_ud);
 
 // lockstep groups of solves (solve.cu), for the grouped server: a solve
 // (started on creation: workspace, initial guess, ||b||) and rounds over a set
@@ -343,6 +348,16 @@ void launch_lincomb_df(rte_ctx* ctx, const float* V, int K, const double* y, dou
 // w (df64) = z - P R z for z the FP32 vector z_hi (z_lo null) or the df64
 // vector (z_hi, z_lo); R z in FP32 from z_hi
 void launch_response_apply_df(rte_ctx* ctx, const float* z_hi, const float* z_lo, float* w);
+// One Arnoldi step's Gram-Schmidt in the deferred form, two HBM passes: row
+// j of V holds u_j, the previous step's w' (for j = 0, v_0 itself with
+// c = 0 and beta = 1); pass 1 fixes it, v_j = (u_j - V[0..j) c) / beta_j[0],
+// in place and forms h1 = V[0..j]^T w; pass 2 writes w' = w - V[0..j] h1 into
+// row j + 1 and forms h2 = V[0..j]^T w' (h2nu[0..j]) and ||w'||^2
+// (h2nu[j + 1]).  The step's Hessenberg column is (h1 + h2, beta_{j+1}) with
+// beta_{j+1}^2 = ||w'||^2 - ||h2||^2; h2 and beta_{j+1} fix row j + 1 in the
+// next step.
+void launch_cgs2_deferred_df(rte_ctx* ctx, float* V, int j, const float* w, const double* c,
+                             const double* beta_j, double* h1, double* h2nu);
 // 1 if a bounded wait of a df64 Gram-Schmidt pass ran out (reset clears), -1 on error
 int krylov_timeout_flag(bool reset);
 // reads and clears the device flags of the bounded waits (Gram-Schmidt passes,

@@ -59,7 +59,7 @@ const char* const kKernelNames[K_COUNT] = {
     "traces", "combine", "adjoint", "reconstruct", "rhs", "build_invert", "block_apply",
     "block_apply_t", "mdot", "update_dot", "update_norm", "norm", "scale", "x_update",
     "givens", "backsub", "cycle_start", "f2d", "mgnet", "response_build", "response_apply",
-    "gather", "response_tc", "tile_order"};
+    "gather", "response_tc", "tile_order", "fix_dot", "update_dot_norm"};
 
 static cudaEvent_t prof_event(rte_ctx* ctx) {
     if (!ctx->prof.pool.empty()) {
@@ -551,7 +551,7 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     ctx->trace_out = static_cast<double*>(dev_alloc(ctx, 2 * ctx->n * sizeof(double)));
     ctx->max_red_blocks = ctx->num_sms * 4;
     ctx->partials = static_cast<double*>(
-        dev_alloc(ctx, (size_t)ctx->max_red_blocks * kMaxKrylov * sizeof(double)));
+        dev_alloc(ctx, (size_t)ctx->max_red_blocks * (kMaxKrylov + 1) * sizeof(double)));
     ctx->counter = static_cast<unsigned*>(dev_alloc(ctx, 64));
     ctx->scal = static_cast<double*>(dev_alloc(ctx, kScal * sizeof(double)));
     ctx->Dt = static_cast<double*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(double)));

@@ -43,6 +43,12 @@ struct Workspace {
     double* h1 = nullptr;     // [m+1]
     double* h2 = nullptr;     // [m+1]
     double* hcol = nullptr;   // [m+2]
+    // deferred Gram-Schmidt: betas[i] = beta_{i-1} (betas[0] = 1), the
+    // coefficients that fix the next row (the last step's h2), and
+    // U[(j) (m+1) + i] = h2_{j-1}[i] / beta_{j-1} for the V-based update
+    double* betas = nullptr;  // [m+1]
+    double* cfix = nullptr;   // [m+1]
+    double* U = nullptr;      // [(m+1) (m+1)]
     double* est = nullptr;    // [4] device status: est, beta, bnorm
     double* est_host = nullptr;   // pinned [4]
     std::vector<void*> allocs;
@@ -94,6 +100,9 @@ Workspace* get_workspace(rte_ctx* ctx, int m) {
     ws->h1 = ws_alloc<double>(ctx, ws, m + 1);
     ws->h2 = ws_alloc<double>(ctx, ws, m + 1);
     ws->hcol = ws_alloc<double>(ctx, ws, m + 2);
+    ws->betas = ws_alloc<double>(ctx, ws, m + 1);
+    ws->cfix = ws_alloc<double>(ctx, ws, m + 1);
+    ws->U = ws_alloc<double>(ctx, ws, (size_t)(m + 1) * (m + 1));
     ws->est = ws_alloc<double>(ctx, ws, 4);
     check(cudaMallocHost(&ws->est_host, 4 * sizeof(double)), "cudaMallocHost");
     return ws;
@@ -109,10 +118,11 @@ void orthogonalise64(rte_ctx* ctx, Workspace* ws, const double* V, int K, double
     launch_update_norm(ctx, V, K, w, ws->h1, ws->h2, ws->hcol);
 }
 
-// Start of a cycle: g = (beta, 0, ...), H = 0.
-__global__ void k_cycle_start(int m, const double* __restrict__ beta, double* H, double* g) {
+// Start of a cycle: g = (beta, 0, ...), H = 0, betas[0] = 1 (v_0 is final).
+__global__ void k_cycle_start(int m, const double* __restrict__ beta, double* H, double* g, double* betas) {
     for (int i = threadIdx.x; i < (m + 1) * m; i += blockDim.x) H[i] = 0.0;
     for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta[0] : 0.0;
+    if (threadIdx.x == 0) betas[0] = 1.0;
 }
 
 // Hessenberg column j: apply the previous rotations, make a new one, update g.
@@ -146,6 +156,58 @@ __global__ void k_givens(int j, int m, const double* __restrict__ hcol, double* 
                          double* sn, double* g, double* est) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     givens_run(j, m, hcol, H, cs, sn, g, est);
+}
+
+// Column j of the deferred Gram-Schmidt (launch_cgs2_deferred_df): the step
+// orthogonalised w = B z_j with z_j = M(u_j), u_j = beta_{j-1} v_j + V c, so
+// the flexible-GMRES column of zhat_j = z_j / beta_{j-1} is
+//   (h1 + h2, beta_j) / beta_{j-1},  beta_j^2 = ||w'||^2 - ||h2||^2
+// (Pythagoras: h2 is the small second projection).  Keeps beta_j and h2 to
+// fix row j + 1 in the next step, and h2 / beta_j as column j + 1 of U; then
+// the Givens update of column j.
+__device__ void column_run(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2nu,
+                           double* betas, double* cfix, double* U, double* hcol, double* H, double* cs,
+                           double* sn, double* g, double* est) {
+    const int K = j + 1;
+    const double bprev = betas[j];
+    double hsq = 0.0;
+    for (int i = 0; i < K; ++i) hsq += h2nu[i] * h2nu[i];
+    const double d = h2nu[K] - hsq;
+    const double bj = d > 0.0 ? sqrt(d) : (d <= 0.0 ? 0.0 : d);     // a NaN step stays NaN
+    for (int i = 0; i < K; ++i) {
+        hcol[i] = (h1[i] + h2nu[i]) / bprev;
+        cfix[i] = h2nu[i];
+        U[(size_t)(j + 1) * (m + 1) + i] = bj > 0.0 ? h2nu[i] / bj : 0.0;
+    }
+    hcol[K] = bj / bprev;
+    betas[j + 1] = bj;
+    givens_run(j, m, hcol, H, cs, sn, g, est);
+}
+
+__global__ void k_column_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2nu,
+                                double* betas, double* cfix, double* U, double* hcol, double* H, double* cs,
+                                double* sn, double* g, double* est) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    column_run(j, m, h1, h2nu, betas, cfix, U, hcol, H, cs, sn, g, est);
+}
+
+// The update's coefficients for the stored vectors of a deferred cycle of k
+// columns: the network outputs z_j take y_j / beta_{j-1}; the final Krylov
+// vectors v_i take y_i + sum_{j > i} U[j][i] y_j (zhat_j = v_j + V U[j]).
+// tmp: k doubles of scratch.
+__global__ void k_deferred_y(int k, int m, bool net, const double* __restrict__ betas,
+                             const double* __restrict__ U, double* y, double* tmp) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (net) {
+        for (int i = 0; i < k; ++i) y[i] /= betas[i];
+        return;
+    }
+    for (int i = 0; i < k; ++i) {
+        double s = y[i];
+        for (int j = i + 1; j < k; ++j) s += U[(size_t)j * (m + 1) + i] * y[j];
+        tmp[i] = s;
+    }
+    for (int i = 0; i < k; ++i) y[i] = tmp[i];
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k)  (upper triangular)
@@ -192,7 +254,8 @@ double read_scalar(rte_ctx* ctx, Workspace* ws, const double* dev) {
 __global__ void k_givens_group(const GroupItem* __restrict__ items) {
     if (threadIdx.x != 0) return;
     const GroupItem& it = items[blockIdx.x];
-    givens_run(it.j, it.m, it.hcol, it.H, it.cs, it.sn, it.g, it.est);
+    column_run(it.j, it.m, it.h1, it.h2, it.betas, const_cast<double*>(it.cfix), it.U, it.hcol, it.H, it.cs, it.sn,
+               it.g, it.est);
     it.est_out[0] = it.est[0];
     it.est_out[1] = it.est[1];
 }
@@ -286,7 +349,7 @@ struct Solver {
         launch_split_df(ctx, ws->w64, ws->est + 3, vec(0));        // v_0 = r / beta
         {
             ProfScope ps(ctx, K_CYCLE, 0.0);
-            k_cycle_start<<<1, 256, 0, ctx->stream>>>(m, ws->est + 3, ws->H, ws->g);
+            k_cycle_start<<<1, 256, 0, ctx->stream>>>(m, ws->est + 3, ws->H, ws->g, ws->betas);
             check(cudaGetLastError(), "k_cycle_start");
         }
         cycle_net = use_net;
@@ -334,15 +397,14 @@ struct Solver {
         }
     }
 
-    // CGS2, v_{j+1}, Givens
+    // deferred CGS2 (v_j fixed, u_{j+1} = w' into row j + 1), the column, Givens
     void orthogonalise_step() {
         NvtxRange range("Gram-Schmidt and Givens");
-        const int K = j + 1;
-        launch_orthogonalise_df(ctx, ws->V, K, ws->w, ws->h1, ws->h2, ws->hcol);
-        launch_scale_df(ctx, ws->w, ws->hcol + K, vec(j + 1));
+        launch_cgs2_deferred_df(ctx, ws->V, j, ws->w, ws->cfix, ws->betas + j, ws->h1, ws->h2);
         ProfScope ps(ctx, K_GIVENS, 0.0);
-        k_givens<<<1, 32, 0, ctx->stream>>>(j, m, ws->hcol, ws->H, ws->cs, ws->sn, ws->g, ws->est);
-        check(cudaGetLastError(), "k_givens");
+        k_column_givens<<<1, 32, 0, ctx->stream>>>(j, m, ws->h1, ws->h2, ws->betas, ws->cfix, ws->U, ws->hcol,
+                                                   ws->H, ws->cs, ws->sn, ws->g, ws->est);
+        check(cudaGetLastError(), "k_column_givens");
     }
 
     // after the step's residual estimate est and ||w|| wn were read: false
@@ -368,6 +430,8 @@ struct Solver {
                 ProfScope ps(ctx, K_BACKSUB, 0.0);
                 k_backsub<<<1, 32, 0, ctx->stream>>>(k, m, ws->H, ws->g, ws->y);
                 check(cudaGetLastError(), "k_backsub");
+                k_deferred_y<<<1, 32, 0, ctx->stream>>>(k, m, cycle_net, ws->betas, ws->U, ws->y, ws->h1);
+                check(cudaGetLastError(), "k_deferred_y");
             }
             if (cycle_net) {
                 ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + 4 * k));
@@ -462,7 +526,7 @@ struct GroupRunner {
             }
             mgnet_precondition_batch_f(s.pc, cs.data(), vs.data(), zs.data(), (int)same.size());
         }
-        int ba = 0, ga = 0, gt = 0, md = 0, ud = 0, rd = 0, sc = 0, kmax = 1;
+        int ba = 0, ga = 0, gt = 0, md = 0, ud = 0, kmax = 1;
         size_t smem_ba = 0;
         bool f32 = true;
         for (size_t q = 0; q < live.size(); ++q) {
@@ -470,7 +534,7 @@ struct GroupRunner {
             GroupItem& it = items_h[q];
             rte_ctx* c = s.ctx;
             const int K = s.j + 1;
-            int nba = 0, nga = 0, nmd = 0, nud = 0, nrd = 0, nsc = 0;
+            int nba = 0, nga = 0, nmd = 0, nud = 0;
             size_t sm = 0;
             int ngt = 0;
             group_response_geometry(c, &nba, &nga, &sm);
@@ -479,7 +543,7 @@ struct GroupRunner {
                 nba = nga = 0;
                 ngt = tile_gather_blocks(c);
             }
-            group_ortho_geometry_df(c, K, &nmd, &nud, &nrd, &nsc);
+            group_ortho_geometry_df(c, K, &nmd, &nud);
             f32 = f32 && s.opts.inner_precision == RTE_F32;
             it.Rt = c->Rt;
             it.z = s.zj;
@@ -495,7 +559,9 @@ struct GroupRunner {
             it.h1 = s.ws->h1;
             it.h2 = s.ws->h2;
             it.hcol = s.ws->hcol;
-            it.Vnext = s.vec(s.j + 1);
+            it.cfix = s.ws->cfix;
+            it.betas = s.ws->betas;
+            it.U = s.ws->U;
             it.partials = c->partials;
             it.counter = c->counter;
             it.K = K;
@@ -512,8 +578,6 @@ struct GroupRunner {
             it.b_gt = gt; it.n_gt = ngt; gt += ngt;
             it.b_md = md; it.n_md = nmd; md += nmd;
             it.b_ud = ud; it.n_ud = nud; ud += nud;
-            it.b_rd = rd; it.n_rd = nrd; rd += nrd;
-            it.b_sc = sc; it.n_sc = nsc; sc += nsc;
             kmax = K > kmax ? K : kmax;
             smem_ba = sm > smem_ba ? sm : smem_ba;
         }
@@ -529,7 +593,7 @@ struct GroupRunner {
         } else {
             for (Solver* s : live) s->inner_apply();
         }
-        launch_group_orthogonalise_df(items_d, maps_d, nl, md, ud, rd, sc, kmax, st);
+        launch_group_orthogonalise_df(items_d, maps_d, nl, md, ud, kmax, st);
         k_givens_group<<<nl, 32, 0, st>>>(items_d);
         check(cudaGetLastError(), "k_givens_group");
         check(cudaMemcpyAsync(est_h, est_d, 2 * nl * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h est");
