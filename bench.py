@@ -194,14 +194,17 @@ def cpu_baseline(md, gpu_iters):
 # DRAM traffic per launch over the algorithmic bytes, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum); the bench scales it by the
 # algorithmic bytes of its own average launch.  The df64 Gram-Schmidt passes
-# read each basis row once (the second pass re-reads it from shared memory).
+# read each basis row once (the update and the dots of a pass share the
+# staged rows).
 TRAFFIC_RATIO = {"response_apply": 0.9995, "mdot": 1.001, "update_dot": 1.000, "update_norm": 0.999,
-                 "response_tc": 0.793}
+                 "response_tc": 0.793, "fix_dot": 1.000, "update_dot_norm": 0.999}
 TRAFFIC_SOURCE = {"response_apply": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)",
                   "mdot": "ncu DRAM bytes per launch at 256x256, M=64, K=50 basis vectors",
                   "update_dot": "ncu DRAM bytes per launch at 256x256, M=64, K=50 basis vectors",
                   "update_norm": "ncu DRAM bytes per launch at 256x256, M=64, K=50 basis vectors",
-                  "response_tc": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)"}
+                  "response_tc": "ncu DRAM bytes per launch at 256x256, M=64 (this workload)",
+                  "fix_dot": "ncu DRAM bytes per launch inside the solve at 256x256, M=64, K=31..34",
+                  "update_dot_norm": "ncu DRAM bytes per launch inside the solve at 256x256, M=64, K=31..34"}
 
 # Nominal FP64 rate of a GB300 (152 SMs x 2.07 GHz x 2 FP64 FMA per clock x 2
 # flops): the roof of the FP64 operator apply, the one FP64-bound kernel left.

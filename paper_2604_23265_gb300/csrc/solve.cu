@@ -164,30 +164,72 @@ __global__ void k_givens(int j, int m, const double* __restrict__ hcol, double* 
 //   (h1 + h2, beta_j) / beta_{j-1},  beta_j^2 = ||w'||^2 - ||h2||^2
 // (Pythagoras: h2 is the small second projection).  Keeps beta_j and h2 to
 // fix row j + 1 in the next step, and h2 / beta_j as column j + 1 of U; then
-// the Givens update of column j.
+// the Givens update of column j.  One warp: the lanes stage the column and
+// the previous rotations in shared memory, lane 0 applies the rotations.
 __device__ void column_run(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2nu,
                            double* betas, double* cfix, double* U, double* hcol, double* H, double* cs,
                            double* sn, double* g, double* est) {
-    const int K = j + 1;
+    __shared__ double col[kMaxKrylov + 2], scs[kMaxKrylov], ssn[kMaxKrylov];
+    __shared__ double s_bj;
+    const int lane = threadIdx.x & 31, K = j + 1;
     const double bprev = betas[j];
-    double hsq = 0.0;
-    for (int i = 0; i < K; ++i) hsq += h2nu[i] * h2nu[i];
-    const double d = h2nu[K] - hsq;
-    const double bj = d > 0.0 ? sqrt(d) : (d <= 0.0 ? 0.0 : d);     // a NaN step stays NaN
-    for (int i = 0; i < K; ++i) {
-        hcol[i] = (h1[i] + h2nu[i]) / bprev;
-        cfix[i] = h2nu[i];
-        U[(size_t)(j + 1) * (m + 1) + i] = bj > 0.0 ? h2nu[i] / bj : 0.0;
+    double part = 0.0;
+    for (int i = lane; i < K; i += 32) {
+        const double b2 = h2nu[i];
+        part += b2 * b2;
+        const double c = (h1[i] + b2) / bprev;
+        hcol[i] = c;
+        col[i] = c;
+        cfix[i] = b2;
     }
-    hcol[K] = bj / bprev;
-    betas[j + 1] = bj;
-    givens_run(j, m, hcol, H, cs, sn, g, est);
+    for (int i = lane; i < j; i += 32) {
+        scs[i] = cs[i];
+        ssn[i] = sn[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) {
+        const double d = h2nu[K] - part;
+        const double bj = d > 0.0 ? sqrt(d) : (d <= 0.0 ? 0.0 : d);     // a NaN step stays NaN
+        s_bj = bj;
+        betas[j + 1] = bj;
+        hcol[K] = bj / bprev;
+        col[K] = bj / bprev;
+    }
+    __syncwarp();
+    const double bj = s_bj;
+    for (int i = lane; i < K; i += 32) U[(size_t)(j + 1) * (m + 1) + i] = bj > 0.0 ? h2nu[i] / bj : 0.0;
+    if (lane == 0) {
+        for (int i = 0; i < j; ++i) {
+            const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
+            col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
+            col[i] = t;
+        }
+        const double a = col[j], b = col[j + 1];
+        double c = 1.0, s = 0.0;
+        if (b != 0.0) {
+            const double r = hypot(a, b);
+            c = a / r;
+            s = b / r;
+        }
+        cs[j] = c;
+        sn[j] = s;
+        col[j] = c * a + s * b;
+        col[j + 1] = 0.0;
+        g[j + 1] = -s * g[j];
+        g[j] = c * g[j];
+        est[0] = fabs(g[j + 1]);
+        est[1] = bj / bprev;          // the new vector's length before normalisation (breakdown test)
+    }
+    __syncwarp();
+    double* Hc = H + (size_t)j * (m + 1);
+    for (int i = lane; i <= K; i += 32) Hc[i] = col[i];
 }
 
 __global__ void k_column_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2nu,
                                 double* betas, double* cfix, double* U, double* hcol, double* H, double* cs,
                                 double* sn, double* g, double* est) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     column_run(j, m, h1, h2nu, betas, cfix, U, hcol, H, cs, sn, g, est);
 }
 
@@ -252,12 +294,14 @@ double read_scalar(rte_ctx* ctx, Workspace* ws, const double* dev) {
 // Hessenberg column j: apply the previous rotations, make a new one, update
 // g; one block per item of a grouped Arnoldi step.
 __global__ void k_givens_group(const GroupItem* __restrict__ items) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
     const GroupItem& it = items[blockIdx.x];
     column_run(it.j, it.m, it.h1, it.h2, it.betas, const_cast<double*>(it.cfix), it.U, it.hcol, it.H, it.cs, it.sn,
                it.g, it.est);
-    it.est_out[0] = it.est[0];
-    it.est_out[1] = it.est[1];
+    if (threadIdx.x == 0) {
+        it.est_out[0] = it.est[0];
+        it.est_out[1] = it.est[1];
+    }
 }
 
 // One flexible-GMRES solve as a sequence of phases, so that several solves can
