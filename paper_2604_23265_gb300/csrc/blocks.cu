@@ -177,26 +177,65 @@ __global__ void __launch_bounds__(256) k_response(int M, const int* __restrict__
 
 // Blocks of a cell from tabulated nodes (set-up by interpolation in ln tau):
 // for the cells of bin b (all interpolating between the nodes node0 ..
-// node0 + 7), D_C = sum_p w_Cp D_p and R_C = sum_p w_Cp R_p elementwise (FP64,
-// R rounded to FP32 once).  Block (b, y) holds the node values of elements
-// 1024 y .. 1024 y + 1023 in registers and writes them for every cell of the
-// bin.  bins[b] = (node0, first, end) positions in the cell list.
-__global__ void __launch_bounds__(256) k_interp_blocks(int E, const int4* __restrict__ bins,
-                                                       const int* __restrict__ cells,
-                                                       const double* __restrict__ wts,
-                                                       const double* __restrict__ Dn,
-                                                       const double* __restrict__ Rn,
-                                                       double* __restrict__ Dt, float* __restrict__ Rt) {
+// node0 + 7), D_C = sum_p w_Cp D_p elementwise.  Block (b, y) holds the node
+// values of elements 1024 y .. 1024 y + 1023 in registers and writes them for
+// every cell of the bin.  bins[b] = (node0, first, end) positions in the cell
+// list.  The sums are double-float (df64.h: the node values and the weights
+// as float pairs, products by TwoProd, sums by TwoSum) on the FP32 pipe,
+// about 2^-46 relative: far below the FP64 inversion's own rounding of the
+// nodes, cond(G) 2^-52, and eight times faster than the FP64 pipe.
+__global__ void __launch_bounds__(256) k_interp_D(int E, const int4* __restrict__ bins,
+                                                  const int* __restrict__ cells, const double* __restrict__ wts,
+                                                  const double* __restrict__ Dn, double* __restrict__ Dt) {
     const int4 bn = bins[blockIdx.x];
     const int e0 = (blockIdx.y * 256 + threadIdx.x) * 4;
     if (e0 >= E) return;                       // E = (2M)^2, a multiple of 4
-    double dn[8][4], rn[8][4];
+    float dh[8][4], dl[8][4];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const double2* dp = reinterpret_cast<const double2*>(Dn + (size_t)(bn.x + p) * E + e0);
+        const double2 d0 = __ldg(dp), d1 = __ldg(dp + 1);
+        df::from_double(d0.x, dh[p][0], dl[p][0]);
+        df::from_double(d0.y, dh[p][1], dl[p][1]);
+        df::from_double(d1.x, dh[p][2], dl[p][2]);
+        df::from_double(d1.y, dh[p][3], dl[p][3]);
+    }
+    for (int pos = bn.y; pos < bn.z; ++pos) {
+        const int c = __ldg(cells + pos);
+        float wh[8], wl[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) df::from_double(__ldg(wts + (size_t)pos * 8 + p), wh[p], wl[p]);
+        double d[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float S = 0.f, C = 0.f;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                float pr, er;
+                df::mul(dh[p][q], dl[p][q], wh[p], wl[p], pr, er);
+                df::acc(S, C, pr, er);
+            }
+            d[q] = df::to_double(S, C);
+        }
+        double2* dd = reinterpret_cast<double2*>(Dt + (size_t)c * E + e0);
+        dd[0] = make_double2(d[0], d[1]);
+        dd[1] = make_double2(d[2], d[3]);
+    }
+}
+
+// The per-cell response of tabulated blocks, R_C = sum_p w_Cp R_p (FP64,
+// rounded to FP32 once), as k_interp_D.
+__global__ void __launch_bounds__(256) k_interp_R(int E, const int4* __restrict__ bins,
+                                                  const int* __restrict__ cells, const double* __restrict__ wts,
+                                                  const double* __restrict__ Rn, float* __restrict__ Rt) {
+    const int4 bn = bins[blockIdx.x];
+    const int e0 = (blockIdx.y * 256 + threadIdx.x) * 4;
+    if (e0 >= E) return;
+    double rn[8][4];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
         const double2* rp = reinterpret_cast<const double2*>(Rn + (size_t)(bn.x + p) * E + e0);
-        const double2 d0 = __ldg(dp), d1 = __ldg(dp + 1), r0 = __ldg(rp), r1 = __ldg(rp + 1);
-        dn[p][0] = d0.x; dn[p][1] = d0.y; dn[p][2] = d1.x; dn[p][3] = d1.y;
+        const double2 r0 = __ldg(rp), r1 = __ldg(rp + 1);
         rn[p][0] = r0.x; rn[p][1] = r0.y; rn[p][2] = r1.x; rn[p][3] = r1.y;
     }
     for (int pos = bn.y; pos < bn.z; ++pos) {
@@ -204,20 +243,13 @@ __global__ void __launch_bounds__(256) k_interp_blocks(int E, const int4* __rest
         double w[8];
 #pragma unroll
         for (int p = 0; p < 8; ++p) w[p] = __ldg(wts + (size_t)pos * 8 + p);
-        double d[4], r[4];
+        double r[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            d[q] = w[0] * dn[0][q];
             r[q] = w[0] * rn[0][q];
 #pragma unroll
-            for (int p = 1; p < 8; ++p) {
-                d[q] = fma(w[p], dn[p][q], d[q]);
-                r[q] = fma(w[p], rn[p][q], r[q]);
-            }
+            for (int p = 1; p < 8; ++p) r[q] = fma(w[p], rn[p][q], r[q]);
         }
-        double2* dd = reinterpret_cast<double2*>(Dt + (size_t)c * E + e0);
-        dd[0] = make_double2(d[0], d[1]);
-        dd[1] = make_double2(d[2], d[3]);
         *reinterpret_cast<float4*>(Rt + (size_t)c * E + e0) =
             make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
     }
@@ -481,8 +513,9 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
     const int M = ctx->M, n2 = 2 * M, E = n2 * n2;
     const int J = (int)plan.node_tau.size();
     const cudaStream_t st = ctx->stream;
-    // temporary tables: node materials and tau, the nodes' D and R (FP64), the
-    // cell list, weights and bins
+    // temporary tables: node materials and tau, the nodes' D (FP64); kept in
+    // the context for the per-cell R on demand: the nodes' R (FP64), the cell
+    // list, the weights and the bins
     std::vector<void*> tmp;
     auto alloc = [&](size_t bytes) {
         void* p = nullptr;
@@ -497,10 +530,16 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
         int* nmat = static_cast<int*>(alloc(J * sizeof(int)));
         double* ntau = static_cast<double*>(alloc(J * sizeof(double)));
         double* Dn = static_cast<double*>(alloc((size_t)J * E * sizeof(double)));
-        double* Rn = static_cast<double*>(alloc((size_t)J * E * sizeof(double)));
-        int* cells = static_cast<int*>(alloc(plan.cells.size() * sizeof(int)));
-        double* wts = static_cast<double*>(alloc(plan.weights.size() * sizeof(double)));
-        int4* bins = static_cast<int4*>(alloc(plan.bins.size() * sizeof(int4)));
+        double* Rn = static_cast<double*>(dev_alloc(ctx, (size_t)J * E * sizeof(double)));
+        int* cells = static_cast<int*>(dev_alloc(ctx, plan.cells.size() * sizeof(int)));
+        double* wts = static_cast<double*>(dev_alloc(ctx, plan.weights.size() * sizeof(double)));
+        int4* bins = static_cast<int4*>(dev_alloc(ctx, plan.bins.size() * sizeof(int4)));
+        ctx->tab_Rn = Rn;
+        ctx->tab_cells = cells;
+        ctx->tab_wts = wts;
+        ctx->tab_bins = bins;
+        ctx->tab_nbins = (int)plan.bins.size();
+        ctx->rt_ready = false;
         up(nmat, plan.node_mat.data(), J * sizeof(int));
         up(ntau, plan.node_tau.data(), J * sizeof(double));
         up(cells, plan.cells.data(), plan.cells.size() * sizeof(int));
@@ -525,16 +564,31 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
         }
         build_response_tc(ctx, plan, Rn);
         {
-            ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * E * 12);
+            ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * E * 8);
             const dim3 grid((unsigned)plan.bins.size(), (unsigned)((E / 4 + 255) / 256));
-            k_interp_blocks<<<grid, 256, 0, st>>>(E, bins, cells, wts, Dn, Rn, ctx->Dt, ctx->Rt);
-            check(cudaGetLastError(), "k_interp_blocks");
+            k_interp_D<<<grid, 256, 0, st>>>(E, bins, cells, wts, Dn, ctx->Dt);
+            check(cudaGetLastError(), "k_interp_D");
         }
     } catch (...) {
         for (void* p : tmp) cudaFreeAsync(p, st);
         throw;
     }
     for (void* p : tmp) cudaFreeAsync(p, st);
+}
+
+void ensure_cell_response(rte_ctx* ctx) {
+    if (ctx->rt_ready) return;
+    if (!ctx->tab_Rn) throw StatusError{RTE_EINVAL, "per-cell response: no blocks"};
+    const int n2 = 2 * ctx->M, E = n2 * n2;
+    float* Rt = static_cast<float*>(dev_alloc(ctx, (size_t)ctx->N * E * sizeof(float)));
+    {
+        ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * E * 4);
+        const dim3 grid((unsigned)ctx->tab_nbins, (unsigned)((E / 4 + 255) / 256));
+        k_interp_R<<<grid, 256, 0, ctx->stream>>>(E, ctx->tab_bins, ctx->tab_cells, ctx->tab_wts, ctx->tab_Rn, Rt);
+        check(cudaGetLastError(), "k_interp_R");
+    }
+    ctx->Rt = Rt;
+    ctx->rt_ready = true;
 }
 
 namespace {
@@ -589,6 +643,7 @@ void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_d
 }
 
 void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scratch) {
+    ensure_cell_response(ctx);
     const int M = ctx->M, n2 = 2 * M, G = n2 / 4;
     int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
     const int g = (int)(want < cap ? want : cap);
@@ -659,6 +714,7 @@ void launch_response_apply(rte_ctx* ctx, const void* v, bool v_is_double, void* 
         launch_gather_tiles(ctx, v, v_is_double, w, w_is_double);
         return;
     }
+    ensure_cell_response(ctx);
     if (v_is_double)
         block_apply_t<float, double, float>(ctx, ctx->Rt, v, o, K_RESPONSE_APPLY, bytes);
     else
@@ -690,6 +746,7 @@ void launch_response_apply_df(rte_ctx* ctx, const float* z_hi, const float* z_lo
         launch_gather_tiles_df(ctx, z_hi, z_lo, w);
         return;
     }
+    ensure_cell_response(ctx);
     block_apply_t<float, float, float>(ctx, ctx->Rt, z_hi, o, K_RESPONSE_APPLY, bytes);
     int64_t want = (ctx->n + 255) / 256, cap = (int64_t)ctx->num_sms * 8;
     const int g = (int)(want < cap ? want : cap);

@@ -75,7 +75,16 @@ struct rte_ctx {
     float* coef_in = nullptr;        // [4][N] CoeffNet inputs: log sigma_T, log sigma_a, log eps, log tau
     double* b = nullptr;             // [n]
     double* Dt = nullptr;            // [N][2M][2M], Dt[c][j][i] = D_c[i][j]  (FP64)
-    float* Rt = nullptr;             // [N][2M][2M], Rt[c][i][row] = R_c[row][i] (FP32)
+    float* Rt = nullptr;             // [N][2M][2M], Rt[c][i][row] = R_c[row][i] (FP32); built on
+                                     // first use when the blocks are tabulated (ensure_cell_response)
+    bool rt_ready = false;
+    // tabulated blocks, kept for the per-cell R_C built on demand: the nodes'
+    // FP64 R, the bins, the cell list and the FP64 weights
+    double* tab_Rn = nullptr;
+    int4* tab_bins = nullptr;
+    int* tab_cells = nullptr;
+    double* tab_wts = nullptr;
+    int tab_nbins = 0;
 
     // scratch
     double* trace_out = nullptr;     // n elements (float or double) of outgoing traces
@@ -289,6 +298,9 @@ struct TabPlan {
     std::vector<int4> bins;          // (first node, first position, end position) in cells
 };
 void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_dev);
+// the per-cell FP32 R_C (ctx->Rt) of a tabulated context, built on first use
+// (the tensor-core response apply does not need it)
+void ensure_cell_response(rte_ctx* ctx);
 
 // response apply from the node tables on the tensor cores (response_tc.cu)
 bool response_tc_supported(int M);                     // 2M in {32, 64, 128}

@@ -555,7 +555,6 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     ctx->counter = static_cast<unsigned*>(dev_alloc(ctx, 64));
     ctx->scal = static_cast<double*>(dev_alloc(ctx, kScal * sizeof(double)));
     ctx->Dt = static_cast<double*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(double)));
-    ctx->Rt = static_cast<float*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(float)));
     launch_rhs(ctx);
     {
         std::vector<double> eh(N);
@@ -573,6 +572,8 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         ctx->tab_nodes = (int)plan.node_tau.size();
         launch_tabulated_blocks(ctx, plan, sing);
     } else {
+        ctx->Rt = static_cast<float*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(float)));
+        ctx->rt_ready = true;
         launch_build_invert(ctx, sing);
     }
     int sing_h = 0;
@@ -767,6 +768,7 @@ RTE_API rte_status rte_export_blocks(rte_ctx* ctx, double* D_host, float* R_host
                 for (size_t i = 0; i < n2; ++i) D_host[c * per + i * n2 + j] = tmp[c * per + j * n2 + i];
     }
     if (R_host) {
+        ensure_cell_response(ctx);
         std::vector<float> tmp(per * ctx->N);
         check(cudaMemcpyAsync(tmp.data(), ctx->Rt, tmp.size() * sizeof(float),
                               cudaMemcpyDeviceToHost, ctx->stream), "export response");

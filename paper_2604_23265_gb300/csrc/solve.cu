@@ -589,6 +589,7 @@ struct GroupRunner {
             }
             group_ortho_geometry_df(c, K, &nmd, &nud);
             f32 = f32 && s.opts.inner_precision == RTE_F32;
+            if (!tc) ensure_cell_response(c);
             it.Rt = c->Rt;
             it.z = s.zj;
             it.z_lo = s.zj_lo;
