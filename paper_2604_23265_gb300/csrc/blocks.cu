@@ -178,48 +178,72 @@ __global__ void __launch_bounds__(256) k_response(int M, const int* __restrict__
 // Blocks of a cell from tabulated nodes (set-up by interpolation in ln tau):
 // for the cells of bin b (all interpolating between the nodes node0 ..
 // node0 + 7), D_C = sum_p w_Cp D_p elementwise.  Block (b, y) holds the node
-// values of elements 1024 y .. 1024 y + 1023 in registers and writes them for
-// every cell of the bin.  bins[b] = (node0, first, end) positions in the cell
-// list.  The sums are double-float (df64.h: the node values and the weights
-// as float pairs, products by TwoProd, sums by TwoSum) on the FP32 pipe,
-// about 2^-46 relative: far below the FP64 inversion's own rounding of the
-// nodes, cond(G) 2^-52, and eight times faster than the FP64 pipe.
+// values of elements 1024 y .. 1024 y + 1023 in registers (df64, converted
+// once) and writes them for every cell of the bin.  bins[b] = (node0, first,
+// end) positions in the cell list; w16[pos] the position's weights as float
+// pairs (8 hi, 8 lo).  The sums are double-float on the FP32 pipe, two
+// elements a packed instruction (df64.h: TwoProd, TwoSum), about 2^-46
+// relative: far below the FP64 inversion's own rounding of the nodes,
+// cond(G) 2^-52.  The result stays df64 (hi and lo planes of the cell), so
+// no FP64 instruction runs per element: on this GPU the FP64 pipe (and the
+// conversions to and from double) is some 30 times narrower than FP32.
 __global__ void __launch_bounds__(256) k_interp_D(int E, const int4* __restrict__ bins,
-                                                  const int* __restrict__ cells, const double* __restrict__ wts,
-                                                  const double* __restrict__ Dn, double* __restrict__ Dt) {
+                                                  const int* __restrict__ cells, const float* __restrict__ w16,
+                                                  const double* __restrict__ Dn, float* __restrict__ Dt) {
+    using df::f2;
     const int4 bn = bins[blockIdx.x];
     const int e0 = (blockIdx.y * 256 + threadIdx.x) * 4;
     if (e0 >= E) return;                       // E = (2M)^2, a multiple of 4
-    float dh[8][4], dl[8][4];
+    f2 ah[8][2], al[8][2];                     // node p, element pairs (e0, e0 + 1), (e0 + 2, e0 + 3)
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const double2* dp = reinterpret_cast<const double2*>(Dn + (size_t)(bn.x + p) * E + e0);
         const double2 d0 = __ldg(dp), d1 = __ldg(dp + 1);
-        df::from_double(d0.x, dh[p][0], dl[p][0]);
-        df::from_double(d0.y, dh[p][1], dl[p][1]);
-        df::from_double(d1.x, dh[p][2], dl[p][2]);
-        df::from_double(d1.y, dh[p][3], dl[p][3]);
+        float h[4], l[4];
+        df::from_double(d0.x, h[0], l[0]);
+        df::from_double(d0.y, h[1], l[1]);
+        df::from_double(d1.x, h[2], l[2]);
+        df::from_double(d1.y, h[3], l[3]);
+        ah[p][0] = df::pk(h[0], h[1]);
+        al[p][0] = df::pk(l[0], l[1]);
+        ah[p][1] = df::pk(h[2], h[3]);
+        al[p][1] = df::pk(l[2], l[3]);
     }
     for (int pos = bn.y; pos < bn.z; ++pos) {
         const int c = __ldg(cells + pos);
-        float wh[8], wl[8];
+        const float4* wp = reinterpret_cast<const float4*>(w16 + (size_t)pos * 16);
+        const float4 h0 = __ldg(wp), h1 = __ldg(wp + 1), l0 = __ldg(wp + 2), l1 = __ldg(wp + 3);
+        const float wh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        const float wl[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+        f2 S[2] = {0ull, 0ull}, C[2] = {0ull, 0ull};
 #pragma unroll
-        for (int p = 0; p < 8; ++p) df::from_double(__ldg(wts + (size_t)pos * 8 + p), wh[p], wl[p]);
-        double d[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float S = 0.f, C = 0.f;
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                float pr, er;
-                df::mul(dh[p][q], dl[p][q], wh[p], wl[p], pr, er);
-                df::acc(S, C, pr, er);
-            }
-            d[q] = df::to_double(S, C);
+        for (int p = 0; p < 8; ++p) {
+            const f2 bh = df::pk(wh[p], wh[p]), nbh = df::pk(-wh[p], -wh[p]), nbl = df::pk(-wl[p], -wl[p]);
+            df::mac2(S[0], C[0], ah[p][0], al[p][0], nbh, nbl, bh);
+            df::mac2(S[1], C[1], ah[p][1], al[p][1], nbh, nbl, bh);
         }
-        double2* dd = reinterpret_cast<double2*>(Dt + (size_t)c * E + e0);
-        dd[0] = make_double2(d[0], d[1]);
-        dd[1] = make_double2(d[2], d[3]);
+        df::renorm2(S[0], C[0]);
+        df::renorm2(S[1], C[1]);
+        float o[8];
+        df::upk(S[0], o[0], o[1]);
+        df::upk(S[1], o[2], o[3]);
+        df::upk(C[0], o[4], o[5]);
+        df::upk(C[1], o[6], o[7]);
+        float* out = Dt + (size_t)c * 2 * E + e0;
+        *reinterpret_cast<float4*>(out) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(out + E) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+}
+
+// FP64 blocks [cells][E] (per-cell inversion) into the df64 planes of the
+// same cells of Dt
+__global__ void k_blocks_to_df(int64_t total, int E, const double* __restrict__ Dx, float* __restrict__ Dt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / E, i = e - c * E;
+        float h, l;
+        df::from_double(Dx[e], h, l);
+        Dt[c * 2 * E + i] = h;
+        Dt[c * 2 * E + E + i] = l;
     }
 }
 
@@ -444,37 +468,119 @@ __global__ void __launch_bounds__(256) k_response_t(int M, int N, const float* _
     }
 }
 
-// z_C = D_C^T r_C: output j = row j of Dt dotted with r (FP64 accumulation).
-template <typename TIN, typename TOUT>
-__global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const double* __restrict__ Dt,
-                                                       const TIN* __restrict__ r,
-                                                       TOUT* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char smb[];
-    double* rs = reinterpret_cast<double*>(smb);
-    const int n2 = 2 * M, G = n2 / 4;
-    const int cells = blockDim.x / G;
-    double* zs = rs + n2 * cells;
-    const int c0 = blockIdx.x * cells;
+// r (FP32 or FP64) of the block's cells into shared memory as df64 planes
+// [2M][cells]
+template <typename TIN>
+__device__ __forceinline__ void stage_df(int n2, int N, int c0, int cells, const TIN* __restrict__ r, float* rh,
+                                         float* rl) {
     for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
         const int j = e / cells, cc = e - j * cells;
         const int c = c0 + cc;
-        rs[e] = (c < N) ? (double)r[(size_t)j * N + c] : 0.0;
+        float h = 0.f, l = 0.f;
+        if (c < N) {
+            if (sizeof(TIN) == 8)
+                df::from_double((double)r[(size_t)j * N + c], h, l);
+            else
+                h = (float)r[(size_t)j * N + c];
+        }
+        rh[e] = h;
+        rl[e] = l;
     }
+}
+
+// z_C = D_C r_C with D_C as df64 planes (Dt[c][0][j][i] + Dt[c][1][j][i] =
+// D_C[i][j]).  G = 2M/4 threads a cell, four consecutive rows i each, two per
+// packed df64 accumulator; r staged in shared memory as df64.  The sums are
+// df64 (TwoProd and TwoSum on the FP32 pipe, renormalised every 8 terms), as
+// accurate as an FP64 sum of the 2M terms, and the kernel is bound by HBM,
+// not by the FP64 pipe.
+template <typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256) k_block_apply_df(int M, int N, const float* __restrict__ Dt,
+                                                        const TIN* __restrict__ r, TOUT* __restrict__ z) {
+    using df::f2;
+    extern __shared__ __align__(16) unsigned char smb[];
+    const int n2 = 2 * M, G = n2 / 4, E = n2 * n2;
+    const int cells = blockDim.x / G;
+    float* rh = reinterpret_cast<float*>(smb);
+    float* rl = rh + n2 * cells;
+    double* zs = reinterpret_cast<double*>(rl + n2 * cells);
+    const int c0 = blockIdx.x * cells;
+    stage_df<TIN>(n2, N, c0, cells, r, rh, rl);
     __syncthreads();
     const int cc = threadIdx.x / G, g = threadIdx.x - cc * G;
     const int c = c0 + cc;
     if (cc < cells && c < N) {
-        const double* D = Dt + (size_t)c * n2 * n2;
+        const float* Xh = Dt + (size_t)c * 2 * E + 4 * g;
+        const float* Xl = Xh + E;
+        f2 S0 = 0ull, C0 = 0ull, S1 = 0ull, C1 = 0ull;
+        for (int j0 = 0; j0 < n2; j0 += 8) {
+#pragma unroll
+            for (int j = j0; j < j0 + 8; ++j) {
+                const float4 dh = __ldg(reinterpret_cast<const float4*>(Xh + (size_t)j * n2));
+                const float4 dl = __ldg(reinterpret_cast<const float4*>(Xl + (size_t)j * n2));
+                const float vh = rh[j * cells + cc], vl = rl[j * cells + cc];
+                const f2 bh = df::pk(vh, vh), nbh = df::pk(-vh, -vh), nbl = df::pk(-vl, -vl);
+                df::mac2(S0, C0, df::pk(dh.x, dh.y), df::pk(dl.x, dl.y), nbh, nbl, bh);
+                df::mac2(S1, C1, df::pk(dh.z, dh.w), df::pk(dl.z, dl.w), nbh, nbl, bh);
+            }
+            df::renorm2(S0, C0);
+            df::renorm2(S1, C1);
+        }
+        float s[4], t[4];
+        df::upk(S0, s[0], s[1]);
+        df::upk(S1, s[2], s[3]);
+        df::upk(C0, t[0], t[1]);
+        df::upk(C1, t[2], t[3]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zs[(4 * g + q) * cells + cc] = df::to_double(s[q], t[q]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2 * cells; e += blockDim.x) {
+        const int i = e / cells, c2 = e - i * cells;
+        if (c0 + c2 < N) z[(size_t)i * N + c0 + c2] = (TOUT)zs[e];
+    }
+}
+
+// z_C = D_C^T r_C: output j = row j of the planes dotted with r (df64 sums,
+// even and odd i in the two halves of a packed accumulator).
+template <typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const float* __restrict__ Dt,
+                                                       const TIN* __restrict__ r, TOUT* __restrict__ z) {
+    using df::f2;
+    extern __shared__ __align__(16) unsigned char smb[];
+    const int n2 = 2 * M, G = n2 / 4, E = n2 * n2;
+    const int cells = blockDim.x / G;
+    float* rh = reinterpret_cast<float*>(smb);
+    float* rl = rh + n2 * cells;
+    double* zs = reinterpret_cast<double*>(rl + n2 * cells);
+    const int c0 = blockIdx.x * cells;
+    stage_df<TIN>(n2, N, c0, cells, r, rh, rl);
+    __syncthreads();
+    const int cc = threadIdx.x / G, g = threadIdx.x - cc * G;
+    const int c = c0 + cc;
+    if (cc < cells && c < N) {
+        const float* Xh = Dt + (size_t)c * 2 * E;
         for (int t = 0; t < 4; ++t) {
             const int j = 4 * g + t;
-            const double2* row = reinterpret_cast<const double2*>(D + (size_t)j * n2);
-            double acc = 0.0;
-            for (int i2 = 0; i2 < n2 / 2; ++i2) {
-                const double2 d = __ldg(row + i2);
-                acc = fma(d.x, rs[(2 * i2 + 0) * cells + cc], acc);
-                acc = fma(d.y, rs[(2 * i2 + 1) * cells + cc], acc);
+            const float2* rowh = reinterpret_cast<const float2*>(Xh + (size_t)j * n2);
+            const float2* rowl = reinterpret_cast<const float2*>(Xh + E + (size_t)j * n2);
+            f2 S = 0ull, C = 0ull;
+            for (int i0 = 0; i0 < n2 / 2; i0 += 8) {
+                for (int i2 = i0; i2 < i0 + 8 && i2 < n2 / 2; ++i2) {
+                    const float2 dh = __ldg(rowh + i2), dl = __ldg(rowl + i2);
+                    const float xh = rh[(2 * i2) * cells + cc], yh = rh[(2 * i2 + 1) * cells + cc];
+                    const float xl = rl[(2 * i2) * cells + cc], yl = rl[(2 * i2 + 1) * cells + cc];
+                    df::mac2(S, C, df::pk(dh.x, dh.y), df::pk(dl.x, dl.y), df::pk(-xh, -yh), df::pk(-xl, -yl),
+                             df::pk(xh, yh));
+                }
+                df::renorm2(S, C);
             }
-            zs[j * cells + cc] = acc;
+            float sx, sy, cx, cy, h, l;
+            df::upk(S, sx, sy);
+            df::upk(C, cx, cy);
+            df::two_sum(sx, sy, h, l);
+            l = __fadd_rn(l, __fadd_rn(cx, cy));
+            zs[j * cells + cc] = df::to_double(h, l);
         }
     }
     __syncthreads();
@@ -487,26 +593,47 @@ __global__ void __launch_bounds__(256) k_block_apply_t(int M, int N, const doubl
 }  // namespace
 
 void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
-    const int M = ctx->M, n2 = 2 * M;
+    const int M = ctx->M, n2 = 2 * M, E = n2 * n2, N = ctx->N;
     const size_t smem = sizeof(double) * ((size_t)n2 * (n2 + 1) + 3 * n2);
     raise_smem_limit((const void*)k_build_invert, (size_t)(smem));
+    const size_t smem2 = sizeof(double) * ((size_t)n2 * (n2 + 1) + n2);
+    raise_smem_limit((const void*)k_response<float>, (size_t)(smem2));
     // one CTA per SM fits (the block is 2M x (2M+1) doubles): 16 warps hide
     // the shared-memory and FP64 latencies of the elimination
     const int threads_inv = n2 >= 128 ? 512 : (n2 >= 64 ? 256 : 128);
     const int threads = n2 >= 64 ? 256 : 128;
-    {
-        ProfScope ps(ctx, K_INVERT, (double)ctx->N * n2 * n2 * 8);
-        k_build_invert<<<ctx->N, threads_inv, smem, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi,
-                                                               ctx->L64, ctx->rowdir, ctx->Dt,
-                                                               singular_dev);
-        check(cudaGetLastError(), "k_build_invert");
+    // batches of cells: the FP64 inverses of a batch feed the response
+    // matrices, then are stored as df64 planes
+    const int batch = N < 16384 ? N : 16384;
+    double* Dx = nullptr;
+    check(cudaMallocAsync(reinterpret_cast<void**>(&Dx), (size_t)batch * E * sizeof(double), ctx->stream),
+          "cudaMallocAsync (inverses)");
+    try {
+        for (int c0 = 0; c0 < N; c0 += batch) {
+            const int nc = N - c0 < batch ? N - c0 : batch;
+            {
+                ProfScope ps(ctx, K_INVERT, (double)nc * E * 8);
+                k_build_invert<<<nc, threads_inv, smem, ctx->stream>>>(M, ctx->mat + c0, ctx->tau + c0, ctx->xi,
+                                                                       ctx->L64, ctx->rowdir, Dx, singular_dev);
+                check(cudaGetLastError(), "k_build_invert");
+            }
+            {
+                ProfScope ps(ctx, K_RESPONSE, (double)nc * E * 12);
+                k_response<float><<<nc, threads, smem2, ctx->stream>>>(M, ctx->mat + c0, ctx->tau + c0, ctx->xi,
+                                                                       ctx->L64, ctx->rowdir, Dx,
+                                                                       ctx->Rt + (size_t)c0 * E);
+                check(cudaGetLastError(), "k_response");
+            }
+            const int64_t total = (int64_t)nc * E;
+            const int g = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 16);
+            k_blocks_to_df<<<g, 256, 0, ctx->stream>>>(total, E, Dx, ctx->Dt + (size_t)c0 * 2 * E);
+            check(cudaGetLastError(), "k_blocks_to_df");
+        }
+    } catch (...) {
+        cudaFreeAsync(Dx, ctx->stream);
+        throw;
     }
-    const size_t smem2 = sizeof(double) * ((size_t)n2 * (n2 + 1) + n2);
-    raise_smem_limit((const void*)k_response<float>, (size_t)(smem2));
-    ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * n2 * n2 * 12);
-    k_response<float><<<ctx->N, threads, smem2, ctx->stream>>>(M, ctx->mat, ctx->tau, ctx->xi, ctx->L64,
-                                                               ctx->rowdir, ctx->Dt, ctx->Rt);
-    check(cudaGetLastError(), "k_response");
+    check(cudaFreeAsync(Dx, ctx->stream), "cudaFreeAsync (inverses)");
 }
 
 void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_dev) {
@@ -533,10 +660,12 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
         double* Rn = static_cast<double*>(dev_alloc(ctx, (size_t)J * E * sizeof(double)));
         int* cells = static_cast<int*>(dev_alloc(ctx, plan.cells.size() * sizeof(int)));
         double* wts = static_cast<double*>(dev_alloc(ctx, plan.weights.size() * sizeof(double)));
+        float* w16 = static_cast<float*>(dev_alloc(ctx, plan.weights.size() * 2 * sizeof(float)));
         int4* bins = static_cast<int4*>(dev_alloc(ctx, plan.bins.size() * sizeof(int4)));
         ctx->tab_Rn = Rn;
         ctx->tab_cells = cells;
         ctx->tab_wts = wts;
+        ctx->tab_w16 = w16;
         ctx->tab_bins = bins;
         ctx->tab_nbins = (int)plan.bins.size();
         ctx->rt_ready = false;
@@ -544,6 +673,16 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
         up(ntau, plan.node_tau.data(), J * sizeof(double));
         up(cells, plan.cells.data(), plan.cells.size() * sizeof(int));
         up(wts, plan.weights.data(), plan.weights.size() * sizeof(double));
+        // the weights as float pairs (8 hi, then 8 lo a position)
+        std::vector<float> w16h(plan.weights.size() * 2);
+        for (size_t pos = 0; pos < plan.weights.size() / 8; ++pos)
+            for (int p = 0; p < 8; ++p) {
+                const double w = plan.weights[pos * 8 + p];
+                const float hi = (float)w;
+                w16h[pos * 16 + p] = hi;
+                w16h[pos * 16 + 8 + p] = (float)(w - (double)hi);
+            }
+        up(w16, w16h.data(), w16h.size() * sizeof(float));
         up(bins, plan.bins.data(), plan.bins.size() * sizeof(int4));
         const size_t smem = sizeof(double) * ((size_t)n2 * (n2 + 1) + 3 * n2);
         raise_smem_limit((const void*)k_build_invert, smem);
@@ -566,7 +705,7 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
         {
             ProfScope ps(ctx, K_RESPONSE, (double)ctx->N * E * 8);
             const dim3 grid((unsigned)plan.bins.size(), (unsigned)((E / 4 + 255) / 256));
-            k_interp_D<<<grid, 256, 0, st>>>(E, bins, cells, wts, Dn, ctx->Dt);
+            k_interp_D<<<grid, 256, 0, st>>>(E, bins, cells, w16, Dn, ctx->Dt);
             check(cudaGetLastError(), "k_interp_D");
         }
     } catch (...) {
@@ -612,34 +751,33 @@ void launch_block_apply(rte_ctx* ctx, bool transpose, const void* r, bool r_is_d
     const int M = ctx->M, n2 = 2 * M, G = n2 / 4;
     const double bytes = (double)ctx->N * n2 * n2 * 8 +
                          (double)ctx->n * ((r_is_double ? 8 : 4) + (z_is_double ? 8 : 4));
-    if (!transpose) {
-        if (r_is_double && z_is_double)
-            block_apply_t<double, double, double>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
-        else if (r_is_double)
-            block_apply_t<double, double, float>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
-        else if (z_is_double)
-            block_apply_t<double, float, double>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
-        else
-            block_apply_t<double, float, float>(ctx, ctx->Dt, r, z, K_BLOCK, bytes);
-        return;
-    }
     const int threads = G >= 256 ? G : (256 / G) * G;
     const int cells = threads / G;
     const int blocks = (ctx->N + cells - 1) / cells;
-    const size_t smem = sizeof(double) * 2 * n2 * cells;
-    ProfScope ps(ctx, K_BLOCK_T, bytes);
-    if (r_is_double && z_is_double) {
-        raise_smem_limit((const void*)k_block_apply_t<double, double>, smem);
-        k_block_apply_t<double, double><<<blocks, threads, smem, ctx->stream>>>(
-            M, ctx->N, ctx->Dt, (const double*)r, (double*)z);
-    } else if (!r_is_double && !z_is_double) {
-        raise_smem_limit((const void*)k_block_apply_t<float, float>, smem);
-        k_block_apply_t<float, float><<<blocks, threads, smem, ctx->stream>>>(
-            M, ctx->N, ctx->Dt, (const float*)r, (float*)z);
-    } else {
-        throw StatusError{RTE_EINVAL, "transposed block apply needs matching precisions"};
+    // r as df64 planes and z in FP64
+    const size_t smem = (2 * sizeof(float) + sizeof(double)) * n2 * cells;
+    auto run = [&](auto kern, auto rp, auto zp) {
+        raise_smem_limit((const void*)kern, smem);
+        kern<<<blocks, threads, smem, ctx->stream>>>(M, ctx->N, ctx->Dt, rp, zp);
+    };
+    {
+        ProfScope ps(ctx, transpose ? K_BLOCK_T : K_BLOCK, bytes);
+        const double* rd = static_cast<const double*>(r);
+        const float* rf = static_cast<const float*>(r);
+        double* zd = static_cast<double*>(z);
+        float* zf = static_cast<float*>(z);
+        if (!transpose) {
+            if (r_is_double && z_is_double) run(k_block_apply_df<double, double>, rd, zd);
+            else if (r_is_double) run(k_block_apply_df<double, float>, rd, zf);
+            else if (z_is_double) run(k_block_apply_df<float, double>, rf, zd);
+            else run(k_block_apply_df<float, float>, rf, zf);
+        } else {
+            if (r_is_double && z_is_double) run(k_block_apply_t<double, double>, rd, zd);
+            else if (!r_is_double && !z_is_double) run(k_block_apply_t<float, float>, rf, zf);
+            else throw StatusError{RTE_EINVAL, "transposed block apply needs matching precisions"};
+        }
     }
-    check(cudaGetLastError(), "k_block_apply_t");
+    check(cudaGetLastError(), transpose ? "k_block_apply_t" : "k_block_apply_df");
 }
 
 void launch_response_apply_t(rte_ctx* ctx, const float* u, float* w, float* scratch) {

@@ -546,14 +546,6 @@ void build_response_tc(rte_ctx* ctx, const TabPlan& plan, const double* Rn) {
     }
     // the longest tiles start first
     std::stable_sort(tiles.begin(), tiles.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
-    std::vector<float> w16(plan.weights.size() * 2);
-    for (int pos = 0; pos < N; ++pos)
-        for (int p = 0; p < 8; ++p) {
-            const double w = plan.weights[(size_t)pos * 8 + p];
-            const float hi = (float)w;
-            w16[(size_t)pos * 16 + p] = hi;
-            w16[(size_t)pos * 16 + 8 + p] = (float)(w - (double)hi);
-        }
     double sum_nodes = 0.0;
     for (const int4& t : tiles) sum_nodes += t.w;
 
@@ -561,7 +553,7 @@ void build_response_tc(rte_ctx* ctx, const TabPlan& plan, const double* Rn) {
     ctx->tc_tiles = static_cast<int4*>(dev_alloc(ctx, tiles.size() * sizeof(int4)));
     ctx->tc_first = static_cast<int*>(dev_alloc(ctx, (size_t)N * sizeof(int)));
     ctx->tc_pos_of = static_cast<int*>(dev_alloc(ctx, (size_t)N * sizeof(int)));
-    ctx->tc_w16 = static_cast<float*>(dev_alloc(ctx, w16.size() * sizeof(float)));
+    ctx->tc_w16 = ctx->tab_w16;              // Lagrange weights as float pairs
     auto up = [&](void* dst, const void* src, size_t bytes) {
         check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "h2d (response tables)");
     };
@@ -570,7 +562,6 @@ void build_response_tc(rte_ctx* ctx, const TabPlan& plan, const double* Rn) {
     for (int p = 0; p < N; ++p) pos_of[plan.cells[p]] = p;
     up(ctx->tc_pos_of, pos_of.data(), (size_t)N * sizeof(int));
     up(ctx->tc_first, first.data(), (size_t)N * sizeof(int));
-    up(ctx->tc_w16, w16.data(), w16.size() * sizeof(float));
     const int64_t total = (int64_t)J * NO * NO;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 16);
     if (NO == 32) k_pack_nodes<32><<<blocks, 256, 0, st>>>(J, Rn, ctx->tc_nodes);

@@ -74,7 +74,8 @@ struct rte_ctx {
     double* inflow = nullptr;        // [4][I][M]
     float* coef_in = nullptr;        // [4][N] CoeffNet inputs: log sigma_T, log sigma_a, log eps, log tau
     double* b = nullptr;             // [n]
-    double* Dt = nullptr;            // [N][2M][2M], Dt[c][j][i] = D_c[i][j]  (FP64)
+    float* Dt = nullptr;             // [N][2][2M][2M] df64 planes per cell, hi then lo:
+                                     // Dt[c][0][j][i] + Dt[c][1][j][i] = D_c[i][j]
     float* Rt = nullptr;             // [N][2M][2M], Rt[c][i][row] = R_c[row][i] (FP32); built on
                                      // first use when the blocks are tabulated (ensure_cell_response)
     bool rt_ready = false;
@@ -84,6 +85,7 @@ struct rte_ctx {
     int4* tab_bins = nullptr;
     int* tab_cells = nullptr;
     double* tab_wts = nullptr;
+    float* tab_w16 = nullptr;        // [N][16] the weights as float pairs: 8 hi, then 8 lo
     int tab_nbins = 0;
 
     // scratch
@@ -101,7 +103,7 @@ struct rte_ctx {
     int4* tc_tiles = nullptr;        // (first position, cells, first node, nodes)
     int* tc_pos_of = nullptr;        // [N] position of each cell in the list ordered by stencil
     int* tc_first = nullptr;         // [N] first stencil node per position
-    float* tc_w16 = nullptr;         // [N][16] Lagrange weights per position, 8 hi then 8 lo floats
+    float* tc_w16 = nullptr;         // [N][16] Lagrange weights per position (tab_w16)
     int tc_ntiles = 0;               // 0: no node tables
     double tc_mma_flops = 0.0;       // issued tensor flops per apply
     double tc_bytes = 0.0;           // algorithmic bytes per apply
@@ -118,6 +120,7 @@ namespace rte {
 void set_error(rte_ctx* ctx, const std::string& msg);
 rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where);
 void* dev_alloc(rte_ctx* ctx, size_t bytes);      // tracked, zeroed; throws on failure
+void* dev_alloc_raw(rte_ctx* ctx, size_t bytes);  // tracked, not zeroed (the caller writes all of it)
 void free_workspace(rte_ctx* ctx);                 // releases the rte_solve buffers
 
 struct CudaError {
@@ -282,8 +285,9 @@ void atfps_comp_precond(rte_ctx* ctx, const double* z, double* out);
 void atfps_layers(rte_ctx* ctx, double* x);
 
 // block kernels (blocks.cu) ------------------------------------------------
-// builds G_C for every cell, inverts it into ctx->Dt (FP64) and forms the
-// response matrices ctx->Rt (FP32); *singular_dev set to 1 on a zero pivot.
+// builds G_C for every cell, inverts it in FP64 into ctx->Dt (stored as df64)
+// and forms the response matrices ctx->Rt (FP32); *singular_dev set to 1 on a
+// zero pivot.
 void launch_build_invert(rte_ctx* ctx, int* singular_dev);
 // Set-up by interpolation in ln tau (few materials, many cells): nodes of
 // each material at tau = exp(s ds) on a uniform grid of s covering the

@@ -11,9 +11,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 
 #include "rte_internal.h"
 
@@ -31,7 +33,7 @@ rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where) {
     return (e == cudaErrorMemoryAllocation) ? RTE_ENOMEM : RTE_ECUDA;
 }
 
-void* dev_alloc(rte_ctx* ctx, size_t bytes) {
+void* dev_alloc_raw(rte_ctx* ctx, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
     // stream-ordered: a context's allocations and frees never synchronise
@@ -40,7 +42,12 @@ void* dev_alloc(rte_ctx* ctx, size_t bytes) {
     if (e != cudaSuccess) throw CudaError{e, "cudaMallocAsync"};
     ctx->allocations.push_back(p);
     ctx->device_bytes += bytes;
-    check(cudaMemsetAsync(p, 0, bytes, ctx->stream), "cudaMemset");
+    return p;
+}
+
+void* dev_alloc(rte_ctx* ctx, size_t bytes) {
+    void* p = dev_alloc_raw(ctx, bytes);
+    check(cudaMemsetAsync(p, 0, bytes == 0 ? 16 : bytes, ctx->stream), "cudaMemset");
     return p;
 }
 
@@ -368,10 +375,11 @@ constexpr int kTabMinCells = 4096;
 bool plan_tabulation(rte_ctx* ctx, const std::vector<double>& tau, TabPlan& plan) {
     const int N = ctx->N, nmat = ctx->nmat;
     if (ctx->block_mode == RTE_BLOCKS_EXACT) return false;
-    std::vector<double> smin(nmat, 1e300), smax(nmat, -1e300);
+    std::vector<double> smin(nmat, 1e300), smax(nmat, -1e300), lt(N);
     for (int c = 0; c < N; ++c) {
         const int j = ctx->mat_h[c];
         const double sv = std::log(tau[c]);
+        lt[c] = sv;
         smin[j] = std::min(smin[j], sv);
         smax[j] = std::max(smax[j], sv);
     }
@@ -391,20 +399,30 @@ bool plan_tabulation(rte_ctx* ctx, const std::vector<double>& tau, TabPlan& plan
             plan.node_mat[i] = j;
             plan.node_tau[i] = std::exp((double)(base[j] + (i - off[j])) * kTabStep);
         }
-    // stencil of every cell: nodes fl - 3 .. fl + 4 around t = ln(tau) / ds
+    // stencil of every cell: nodes fl - 3 .. fl + 4 around t = ln(tau) / ds;
+    // Lagrange weight m = prod_{q != m} (t - t_q) / prod_{q != m} (m - q),
+    // the numerator from prefix and suffix products
+    double inv_den[8];
+    for (int m = 0; m < 8; ++m) {
+        double d = 1.0;
+        for (int q = 0; q < 8; ++q)
+            if (q != m) d *= (double)(m - q);
+        inv_den[m] = 1.0 / d;
+    }
     std::vector<int> first(N);
     std::vector<double> w((size_t)N * 8);
     for (int c = 0; c < N; ++c) {
         const int j = ctx->mat_h[c];
-        const double t = std::log(tau[c]) / kTabStep;
+        const double t = lt[c] / kTabStep;
         const long long fl = (long long)std::floor(t);
         first[c] = (int)(off[j] + (fl - 3 - base[j]));
-        for (int m = 0; m < 8; ++m) {
-            double v = 1.0;
-            for (int q = 0; q < 8; ++q)
-                if (q != m) v *= (t - (double)(fl - 3 + q)) / (double)(m - q);
-            w[(size_t)c * 8 + m] = v;
-        }
+        double dq[8], pre[8], suf[8];
+        for (int q = 0; q < 8; ++q) dq[q] = t - (double)(fl - 3 + q);
+        pre[0] = 1.0;
+        for (int q = 1; q < 8; ++q) pre[q] = pre[q - 1] * dq[q - 1];
+        suf[7] = 1.0;
+        for (int q = 6; q >= 0; --q) suf[q] = suf[q + 1] * dq[q + 1];
+        for (int m = 0; m < 8; ++m) w[(size_t)c * 8 + m] = pre[m] * suf[m] * inv_den[m];
     }
     // bins by first node (counting sort, cells in ascending order per bin)
     std::vector<int> nb(J + 1, 0);
@@ -466,16 +484,43 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     const bool dev_eig = ctx->nmat > kHostEigenMaterials;
     ctx->xi_h.assign((size_t)ctx->nmat * n2, 0.0);
     if (!dev_eig) ctx->L_h.assign((size_t)ctx->nmat * M * n2, 0.0);
+    // a few materials: the eigenproblems (material, axis) are independent and
+    // run on host threads
+    std::vector<std::vector<double>> exs, els;
+    if (!dev_eig) {
+        const int nt = 2 * ctx->nmat;
+        std::vector<double> omv(ctx->nmat);
+        for (auto& kv : mats) omv[kv.second] = std::min(kv.first, 1.0);
+        exs.resize(nt);
+        els.resize(nt);
+        std::vector<std::exception_ptr> errs(nt);
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            for (int t; (t = next.fetch_add(1)) < nt;) {
+                try {
+                    eigenbasis(M, omv[t / 2], K, t % 2 == 0 ? cdir : sdir, t % 2, exs[t], els[t]);
+                } catch (...) {
+                    errs[t] = std::current_exception();
+                }
+            }
+        };
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nthreads = std::min<int>(nt, hw > 1 ? (int)hw : 1);
+        std::vector<std::thread> pool;
+        for (int w = 1; w < nthreads; ++w) pool.emplace_back(work);
+        work();
+        for (auto& th : pool) th.join();
+        for (auto& e : errs)
+            if (e) std::rethrow_exception(e);
+    }
     for (auto& kv : mats) {
         if (dev_eig) break;
-        std::vector<double> xx, Lx, xy, Ly;
-        eigenbasis(M, std::min(kv.first, 1.0), K, cdir, 0, xx, Lx);
-        eigenbasis(M, std::min(kv.first, 1.0), K, sdir, 1, xy, Ly);
+        const int j = kv.second;
+        const std::vector<double>&xx = exs[2 * j], &Lx = els[2 * j], &xy = exs[2 * j + 1], &Ly = els[2 * j + 1];
         for (int k = 0; k < M2; ++k) {
             if (!(xx[k] < 0 && xx[M2 + k] > 0 && xy[k] < 0 && xy[M2 + k] > 0))
                 throw StatusError{RTE_ESINGULAR, "eigenvalue inertia is not M/2 negative, M/2 positive"};
         }
-        const int j = kv.second;
         for (int k = 0; k < M; ++k) {
             ctx->xi_h[(size_t)j * n2 + k] = xx[k];
             ctx->xi_h[(size_t)j * n2 + M + k] = xy[k];
@@ -554,7 +599,8 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         dev_alloc(ctx, (size_t)ctx->max_red_blocks * (kMaxKrylov + 1) * sizeof(double)));
     ctx->counter = static_cast<unsigned*>(dev_alloc(ctx, 64));
     ctx->scal = static_cast<double*>(dev_alloc(ctx, kScal * sizeof(double)));
-    ctx->Dt = static_cast<double*>(dev_alloc(ctx, (size_t)N * n2 * n2 * sizeof(double)));
+    // every element of D is written by the set-up kernels
+    ctx->Dt = static_cast<float*>(dev_alloc_raw(ctx, (size_t)N * 2 * n2 * n2 * sizeof(float)));
     launch_rhs(ctx);
     {
         std::vector<double> eh(N);
@@ -759,13 +805,17 @@ RTE_API rte_status rte_export_blocks(rte_ctx* ctx, double* D_host, float* R_host
     RTE_GUARD_BEGIN
     const size_t n2 = 2 * (size_t)ctx->M, per = n2 * n2;
     if (D_host) {
-        std::vector<double> tmp(per * ctx->N);
-        check(cudaMemcpyAsync(tmp.data(), ctx->Dt, tmp.size() * sizeof(double),
+        std::vector<float> tmp(2 * per * ctx->N);
+        check(cudaMemcpyAsync(tmp.data(), ctx->Dt, tmp.size() * sizeof(float),
                               cudaMemcpyDeviceToHost, ctx->stream), "export blocks");
         check(cudaStreamSynchronize(ctx->stream), "export sync");
-        for (int c = 0; c < ctx->N; ++c)
+        for (int c = 0; c < ctx->N; ++c) {
+            const float* hi = tmp.data() + 2 * c * per;
+            const float* lo = hi + per;
             for (size_t j = 0; j < n2; ++j)
-                for (size_t i = 0; i < n2; ++i) D_host[c * per + i * n2 + j] = tmp[c * per + j * n2 + i];
+                for (size_t i = 0; i < n2; ++i)
+                    D_host[c * per + i * n2 + j] = (double)hi[j * n2 + i] + (double)lo[j * n2 + i];
+        }
     }
     if (R_host) {
         ensure_cell_response(ctx);
