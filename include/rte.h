@@ -167,7 +167,16 @@ typedef enum rte_response_path {
 RTE_API rte_status rte_set_response_path(rte_ctx* ctx, int path);
 RTE_API int rte_response_on_tensor_cores(const rte_ctx* ctx);
 
+/* Frees the context's device memory (stream-ordered on its stream).  The
+ * blocks return to the library's memory pool of the device, which keeps up
+ * to a quarter of the device memory mapped for the next context; see
+ * rte_trim_memory. */
 RTE_API void rte_destroy(rte_ctx* ctx);
+
+/* Returns every unused block of the library's memory pools to the devices
+ * (cudaMemPoolTrimTo(pool, 0)); blocks still held by live contexts stay.
+ * RTE_ECUDA on a CUDA error. */
+RTE_API rte_status rte_trim_memory(void);
 
 /* Message of the last error of ctx (or of the calling thread if ctx is NULL). */
 RTE_API const char* rte_last_error(const rte_ctx* ctx);

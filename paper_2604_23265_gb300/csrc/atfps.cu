@@ -376,7 +376,7 @@ template <typename T>
 T* atfps_alloc(rte_ctx* ctx, Atfps* a, size_t count) {
     void* p = nullptr;
     const size_t bytes = count * sizeof(T) + 16;
-    check(cudaMallocAsync(&p, bytes, ctx->stream), "cudaMallocAsync (ATFPS)");
+    check(pool_malloc(&p, bytes, ctx->stream), "cudaMallocFromPoolAsync (ATFPS)");
     a->allocs.push_back(p);
     a->bytes += bytes;
     ctx->device_bytes += bytes;

@@ -606,8 +606,8 @@ void launch_build_invert(rte_ctx* ctx, int* singular_dev) {
     // matrices, then are stored as df64 planes
     const int batch = N < 16384 ? N : 16384;
     double* Dx = nullptr;
-    check(cudaMallocAsync(reinterpret_cast<void**>(&Dx), (size_t)batch * E * sizeof(double), ctx->stream),
-          "cudaMallocAsync (inverses)");
+    check(pool_malloc(reinterpret_cast<void**>(&Dx), (size_t)batch * E * sizeof(double), ctx->stream),
+          "cudaMallocFromPoolAsync (inverses)");
     try {
         for (int c0 = 0; c0 < N; c0 += batch) {
             const int nc = N - c0 < batch ? N - c0 : batch;
@@ -646,7 +646,7 @@ void launch_tabulated_blocks(rte_ctx* ctx, const TabPlan& plan, int* singular_de
     std::vector<void*> tmp;
     auto alloc = [&](size_t bytes) {
         void* p = nullptr;
-        check(cudaMallocAsync(&p, bytes, st), "cudaMallocAsync (tabulated blocks)");
+        check(pool_malloc(&p, bytes, st), "cudaMallocFromPoolAsync (tabulated blocks)");
         tmp.push_back(p);
         return p;
     };

@@ -295,7 +295,7 @@ void device_eigenbases(rte_ctx* ctx, const std::vector<double>& omg, const std::
     const size_t bytes = al(omg.size() * 8) + al(K.size() * 8) + 3 * al((size_t)M * 8) + al(pairm.size() * 4) +
                          al(refl.size() * 4) + al(pencils * h * 8) + al(pencils * h * M * 8) + al(4);
     char* buf = nullptr;
-    check(cudaMallocAsync(&buf, bytes, ctx->stream), "cudaMallocAsync (eigenbases)");
+    check(pool_malloc(reinterpret_cast<void**>(&buf), bytes, ctx->stream), "cudaMallocFromPoolAsync (eigenbases)");
     struct Scratch {                    // released on every path out of here
         char* p;
         cudaStream_t st;

@@ -119,6 +119,9 @@ namespace rte {
 // error helpers ------------------------------------------------------------
 void set_error(rte_ctx* ctx, const std::string& msg);
 rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where);
+// stream-ordered allocation from the library's memory pool of the current
+// device (freed with cudaFreeAsync)
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
 void* dev_alloc(rte_ctx* ctx, size_t bytes);      // tracked, zeroed; throws on failure
 void* dev_alloc_raw(rte_ctx* ctx, size_t bytes);  // tracked, not zeroed (the caller writes all of it)
 void free_workspace(rte_ctx* ctx);                 // releases the rte_solve buffers

@@ -176,8 +176,8 @@ void worker_main(rte_server* s, int slot) {
                 const int64_t n = (int64_t)2 * job->M * job->I * job->I;
                 double* x = nullptr;
                 double* psi = nullptr;
-                cudaError_t e = cudaMallocAsync(&x, n * sizeof(double), st);
-                if (e == cudaSuccess) e = cudaMallocAsync(&psi, (size_t)job->M * job->I * job->I * sizeof(double), st);
+                cudaError_t e = pool_malloc(reinterpret_cast<void**>(&x), n * sizeof(double), st);
+                if (e == cudaSuccess) e = pool_malloc(reinterpret_cast<void**>(&psi), (size_t)job->M * job->I * job->I * sizeof(double), st);
                 if (e != cudaSuccess) {
                     job->status = RTE_ENOMEM;
                     job->err = cudaGetErrorString(e);
@@ -294,9 +294,9 @@ void setup_main(rte_server* s) {
                                     s->gst, &job->ctx);
             if (job->status == RTE_OK) {
                 const int64_t n = (int64_t)2 * job->M * job->I * job->I;
-                cudaError_t e = cudaMallocAsync(&job->x, n * sizeof(double), s->gst);
+                cudaError_t e = pool_malloc(reinterpret_cast<void**>(&job->x), n * sizeof(double), s->gst);
                 if (e == cudaSuccess)
-                    e = cudaMallocAsync(&job->psi_dev, (size_t)job->M * job->I * job->I * sizeof(double), s->gst);
+                    e = pool_malloc(reinterpret_cast<void**>(&job->psi_dev), (size_t)job->M * job->I * job->I * sizeof(double), s->gst);
                 if (e != cudaSuccess) {
                     job->status = RTE_ENOMEM;
                     job->err = cudaGetErrorString(e);

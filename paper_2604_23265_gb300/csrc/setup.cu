@@ -33,13 +33,59 @@ rte_status cuda_status(rte_ctx* ctx, cudaError_t e, const char* where) {
     return (e == cudaErrorMemoryAllocation) ? RTE_ENOMEM : RTE_ECUDA;
 }
 
+namespace {
+// The library's stream-ordered memory pool of each device.  Freed blocks stay
+// mapped up to a quarter of the device memory, so a context set up after
+// another one was destroyed (a serving loop, repeated solves) reuses the
+// physical pages instead of mapping gigabytes again; rte_trim_memory returns
+// them to the device.
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = (uint64_t)total_b / 4;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    g_pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = library_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes == 0 ? 16 : bytes, pool, st);
+}
+
 void* dev_alloc_raw(rte_ctx* ctx, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
     // stream-ordered: a context's allocations and frees never synchronise
     // the device, so concurrent solves on other streams keep running
-    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
-    if (e != cudaSuccess) throw CudaError{e, "cudaMallocAsync"};
+    cudaError_t e = pool_malloc(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) throw CudaError{e, "cudaMallocFromPoolAsync"};
     ctx->allocations.push_back(p);
     ctx->device_bytes += bytes;
     return p;
@@ -921,6 +967,15 @@ RTE_API int rte_profile_read(rte_ctx* ctx, rte_kernel_stat* out, int max) {
         ++n;
     }
     return out ? n : K_COUNT;
+}
+
+RTE_API rte_status rte_trim_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& kv : g_pools) {
+        const cudaError_t e = cudaMemPoolTrimTo(kv.second, 0);
+        if (e != cudaSuccess) return cuda_status(nullptr, e, "cudaMemPoolTrimTo");
+    }
+    return RTE_OK;
 }
 
 RTE_API void rte_destroy(rte_ctx* ctx) {

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "df64.h"
 #include "rte_internal.h"
 #include "mgnet_internal.h"
 
@@ -70,8 +71,8 @@ template <typename T>
 T* ws_alloc(rte_ctx* ctx, Workspace* ws, size_t count) {
     void* p = nullptr;
     const size_t bytes = count * sizeof(T) + 16;
-    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
-    if (e != cudaSuccess) throw CudaError{e, "cudaMallocAsync (solve workspace)"};
+    cudaError_t e = pool_malloc(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) throw CudaError{e, "cudaMallocFromPoolAsync (solve workspace)"};
     ws->allocs.push_back(p);
     ws->bytes += bytes;
     ctx->device_bytes += bytes;
@@ -263,18 +264,44 @@ __global__ void k_backsub(int k, int m, const double* __restrict__ H, const doub
     }
 }
 
-// out = sum_k Z[k] y[k]   (Z float or double)
-template <typename TZ>
-__global__ void k_lincomb(const TZ* __restrict__ Z, int K, int64_t n, const double* __restrict__ y,
-                          double* __restrict__ out) {
-    __shared__ double sy[kMaxKrylov];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) sy[k] = y[k];
+// out = sum_k Z[k] y[k] for the FP32 network outputs Z: the products of z and
+// the df64 y_k exact to about 2^-47 (TwoProd), summed in df64 (TwoSum), two
+// elements a packed instruction and renormalised every 8 terms -- the
+// accuracy of an FP64 sum of the K terms, with the kernel bound by HBM rather
+// than by the FP64 pipe.  n = 2 M N is even.
+__global__ void __launch_bounds__(256) k_lincomb_z(const float* __restrict__ Z, int K, int64_t n,
+                                                   const double* __restrict__ y, double* __restrict__ out) {
+    using df::f2;
+    __shared__ f2 sb[kMaxKrylov][3];           // (h, h), (-h, -h), (-l, -l) of y_k = h + l
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float h, l;
+        df::from_double(y[k], h, l);
+        sb[k][0] = df::pk(h, h);
+        sb[k][1] = df::pk(-h, -h);
+        sb[k][2] = df::pk(-l, -l);
+    }
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s = fma((double)Z[(size_t)k * n + i], sy[k], s);
-        out[i] = s;
+    const int64_t np = n / 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        f2 S = 0ull, C = 0ull;
+        int k = 0;
+        for (; k + 8 <= K; k += 8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 z = __ldg(reinterpret_cast<const float2*>(Z + (size_t)(k + q) * n) + i);
+                df::mac2(S, C, df::pk(z.x, z.y), 0ull, sb[k + q][1], sb[k + q][2], sb[k + q][0]);
+            }
+            df::renorm2(S, C);
+        }
+        for (; k < K; ++k) {
+            const float2 z = __ldg(reinterpret_cast<const float2*>(Z + (size_t)k * n) + i);
+            df::mac2(S, C, df::pk(z.x, z.y), 0ull, sb[k][1], sb[k][2], sb[k][0]);
+        }
+        df::renorm2(S, C);
+        float sx, sy, cx, cy;
+        df::upk(S, sx, sy);
+        df::upk(C, cx, cy);
+        reinterpret_cast<double2*>(out)[i] = make_double2(df::to_double(sx, cx), df::to_double(sy, cy));
     }
 }
 
@@ -479,8 +506,8 @@ struct Solver {
             }
             if (cycle_net) {
                 ProfScope ps(ctx, K_XUPDATE, (double)n * (8 + 4 * k));
-                k_lincomb<float><<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
-                check(cudaGetLastError(), "k_lincomb");
+                k_lincomb_z<<<gblk, 256, 0, ctx->stream>>>(ws->Z, k, n, ws->y, ws->tmp);
+                check(cudaGetLastError(), "k_lincomb_z");
             } else {
                 launch_lincomb_df(ctx, ws->V, k, ws->y, ws->tmp);
             }
@@ -515,9 +542,9 @@ struct GroupRunner {
         check(cudaMallocHost(&items_h, cap * sizeof(GroupItem)), "cudaMallocHost");
         check(cudaMallocHost(&maps_h, cap * group_gs_maps_bytes()), "cudaMallocHost");
         check(cudaMallocHost(&est_h, 2 * cap * sizeof(double)), "cudaMallocHost");
-        check(cudaMallocAsync(&items_d, cap * sizeof(GroupItem), st), "cudaMallocAsync");
-        check(cudaMallocAsync(&maps_d, cap * group_gs_maps_bytes(), st), "cudaMallocAsync");
-        check(cudaMallocAsync(&est_d, 2 * cap * sizeof(double), st), "cudaMallocAsync");
+        check(pool_malloc(reinterpret_cast<void**>(&items_d), cap * sizeof(GroupItem), st), "cudaMallocFromPoolAsync");
+        check(pool_malloc(&maps_d, cap * group_gs_maps_bytes(), st), "cudaMallocFromPoolAsync");
+        check(pool_malloc(reinterpret_cast<void**>(&est_d), 2 * cap * sizeof(double), st), "cudaMallocFromPoolAsync");
     }
     ~GroupRunner() {
         if (items_d) cudaFreeAsync(items_d, st);

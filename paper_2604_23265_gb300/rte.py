@@ -80,6 +80,7 @@ SIGNATURES = {
     "rte_set_response_path": (_I, [_P, _I]),
     "rte_response_on_tensor_cores": (_I, [_P]),
     "rte_destroy": (None, [_P]),
+    "rte_trim_memory": (_I, []),
     "rte_last_error": (ctypes.c_char_p, [_P]),
     "rte_info": (_I, [_P, ctypes.POINTER(CtxInfo)]),
     "rte_rhs": (_I, [_P, _P]),
@@ -181,6 +182,12 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def trim_memory():
+    """Return the unused blocks of the library's device memory pools
+    (rte_trim_memory); contexts keep what they hold."""
+    _check(load().rte_trim_memory())
 
 
 def fp64_fma_rate(stream=None):
