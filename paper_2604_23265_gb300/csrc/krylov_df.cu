@@ -66,7 +66,14 @@ constexpr int kStageBudget = 102 * 1024;      // shared memory the stages of a b
 // kDot, kUpdateDot, kUpdateNorm: the three passes of CGS2 (below).  The
 // solver's deferred form uses two passes a step (launch_cgs2_deferred_df):
 //   kFixDot        v_j = (u_j - V c) / beta on the staged row j (the previous
-//                  step's second projection, deferred), then h1 = V^T w
+//                  step's second projection, deferred), then h1 = V^T w.
+//                  h1 is formed in FP32 from the hi planes (about 1e-5 of
+//                  ||w||): the step subtracts exactly the h1 it formed (the
+//                  next pass, in df64), and the second projection h2 = V^T w'
+//                  is df64, so h1 + h2 is V^T w and the basis orthogonal to
+//                  df64 accuracy as long as ||w'|| is not below about 1e-4
+//                  ||w|| (below, the loss of orthogonality grows as
+//                  1e-4 ||w|| / ||w'|| times 2^-48)
 //   kUpdateDotNorm w' = w - V h1 into the slot of u_{j+1}, then h2 = V^T w'
 //                  and ||w'||^2
 enum Mode { kDot = 0, kUpdateDot = 1, kUpdateNorm = 2, kFixDot = 3, kUpdateDotNorm = 4 };
@@ -327,14 +334,25 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                 for (int r = 0; r < kOwnB; ++r) {
                     if (r < RB) {
                         const float* row = row_of(gw + kGW * half + 2 * kGW * r);
+                        if (MODE == kFixDot) {
+                            // the first projection h1 of the deferred step:
+                            // FP32 products of the hi planes, summed in FP32
+                            // per lane (see kFixDot above)
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int e0 = 2 * (l16 + 16 * t);
-                            const f2 vh = *reinterpret_cast<const f2*>(row + e0);
-                            const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
-                            df::mac2(S2[r], C2[r], vh, vl, nwh2[t], nwl2[t], wh2[t]);
+                            for (int t = 0; t < 4; ++t) {
+                                const f2 vh = *reinterpret_cast<const f2*>(row + 2 * (l16 + 16 * t));
+                                S2[r] = df::fma2(vh, wh2[t], S2[r]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const int e0 = 2 * (l16 + 16 * t);
+                                const f2 vh = *reinterpret_cast<const f2*>(row + e0);
+                                const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
+                                df::mac2(S2[r], C2[r], vh, vl, nwh2[t], nwl2[t], wh2[t]);
+                            }
+                            df::renorm2(S2[r], C2[r]);
                         }
-                        df::renorm2(S2[r], C2[r]);
                     }
                 }
             }

@@ -16,7 +16,9 @@ orthonormal, and zhat_j = v_j + V c_j / beta_{j-1} when M is the identity
 import numpy as np
 
 
-def _deferred_arnoldi(A, Ms, v0, k):
+def _deferred_arnoldi(A, Ms, v0, k, h1_error=0.0, rng=None):
+    """h1_error > 0: the first projection carries an absolute error of that
+    size times ||w|| per component, as an FP32 dot would."""
     n = A.shape[0]
     V = np.zeros((k + 1, n))
     V[0] = v0
@@ -32,6 +34,8 @@ def _deferred_arnoldi(A, Ms, v0, k):
         w = A @ z
         V[j] = (u - V[:j].T @ c) / betas[j]                       # pass 1: fix row j
         h1 = V[:j + 1] @ w
+        if h1_error:
+            h1 = h1 + h1_error * np.linalg.norm(w) * rng.standard_normal(j + 1)
         wp = w - V[:j + 1].T @ h1                                  # pass 2
         h2 = V[:j + 1] @ wp
         nu = wp @ wp
@@ -92,3 +96,50 @@ def test_gmres_minimum_from_the_deferred_relation():
     # and it is the minimum over span(Zhat)
     yd, *_ = np.linalg.lstsq(A @ Zhat.T, b, rcond=None)
     assert r_true <= np.linalg.norm(b - A @ Zhat.T @ yd) * (1 + 1e-8)
+
+
+def test_inexact_first_projection_keeps_the_relations():
+    """The solver forms h1 in FP32 (error about 1e-5 ||w||): the step subtracts
+    the h1 it formed and the second projection removes what h1 missed, so
+    A Zhat = V H and the orthogonality of V hold as with an exact h1."""
+    rng = np.random.default_rng(3)
+    n, k = 300, 40
+    A = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)
+    Ms = [np.eye(n) + 0.05 * rng.standard_normal((n, n)) / np.sqrt(n) for _ in range(k)]
+    v0 = rng.standard_normal(n)
+    v0 /= np.linalg.norm(v0)
+    V, H, Zhat, _ = _deferred_arnoldi(A, Ms, v0, k, h1_error=3e-5, rng=np.random.default_rng(4))
+    assert np.abs(V @ V.T - np.eye(k + 1)).max() <= 1e-13
+    assert np.abs(A @ Zhat.T - V.T @ H).max() <= 1e-12 * np.abs(A).max() * np.sqrt(n)
+    # with one linear preconditioner the Krylov space is the exact one, so
+    # the GMRES residual after k steps is too (the basis of span(Zhat) is
+    # not: the preconditioner sees u_j = beta v_j + V c_j, and c_j is larger)
+    Mfix = [Ms[0]] * k
+    b = v0 * 3.0
+    res = []
+    for err in (0.0, 3e-5):
+        V, H, Zhat, _ = _deferred_arnoldi(A, Mfix, v0, k, h1_error=err, rng=np.random.default_rng(6))
+        e1 = np.zeros(k + 1)
+        e1[0] = 3.0
+        y, *_ = np.linalg.lstsq(H, e1, rcond=None)
+        res.append(np.linalg.norm(b - A @ (Zhat.T @ y)))
+    assert abs(res[0] - res[1]) <= 1e-9 * 3.0
+
+
+def test_inexact_first_projection_near_breakdown():
+    """With w nearly in the span of V (||w'|| = 1e-7 ||w||) the loss of
+    orthogonality grows as (h1 error / ||w'||) times the working precision."""
+    rng = np.random.default_rng(5)
+    n, k = 200, 10
+    Q, _ = np.linalg.qr(rng.standard_normal((n, k + 1)))
+    V = Q[:, :k].T
+    w = V.T @ rng.standard_normal(k) + 1e-7 * Q[:, k]
+    h1 = V @ w + 3e-5 * np.linalg.norm(w) * rng.standard_normal(k)
+    wp = w - V.T @ h1
+    h2 = V @ wp
+    wpp = wp - V.T @ h2
+    v = wpp / np.linalg.norm(wpp)
+    loss = np.abs(V @ v).max()
+    bound = 8 * 2.0 ** -52 * np.linalg.norm(wp) / np.linalg.norm(wpp)
+    assert loss <= bound
+    assert abs(np.linalg.norm(wpp) - 1e-7 * np.linalg.norm(Q[:, k])) <= 1e-3 * 1e-7
