@@ -37,9 +37,9 @@
 // The four parity classes of a transposed convolution run as one launch
 // (blockIdx.y = class, each with its own taps, weights and output offset).
 // Layers are chained by programmatic dependent launch: a layer allocates its
-// tensor memory and copies its weights while the previous layer finishes,
-// waits for it only before touching activations, and signals its dependents
-// after its last store (the signal is what makes those stores visible).
+// tensor memory and copies its weights while the previous layer runs, waits
+// for the previous grid's completion only before touching activations, and
+// lets the next layer launch right after that wait.
 //
 // The epilogue reads the accumulators back with tcgen05.ld (warp w sees lanes
 // 32 (w mod 4) ...; the two warps on the same lanes take alternate 16-column
@@ -231,9 +231,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
                 : "memory");
         }
     }
-    // the inputs are the previous layer's outputs: wait for that grid (its
-    // writes before its trigger are visible after this)
+    // the inputs are the previous layer's outputs: wait for that grid to
+    // complete (its writes are visible after this).  Then let the next layer
+    // launch: its CTAs set up (tensor memory, barriers, weight copies) while
+    // this one computes, and its own wait holds its reads until this grid has
+    // completed, so the trigger's place only moves the launch latency off the
+    // chain of dependent layers.  The next grid launches once every CTA of
+    // this one has reached this point (a CTA of it may wait in tcgen05.alloc
+    // until a CTA of this grid on its SM releases its columns).
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (MODE == kHalo && tid == 0) {
         mbar_expect(&x_bar, (uint32_t)KCi * g.BH * g.BW * 16);
         tma_load_4d(xbase, &a.tmap, 0, x0 - 1, y0 - 1, tb * KCi, &x_bar);
@@ -564,11 +571,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(const __grid_constant__
             eb8[i] = bn[i];
         }
     }
-    // every output of this CTA is written: the next layer may launch (its
-    // CTAs may wait in tcgen05.alloc until this CTA releases its columns)
     tc_fence_before();
     __syncthreads();
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.ncols) : "memory");

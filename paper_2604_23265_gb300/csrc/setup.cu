@@ -149,13 +149,19 @@ ProfScope::~ProfScope() {
 }
 
 void prof_resolve(rte_ctx* ctx) {
+    // launches still running (queued ahead of the host) stay pending
+    size_t keep = 0;
     for (auto& p : ctx->prof.pending) {
+        if (cudaEventQuery(p.b) == cudaErrorNotReady) {
+            ctx->prof.pending[keep++] = p;
+            continue;
+        }
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) ctx->prof.ms[p.kid] += ms;
         ctx->prof.pool.push_back(p.a);
         ctx->prof.pool.push_back(p.b);
     }
-    ctx->prof.pending.clear();
+    ctx->prof.pending.erase(ctx->prof.pending.begin() + (std::ptrdiff_t)keep, ctx->prof.pending.end());
 }
 
 void prof_free(rte_ctx* ctx) {

@@ -52,6 +52,7 @@ struct Workspace {
     double* U = nullptr;      // [(m+1) (m+1)]
     double* est = nullptr;    // [4] device status: est, beta, bnorm
     double* est_host = nullptr;   // pinned [4]
+    cudaEvent_t est_ready = nullptr;   // the step's estimate has reached est_host
     std::vector<void*> allocs;
     size_t bytes = 0;
 };
@@ -60,6 +61,7 @@ void free_workspace(rte_ctx* ctx) {
     if (!ctx || !ctx->ws) return;
     for (void* p : ctx->ws->allocs) cudaFreeAsync(p, ctx->stream);
     if (ctx->ws->est_host) cudaFreeHost(ctx->ws->est_host);
+    if (ctx->ws->est_ready) cudaEventDestroy(ctx->ws->est_ready);
     ctx->device_bytes -= ctx->ws->bytes;
     delete ctx->ws;
     ctx->ws = nullptr;
@@ -106,6 +108,7 @@ Workspace* get_workspace(rte_ctx* ctx, int m) {
     ws->U = ws_alloc<double>(ctx, ws, (size_t)(m + 1) * (m + 1));
     ws->est = ws_alloc<double>(ctx, ws, 4);
     check(cudaMallocHost(&ws->est_host, 4 * sizeof(double)), "cudaMallocHost");
+    check(cudaEventCreateWithFlags(&ws->est_ready, cudaEventDisableTiming), "cudaEventCreate");
     return ws;
 }
 
@@ -450,6 +453,18 @@ struct Solver {
         return nullptr;
     }
 
+    // the preconditioner and operator of step j + 1, queued before the host
+    // reads step j's residual estimate so that the device does not idle
+    // while the host decides; when the cycle ends at step j instead, the
+    // work is discarded (it wrote only Z[j + 1] and scratch vectors that the
+    // cycle end and the next cycle overwrite)
+    void queue_next_step() {
+        ++j;
+        precondition();
+        inner_apply();
+        --j;
+    }
+
     // w = B z_j
     void inner_apply() {
         if (comp) {
@@ -748,15 +763,18 @@ rte_status run_solve(rte_ctx* ctx, mgnet* pc, const rte_solve_opts* opts_in, dou
         if (comp && !ctx->atfps) throw StatusError{RTE_EINVAL, "no ATFPS filter on this context (rte_atfps_setup)"};
         if (S.start()) {
             while (S.cycle_begin()) {
-                do {
-                    S.precondition();
-                    S.inner_apply();
+                S.precondition();
+                S.inner_apply();
+                for (;;) {
                     S.orthogonalise_step();
                     check(cudaMemcpyAsync(S.ws->est_host, S.ws->est, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                           ctx->stream), "d2h est");
-                    check(cudaStreamSynchronize(ctx->stream), "step sync");
+                    check(cudaEventRecord(S.ws->est_ready, ctx->stream), "event record");
+                    if (S.j + 1 < S.m) S.queue_next_step();
+                    check(cudaEventSynchronize(S.ws->est_ready), "step sync");
                     prof_resolve(ctx);
-                } while (S.after_step(S.ws->est_host[0], S.ws->est_host[1]));
+                    if (!S.after_step(S.ws->est_host[0], S.ws->est_host[1])) break;
+                }
                 S.cycle_end();
             }
         }
