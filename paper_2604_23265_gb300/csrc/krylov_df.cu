@@ -127,15 +127,16 @@ __device__ __forceinline__ double half_warp_sum(double v) {
 }
 
 // Pipeline depth of a block for K basis rows: as many stages as fit the
-// budget, an even number in 2..8, so that every stage serves one consumer
-// group (chunk i: stage i mod NS, group i mod 2).  With an odd count a stage
-// would alternate between the groups, and a group could wait on a stage's
+// budget, 2..8 (chunk i: stage i mod NS, group i mod 2).  With an odd count a
+// stage serves the two groups in turn, and a group could reach a stage's
 // "full" barrier two phases ahead of the other group's use of it, which the
-// parity wait cannot tell from a completed phase.  Shared memory of the
+// parity wait cannot tell from a completed phase; so there a group first
+// waits for the other group's release of the stage's previous chunk (its
+// "empty" phase, which cannot be two phases behind).  Shared memory of the
 // block: NS stages of (K + 1) rows.
 __host__ __device__ __forceinline__ int gs_stages(int K) {
     const int stage = (K + 1) * kRowBytes;
-    int ns = (kStageBudget / stage) & ~1;
+    const int ns = kStageBudget / stage;
     return ns < 2 ? 2 : (ns > kMaxStages ? kMaxStages : ns);
 }
 __host__ __device__ __forceinline__ size_t gs_smem(int K) {
@@ -248,7 +249,9 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
         const int RB = (K + 2 * kGW - 1) / (2 * kGW);              // phase B rows of a half warp
         for (int i = g; i < mine; i += kGroups) {
             const int s = i % NS;
-            const bool got = mbar_wait(&full[s], (unsigned)(i / NS) & 1u);
+            bool got = true;
+            if ((NS & 1) && i >= NS) got = mbar_wait(&empty[s], (unsigned)((i / NS) - 1) & 1u);
+            got = got && mbar_wait(&full[s], (unsigned)(i / NS) & 1u);
             if (!group_all(g, got)) {
                 ok = false;
                 break;
@@ -351,7 +354,9 @@ __device__ void gs_run(const GsArgs& a, const CUtensorMap* mv, const CUtensorMap
                                 const f2 vl = *reinterpret_cast<const f2*>(row + kE + e0);
                                 df::mac2(S2[r], C2[r], vh, vl, nwh2[t], nwl2[t], wh2[t]);
                             }
-                            df::renorm2(S2[r], C2[r]);
+                            // renormalised every second chunk of the group
+                            // (the small parts of eight products at most)
+                            if ((i >> 1) & 1) df::renorm2(S2[r], C2[r]);
                         }
                     }
                 }
