@@ -203,9 +203,10 @@ RTE_API rte_status rte_apply_adjoint(rte_ctx* ctx, int precision, const void* y_
 /* ---------------------------------------------------------------------------
  * rte_block_apply -- z_C = D_C r_C (transpose = 0) or D_C^T r_C (1) for every
  * cell, D_C = G_C^{-1} the inverse of the cell's diagonal block of A: the
- * block-Jacobi preconditioner of Sec. 4 and the map D of Eq. loss (D in FP64,
- * FP64 accumulation).  r_dev, z_dev: float [n], must not overlap.
- * Asynchronous.
+ * block-Jacobi preconditioner of Sec. 4 and the map D of Eq. loss (D inverted
+ * in FP64 and stored as double-float pairs, 48 significant bits; the sums in
+ * double-float, as accurate as FP64 sums).  r_dev, z_dev: float [n], must not
+ * overlap.  Asynchronous.
  * ------------------------------------------------------------------------- */
 RTE_API rte_status rte_block_apply(rte_ctx* ctx, int transpose, const float* r_dev, float* z_dev);
 
@@ -233,7 +234,8 @@ RTE_API rte_status rte_eigenbasis(int M, double g, double one_minus_gamma, int a
                                   double* L);
 
 /* Copy the per-cell matrices out (host, row-major, either pointer may be NULL):
- * D [N][2M][2M] double, D_C = G_C^{-1} (rows = slots, columns = rows of A);
+ * D [N][2M][2M] double, D_C = G_C^{-1} (rows = slots, columns = rows of A;
+ * the stored double-float value, 48 significant bits);
  * R [N][2M][2M] float, the response R_C = T_out,C D_C whose row (f, j) is
  * the value leaving C through face f in direction dirs[opp f][j] for unit
  * incoming data.  Synchronous. */

@@ -523,13 +523,18 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         if (!(omg[c] < 1.0 + 1e-15))
             throw StatusError{RTE_EINVAL, "eps^2 sigma_a must not exceed sigma_T (negative scattering)"};
     }
-    std::map<double, int> mats;
-    for (int c = 0; c < N; ++c) mats.emplace(omg[c], 0);
-    int id = 0;
-    for (auto& kv : mats) kv.second = id++;
-    ctx->nmat = id;
+    // the distinct values of 1 - gamma, ascending; a material's id is its rank
+    std::vector<double> mvals(omg);
+    std::sort(mvals.begin(), mvals.end());
+    mvals.erase(std::unique(mvals.begin(), mvals.end()), mvals.end());
+    ctx->nmat = (int)mvals.size();
     ctx->mat_h.resize(N);
-    for (int c = 0; c < N; ++c) ctx->mat_h[c] = mats[omg[c]];
+    for (int c = 0, last = 0; c < N; ++c) {
+        // cells of one material come in runs: the last id is tried first
+        if (mvals[last] != omg[c])
+            last = (int)(std::lower_bound(mvals.begin(), mvals.end(), omg[c]) - mvals.begin());
+        ctx->mat_h[c] = last;
+    }
     const int n2 = 2 * M;
     // many materials (1 - gamma varying from cell to cell): the eigenbases are
     // computed on the device, batched; a few: on the host
@@ -542,7 +547,7 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
     if (!dev_eig) {
         const int nt = 2 * ctx->nmat;
         std::vector<double> omv(ctx->nmat);
-        for (auto& kv : mats) omv[kv.second] = std::min(kv.first, 1.0);
+        for (int j = 0; j < ctx->nmat; ++j) omv[j] = std::min(mvals[j], 1.0);
         exs.resize(nt);
         els.resize(nt);
         std::vector<std::exception_ptr> errs(nt);
@@ -565,9 +570,8 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         for (auto& e : errs)
             if (e) std::rethrow_exception(e);
     }
-    for (auto& kv : mats) {
+    for (int j = 0; j < ctx->nmat; ++j) {
         if (dev_eig) break;
-        const int j = kv.second;
         const std::vector<double>&xx = exs[2 * j], &Lx = els[2 * j], &xy = exs[2 * j + 1], &Ly = els[2 * j + 1];
         for (int k = 0; k < M2; ++k) {
             if (!(xx[k] < 0 && xx[M2 + k] > 0 && xy[k] < 0 && xy[M2 + k] > 0))
@@ -612,7 +616,7 @@ void build(rte_ctx* ctx, const double* sigma_T, const double* sigma_a, const dou
         ctx->Lt32 = static_cast<float*>(dev_alloc(ctx, nb * sizeof(float)));
         ctx->L32 = static_cast<float*>(dev_alloc(ctx, nb * sizeof(float)));
         std::vector<double> omv(ctx->nmat);
-        for (auto& kv : mats) omv[kv.second] = std::min(kv.first, 1.0);
+        for (int j = 0; j < ctx->nmat; ++j) omv[j] = std::min(mvals[j], 1.0);
         device_eigenbases(ctx, omv, K, cdir, sdir, ctx->xi, ctx->L64, ctx->Lt64, ctx->Lt32, ctx->L32);
         check(cudaMemcpyAsync(ctx->xi_h.data(), ctx->xi, ctx->xi_h.size() * sizeof(double), cudaMemcpyDeviceToHost,
                               ctx->stream), "d2h xi");
