@@ -12,7 +12,8 @@ learned MgNet V-cycle over block Jacobi.  The network is trained first (on
 as mgnet.train_seconds);
 block-Jacobi GMRES on the same medium is timed in the same run for comparison.  `e2e` times the public
 API end to end per step: rte_setup from pinned host arrays (H2D inside),
-the solve, the angular-flux reconstruction and its copy back to the host.
+the solve, the angular-flux reconstruction and its copy back to the host
+(W untimed warm-up steps first, like the device-resident measurement).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own instance of the workload
@@ -475,7 +476,9 @@ def run_ours(args):
     psi_host = torch.empty(md.M * md.I * md.I, dtype=torch.float64).pin_memory()
     d2h = psi_host.numel() * 8
     e2e_times, e2e_parts = [], []
-    for _ in range(0 if args.no_e2e else args.steps):
+    # the same W untimed warm-up steps as the device-resident measurement (the
+    # first set-ups map the library's memory pool), then K timed steps
+    for it in range(0 if args.no_e2e else args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = rte.Context(md.I, md.M, hs[0], hs[1], hs[2], hs[3], md.g, hs[4], stream=stream)
@@ -489,8 +492,9 @@ def run_ours(args):
         psi_host.copy_(psi, non_blocking=True)
         torch.cuda.synchronize()
         t3 = time.perf_counter()
-        e2e_times.append(t3 - t0)
-        e2e_parts.append((t1 - t0, t2 - t1, t3 - t2))
+        if it >= args.warmup:
+            e2e_times.append(t3 - t0)
+            e2e_parts.append((t1 - t0, t2 - t1, t3 - t2))
         c2.close()
         converged = converged and bool(i2["converged"])
     e2e_s = _max_over_ranks(world, sum(e2e_times)) if e2e_times else float("nan")
