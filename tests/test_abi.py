@@ -72,6 +72,15 @@ def test_setup_rejects_bad_arguments_without_gpu(libpath):
     assert opts.tol == 1e-8 and opts.restart == 50 and opts.inner_precision == rte.RTE_F32
 
 
+def test_trim_memory_without_pools_is_a_no_op(libpath):
+    """rte_trim_memory only visits the memory pools the library created; in a
+    process that never set up a context it touches no device."""
+    from paper_2604_23265_gb300 import rte
+    lib = rte.load(libpath)
+    assert lib.rte_trim_memory() == rte.RTE_OK
+    rte.trim_memory()
+
+
 # the ctypes mirrors of the public structs and the C declarations agree on
 # size and on every field offset (compiled with the host C compiler)
 STRUCTS = {
