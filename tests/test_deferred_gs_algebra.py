@@ -143,3 +143,24 @@ def test_inexact_first_projection_near_breakdown():
     bound = 8 * 2.0 ** -52 * np.linalg.norm(wp) / np.linalg.norm(wpp)
     assert loss <= bound
     assert abs(np.linalg.norm(wpp) - 1e-7 * np.linalg.norm(Q[:, k])) <= 1e-3 * 1e-7
+
+
+def test_fp32_first_projection_error_is_about_1e5_of_w():
+    """The first projection as the kernel forms it: FP32 products of the hi
+    planes, summed in FP32 per lane over the lane's share of the vector (a few
+    hundred products), then the lane sums in FP64.  Its error against the
+    exact V^T w stays near 1e-5 ||w|| or below."""
+    rng = np.random.default_rng(7)
+    n, k, lanes = 1 << 18, 4, 512
+    Q, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    V = Q.T
+    w = rng.standard_normal(n) + V.T @ (10.0 * rng.standard_normal(k))
+    Vh, wh = V.astype(np.float32), w.astype(np.float32)
+    exact = V @ w
+    for r in range(k):
+        prod = (Vh[r] * wh).reshape(-1, lanes)          # row i: one product per lane
+        acc = np.zeros(lanes, np.float32)
+        for row in prod:                                 # sequential FP32 sums per lane
+            acc = (acc + row).astype(np.float32)
+        h1 = float(np.sum(acc.astype(np.float64)))
+        assert abs(h1 - exact[r]) <= 3e-5 * np.linalg.norm(w)
