@@ -62,10 +62,12 @@ cudaError_t library_pool(cudaMemPool_t* out) {
     if (e != cudaSuccess) return e;
     size_t free_b = 0, total_b = 0;
     e = cudaMemGetInfo(&free_b, &total_b);
-    if (e != cudaSuccess) return e;
     uint64_t keep = (uint64_t)total_b / 4;
-    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);       // not cached: the next allocation tries again
+        return e;
+    }
     g_pools[dev] = pool;
     *out = pool;
     return cudaSuccess;
